@@ -1,0 +1,303 @@
+"""FP64 CPU oracle for the SPH view path: test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this package.  The
+CUDA library and its Python binding never import it, and it imports nothing from them.  It wraps the plain C
+restatement in ``sph_oracle.c`` (brute-force all-pairs sums, no cell list) with ctypes and composes its pieces
+into whole passes.
+
+Each function names the passage of the paper (arXiv 2502.16517) it follows.  Where the paper fixes no formula,
+the C file names the textbook form that is used.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile sph_oracle.c into a shared library (gcc, no FP contraction, so every op rounds as written)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                        "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            lib = ctypes.CDLL(path)
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+            sig = {
+                "or_w": (dbl, [dbl, dbl]),
+                "or_dwdr": (dbl, [dbl, dbl]),
+                "or_w_array": (None, [i64, _D, _D, _D]),
+                "or_dwdr_array": (None, [i64, _D, _D, _D]),
+                "or_density": (None, [i64, _D, _D, _D, _D, ctypes.c_int, i64, _I64, _D]),
+                "or_eos": (None, [i64, _D, _D, dbl, _D, _D]),
+                "or_force": (None, [i64, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int, dbl, dbl, dbl, i64,
+                                    _I64, _D, _D]),
+                "or_neighbours": (i64, [i64, _D, _D, _D, ctypes.c_int, i64, dbl, i64, _I64]),
+                "or_bin": (i64, [i64, _D, _D, _I32, _I32, _I32, _I32, _I32]),
+                "or_gather_f64": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _D]),
+                "or_gather_f32": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _F]),
+                "or_gather_pos_f32": (None, [_U8, i64, i64, _I32, i64, _I32, _D, _I32, _F]),
+                "or_scatter_f64": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _D]),
+                "or_scatter_f32": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _F]),
+                "or_reduce": (None, [i64, _D, _D, _D, _D, _D, _D]),
+                "or_kick": (None, [i64, dbl, _D, _D, _D, _D]),
+                "or_drift": (None, [i64, dbl, _D, _D, ctypes.c_int, _D]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a, ptype):
+    return a.ctypes.data_as(ptype)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Kernel (cubic spline, support 2h).
+# ----------------------------------------------------------------------------------------------------------
+def w(r, h):
+    """W(r, h) of the 3D cubic spline, elementwise."""
+    r, h = np.broadcast_arrays(np.asarray(r, np.float64), np.asarray(h, np.float64))
+    r, h = _c(r, np.float64).ravel(), _c(h, np.float64).ravel()
+    out = np.empty_like(r)
+    _load().or_w_array(r.size, _p(r, _D), _p(h, _D), _p(out, _D))
+    return out
+
+
+def dwdr(r, h):
+    """dW/dr of the 3D cubic spline, elementwise."""
+    r, h = np.broadcast_arrays(np.asarray(r, np.float64), np.asarray(h, np.float64))
+    r, h = _c(r, np.float64).ravel(), _c(h, np.float64).ravel()
+    out = np.empty_like(r)
+    _load().or_dwdr_array(r.size, _p(r, _D), _p(h, _D), _p(out, _D))
+    return out
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Pair sums (Section 2.1 steps 1-2, predicate of Listing 1 as a branch, all pairs).
+# ----------------------------------------------------------------------------------------------------------
+def density(x, m, h, box, periodic=True, targets=None):
+    """rho_i for the target particles (all particles if targets is None), brute force over all j."""
+    x, m, h = _c(x, np.float64), _c(m, np.float64), _c(h, np.float64)
+    box = _c(box, np.float64)
+    n = m.size
+    tg = np.arange(n, dtype=np.int64) if targets is None else _c(targets, np.int64)
+    out = np.empty(tg.size, np.float64)
+    _load().or_density(n, _p(x, _D), _p(m, _D), _p(h, _D), _p(box, _D), int(bool(periodic)), tg.size,
+                       _p(tg, _I64), _p(out, _D))
+    return out
+
+
+def eos(rho, u, gamma):
+    """Ideal-gas P and c_s."""
+    rho, u = _c(rho, np.float64), _c(u, np.float64)
+    P = np.empty_like(rho)
+    cs = np.empty_like(rho)
+    _load().or_eos(rho.size, _p(rho, _D), _p(u, _D), float(gamma), _p(P, _D), _p(cs, _D))
+    return P, cs
+
+
+def force(x, v, m, h, rho, P, cs, box, periodic=True, alpha=1.0, beta=2.0, eps=0.01, targets=None):
+    """(a_i, du_i/dt) for the target particles, brute force over all j."""
+    x, v = _c(x, np.float64), _c(v, np.float64)
+    m, h, rho, P, cs = (_c(q, np.float64) for q in (m, h, rho, P, cs))
+    box = _c(box, np.float64)
+    n = m.size
+    tg = np.arange(n, dtype=np.int64) if targets is None else _c(targets, np.int64)
+    a = np.empty((tg.size, 3), np.float64)
+    du = np.empty(tg.size, np.float64)
+    _load().or_force(n, _p(x, _D), _p(v, _D), _p(m, _D), _p(h, _D), _p(rho, _D), _p(P, _D), _p(cs, _D),
+                     _p(box, _D), int(bool(periodic)), float(alpha), float(beta), float(eps), tg.size,
+                     _p(tg, _I64), _p(a, _D), _p(du, _D))
+    return a, du
+
+
+def neighbours(x, h, box, i, periodic=True, rad_factor=2.0):
+    """All j (including i) with |r_ij| < rad_factor * max(h_i, h_j)."""
+    x, h, box = _c(x, np.float64), _c(h, np.float64), _c(box, np.float64)
+    n = h.size
+    cap = 4096
+    while True:
+        out = np.empty(cap, np.int64)
+        cnt = _load().or_neighbours(n, _p(x, _D), _p(h, _D), _p(box, _D), int(bool(periodic)), int(i),
+                                     float(rad_factor), cap, _p(out, _I64))
+        if cnt <= cap:
+            return out[:cnt].copy()
+        cap = int(cnt)
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Cell bucketing and view conversions (Sections 2.1-2.2, 4).
+# ----------------------------------------------------------------------------------------------------------
+def bin_cells(x, box, ncell):
+    """Stable counting sort into cells: returns (cell_of, cell_start, perm, cell_of_slot, n_out_of_box)."""
+    x, box = _c(x, np.float64), _c(box, np.float64)
+    nc = _c(ncell, np.int32)
+    n = x.shape[0]
+    ncells = int(nc[0]) * int(nc[1]) * int(nc[2])
+    cell_of = np.empty(n, np.int32)
+    cell_start = np.empty(ncells + 1, np.int32)
+    perm = np.empty(n, np.int32)
+    cos = np.empty(n, np.int32)
+    bad = _load().or_bin(n, _p(x, _D), _p(box, _D), _p(nc, _I32), _p(cell_of, _I32), _p(cell_start, _I32),
+                         _p(perm, _I32), _p(cos, _I32))
+    return cell_of, cell_start, perm, cos, int(bad)
+
+
+def gather(aos, stride, perm, off, ncomp, dtype=np.float64):
+    """Narrow + AoS->SoA (Eq. 5-7): array [ncomp, n] of the field at byte `off` of each record perm[s]."""
+    aos = _c(aos, np.uint8)
+    perm = _c(perm, np.int32)
+    n = perm.size
+    if dtype == np.float64:
+        out = np.empty((ncomp, n), np.float64)
+        _load().or_gather_f64(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), int(ncomp), _p(out, _D))
+    else:
+        out = np.empty((ncomp, n), np.float32)
+        _load().or_gather_f32(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), int(ncomp), _p(out, _F))
+    return out
+
+
+def gather_pos_f32(aos, stride, perm, off, cell_of_slot, box, ncell):
+    """FP32 cell-relative positions: (float)(x - k * (box / ncell)) per axis, array [3, n]."""
+    aos = _c(aos, np.uint8)
+    perm = _c(perm, np.int32)
+    cos = _c(cell_of_slot, np.int32)
+    box = _c(box, np.float64)
+    nc = _c(ncell, np.int32)
+    n = perm.size
+    out = np.empty((3, n), np.float32)
+    _load().or_gather_pos_f32(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), _p(cos, _I32),
+                              _p(box, _D), _p(nc, _I32), _p(out, _F))
+    return out
+
+
+def scatter(aos, stride, perm, off, values):
+    """SoA->AoS + widen (Eq. 7), in place on a writable uint8 [n, stride] array; values is [ncomp, n]."""
+    assert aos.dtype == np.uint8 and aos.flags.c_contiguous
+    perm = _c(perm, np.int32)
+    n = perm.size
+    vals = np.ascontiguousarray(values)
+    ncomp = vals.shape[0]
+    if vals.dtype == np.float64:
+        _load().or_scatter_f64(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), ncomp, _p(vals, _D))
+    elif vals.dtype == np.float32:
+        _load().or_scatter_f32(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), ncomp, _p(vals, _F))
+    else:
+        raise TypeError(vals.dtype)
+    return aos
+
+
+def reduce_sums(m, v, a, u, dudt):
+    """[sum m v (3), sum m a (3), sum m (v^2/2 + u), sum m (v.a + du/dt)] in FP64."""
+    m, v, a, u, dudt = (_c(q, np.float64) for q in (m, v, a, u, dudt))
+    out = np.empty(8, np.float64)
+    _load().or_reduce(m.size, _p(m, _D), _p(v, _D), _p(a, _D), _p(u, _D), _p(dudt, _D), _p(out, _D))
+    return out
+
+
+def kick(dtk, a, dudt, v, u):
+    """v += a dtk, u += du/dt dtk, in place on copies; returns (v, u)."""
+    a, dudt = _c(a, np.float64), _c(dudt, np.float64)
+    v, u = np.array(v, np.float64, copy=True, order="C"), np.array(u, np.float64, copy=True, order="C")
+    _load().or_kick(u.size, float(dtk), _p(a, _D), _p(dudt, _D), _p(v, _D), _p(u, _D))
+    return v, u
+
+
+def drift(dt, v, x, box, periodic=True):
+    """x += v dt, wrapped into the periodic box; returns the new x."""
+    v, box = _c(v, np.float64), _c(box, np.float64)
+    x = np.array(x, np.float64, copy=True, order="C")
+    _load().or_drift(x.shape[0], float(dt), _p(v, _D), _p(box, _D), int(bool(periodic)), _p(x, _D))
+    return x
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Whole passes on AoS bytes (the composition f = W o C o f^ o C o N of Eq. 7, evaluated by the definition).
+# ----------------------------------------------------------------------------------------------------------
+def unpack(aos, layout):
+    """All physics fields of an AoS buffer in record order: dict name -> array ([n,3] for vectors)."""
+    aos = _c(aos, np.uint8)
+    stride = int(layout["stride"])
+    n = aos.size // stride
+    ident = np.arange(n, dtype=np.int32)
+    out = {}
+    for name, off in layout["offsets"].items():
+        nc = 3 if name in ("x", "v", "a") else 1
+        g = gather(aos, stride, ident, off, nc)
+        out[name] = g.T.copy() if nc == 3 else g[0].copy()
+    return out
+
+
+def density_pass(aos, layout, box, gamma, periodic=True, targets=None):
+    """rho, P, c_s of the target records (all if None) from the AoS state."""
+    f = unpack(aos, layout)
+    rho = density(f["x"], f["mass"], f["h"], box, periodic, targets)
+    u = f["u"] if targets is None else f["u"][np.asarray(targets)]
+    P, cs = eos(rho, u, gamma)
+    return rho, P, cs
+
+
+def step_all(aos, layout, box, params, periodic=True):
+    """Expected results of one density + force pass over every record: dict rho, P, cs, a, dudt."""
+    f = unpack(aos, layout)
+    rho = density(f["x"], f["mass"], f["h"], box, periodic)
+    P, cs = eos(rho, f["u"], params["gamma"])
+    a, du = force(f["x"], f["v"], f["mass"], f["h"], rho, P, cs, box, periodic, params["alpha"],
+                  params["beta"], params["eps"])
+    return {"rho": rho, "P": P, "cs": cs, "a": a, "dudt": du}
+
+
+def step_sampled(aos, layout, box, params, targets, periodic=True):
+    """Expected rho, P, c_s, a, du/dt of sampled records of a large state, one by one.
+
+    The force of i needs rho, P, c_s of every j within 2 max(h_i, h_j); those densities are computed here by
+    brute force too, so no value comes from anywhere but this oracle."""
+    f = unpack(aos, layout)
+    x, h = f["x"], f["h"]
+    targets = np.asarray(targets, np.int64)
+    need = set(int(t) for t in targets)
+    for t in targets:
+        need.update(int(j) for j in neighbours(x, h, box, int(t), periodic, 2.0))
+    need = np.array(sorted(need), np.int64)
+    n = h.size
+    rho = np.full(n, np.nan)
+    rho[need] = density(x, f["mass"], h, box, periodic, need)
+    P = np.full(n, np.nan)
+    cs = np.full(n, np.nan)
+    P[need], cs[need] = eos(rho[need], f["u"][need], params["gamma"])
+    a, du = force(x, f["v"], f["mass"], h, rho, P, cs, box, periodic, params["alpha"], params["beta"],
+                  params["eps"], targets)
+    return {"rho": rho[targets], "P": P[targets], "cs": cs[targets], "a": a, "dudt": du}

@@ -1,0 +1,364 @@
+/*
+ * sph_oracle.c -- plain, slow FP64 CPU oracle for the SPH view path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this
+ * library.  The CUDA library never includes, links or calls anything here, and this file includes nothing of
+ * the CUDA side: the two share no code, no headers and no constants.
+ *
+ * What it computes, and where each piece comes from:
+ *   - the view operators of the paper's Section 4 (Eq. 5-7): narrowing+AoS->SoA gather of the read set A_in
+ *     (the "prologue" of Section 3.1) and the widening SoA->AoS scatter of the write set A_out (the
+ *     "epilogue");  or_gather_f64 / or_gather_f32 / or_gather_pos_f32 / or_scatter_f64 / or_scatter_f32;
+ *   - the cell bucketing of Section 2.1 (cells at least as wide as the interaction radius; particles of one
+ *     cell stored as one contiguous chunk as in Section 2.2 and the chunk lists of Section 5.2):  or_bin;
+ *   - the density and force sums of Section 2.1 (steps 1 and 2) written as their plain definitions: a sum over
+ *     ALL particle pairs with the predicate of Listing 1 as a branch (no cell list, no masking), in the periodic
+ *     minimum image.  The paper fixes no SPH formula; the textbook forms used are the 3D cubic spline
+ *     (Monaghan & Lattanzio 1985), an ideal-gas EOS and the Monaghan (1992) artificial viscosity, with the
+ *     symmetrised momentum / energy equations of Price (2012);  or_density / or_eos / or_force;
+ *   - the FP64 global momentum and energy sums; or_reduce.
+ *   - the leapfrog kick-drift-kick of Section 2.1 (steps 3-5); or_kick / or_drift.
+ *
+ * Compile with -ffp-contract=off: every product and sum below is rounded on its own, exactly as written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Kernel: 3D cubic spline with support 2h (Monaghan & Lattanzio 1985).  W(r,h) = f(q) / (pi h^3), q = r/h,
+ *   f(q) = 1 - 3/2 q^2 + 3/4 q^3   (0 <= q < 1)
+ *        = 1/4 (2 - q)^3           (1 <= q < 2)
+ *        = 0                        (q >= 2)
+ * dW/dr = f'(q) / (pi h^4), f'(q) = -3 q + 9/4 q^2 (q < 1), -3/4 (2 - q)^2 (1 <= q < 2), 0 otherwise.
+ * ------------------------------------------------------------------------------------------------------- */
+double or_w(double r, double h)
+{
+    double q = r / h;
+    double f;
+    if (q < 1.0) {
+        f = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+    } else if (q < 2.0) {
+        double t = 2.0 - q;
+        f = 0.25 * t * t * t;
+    } else {
+        f = 0.0;
+    }
+    return f / (OR_PI * h * h * h);
+}
+
+double or_dwdr(double r, double h)
+{
+    double q = r / h;
+    double fp;
+    if (q < 1.0) {
+        fp = -3.0 * q + 2.25 * q * q;
+    } else if (q < 2.0) {
+        double t = 2.0 - q;
+        fp = -0.75 * t * t;
+    } else {
+        fp = 0.0;
+    }
+    return fp / (OR_PI * h * h * h * h);
+}
+
+void or_w_array(int64_t n, const double *r, const double *h, double *w)
+{
+    for (int64_t k = 0; k < n; ++k) w[k] = or_w(r[k], h[k]);
+}
+
+void or_dwdr_array(int64_t n, const double *r, const double *h, double *dw)
+{
+    for (int64_t k = 0; k < n; ++k) dw[k] = or_dwdr(r[k], h[k]);
+}
+
+/* Periodic minimum image of one coordinate difference (box edge L). */
+static double or_min_image(double d, double L, int periodic)
+{
+    if (!periodic) return d;
+    if (d > 0.5 * L) {
+        d = d - L;
+    } else if (d < -0.5 * L) {
+        d = d + L;
+    }
+    return d;
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Density (Section 2.1 step 1; Listing 1's DensityPredicate + Density as a branch):
+ *   rho_i = sum_j m_j W(|r_ij|, h_i) over all j with |r_ij| < 2 h_i, the self term j = i included.
+ * x is n x 3 (row = particle), targets lists the i to evaluate (nt of them), rho_out has nt entries.
+ * ------------------------------------------------------------------------------------------------------- */
+void or_density(int64_t n, const double *x, const double *m, const double *h, const double *box, int periodic,
+                int64_t nt, const int64_t *targets, double *rho_out)
+{
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets[t];
+        double sum = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double dx = or_min_image(x[3 * i + 0] - x[3 * j + 0], box[0], periodic);
+            double dy = or_min_image(x[3 * i + 1] - x[3 * j + 1], box[1], periodic);
+            double dz = or_min_image(x[3 * i + 2] - x[3 * j + 2], box[2], periodic);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < 2.0 * h[i]) {
+                sum += m[j] * or_w(r, h[i]);
+            }
+        }
+        rho_out[t] = sum;
+    }
+}
+
+/* Ideal-gas equation of state: P = (gamma - 1) rho u, c_s = sqrt(gamma P / rho). */
+void or_eos(int64_t n, const double *rho, const double *u, double gamma, double *P, double *cs)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        P[i] = (gamma - 1.0) * rho[i] * u[i];
+        cs[i] = sqrt(gamma * P[i] / rho[i]);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Force (Section 2.1 step 2), symmetrised SPH momentum and energy equations with Monaghan viscosity:
+ *   a_i      = - sum_j m_j [ P_i/rho_i^2 grad_i W(r_ij,h_i) + P_j/rho_j^2 grad_i W(r_ij,h_j) + Pi_ij gradbar ]
+ *   du_i/dt  =   sum_j m_j [ P_i/rho_i^2 v_ij . grad_i W(r_ij,h_i) + 1/2 Pi_ij v_ij . gradbar ]
+ *   grad_i W(r_ij, h) = dW/dr(r, h) r_ij / r,  gradbar = (grad_i W(r_ij,h_i) + grad_i W(r_ij,h_j)) / 2,
+ *   Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar  if v_ij . r_ij < 0, else 0,
+ *   mu = hbar v_ij . r_ij / (r^2 + eps hbar^2); hbar, cbar, rhobar are pair means.
+ * Pairs: every j != i with |r_ij| < 2 max(h_i, h_j) (the force predicate; no symmetry is exploited, as in the
+ * paper's Section 5.3).  A coincident pair (r = 0) contributes nothing: every term carries r_ij or v_ij . r_ij.
+ * rho, P, cs must be valid for every j that lies within the support of a target.
+ * ------------------------------------------------------------------------------------------------------- */
+void or_force(int64_t n, const double *x, const double *v, const double *m, const double *h, const double *rho,
+              const double *P, const double *cs, const double *box, int periodic, double alpha, double beta,
+              double eps, int64_t nt, const int64_t *targets, double *a_out, double *dudt_out)
+{
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets[t];
+        double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = or_min_image(x[3 * i + 0] - x[3 * j + 0], box[0], periodic);
+            double dy = or_min_image(x[3 * i + 1] - x[3 * j + 1], box[1], periodic);
+            double dz = or_min_image(x[3 * i + 2] - x[3 * j + 2], box[2], periodic);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double hmax = h[i] > h[j] ? h[i] : h[j];
+            if (!(r < 2.0 * hmax)) continue;
+            if (r == 0.0) continue;
+            double gi = or_dwdr(r, h[i]) / r; /* grad_i W(r_ij, h_i) = gi * r_ij */
+            double gj = or_dwdr(r, h[j]) / r; /* grad_i W(r_ij, h_j) = gj * r_ij */
+            double gbar = 0.5 * (gi + gj);
+            double vx = v[3 * i + 0] - v[3 * j + 0];
+            double vy = v[3 * i + 1] - v[3 * j + 1];
+            double vz = v[3 * i + 2] - v[3 * j + 2];
+            double vdotr = vx * dx + vy * dy + vz * dz;
+            double visc = 0.0;
+            if (vdotr < 0.0) {
+                double hbar = 0.5 * (h[i] + h[j]);
+                double mu = hbar * vdotr / (r * r + eps * hbar * hbar);
+                double cbar = 0.5 * (cs[i] + cs[j]);
+                double rhobar = 0.5 * (rho[i] + rho[j]);
+                visc = (-alpha * cbar * mu + beta * mu * mu) / rhobar;
+            }
+            double Ai = P[i] / (rho[i] * rho[i]);
+            double Aj = P[j] / (rho[j] * rho[j]);
+            double coef = m[j] * (Ai * gi + Aj * gj + visc * gbar);
+            ax -= coef * dx;
+            ay -= coef * dy;
+            az -= coef * dz;
+            du += m[j] * (Ai * gi * vdotr + 0.5 * visc * gbar * vdotr);
+        }
+        a_out[3 * t + 0] = ax;
+        a_out[3 * t + 1] = ay;
+        a_out[3 * t + 2] = az;
+        dudt_out[t] = du;
+    }
+}
+
+/* Indices of all j within distance < rad_factor * max(h_i, h_j) of i (minimum image), j != i excluded iff
+ * exclude_self.  Returns the count written (at most cap). Used to find the particles whose density a sampled
+ * force evaluation depends on. */
+int64_t or_neighbours(int64_t n, const double *x, const double *h, const double *box, int periodic, int64_t i,
+                      double rad_factor, int64_t cap, int64_t *out)
+{
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        double dx = or_min_image(x[3 * i + 0] - x[3 * j + 0], box[0], periodic);
+        double dy = or_min_image(x[3 * i + 1] - x[3 * j + 1], box[1], periodic);
+        double dz = or_min_image(x[3 * i + 2] - x[3 * j + 2], box[2], periodic);
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double hmax = h[i] > h[j] ? h[i] : h[j];
+        if (r < rad_factor * hmax) {
+            if (cnt < cap) out[cnt] = j;
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Cell bucketing (Section 2.1: cells at least as wide as the interaction radius, particles sorted into them;
+ * Section 2.2 / 5.2: the particles of one cell form one contiguous chunk, indexed by a CSR-like list).
+ * Cell of a coordinate: k = floor(x * (ncell / box)), clamped into [0, ncell-1].  Linear cell index
+ * c = kx + nx (ky + ny kz).  Slot order: cell-major, and inside a cell ascending particle index (a stable
+ * counting sort).  Outputs: cell_of[i] per particle, cell_start[c] (ncells+1 entries), perm[s] = particle held
+ * by slot s, cell_of_slot[s].  Returns the number of coordinates that fell outside [0, box] (they are clamped).
+ * ------------------------------------------------------------------------------------------------------- */
+int64_t or_bin(int64_t n, const double *x, const double *box, const int32_t *ncell, int32_t *cell_of,
+               int32_t *cell_start, int32_t *perm, int32_t *cell_of_slot)
+{
+    int64_t bad = 0;
+    int64_t ncells = (int64_t)ncell[0] * ncell[1] * ncell[2];
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t k[3];
+        for (int d = 0; d < 3; ++d) {
+            double inv = (double)ncell[d] / box[d];
+            double xv = x[3 * i + d];
+            if (!(xv >= 0.0 && xv <= box[d])) ++bad;
+            double f = floor(xv * inv);
+            int32_t kk;
+            if (!(f >= 0.0)) kk = 0;                       /* also catches NaN */
+            else if (f > (double)(ncell[d] - 1)) kk = ncell[d] - 1;
+            else kk = (int32_t)f;
+            k[d] = kk;
+        }
+        cell_of[i] = k[0] + ncell[0] * (k[1] + ncell[1] * k[2]);
+    }
+    for (int64_t c = 0; c <= ncells; ++c) cell_start[c] = 0;
+    for (int64_t i = 0; i < n; ++i) cell_start[cell_of[i] + 1] += 1;
+    for (int64_t c = 0; c < ncells; ++c) cell_start[c + 1] += cell_start[c];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncells > 0 ? ncells : 1));
+    for (int64_t c = 0; c < ncells; ++c) fill[c] = cell_start[c];
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t s = fill[cell_of[i]]++;
+        perm[s] = (int32_t)i;
+        cell_of_slot[s] = cell_of[i];
+    }
+    free(fill);
+    return bad;
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * View conversions (Section 4, Eq. 5-7).  The gather is narrowing N followed by C_AoS^SoA, fused: for every
+ * slot s, out[comp][s] = field component of record perm[s].  The scatter is C_SoA^AoS followed by widening W:
+ * the field of record perm[s] is overwritten from in[comp][s]; no other byte of the record is touched.
+ * A field is ncomp contiguous doubles at byte offset off inside a record of `stride` bytes.  SoA storage is
+ * component-major: component k of slot s lives at out[k * n + s].
+ * ------------------------------------------------------------------------------------------------------- */
+void or_gather_f64(const uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off, int ncomp,
+                   double *out)
+{
+    for (int k = 0; k < ncomp; ++k) {
+        for (int64_t s = 0; s < n; ++s) {
+            memcpy(&out[(int64_t)k * n + s], aos + (int64_t)perm[s] * stride + off + 8 * k, 8);
+        }
+    }
+}
+
+/* FP32 views: every value is the round-to-nearest cast of the double. */
+void or_gather_f32(const uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off, int ncomp,
+                   float *out)
+{
+    for (int k = 0; k < ncomp; ++k) {
+        for (int64_t s = 0; s < n; ++s) {
+            double d;
+            memcpy(&d, aos + (int64_t)perm[s] * stride + off + 8 * k, 8);
+            out[(int64_t)k * n + s] = (float)d;
+        }
+    }
+}
+
+/* FP32 positions are stored relative to the origin of the slot's cell: (float)(x - k_d * (box_d / ncell_d)),
+ * the subtraction and the product each rounded in FP64, then one round-to-nearest cast. */
+void or_gather_pos_f32(const uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off,
+                       const int32_t *cell_of_slot, const double *box, const int32_t *ncell, float *out)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        int32_t c = cell_of_slot[s];
+        int32_t k[3];
+        k[0] = c % ncell[0];
+        k[1] = (c / ncell[0]) % ncell[1];
+        k[2] = c / (ncell[0] * ncell[1]);
+        for (int d = 0; d < 3; ++d) {
+            double xv;
+            memcpy(&xv, aos + (int64_t)perm[s] * stride + off + 8 * d, 8);
+            double edge = box[d] / (double)ncell[d];
+            double origin = (double)k[d] * edge;
+            out[(int64_t)d * n + s] = (float)(xv - origin);
+        }
+    }
+}
+
+void or_scatter_f64(uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off, int ncomp,
+                    const double *in)
+{
+    for (int k = 0; k < ncomp; ++k) {
+        for (int64_t s = 0; s < n; ++s) {
+            memcpy(aos + (int64_t)perm[s] * stride + off + 8 * k, &in[(int64_t)k * n + s], 8);
+        }
+    }
+}
+
+/* FP32 views widen exactly: (double)float. */
+void or_scatter_f32(uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off, int ncomp,
+                    const float *in)
+{
+    for (int k = 0; k < ncomp; ++k) {
+        for (int64_t s = 0; s < n; ++s) {
+            double d = (double)in[(int64_t)k * n + s];
+            memcpy(aos + (int64_t)perm[s] * stride + off + 8 * k, &d, 8);
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * FP64 global sums: out[0..2] = sum m v, out[3..5] = sum m a, out[6] = sum m (|v|^2/2 + u),
+ * out[7] = sum m (v . a + du/dt).  Straight loop in particle order.
+ * ------------------------------------------------------------------------------------------------------- */
+void or_reduce(int64_t n, const double *m, const double *v, const double *a, const double *u,
+               const double *dudt, double *out)
+{
+    for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        out[0] += m[i] * v[3 * i + 0];
+        out[1] += m[i] * v[3 * i + 1];
+        out[2] += m[i] * v[3 * i + 2];
+        out[3] += m[i] * a[3 * i + 0];
+        out[4] += m[i] * a[3 * i + 1];
+        out[5] += m[i] * a[3 * i + 2];
+        double v2 = v[3 * i + 0] * v[3 * i + 0] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+        out[6] += m[i] * (0.5 * v2 + u[i]);
+        double va = v[3 * i + 0] * a[3 * i + 0] + v[3 * i + 1] * a[3 * i + 1] + v[3 * i + 2] * a[3 * i + 2];
+        out[7] += m[i] * (va + dudt[i]);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Leapfrog pieces (Section 2.1 steps 3-5): a kick v += a dt_k, u += du/dt dt_k, and a drift x += v dt followed
+ * by the periodic wrap into [0, box) (x - box if x >= box, x + box if x < 0).
+ * ------------------------------------------------------------------------------------------------------- */
+void or_kick(int64_t n, double dtk, const double *a, const double *dudt, double *v, double *u)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        v[3 * i + 0] = v[3 * i + 0] + a[3 * i + 0] * dtk;
+        v[3 * i + 1] = v[3 * i + 1] + a[3 * i + 1] * dtk;
+        v[3 * i + 2] = v[3 * i + 2] + a[3 * i + 2] * dtk;
+        u[i] = u[i] + dudt[i] * dtk;
+    }
+}
+
+void or_drift(int64_t n, double dt, const double *v, const double *box, int periodic, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            double xn = x[3 * i + d] + v[3 * i + d] * dt;
+            if (periodic) {
+                if (xn >= box[d]) xn = xn - box[d];
+                else if (xn < 0.0) xn = xn + box[d];
+            }
+            x[3 * i + d] = xn;
+        }
+    }
+}
