@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Benchmark of the SPH view path on GB300: pair interactions per second including the AoS<->SoA view conversions.
+
+Workload (the plain FP64 configuration): 262,144 particles on a 64^3 lattice jittered by U(-0.1, 0.1) * spacing,
+v ~ N(0, 0.1), equal mass, cubic spline with h = 1.2 spacing, 26^3 periodic cells of edge >= 2h, ideal gas
+gamma = 5/3, u = 1, in 160-byte AoS records stored in a seeded random order (heap-scattered records).  One step =
+sph_step: bin, gather the density view, density loop, scatter rho/P/c_s, gather the force view, force loop,
+scatter a/du/dt.  value = (density pairs incl. self + ordered force pairs) per step / device time per step.
+The AoS (42 MB) fits in the 129 MB L2, so a 256 MB buffer is written between timed steps (outside the events).
+
+Also reported: the FP32 form on the same input (forms.f32), the end-to-end figure through sph_step_host with
+pinned host records (copies inside the timed region), per-phase device times, conversion bandwidth, the
+roofline of the dominant kernel, SM clocks sampled during the timed region, and the FP64 CPU oracle timed on a
+bounded sample of the same workload (cpu_baseline).  --impl reference times that oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pair interactions/sec incl. AoS<->SoA conversion, FP32 vs FP64; conversion HBM GB/s"
+UNIT = "pair interactions/s"
+WORKLOAD = ("plain FP64 method: 262,144 particles, jittered 64^3 lattice, v ~ N(0,0.1), cubic spline h=1.2 s, "
+            "26^3 periodic cells, 160 B AoS records in scattered order, one density + force pass with view "
+            "conversion in and out")
+
+# Algorithmic FP64/FP32 flops per in-support pair, counted from the pair terms of the loop bodies (one kernel
+# piece per pair, the viscosity block for half of the pairs): density 17, force 64.
+FLOPS_DENSITY_PAIR = 17
+FLOPS_FORCE_PAIR = 64
+# ALU peaks derived from unit counts and clocks: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz;
+# FP64 = the GB300's nominal 1.25 TFLOP/s.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------------------------------------
+def _inputs():
+    from paper_2502_16517_gb300 import workloads as wl
+    f = wl.plain()
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled")
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    return f, lay, aos_h, ncell
+
+
+def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None):
+    import torch
+    from paper_2502_16517_gb300 import sph
+    from paper_2502_16517_gb300 import workloads as wl
+    n = aos_h.shape[0]
+    aos = torch.from_numpy(aos_h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    view = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
+    try:
+        for _ in range(max(warmup, 0)):
+            flush.zero_()
+            sph.sph_step(view, aos, n, wl.SPH_PARAMS)
+        sph.sph_view_sync(view)
+        sph.sph_pair_counts(view, reset=True)
+        sph.sph_view_timing(view, True)
+        sph.sph_view_phase_times(view, reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sampler = ClockSampler(clocks_gpu) if clocks_gpu is not None else None
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        if sampler:
+            sampler.__enter__()
+        try:
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                sph.sph_step(view, aos, n, wl.SPH_PARAMS)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+        finally:
+            if sampler:
+                sampler.__exit__(None, None, None)
+        wall = time.perf_counter() - t0
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        sph.sph_view_sync(view)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        counts = sph.sph_pair_counts(view)
+        phase_ms, launches = sph.sph_view_phase_times(view)
+        sph.sph_view_timing(view, False)
+    finally:
+        sph.sph_view_destroy(view)
+    return {
+        "step_ms": step_ms, "wall_s": wall, "counts": counts, "phase_ms": phase_ms, "launches": launches,
+        "clocks": sampler.summary() if sampler else None,
+    }
+
+
+def run_e2e(prec, steps, warmup, dev, aos_h, lay, box, ncell):
+    """sph_step_host on pinned host records: H2D of the records, the pass, D2H of the records, every step."""
+    import torch
+    from paper_2502_16517_gb300 import sph
+    from paper_2502_16517_gb300 import workloads as wl
+    n = aos_h.shape[0]
+    host = torch.from_numpy(aos_h.copy()).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    view = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
+    try:
+        for _ in range(max(warmup, 1)):
+            sph.sph_step_host(view, host, n, wl.SPH_PARAMS)
+        sph.sph_pair_counts(view, reset=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            sph.sph_step_host(view, host, n, wl.SPH_PARAMS)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        counts = sph.sph_pair_counts(view)
+    finally:
+        sph.sph_view_destroy(view)
+    pairs = (counts[1] + counts[2])
+    return {"value": pairs / wall, "unit": UNIT, "h2d_bytes_per_step": int(n * lay["stride"]),
+            "d2h_bytes_per_step": int(n * lay["stride"]), "ms_per_step": wall * 1e3 / steps}
+
+
+def conversion_bytes(prec, n):
+    """Algorithmic bytes of the four view conversions of one pass (read + written, incl. the 4-byte perm read;
+    FP32 positions also read the 4-byte cell of the slot)."""
+    e = 8 if prec == 0 else 4
+    pos_extra = 0 if prec == 0 else 4
+    gather_d = n * (6 * 8 + 6 * e + 4 + pos_extra)
+    gather_f = n * (11 * 8 + 11 * e + 4 + pos_extra)
+    scatter_d = n * (3 * 8 + 3 * e + 4)
+    scatter_f = n * (4 * 8 + 4 * e + 4)
+    return gather_d + gather_f, scatter_d + scatter_f
+
+
+def summarize_form(prec, r, n, steps, world):
+    from paper_2502_16517_gb300 import sph
+    ms = float(np.sum(r["step_ms"]))
+    pairs_step = (r["counts"][1] + r["counts"][2]) / steps
+    value = world * pairs_step * steps / (ms / 1e3)
+    ph = {name: float(r["phase_ms"][i]) / steps for i, name in enumerate(sph.PHASE_NAMES)}
+    nl = {name: int(r["launches"][i]) for i, name in enumerate(sph.PHASE_NAMES)}
+    g_bytes, s_bytes = conversion_bytes(prec, n)
+    conv = {
+        "gather_GBps": g_bytes / (ph["gather"] * 1e-3) / 1e9 if ph["gather"] > 0 else None,
+        "scatter_GBps": s_bytes / (ph["scatter"] * 1e-3) / 1e9 if ph["scatter"] > 0 else None,
+        "gather_bytes_per_step": g_bytes, "scatter_bytes_per_step": s_bytes,
+    }
+    return {"value": value, "ms_per_step": ms / steps, "pairs_per_step": pairs_step,
+            "density_pairs_per_step": r["counts"][1] / steps, "force_pairs_per_step": r["counts"][2] / steps,
+            "candidates_per_step": (r["counts"][0] + r["counts"][3]) / steps, "phases_ms_per_step": ph,
+            "launches": nl, "conversion": conv}
+
+
+def roofline_of(prec, s, steps, peaks):
+    """Dominant kernel = the phase with the largest device time (the force pair kernel)."""
+    ph = s["phases_ms_per_step"]
+    dom = max(("density", "force"), key=lambda k: ph[k])
+    pairs = s["force_pairs_per_step"] if dom == "force" else s["density_pairs_per_step"]
+    flops = pairs * (FLOPS_FORCE_PAIR if dom == "force" else FLOPS_DENSITY_PAIR)
+    dur = ph[dom] * 1e-3  # one launch of the pair kernel per step
+    achieved = flops / dur / 1e12
+    peak = PEAK_FP64_TFLOPS if prec == 0 else PEAK_FP32_TFLOPS
+    return {"kernel": f"k_cell_pairs<{'Force' if dom == 'force' else 'Dens'}{'F64' if prec == 0 else 'F32'}>",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "peak_source": ("derived: GB300 nominal FP64 1.25 TFLOP/s" if prec == 0 else
+                            "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
+            "algorithmic_flops_per_launch": flops, "flops_per_pair": FLOPS_FORCE_PAIR if dom == "force" else
+            FLOPS_DENSITY_PAIR, "launch_ms": ph[dom]}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# the oracle on a bounded sample (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------------------------------
+def oracle_sample(aos_h, lay, f, block_cells, seed=0):
+    """Time the FP64 oracle on a compact sample: the force of every particle in a cube of block_cells^3 lattice
+    spacings, and the density of every particle within 2 h_max of that cube (all the force needs).  Work and
+    pairs are those of the same pass restricted to the sample.  Returns (pairs, seconds, description)."""
+    import oracle
+    p = {"gamma": 5.0 / 3.0, "alpha": 1.0, "beta": 2.0, "eps": 0.01}
+    n = aos_h.shape[0]
+    box = f["box"]
+    s = 1.0 / round(n ** (1 / 3))
+    hmax = float(f["h"].max())
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.2, 0.8, size=3)
+    t0 = time.perf_counter()
+    st = oracle.unpack(aos_h, lay)
+    x = st["x"]
+    d = x - c
+    d -= box * np.round(d / box)
+    half = 0.5 * block_cells * s
+    blk = np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
+    halo = np.nonzero(np.all(np.abs(d) <= half + 2.0 * hmax * (1 + 1e-9), axis=1))[0]
+    rho = np.full(n, np.nan)
+    rho[halo] = oracle.density(x, st["mass"], st["h"], box, True, halo)
+    P = np.full(n, np.nan)
+    cs = np.full(n, np.nan)
+    P[halo], cs[halo] = oracle.eos(rho[halo], st["u"][halo], p["gamma"])
+    a, du = oracle.force(x, st["v"], st["mass"], st["h"], rho, P, cs, box, True, p["alpha"], p["beta"], p["eps"],
+                         blk)
+    secs = time.perf_counter() - t0
+    # in-support pairs of the sample (counted outside the timed region)
+    dens_pairs = sum(oracle.neighbours(x, st["h"], box, int(i)).size for i in halo)
+    force_pairs = sum(oracle.neighbours(x, st["h"], box, int(i)).size - 1 for i in blk)
+    desc = (f"brute-force FP64 oracle, single thread: density of {halo.size} and force of {blk.size} particles "
+            f"(a {block_cells}^3-spacing cube plus its 2h halo) of the 262,144-particle workload, each against "
+            f"all {n} particles")
+    return dens_pairs + force_pairs, secs, desc
+
+
+def cpu_baseline(aos_h, lay, f, block_cells):
+    pairs, secs, desc = oracle_sample(aos_h, lay, f, block_cells)
+    return {"value": pairs / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": secs}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    f, lay, aos_h, ncell = _inputs()
+    block = args.ref_block
+    for _ in range(args.warmup):
+        oracle_sample(aos_h, lay, f, block, seed=1)
+    tot_pairs, tot_s = 0, 0.0
+    for k in range(args.steps):
+        pairs, secs, desc = oracle_sample(aos_h, lay, f, block, seed=2 + k)
+        tot_pairs += pairs
+        tot_s += secs
+    value = tot_pairs / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": int(aos_h.shape[0]),
+                       "step": "one bounded sample of the pass (see cpu_baseline.sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-block", type=int, default=10, help="oracle sample cube (lattice spacings) for cpu_baseline")
+    ap.add_argument("--ref-block", type=int, default=4, help="oracle sample cube per step of --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2502_16517_gb300 import build as b
+    b.build()
+    f, lay, aos_h, ncell = _inputs()
+    n = aos_h.shape[0]
+    steps, warmup = args.steps, max(args.warmup, 3)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else local
+
+    r64 = run_form(0, steps, warmup, dev, aos_h, lay, f["box"], ncell, clocks_gpu=gpu_index)
+    r32 = run_form(1, steps, warmup, dev, aos_h, lay, f["box"], ncell)
+    # max over ranks of the summed step time
+    tot = torch.tensor([float(np.sum(r64["step_ms"])), float(np.sum(r32["step_ms"]))], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    r64["step_ms"] = [tot[0].item() / steps] * steps
+    r32["step_ms"] = [tot[1].item() / steps] * steps
+    s64 = summarize_form(0, r64, n, steps, world)
+    s32 = summarize_form(1, r32, n, steps, world)
+    e2e = run_e2e(0, max(steps // 2, 3), 2, dev, aos_h, lay, f["box"], ncell)
+    e2e["value"] *= world
+    peaks = measured_peaks()
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(aos_h, lay, f, args.cpu_block)
+    hbm = peaks.get("hbm_gbs")
+    conv = dict(s64["conversion"])
+    if hbm:
+        conv["hbm_peak_GBps"] = hbm
+        conv["gather_frac"] = conv["gather_GBps"] / hbm if conv["gather_GBps"] else None
+        conv["scatter_frac"] = conv["scatter_GBps"] / hbm if conv["scatter_GBps"] else None
+    line = {
+        "metric": METRIC, "value": s64["value"], "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": s64["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "cells": int(np.prod(ncell)), "record_bytes": lay["stride"],
+                   "l2": "256 MB buffer written between timed steps (outside the step events)",
+                   "step": "sph_step: bin + gather + density + scatter + gather + force + scatter",
+                   "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline_of(0, s64, steps, peaks),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(s64["launches"].values())),
+        "clocks": r64["clocks"],
+        "phases_ms_per_step": s64["phases_ms_per_step"],
+        "pairs_per_step": s64["pairs_per_step"],
+        "candidates_per_step": s64["candidates_per_step"],
+        "conversion": conv,
+        "forms": {"f32": {"value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
+                          "speedup_vs_f64": s32["value"] / s64["value"],
+                          "phases_ms_per_step": s32["phases_ms_per_step"],
+                          "roofline": roofline_of(1, s32, steps, peaks), "conversion": s32["conversion"],
+                          "gpu_launches": int(sum(s32["launches"].values()))}},
+        "wall_s_timed_bracket": r64["wall_s"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * sph.h -- C ABI of libsph: field-selective AoS<->SoA particle views fused with cell-linked-list SPH density and
+ * force loops, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the paper's (arXiv 2502.16517) temporary, local "view" over an array of particle structs:
+ *   f(D) = (W_Aout o C_SoA^AoS o f^ o C_AoS^SoA o N_{Ain u Aout})(D)          (Section 4, Eq. 5)
+ * N narrows a record to the members a loop reads (A_in) or writes (A_out), C_AoS^SoA transposes the narrowed
+ * records into one array per member (the "prologue" of Section 3.1), f^ is the loop body over those arrays, and
+ * the "epilogue" C_SoA^AoS + W writes back only A_out; every other byte of every record stays as it was
+ * (Section 3.2).  Conversions run on the device (the permuted operator order of Eq. 7), so the AoS never leaves
+ * HBM on the hot path.  The loop bodies are the SPH density and force kernels of Section 2.1, evaluated per cell
+ * over the local particles of the cell and the active particles of its 3^3 vertex-connected neighbour cells
+ * (Section 2.3), local-active loop order, masking instead of branching (Section 5.6), no pair symmetry exploited
+ * (Section 5.3).
+ *
+ * General rules for every call:
+ *   - Every call taking a view enqueues its work on the view's CUDA stream and returns without waiting, except
+ *     sph_view_sync, sph_reduce, sph_pair_counts, sph_step with stats_out != NULL and sph_step_host, which wait
+ *     for the stream.
+ *   - Device pointers (suffix _dev) must be device memory of the view's GPU.  Host pointers are plain host
+ *     memory.  The caller owns every buffer it passes; the view owns the memory it allocated in
+ *     sph_view_create and frees it in sph_view_destroy.  No call other than sph_view_create and
+ *     sph_step_host's first use allocates device memory.
+ *   - Arguments are checked on the host first; a bad argument returns SPH_E_INVAL and enqueues nothing.
+ *   - Problems found on the device (a position outside the box, 2h larger than a cell, a non-finite density)
+ *     set bits in the view's device status word; the next waiting call returns SPH_E_DEVICE and
+ *     sph_view_status reports the bits.  Kernels never trap and never wait without a bound.
+ *   - A view is used from one host thread at a time.
+ */
+#ifndef LIBSPH_SPH_H_
+#define LIBSPH_SPH_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPH_API __attribute__((visibility("default")))
+#else
+#define SPH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sph_status {
+    SPH_OK = 0,
+    SPH_E_INVAL = 1,   /* bad argument: null pointer, bad layout or domain, n > n_max, field absent ...     */
+    SPH_E_NOMEM = 2,   /* a device or pinned allocation failed (sph_view_create, first sph_step_host)        */
+    SPH_E_CUDA = 3,    /* a CUDA runtime call or a kernel launch failed                                      */
+    SPH_E_DEVICE = 4,  /* the device status word has error bits set (see SPH_DEV_*)                          */
+    SPH_E_TIMEOUT = 5, /* a bounded device-side wait gave up                                                 */
+    SPH_E_NOTCONV = 6, /* an iteration did not converge                                                      */
+    SPH_E_STATE = 7    /* call order: e.g. sph_density before the density view was gathered                   */
+} sph_status;
+
+typedef enum sph_prec {
+    SPH_F64 = 0, /* SoA views and pair loops in FP64                                                       */
+    SPH_F32 = 1  /* SoA views in FP32 (positions relative to their cell's origin), FP32 pair loops with
+                    Kahan-compensated sums, FP64 global reductions                                          */
+} sph_prec;
+
+/* Particle members known to the library, in the order of sph_layout.off[].  x, v and a are three contiguous
+ * doubles; every other member is one double.  All members are IEEE binary64 in the records. */
+enum {
+    SPH_X = 0, SPH_V = 1, SPH_A = 2, SPH_MASS = 3, SPH_H = 4, SPH_RHO = 5, SPH_P = 6, SPH_U = 7, SPH_DUDT = 8,
+    SPH_CS = 9, SPH_NFIELDS = 10
+};
+#define SPH_BIT(f) (1u << (f))
+
+/* The access sets A_in / A_out of the two pair loops (Section 3.1; Table 1 lists the paper's larger sets). */
+#define SPH_DENSITY_IN (SPH_BIT(SPH_X) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_U))
+#define SPH_DENSITY_OUT (SPH_BIT(SPH_RHO) | SPH_BIT(SPH_P) | SPH_BIT(SPH_CS))
+#define SPH_FORCE_IN                                                                                         \
+    (SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_RHO) | SPH_BIT(SPH_P) | \
+     SPH_BIT(SPH_CS))
+#define SPH_FORCE_OUT (SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT))
+#define SPH_ALL_FIELDS ((1u << SPH_NFIELDS) - 1u)
+
+/* Device status bits (sph_view_status). */
+#define SPH_DEV_POS_RANGE 0x1u  /* a position was outside [0, box] or not finite; it was clamped into a cell */
+#define SPH_DEV_H_TOO_BIG 0x2u  /* 2h exceeded the smallest cell edge: the 3^3 stencil may miss pairs      */
+#define SPH_DEV_NONFINITE 0x4u  /* a density, pressure or sound speed came out non-finite or <= 0           */
+#define SPH_DEV_TIMEOUT 0x8u    /* a bounded device-side wait gave up                                       */
+
+/* Record layout: `stride` bytes per record (a multiple of 8, at most 65536); off[f] is the byte offset of
+ * member f inside a record (a multiple of 8), or -1 if the record has no such member.  Present members must
+ * lie inside the record and must not overlap.  Records are packed back to back: record k starts at byte
+ * k * stride of the AoS buffer, which must be 8-byte aligned (16-byte alignment of the buffer and a stride that
+ * is a multiple of 16 enable 128-bit loads). */
+typedef struct sph_layout {
+    int64_t stride;
+    int32_t off[SPH_NFIELDS];
+} sph_layout;
+
+/* Domain [0, box[0]) x [0, box[1]) x [0, box[2]), cut into ncell[0] x ncell[1] x ncell[2] equal cells.  The
+ * cell edge box[d]/ncell[d] must be at least 2 h of every particle (the interaction radius, Section 2.1); this is
+ * checked on the device (SPH_DEV_H_TOO_BIG).  periodic != 0 wraps every axis (minimum image) and then needs
+ * ncell[d] >= 3; periodic == 0 is an open box.  At most 2^27 cells. */
+typedef struct sph_domain {
+    double box[3];
+    int32_t ncell[3];
+    int32_t periodic;
+} sph_domain;
+
+/* Physics constants: ideal gas gamma; Monaghan viscosity alpha, beta, eps. */
+typedef struct sph_params {
+    double gamma;
+    double alpha;
+    double beta;
+    double eps;
+} sph_params;
+
+typedef struct sph_view_s *sph_view;
+
+/* Create a view for up to n_max particles of the given record layout, on the CUDA device that is current on the
+ * calling thread, enqueueing on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Allocates
+ * the SoA arrays of every member in the layout at precision `prec`, the cell index (perm, cell_start,
+ * cell_of_slot) and the status word once, for n_max particles (the paper's allocation-free prologue, Section
+ * 6.3).  Errors: SPH_E_INVAL (null out, bad layout/domain, n_max < 0 or > 2^31-1), SPH_E_NOMEM, SPH_E_CUDA. */
+SPH_API sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_max, const sph_domain *domain,
+                           void *cuda_stream, sph_view *out);
+
+/* Wait for the view's stream, free everything the view allocated.  NULL is accepted. */
+SPH_API sph_status sph_view_destroy(sph_view view);
+
+/* Cell bucketing (Section 2.1; chunk lists of Section 5.2): reads the positions of records [0, n) of aos_dev and
+ * builds the cell-major slot order: perm[s] = record held by slot s, cell_start[c] (CSR offsets, ncells + 1
+ * entries), cell_of_slot[s].  Inside a cell the slots hold ascending record indices, so the order is
+ * deterministic.  Invalidates every SoA member previously gathered.  Needs SPH_X in the layout.
+ * Errors: SPH_E_INVAL (null view/aos_dev, n < 0 or n > n_max, misaligned aos_dev), SPH_E_CUDA. */
+SPH_API sph_status sph_bin(sph_view view, const void *aos_dev, int64_t n);
+
+/* Prologue (Section 3.1, C_AoS^SoA o N of Eq. 5): for every member in in_mask, copy it from the records in slot
+ * order (record perm[s] -> SoA slot s).  FP64 views copy the bits; FP32 views store the round-to-nearest cast,
+ * positions as (float)(x - k * box/ncell) relative to the origin of the slot's cell k.  n must equal the n of
+ * the last sph_bin.  Errors: SPH_E_INVAL (member absent from the layout, mask outside SPH_ALL_FIELDS, n
+ * mismatch), SPH_E_STATE (no sph_bin yet), SPH_E_CUDA. */
+SPH_API sph_status sph_aos_to_soa(sph_view view, const void *aos_dev, int64_t n, uint32_t in_mask);
+
+/* Density loop (Section 2.1 step 1; local-active order of Section 5.4): for every particle i,
+ * rho_i = sum_j m_j W(|r_ij|, h_i) over the 3^3 neighbour cells of i's cell (self term included, cubic spline
+ * with support 2h), then P_i = (gamma - 1) rho_i u_i and c_s,i = sqrt(gamma P_i / rho_i), written to the SoA
+ * members rho, P, cs.  Needs SPH_DENSITY_IN resident (SPH_E_STATE otherwise) and SPH_DENSITY_OUT in the layout. */
+SPH_API sph_status sph_density(sph_view view, const sph_params *params);
+
+/* Force loop (Section 2.1 step 2): for every particle i and every j != i of the 3^3 neighbour cells with
+ * |r_ij| < 2 max(h_i, h_j):
+ *   a_i     = -sum_j m_j [P_i/rho_i^2 grad W(r_ij,h_i) + P_j/rho_j^2 grad W(r_ij,h_j) + Pi_ij gradbar]
+ *   du_i/dt =  sum_j m_j [P_i/rho_i^2 v_ij . grad W(r_ij,h_i) + Pi_ij v_ij . gradbar / 2]
+ * with the Monaghan viscosity Pi_ij (alpha, beta, eps of params) for approaching pairs, written to the SoA
+ * members a, dudt.  Needs SPH_FORCE_IN resident (SPH_E_STATE otherwise). */
+SPH_API sph_status sph_force(sph_view view, const sph_params *params);
+
+/* Epilogue (Section 3.1, W o C_SoA^AoS of Eq. 5): for every member in out_mask, write SoA slot s back into record
+ * perm[s].  Only those members' bytes change; every other byte of every record is left as it was.  FP32 views
+ * widen exactly.  The members must be resident.  n must equal the n of the last sph_bin. */
+SPH_API sph_status sph_soa_to_aos(sph_view view, void *aos_dev, int64_t n, uint32_t out_mask);
+
+/* One whole pass on device-resident records: bin, gather SPH_DENSITY_IN, density, scatter SPH_DENSITY_OUT, gather
+ * SPH_FORCE_IN, force, scatter SPH_FORCE_OUT.  With dt > 0, nsteps leapfrog kick-drift-kick steps follow the
+ * pass (Section 2.1 steps 3-5): kick v, u by dt/2; drift x by dt (periodic wrap); rebin; density; force;
+ * kick by dt/2.  If stats_out is not NULL, waits and writes the eight FP64 sums of sph_reduce after the last
+ * force pass. */
+SPH_API sph_status sph_step(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps,
+                    double *stats_out);
+
+/* sph_step on records in HOST memory: copies the n records host->device into a staging buffer that the view
+ * allocates on first use (n_max records), runs sph_step (dt, nsteps as there) and copies the records back,
+ * then waits.  aos_host should be page-locked for full copy speed. */
+SPH_API sph_status sph_step_host(sph_view view, void *aos_host, int64_t n, const sph_params *params, double dt,
+                         int32_t nsteps, double *stats_out);
+
+/* FP64 global sums over the SoA members, in a fixed order (deterministic): out[0..2] = sum m v,
+ * out[3..5] = sum m a, out[6] = sum m (|v|^2/2 + u), out[7] = sum m (v . a + du/dt).  Needs x, v, a, mass, u,
+ * dudt resident.  Waits. */
+SPH_API sph_status sph_reduce(sph_view view, double out[8]);
+
+/* Wait for the view's stream; SPH_E_DEVICE if the device status word is non-zero. */
+SPH_API sph_status sph_view_sync(sph_view view);
+
+/* Wait, then report (and clear if clear != 0) the device status bits SPH_DEV_*. */
+SPH_API sph_status sph_view_status(sph_view view, uint32_t *bits, int32_t clear);
+
+/* Device pointer of SoA member `field`, component `comp` (0..2 for x, v, a; 0 otherwise): n_max elements of
+ * 8 bytes (SPH_F64) or 4 bytes (SPH_F32), in slot order.  Owned by the view. */
+SPH_API sph_status sph_view_soa(sph_view view, int32_t field, int32_t comp, void **dev_ptr);
+
+/* Device pointers of the cell index: which = 0 perm (int32, n_max), 1 cell_start (int32, ncells + 1),
+ * 2 cell_of_slot (int32, n_max).  Owned by the view. */
+SPH_API sph_status sph_view_index(sph_view view, int32_t which, void **dev_ptr);
+
+/* Copy `count` elements of SoA member `field`/`comp` (slot order) to dst, which may be host or device memory
+ * (unified addressing), then wait.  count <= n_max. */
+SPH_API sph_status sph_view_export(sph_view view, int32_t field, int32_t comp, void *dst, int64_t count);
+
+/* Copy `count` int32 entries of index array `which` (as in sph_view_index) to dst (host or device), then wait. */
+SPH_API sph_status sph_view_export_index(sph_view view, int32_t which, void *dst, int64_t count);
+
+/* n of the last sph_bin and the number of cells. */
+SPH_API sph_status sph_view_info(sph_view view, int64_t *n, int64_t *ncells);
+
+/* Waits, then counts[0] = candidate pairs the density loop visited (local x active of every cell),
+ * counts[1] = pairs inside the density support (self included), counts[2] = ordered pairs inside the force
+ * support (j != i), counts[3] = candidate pairs of the force loop; all since the last reset (reset != 0
+ * clears them after reading). */
+SPH_API sph_status sph_pair_counts(sph_view view, uint64_t counts[4], int32_t reset);
+
+/* Phases of the path, for sph_view_phase_times. */
+enum {
+    SPH_PH_BIN = 0,          /* cell bucketing kernels                                                     */
+    SPH_PH_GATHER = 1,       /* prologue: AoS -> SoA                                                       */
+    SPH_PH_DENSITY_PREP = 2, /* density loop's per-particle preparation                                    */
+    SPH_PH_DENSITY = 3,      /* density pair kernel                                                        */
+    SPH_PH_SCATTER = 4,      /* epilogue: SoA -> AoS                                                       */
+    SPH_PH_FORCE_PREP = 5,   /* force loop's per-particle preparation                                      */
+    SPH_PH_FORCE = 6,        /* force pair kernel                                                          */
+    SPH_PH_REDUCE = 7,       /* FP64 global sums                                                           */
+    SPH_PH_KDK = 8,          /* kicks and drifts                                                           */
+    SPH_NPHASES = 9
+};
+
+/* Enable (enable != 0) or disable per-phase device timing: with timing on, every phase brackets its launches
+ * with two CUDA events on the view's stream.  Launch counting is always on. */
+SPH_API sph_status sph_view_timing(sph_view view, int32_t enable);
+
+/* Waits, then ms[p] = summed device time of phase p (0 where timing was off) and launches[p] = kernels
+ * launched by phase p, since the last reset (reset != 0 clears both after reading). */
+SPH_API sph_status sph_view_phase_times(sph_view view, double ms[SPH_NPHASES], int64_t launches[SPH_NPHASES],
+                                        int32_t reset);
+
+/* Human-readable name of a status code (static storage). */
+SPH_API const char *sph_strerror(sph_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBSPH_SPH_H_ */

@@ -64,6 +64,7 @@ def _load():
                 "or_gather_pos_f32": (None, [_U8, i64, i64, _I32, i64, _I32, _D, _I32, _F]),
                 "or_scatter_f64": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _D]),
                 "or_scatter_f32": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _F]),
+                "or_scatter_pos_f32": (None, [_U8, i64, i64, _I32, i64, _I32, _D, _I32, _F]),
                 "or_reduce": (None, [i64, _D, _D, _D, _D, _D, _D]),
                 "or_kick": (None, [i64, dbl, _D, _D, _D, _D]),
                 "or_drift": (None, [i64, dbl, _D, _D, ctypes.c_int, _D]),
@@ -159,7 +160,7 @@ def neighbours(x, h, box, i, periodic=True, rad_factor=2.0):
 
 
 # ----------------------------------------------------------------------------------------------------------
-# Cell bucketing and view conversions (Sections 2.1-2.2, 4).
+# Cell bucketing and view conversions (Sections 2.1-2.2, 4.2).
 # ----------------------------------------------------------------------------------------------------------
 def bin_cells(x, box, ncell):
     """Stable counting sort into cells: returns (cell_of, cell_start, perm, cell_of_slot, n_out_of_box)."""
@@ -177,7 +178,7 @@ def bin_cells(x, box, ncell):
 
 
 def gather(aos, stride, perm, off, ncomp, dtype=np.float64):
-    """Narrow + AoS->SoA (Eq. 5-7): array [ncomp, n] of the field at byte `off` of each record perm[s]."""
+    """Narrow + AoS->SoA (Eq. 3-5): array [ncomp, n] of the field at byte `off` of each record perm[s]."""
     aos = _c(aos, np.uint8)
     perm = _c(perm, np.int32)
     n = perm.size
@@ -205,7 +206,7 @@ def gather_pos_f32(aos, stride, perm, off, cell_of_slot, box, ncell):
 
 
 def scatter(aos, stride, perm, off, values):
-    """SoA->AoS + widen (Eq. 7), in place on a writable uint8 [n, stride] array; values is [ncomp, n]."""
+    """SoA->AoS + widen (Eq. 5), in place on a writable uint8 [n, stride] array; values is [ncomp, n]."""
     assert aos.dtype == np.uint8 and aos.flags.c_contiguous
     perm = _c(perm, np.int32)
     n = perm.size
@@ -217,6 +218,19 @@ def scatter(aos, stride, perm, off, values):
         _load().or_scatter_f32(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), ncomp, _p(vals, _F))
     else:
         raise TypeError(vals.dtype)
+    return aos
+
+
+def scatter_pos_f32(aos, stride, perm, off, cell_of_slot, box, ncell, rel):
+    """Widen FP32 cell-relative positions [3, n] back into the records' x member (in place)."""
+    assert aos.dtype == np.uint8 and aos.flags.c_contiguous
+    perm = _c(perm, np.int32)
+    cos = _c(cell_of_slot, np.int32)
+    box = _c(box, np.float64)
+    nc = _c(ncell, np.int32)
+    rel = _c(rel, np.float32)
+    _load().or_scatter_pos_f32(_p(aos, _U8), int(stride), perm.size, _p(perm, _I32), int(off), _p(cos, _I32),
+                               _p(box, _D), _p(nc, _I32), _p(rel, _F))
     return aos
 
 
@@ -245,7 +259,7 @@ def drift(dt, v, x, box, periodic=True):
 
 
 # ----------------------------------------------------------------------------------------------------------
-# Whole passes on AoS bytes (the composition f = W o C o f^ o C o N of Eq. 7, evaluated by the definition).
+# Whole passes on AoS bytes (the composition f = W o C o f^ o C o N of Eq. 5, evaluated by the definition).
 # ----------------------------------------------------------------------------------------------------------
 def unpack(aos, layout):
     """All physics fields of an AoS buffer in record order: dict name -> array ([n,3] for vectors)."""

@@ -6,7 +6,7 @@
  * the CUDA side: the two share no code, no headers and no constants.
  *
  * What it computes, and where each piece comes from:
- *   - the view operators of the paper's Section 4 (Eq. 5-7): narrowing+AoS->SoA gather of the read set A_in
+ *   - the view operators of the paper's Section 4 (Eq. 3-5): narrowing+AoS->SoA gather of the read set A_in
  *     (the "prologue" of Section 3.1) and the widening SoA->AoS scatter of the write set A_out (the
  *     "epilogue");  or_gather_f64 / or_gather_f32 / or_gather_pos_f32 / or_scatter_f64 / or_scatter_f32;
  *   - the cell bucketing of Section 2.1 (cells at least as wide as the interaction radius; particles of one
@@ -241,7 +241,7 @@ int64_t or_bin(int64_t n, const double *x, const double *box, const int32_t *nce
 }
 
 /* ---------------------------------------------------------------------------------------------------------
- * View conversions (Section 4, Eq. 5-7).  The gather is narrowing N followed by C_AoS^SoA, fused: for every
+ * View conversions (Section 4, Eq. 3-5).  The gather is narrowing N followed by C_AoS^SoA, fused: for every
  * slot s, out[comp][s] = field component of record perm[s].  The scatter is C_SoA^AoS followed by widening W:
  * the field of record perm[s] is overwritten from in[comp][s]; no other byte of the record is touched.
  * A field is ncomp contiguous doubles at byte offset off inside a record of `stride` bytes.  SoA storage is
@@ -309,6 +309,25 @@ void or_scatter_f32(uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm
         for (int64_t s = 0; s < n; ++s) {
             double d = (double)in[(int64_t)k * n + s];
             memcpy(aos + (int64_t)perm[s] * stride + off + 8 * k, &d, 8);
+        }
+    }
+}
+
+/* FP32 cell-relative positions widen back to the box: k_d * (box_d / ncell_d) + (double)rel, each op rounded in
+ * FP64. */
+void or_scatter_pos_f32(uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off,
+                        const int32_t *cell_of_slot, const double *box, const int32_t *ncell, const float *in)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        int32_t c = cell_of_slot[s];
+        int32_t k[3];
+        k[0] = c % ncell[0];
+        k[1] = (c / ncell[0]) % ncell[1];
+        k[2] = c / (ncell[0] * ncell[1]);
+        for (int d = 0; d < 3; ++d) {
+            double edge = box[d] / (double)ncell[d];
+            double xv = (double)k[d] * edge + (double)in[(int64_t)d * n + s];
+            memcpy(aos + (int64_t)perm[s] * stride + off + 8 * d, &xv, 8);
         }
     }
 }

@@ -1,0 +1,330 @@
+// sph_convert.cu -- cell bucketing and the field-selective AoS<->SoA view conversions.
+//
+// Bucketing (paper Section 2.1: particles sorted into cells at least as wide as the interaction radius; Section
+// 2.2 / 5.2: the particles of a cell form one contiguous chunk indexed by a CSR-like list):
+//   k_bin_count   one thread per record: cell coordinate floor(x * n/box) per axis, clamped, linear cell id,
+//                 histogram by atomicAdd;
+//   k_scan_cells  one CTA: exclusive scan of the histogram into cell_start (CSR) and the fill cursors;
+//   k_bin_place   one thread per record: claims a slot of its cell (atomic cursor);
+//   k_cell_sort   one warp per cell: ranks the claimed record indices so that each cell holds ascending record
+//                 indices (the slot order is then independent of atomic timing, i.e. deterministic).
+//
+// Views (Section 4, Eq. 3-5; prologue/epilogue of Section 3.1):
+//   k_gather      CTA per tile of 256 slots.  Phase 1 reads, per record, only the 16-byte chunks that hold a
+//                 member of the mask (128-bit loads; consecutive threads take consecutive chunks of one record)
+//                 into shared memory; phase 2 transposes them out of shared memory into one SoA array per
+//                 member component, consecutive threads writing consecutive slots (coalesced).
+//   k_scatter     the reverse: phase 1 reads the SoA arrays coalesced into shared memory, phase 2 writes each
+//                 member's 8 bytes back into its record; no other byte of a record is written.
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+namespace {
+
+constexpr int kTile = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int cell_coord(double x, double inv, int n, double box, bool &bad)
+{
+    if (!(x >= 0.0 && x <= box)) bad = true;
+    const double f = floor(__dmul_rn(x, inv));
+    int k;
+    if (!(f >= 0.0)) {
+        k = 0;  // also NaN
+    } else if (f > (double)(n - 1)) {
+        k = n - 1;
+    } else {
+        k = (int)f;
+    }
+    return k;
+}
+
+__global__ void k_bin_count(const uint8_t *__restrict__ aos, int64_t stride, int off_x, int n, Grid g,
+                            int *__restrict__ cell_of, int *__restrict__ count, unsigned *status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *xp = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_x);
+    bool bad = false;
+    const int kx = cell_coord(__ldg(xp + 0), g.inv[0], g.n[0], g.box[0], bad);
+    const int ky = cell_coord(__ldg(xp + 1), g.inv[1], g.n[1], g.box[1], bad);
+    const int kz = cell_coord(__ldg(xp + 2), g.inv[2], g.n[2], g.box[2], bad);
+    const int c = kx + g.n[0] * (ky + g.n[1] * kz);
+    cell_of[i] = c;
+    atomicAdd(&count[c], 1);
+    if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
+}
+
+// Single-CTA exclusive scan over the cell histogram, 4 cells per thread per round.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan_cells(const int *__restrict__ count, int ncells,
+                                                             int *__restrict__ cell_start, int *__restrict__ fill)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < ncells; base += kScanThreads * 4) {
+        const int idx = base + tid * 4;
+        int v[4];
+        int t = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (idx + k < ncells) ? count[idx + k] : 0;
+            t += v[k];
+        }
+        // inclusive warp scan of t
+        int incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_tot[lane];
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        int run = carry + warp_tot[warp] + incl - t;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (idx + k < ncells) {
+                cell_start[idx + k] = run;
+                fill[idx + k] = run;
+            }
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == kScanThreads - 1) carry_s = run;  // last thread's running total = carry + round total
+        __syncthreads();
+    }
+    if (tid == 0) cell_start[ncells] = carry_s;
+}
+
+__global__ void k_bin_place(const int *__restrict__ cell_of, int n, int *__restrict__ fill,
+                            int *__restrict__ perm_tmp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = atomicAdd(&fill[cell_of[i]], 1);
+    perm_tmp[s] = i;
+}
+
+// One warp per cell: rank every record index of the cell among the cell's indices (all distinct), write it to
+// its sorted slot.  O(L^2 / 32) per cell of L particles, with the compared values broadcast by shuffles.
+__global__ void k_cell_sort(const int *__restrict__ cell_start, int ncells, const int *__restrict__ perm_tmp,
+                            int *__restrict__ perm, int *__restrict__ cell_of_slot)
+{
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncells) return;
+    const int b = cell_start[c], L = cell_start[c + 1] - b;
+    for (int k0 = 0; k0 < L; k0 += 32) {
+        const int k = k0 + lane;
+        const int v = (k < L) ? perm_tmp[b + k] : 0x7fffffff;
+        int rank = 0;
+        for (int t0 = 0; t0 < L; t0 += 32) {
+            const int w = (t0 + lane < L) ? perm_tmp[b + t0 + lane] : 0x7fffffff;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) rank += (__shfl_sync(kFull, w, t) < v) ? 1 : 0;
+        }
+        if (k < L) {
+            perm[b + rank] = v;
+            cell_of_slot[b + rank] = c;
+        }
+    }
+}
+
+__device__ __forceinline__ int cell_axis_coord(int c, int axis, const Grid &g)
+{
+    if (axis == 0) return c % g.n[0];
+    if (axis == 1) return (c / g.n[0]) % g.n[1];
+    return c / (g.n[0] * g.n[1]);
+}
+
+// g.edge[axis] without dynamic indexing of the kernel parameter (keeps it out of local memory)
+__device__ __forceinline__ double edge_of(int axis, const Grid &g)
+{
+    return axis == 0 ? g.edge[0] : (axis == 1 ? g.edge[1] : g.edge[2]);
+}
+
+// Gather: VEC16 selects 16-byte chunks (record stride and buffer 16-byte aligned) or 8-byte items.
+template <bool VEC16, bool F32>
+__global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ aos, int64_t stride,
+                                                  const int *__restrict__ perm,
+                                                  const int *__restrict__ cell_of_slot, int n,
+                                                  const ConvPlan plan, const Grid g)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int srec[kTile];
+    const int base = blockIdx.x * kTile;
+    const int cnt = min(kTile, n - base);
+    const int tid = threadIdx.x;
+    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    __syncthreads();
+    const int nch = plan.nchunks;
+    const int nload = cnt * nch;
+    if (VEC16) {
+        uint4 *buf = reinterpret_cast<uint4 *>(smem);
+        for (int idx = tid; idx < nload; idx += kTile) {
+            const int s = idx / nch;
+            const int c = idx - s * nch;
+            const uint4 *p = reinterpret_cast<const uint4 *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]);
+            buf[idx] = __ldg(p);
+        }
+    } else {
+        unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);
+        for (int idx = tid; idx < nload; idx += kTile) {
+            const int s = idx / nch;
+            const int c = idx - s * nch;
+            const unsigned long long *p =
+                reinterpret_cast<const unsigned long long *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]);
+            buf[idx] = __ldg(p);
+        }
+    }
+    __syncthreads();
+    const double *dbuf = reinterpret_cast<const double *>(smem);
+    const int cw = VEC16 ? 2 : 1;  // doubles per chunk
+    const int nout = cnt * plan.nitems;
+    for (int idx = tid; idx < nout; idx += kTile) {
+        const int k = idx / cnt;
+        const int s = idx - k * cnt;
+        const double v = dbuf[(s * nch + plan.item_chunk[k]) * cw + plan.item_sub[k]];
+        if (!F32) {
+            static_cast<double *>(plan.soa[k])[base + s] = v;
+        } else {
+            const int axis = plan.item_pos[k];
+            float o;
+            if (axis >= 0) {
+                const int kc = cell_axis_coord(cell_of_slot[base + s], axis, g);
+                const double origin = __dmul_rn((double)kc, edge_of(axis, g));
+                o = __double2float_rn(__dsub_rn(v, origin));
+            } else {
+                o = __double2float_rn(v);
+            }
+            static_cast<float *>(plan.soa[k])[base + s] = o;
+        }
+    }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, int64_t stride,
+                                                   const int *__restrict__ perm,
+                                                   const int *__restrict__ cell_of_slot, int n,
+                                                   const ConvPlan plan, const Grid g)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int srec[kTile];
+    double *sval = reinterpret_cast<double *>(smem);
+    const int base = blockIdx.x * kTile;
+    const int cnt = min(kTile, n - base);
+    const int tid = threadIdx.x;
+    const int ni = plan.nitems;
+    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    const int nin = cnt * ni;
+    for (int idx = tid; idx < nin; idx += kTile) {
+        const int k = idx / cnt;
+        const int s = idx - k * cnt;
+        double v;
+        if (!F32) {
+            v = static_cast<const double *>(plan.soa[k])[base + s];
+        } else {
+            v = (double)static_cast<const float *>(plan.soa[k])[base + s];
+            const int axis = plan.item_pos[k];
+            if (axis >= 0) {
+                const int kc = cell_axis_coord(cell_of_slot[base + s], axis, g);
+                v = __dadd_rn(__dmul_rn((double)kc, edge_of(axis, g)), v);
+            }
+        }
+        sval[s * ni + k] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nin; idx += kTile) {
+        const int s = idx / ni;
+        const int k = idx - s * ni;
+        double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.item_off[k]);
+        *p = sval[idx];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
+                       int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
+                       int *cell_of_slot, unsigned *status, cudaStream_t st, int *nl)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status);
+        ++*nl;
+    }
+    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells, cell_start, fill);
+    ++*nl;
+    if (n > 0) {
+        *nl += 2;
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        const long long threads = (long long)ncells * 32;
+        k_cell_sort<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(cell_start, ncells, perm_tmp, perm,
+                                                                      cell_of_slot);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
+                          const int *cell_of_slot, int n, const ConvPlan &plan, const Grid &g, bool f32,
+                          cudaStream_t st, int *nl)
+{
+    if (n <= 0 || plan.nitems == 0) return cudaSuccess;
+    ++*nl;
+    const int blocks = (n + kTile - 1) / kTile;
+    const size_t smem = (size_t)kTile * plan.nchunks * (vec16 ? 16 : 8);
+    if (vec16) {
+        if (f32) {
+            cudaFuncSetAttribute(k_gather<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gather<true, true><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+        } else {
+            cudaFuncSetAttribute(k_gather<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gather<true, false><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+        }
+    } else {
+        if (f32) {
+            cudaFuncSetAttribute(k_gather<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gather<false, true><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+        } else {
+            cudaFuncSetAttribute(k_gather<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_gather<false, false><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const int *cell_of_slot, int n,
+                           const ConvPlan &plan, const Grid &g, bool f32, cudaStream_t st, int *nl)
+{
+    if (n <= 0 || plan.nitems == 0) return cudaSuccess;
+    ++*nl;
+    const int blocks = (n + kTile - 1) / kTile;
+    const size_t smem = (size_t)kTile * plan.nitems * 8;
+    if (f32) {
+        cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_scatter<true><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+    } else {
+        cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_scatter<false><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sphk

@@ -1,0 +1,98 @@
+// sph_internal.cuh -- definitions shared by the translation units of libsph (device side and host runtime).
+//
+// Nothing here is visible through the C ABI; include/sph.h is the public surface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph.h"
+
+namespace sphk {
+
+// 1/pi: normalisation of the 3D cubic spline W(r,h) = f(r/h) / (pi h^3) (Monaghan & Lattanzio 1985).
+constexpr double kInvPi = 0.318309886183790671537767526745028724;
+
+constexpr int kMaxItems = 17;   // double components of all ten members (x, v, a are three each)
+constexpr int kMaxChunks = 40;  // 16-byte chunks loaded per record by the gather (stride <= 640 B), or items
+
+// Cell grid of a domain (host fills it once per view).
+struct Grid {
+    int n[3];          // cells per axis
+    int periodic;      // wrap every axis
+    double box[3];     // domain edge
+    double edge[3];    // cell edge = box / n, rounded once in FP64
+    double inv[3];     // n / box, rounded once in FP64: cell coordinate = floor(x * inv)
+    float edgef[3];    // (float) edge
+    double min_edge;   // smallest cell edge: every 2h must fit
+};
+
+// Field-selective conversion plan (host builds it from a member mask and the record layout).
+// Items are the double components moved; for the 16-byte path the record bytes holding them are loaded as a
+// few 16-byte chunks per record, for the 8-byte path every item is its own 8-byte chunk.
+struct ConvPlan {
+    int nitems;
+    int nchunks;
+    int chunk_off[kMaxChunks];  // byte offset of each loaded chunk inside a record
+    int item_off[kMaxItems];    // byte offset of the item inside a record
+    int item_chunk[kMaxItems];  // which loaded chunk holds the item
+    int item_sub[kMaxItems];    // which 8-byte half of that chunk
+    int item_pos[kMaxItems];    // -1, or the axis of a position component (FP32 views store it cell-relative)
+    void *soa[kMaxItems];       // SoA array of the item (n_max elements)
+};
+
+// SoA arrays of one view, by member and component.  Element type is double (SPH_F64) or float (SPH_F32).
+struct SoaPtrs {
+    void *p[SPH_NFIELDS][3];
+};
+
+// View-owned scratch of the pair loops (n_max elements each).
+struct Scratch {
+    float *xf, *yf, *zf;  // FP64 views: cell-relative float copies of the positions (input of the FP32 filter)
+    float *hf;            // FP64 views: (float) h, rounded up (filter radius)
+    void *hinv;           // force loop, view precision: 1/h
+    void *k5;             // force loop, view precision: 1/(pi h^5), so grad W(r,h) = k5 g(q) r_vec, g = f'(q)/q
+    void *A;              // force loop, view precision: P / rho^2
+};
+
+struct Counters {
+    unsigned long long dens_cand, dens_pairs, force_pairs, force_cand;
+};
+
+// ---- launchers: each enqueues on `st`, adds the number of kernels it launched to *nl and returns the first
+// CUDA error (cudaGetLastError after the launches). ----
+cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
+                       int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
+                       int *cell_of_slot, unsigned *status, cudaStream_t st, int *nl);
+
+cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
+                          const int *cell_of_slot, int n, const ConvPlan &plan, const Grid &g, bool f32,
+                          cudaStream_t st, int *nl);
+
+cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const int *cell_of_slot, int n,
+                           const ConvPlan &plan, const Grid &g, bool f32, cudaStream_t st, int *nl);
+
+// Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h); force: 1/h,
+// 1/(pi h^5), P/rho^2).
+cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
+                                const Grid &g, cudaStream_t st, int *nl);
+cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
+                              const Grid &g, cudaStream_t st, int *nl);
+
+// The pair kernels.  tj: active particles staged per shared-memory tile (0 = default of the path).
+cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
+                                 int ncells, int n, const Grid &g, double gamma, int tj, unsigned *status,
+                                 Counters *counters, cudaStream_t st, int *nl);
+cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
+                               int ncells, int n, const Grid &g, const sph_params &prm, int tj, unsigned *status,
+                               Counters *counters, cudaStream_t st, int *nl);
+
+cudaError_t launch_reduce(bool f32, const SoaPtrs &soa, int n, double *partials, double *out, cudaStream_t st,
+                          int *nl);
+
+cudaError_t launch_kick(bool f32, const SoaPtrs &soa, int n, double dtk, cudaStream_t st, int *nl);
+
+cudaError_t launch_drift_aos(uint8_t *aos, int64_t stride, int off_x, int off_v, int n, const Grid &g,
+                             double dt, cudaStream_t st, int *nl);
+
+}  // namespace sphk

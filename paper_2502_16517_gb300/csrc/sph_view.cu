@@ -1,0 +1,715 @@
+// sph_view.cu -- host runtime of libsph: the C ABI of include/sph.h.
+//
+// A view (paper Concept 5, Section 2.4: a logical object over a struct that knows which members are read, which
+// are written and how they are stored) is here a runtime object: the record layout (stride + member offsets),
+// the precision of its SoA storage, one SoA array per member the layout has, the cell index of the current
+// slot order and a host-side mask of which SoA members currently hold valid data ("resident").  All device
+// memory is allocated once at creation for n_max particles (the paper's allocation-free prologue, Section
+// 6.3); the hot calls only enqueue kernels on the view's stream (asynchronous map/compute/map of Section 6.5,
+// here without host copies since the records stay in device memory).
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using sphk::ConvPlan;
+using sphk::Grid;
+
+namespace {
+
+const int kNcomp[SPH_NFIELDS] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 1};
+
+}  // namespace
+
+struct PendingTiming {
+    int phase;
+    cudaEvent_t e0, e1;
+};
+
+struct sph_view_s {
+    sph_layout layout;
+    sph_prec prec;
+    int64_t n_max;
+    sph_domain dom;
+    cudaStream_t st;
+    Grid g;
+    int ncells;
+    size_t esz;
+
+    int64_t n;
+    bool binned;
+    uint32_t resident;
+    uint32_t present;
+
+    void *arena;
+    sphk::SoaPtrs soa;
+    sphk::Scratch scr;
+    int *cell_of, *count, *cell_start, *fill, *perm_tmp, *perm, *cell_of_slot;
+    unsigned *status;
+    sphk::Counters *counters;
+    double *red_partials, *red_out;
+
+    unsigned *h_status;
+    double *h_red;
+    sphk::Counters *h_counters;
+
+    void *aos_stage;
+
+    // launch counters and optional per-phase event timing
+    int64_t launches[SPH_NPHASES];
+    double phase_ms[SPH_NPHASES];
+    bool timing;
+    std::vector<cudaEvent_t> *ev_free;
+    std::vector<PendingTiming> *ev_pending;
+    int tile_density, tile_force;  // staged particles per tile (0 = default)
+};
+
+namespace {
+
+sph_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? SPH_OK : SPH_E_CUDA; }
+
+bool layout_valid(const sph_layout *L, uint32_t *present)
+{
+    if (!L) return false;
+    if (L->stride <= 0 || (L->stride % 8) != 0 || L->stride > 65536) return false;
+    struct Iv {
+        int64_t a, b;
+    };
+    std::vector<Iv> iv;
+    uint32_t pres = 0;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        const int32_t off = L->off[f];
+        if (off == -1) continue;
+        if (off < 0 || (off % 8) != 0) return false;
+        const int64_t len = 8 * kNcomp[f];
+        if ((int64_t)off + len > L->stride) return false;
+        iv.push_back({off, off + len});
+        pres |= SPH_BIT(f);
+    }
+    std::sort(iv.begin(), iv.end(), [](const Iv &x, const Iv &y) { return x.a < y.a; });
+    for (size_t k = 1; k < iv.size(); ++k) {
+        if (iv[k].a < iv[k - 1].b) return false;
+    }
+    *present = pres;
+    return true;
+}
+
+bool domain_valid(const sph_domain *D)
+{
+    if (!D) return false;
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(D->box[a] > 0.0) || !(D->box[a] < 1e300)) return false;
+        if (D->ncell[a] < 1) return false;
+        if (D->periodic && D->ncell[a] < 3) return false;
+        cells *= D->ncell[a];
+        if (cells > (int64_t(1) << 27)) return false;
+    }
+    return true;
+}
+
+Grid make_grid(const sph_domain &D)
+{
+    Grid g;
+    g.periodic = D.periodic ? 1 : 0;
+    g.min_edge = 1e308;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = D.ncell[a];
+        g.box[a] = D.box[a];
+        g.edge[a] = D.box[a] / (double)D.ncell[a];
+        g.inv[a] = (double)D.ncell[a] / D.box[a];
+        g.edgef[a] = (float)g.edge[a];
+        g.min_edge = std::min(g.min_edge, g.edge[a]);
+    }
+    return g;
+}
+
+// Build the conversion plan for the members in `mask`.  vec16: items are served from 16-byte chunks.
+void build_plan(const sph_view_s *v, uint32_t mask, bool vec16, ConvPlan *p)
+{
+    memset(p, 0, sizeof(*p));
+    std::vector<int> chunks;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(mask & SPH_BIT(f))) continue;
+        for (int c = 0; c < kNcomp[f]; ++c) {
+            const int off = v->layout.off[f] + 8 * c;
+            chunks.push_back(vec16 ? (off / 16) * 16 : off);
+        }
+    }
+    std::sort(chunks.begin(), chunks.end());
+    chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
+    p->nchunks = (int)chunks.size();
+    for (size_t k = 0; k < chunks.size(); ++k) p->chunk_off[k] = chunks[k];
+    int k = 0;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(mask & SPH_BIT(f))) continue;
+        for (int c = 0; c < kNcomp[f]; ++c, ++k) {
+            const int off = v->layout.off[f] + 8 * c;
+            p->item_off[k] = off;
+            const int ch = vec16 ? (off / 16) * 16 : off;
+            p->item_chunk[k] = (int)(std::lower_bound(chunks.begin(), chunks.end(), ch) - chunks.begin());
+            p->item_sub[k] = vec16 ? (off - ch) / 8 : 0;
+            p->item_pos[k] = (f == SPH_X && v->prec == SPH_F32) ? c : -1;
+            p->soa[k] = v->soa.p[f][c];
+        }
+    }
+    p->nitems = k;
+}
+
+// Bump allocator over one device allocation, 256-byte aligned pieces.
+struct Bump {
+    size_t off = 0;
+    char *base = nullptr;
+    void *take(size_t bytes)
+    {
+        const size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return base ? base + o : nullptr;
+    }
+};
+
+void carve(sph_view_s *v, Bump &b)
+{
+    const size_t nm = (size_t)std::max<int64_t>(v->n_max, 1);
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        for (int c = 0; c < 3; ++c) v->soa.p[f][c] = nullptr;
+        if (!(v->present & SPH_BIT(f))) continue;
+        for (int c = 0; c < kNcomp[f]; ++c) v->soa.p[f][c] = b.take(nm * v->esz);
+    }
+    memset(&v->scr, 0, sizeof(v->scr));
+    if (v->prec == SPH_F64) {
+        v->scr.xf = (float *)b.take(nm * 4);
+        v->scr.yf = (float *)b.take(nm * 4);
+        v->scr.zf = (float *)b.take(nm * 4);
+        v->scr.hf = (float *)b.take(nm * 4);
+    }
+    v->scr.hinv = b.take(nm * v->esz);
+    v->scr.k5 = b.take(nm * v->esz);
+    v->scr.A = b.take(nm * v->esz);
+    const size_t nc = (size_t)v->ncells;
+    v->cell_of = (int *)b.take(nm * 4);
+    v->count = (int *)b.take(nc * 4);
+    v->cell_start = (int *)b.take((nc + 1) * 4);
+    v->fill = (int *)b.take(nc * 4);
+    v->perm_tmp = (int *)b.take(nm * 4);
+    v->perm = (int *)b.take(nm * 4);
+    v->cell_of_slot = (int *)b.take(nm * 4);
+    v->status = (unsigned *)b.take(sizeof(unsigned));
+    v->counters = (sphk::Counters *)b.take(sizeof(sphk::Counters));
+    v->red_partials = (double *)b.take(1024 * 8 * sizeof(double));
+    v->red_out = (double *)b.take(8 * sizeof(double));
+}
+
+bool aos_aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool mask_present(const sph_view_s *v, uint32_t mask)
+{
+    return (mask & ~SPH_ALL_FIELDS) == 0 && (mask & ~v->present) == 0;
+}
+
+cudaEvent_t take_event(sph_view_s *v)
+{
+    if (!v->ev_free->empty()) {
+        cudaEvent_t e = v->ev_free->back();
+        v->ev_free->pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets the launches of one phase: counts them, and with timing on records two events around them.
+struct Phase {
+    sph_view_s *v;
+    int ph;
+    cudaEvent_t e0 = nullptr;
+    int nl = 0;
+    Phase(sph_view_s *view, int phase) : v(view), ph(phase)
+    {
+        if (v->timing) {
+            e0 = take_event(v);
+            if (e0) cudaEventRecord(e0, v->st);
+        }
+    }
+    ~Phase()
+    {
+        v->launches[ph] += nl;
+        if (e0) {
+            cudaEvent_t e1 = take_event(v);
+            if (e1) {
+                cudaEventRecord(e1, v->st);
+                v->ev_pending->push_back({ph, e0, e1});
+            } else {
+                v->ev_free->push_back(e0);
+            }
+        }
+    }
+};
+
+sph_status drain_timings(sph_view_s *v)
+{
+    if (v->ev_pending->empty()) return SPH_OK;
+    if (cudaStreamSynchronize(v->st) != cudaSuccess) return SPH_E_CUDA;
+    for (const PendingTiming &p : *v->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) v->phase_ms[p.phase] += ms;
+        v->ev_free->push_back(p.e0);
+        v->ev_free->push_back(p.e1);
+    }
+    v->ev_pending->clear();
+    return SPH_OK;
+}
+
+sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
+{
+    if (!aos || n < 0 || n > v->n_max || !aos_aligned(aos, 8)) return SPH_E_INVAL;
+    if (!(v->present & SPH_BIT(SPH_X))) return SPH_E_INVAL;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_BIN);
+        e = sphk::launch_bin(static_cast<const uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X], (int)n, v->g,
+                             v->ncells, v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
+                             v->cell_of_slot, v->status, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->n = n;
+    v->binned = true;
+    v->resident = 0;
+    return SPH_OK;
+}
+
+sph_status do_gather(sph_view_s *v, const void *aos, int64_t n, uint32_t mask)
+{
+    if (!aos || !aos_aligned(aos, 8) || !mask_present(v, mask)) return SPH_E_INVAL;
+    if (!v->binned) return SPH_E_STATE;
+    if (n != v->n) return SPH_E_INVAL;
+    const bool vec16 = (v->layout.stride % 16) == 0 && aos_aligned(aos, 16) && v->layout.stride <= 16 * sphk::kMaxChunks;
+    ConvPlan plan;
+    build_plan(v, mask, vec16, &plan);
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_GATHER);
+        e = sphk::launch_gather(static_cast<const uint8_t *>(aos), v->layout.stride, vec16, v->perm, v->cell_of_slot,
+                                (int)n, plan, v->g, v->prec == SPH_F32, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->resident |= mask;
+    return SPH_OK;
+}
+
+sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask)
+{
+    if (!aos || !aos_aligned(aos, 8) || !mask_present(v, mask)) return SPH_E_INVAL;
+    if (!v->binned) return SPH_E_STATE;
+    if (n != v->n) return SPH_E_INVAL;
+    if ((mask & ~v->resident) != 0) return SPH_E_STATE;
+    ConvPlan plan;
+    build_plan(v, mask, false, &plan);
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_SCATTER);
+        e = sphk::launch_scatter(static_cast<uint8_t *>(aos), v->layout.stride, v->perm, v->cell_of_slot, (int)n,
+                                 plan, v->g, v->prec == SPH_F32, v->st, &ph.nl);
+    }
+    return cuda_fail(e);
+}
+
+sph_status do_density(sph_view_s *v, const sph_params *p)
+{
+    if (!p) return SPH_E_INVAL;
+    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
+    const bool f32 = v->prec == SPH_F32;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_DENSITY_PREP);
+        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    {
+        Phase ph(v, SPH_PH_DENSITY);
+        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->g, p->gamma,
+                                       v->tile_density, v->status, v->counters, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->resident |= SPH_DENSITY_OUT;
+    return SPH_OK;
+}
+
+sph_status do_force(sph_view_s *v, const sph_params *p)
+{
+    if (!p) return SPH_E_INVAL;
+    if (!mask_present(v, SPH_FORCE_OUT)) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & SPH_FORCE_IN) != SPH_FORCE_IN) return SPH_E_STATE;
+    const bool f32 = v->prec == SPH_F32;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_FORCE_PREP);
+        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    {
+        Phase ph(v, SPH_PH_FORCE);
+        e = sphk::launch_force_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->g, *p,
+                                     v->tile_force, v->status, v->counters, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->resident |= SPH_FORCE_OUT;
+    return SPH_OK;
+}
+
+sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
+{
+    sph_status s;
+    if ((s = do_bin(v, aos, n)) != SPH_OK) return s;
+    if ((s = do_gather(v, aos, n, SPH_DENSITY_IN)) != SPH_OK) return s;
+    if ((s = do_density(v, p)) != SPH_OK) return s;
+    if ((s = do_scatter(v, aos, n, SPH_DENSITY_OUT)) != SPH_OK) return s;
+    if ((s = do_gather(v, aos, n, SPH_FORCE_IN)) != SPH_OK) return s;
+    if ((s = do_force(v, p)) != SPH_OK) return s;
+    return do_scatter(v, aos, n, SPH_FORCE_OUT);
+}
+
+// Half kick on the view (v += a dt/2, u += du/dt dt/2), then write v and u back into the records.
+sph_status do_kick(sph_view_s *v, void *aos, int64_t n, double dtk)
+{
+    const uint32_t need = SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
+    if ((v->resident & need) != need) return SPH_E_STATE;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_KDK);
+        e = sphk::launch_kick(v->prec == SPH_F32, v->soa, (int)n, dtk, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    return do_scatter(v, aos, n, SPH_BIT(SPH_V) | SPH_BIT(SPH_U));
+}
+
+sph_status do_reduce(sph_view_s *v, double *out)
+{
+    const uint32_t need = SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
+    if (!out) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & need) != need) return SPH_E_STATE;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_REDUCE);
+        e = sphk::launch_reduce(v->prec == SPH_F32, v->soa, (int)v->n, v->red_partials, v->red_out, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    e = cudaMemcpyAsync(v->h_red, v->red_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, v->st);
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    e = cudaStreamSynchronize(v->st);
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    memcpy(out, v->h_red, 8 * sizeof(double));
+    return SPH_OK;
+}
+
+sph_status read_status(sph_view_s *v, uint32_t *bits, bool clear)
+{
+    cudaError_t e = cudaMemcpyAsync(v->h_status, v->status, sizeof(unsigned), cudaMemcpyDeviceToHost, v->st);
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    if (clear) {
+        e = cudaMemsetAsync(v->status, 0, sizeof(unsigned), v->st);
+        if (e != cudaSuccess) return SPH_E_CUDA;
+    }
+    e = cudaStreamSynchronize(v->st);
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    *bits = *v->h_status;
+    return SPH_OK;
+}
+
+sph_status do_step(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double dt, int32_t nsteps,
+                   double *stats_out)
+{
+    if (!p || !aos || nsteps < 0 || !(dt >= 0.0) || !(dt < 1e300)) return SPH_E_INVAL;
+    const bool kdk = dt > 0.0 && nsteps > 0;
+    if (kdk && !mask_present(v, SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT)))
+        return SPH_E_INVAL;
+    sph_status s = do_pass(v, aos, n, p);
+    if (s != SPH_OK) return s;
+    for (int32_t k = 0; kdk && k < nsteps; ++k) {
+        if ((s = do_kick(v, aos, n, 0.5 * dt)) != SPH_OK) return s;
+        cudaError_t e;
+        {
+            Phase ph(v, SPH_PH_KDK);
+            e = sphk::launch_drift_aos(static_cast<uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X],
+                                       v->layout.off[SPH_V], (int)n, v->g, dt, v->st, &ph.nl);
+        }
+        if (e != cudaSuccess) return SPH_E_CUDA;
+        if ((s = do_pass(v, aos, n, p)) != SPH_OK) return s;
+        if ((s = do_kick(v, aos, n, 0.5 * dt)) != SPH_OK) return s;
+    }
+    if (stats_out) return do_reduce(v, stats_out);
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_max, const sph_domain *domain,
+                           void *cuda_stream, sph_view *out)
+{
+    if (!out) return SPH_E_INVAL;
+    *out = nullptr;
+    uint32_t present = 0;
+    if (!layout_valid(layout, &present) || !domain_valid(domain)) return SPH_E_INVAL;
+    if (prec != SPH_F64 && prec != SPH_F32) return SPH_E_INVAL;
+    if (n_max < 0 || n_max > 0x7fffffffLL) return SPH_E_INVAL;
+    sph_view_s *v = new (std::nothrow) sph_view_s;
+    if (!v) return SPH_E_NOMEM;
+    memset(v, 0, sizeof(*v));
+    v->layout = *layout;
+    v->prec = prec;
+    v->n_max = n_max;
+    v->dom = *domain;
+    v->st = static_cast<cudaStream_t>(cuda_stream);
+    v->g = make_grid(*domain);
+    v->ncells = domain->ncell[0] * domain->ncell[1] * domain->ncell[2];
+    v->esz = prec == SPH_F64 ? 8 : 4;
+    v->present = present;
+    v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
+    v->ev_pending = new (std::nothrow) std::vector<PendingTiming>();
+    if (!v->ev_free || !v->ev_pending) {
+        delete v->ev_free;
+        delete v->ev_pending;
+        delete v;
+        return SPH_E_NOMEM;
+    }
+    Bump sizing;
+    carve(v, sizing);
+    if (cudaMalloc(&v->arena, sizing.off) != cudaSuccess) {
+        v->arena = nullptr;
+        sph_view_destroy(v);
+        return SPH_E_NOMEM;
+    }
+    Bump real;
+    real.base = static_cast<char *>(v->arena);
+    carve(v, real);
+    if (cudaMallocHost(&v->h_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&v->h_red, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess) {
+        sph_view_destroy(v);
+        return SPH_E_NOMEM;
+    }
+    if (cudaMemsetAsync(v->status, 0, sizeof(unsigned), v->st) != cudaSuccess ||
+        cudaMemsetAsync(v->counters, 0, sizeof(sphk::Counters), v->st) != cudaSuccess ||
+        cudaStreamSynchronize(v->st) != cudaSuccess) {
+        sph_view_destroy(v);
+        return SPH_E_CUDA;
+    }
+    *out = v;
+    return SPH_OK;
+}
+
+sph_status sph_view_destroy(sph_view v)
+{
+    if (!v) return SPH_OK;
+    cudaStreamSynchronize(v->st);
+    if (v->arena) cudaFree(v->arena);
+    if (v->aos_stage) cudaFree(v->aos_stage);
+    if (v->h_status) cudaFreeHost(v->h_status);
+    if (v->h_red) cudaFreeHost(v->h_red);
+    if (v->h_counters) cudaFreeHost(v->h_counters);
+    if (v->ev_pending) {
+        for (const PendingTiming &p : *v->ev_pending) {
+            cudaEventDestroy(p.e0);
+            cudaEventDestroy(p.e1);
+        }
+        delete v->ev_pending;
+    }
+    if (v->ev_free) {
+        for (cudaEvent_t e : *v->ev_free) cudaEventDestroy(e);
+        delete v->ev_free;
+    }
+    delete v;
+    return SPH_OK;
+}
+
+sph_status sph_bin(sph_view v, const void *aos_dev, int64_t n)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_bin(v, aos_dev, n);
+}
+
+sph_status sph_aos_to_soa(sph_view v, const void *aos_dev, int64_t n, uint32_t in_mask)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_gather(v, aos_dev, n, in_mask);
+}
+
+sph_status sph_density(sph_view v, const sph_params *params)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_density(v, params);
+}
+
+sph_status sph_force(sph_view v, const sph_params *params)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_force(v, params);
+}
+
+sph_status sph_soa_to_aos(sph_view v, void *aos_dev, int64_t n, uint32_t out_mask)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_scatter(v, aos_dev, n, out_mask);
+}
+
+sph_status sph_step(sph_view v, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps,
+                    double *stats_out)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_step(v, aos_dev, n, params, dt, nsteps, stats_out);
+}
+
+sph_status sph_step_host(sph_view v, void *aos_host, int64_t n, const sph_params *params, double dt,
+                         int32_t nsteps, double *stats_out)
+{
+    if (!v || !aos_host || !params || n < 0 || n > v->n_max) return SPH_E_INVAL;
+    if (!v->aos_stage) {
+        const size_t bytes = (size_t)std::max<int64_t>(v->n_max, 1) * (size_t)v->layout.stride;
+        if (cudaMalloc(&v->aos_stage, bytes) != cudaSuccess) {
+            v->aos_stage = nullptr;
+            return SPH_E_NOMEM;
+        }
+    }
+    const size_t bytes = (size_t)n * (size_t)v->layout.stride;
+    if (bytes && cudaMemcpyAsync(v->aos_stage, aos_host, bytes, cudaMemcpyHostToDevice, v->st) != cudaSuccess)
+        return SPH_E_CUDA;
+    sph_status s = do_step(v, v->aos_stage, n, params, dt, nsteps, stats_out);
+    if (s != SPH_OK) return s;
+    if (bytes && cudaMemcpyAsync(aos_host, v->aos_stage, bytes, cudaMemcpyDeviceToHost, v->st) != cudaSuccess)
+        return SPH_E_CUDA;
+    return sph_view_sync(v);
+}
+
+sph_status sph_reduce(sph_view v, double out[8])
+{
+    if (!v) return SPH_E_INVAL;
+    return do_reduce(v, out);
+}
+
+sph_status sph_view_sync(sph_view v)
+{
+    if (!v) return SPH_E_INVAL;
+    uint32_t bits = 0;
+    sph_status s = read_status(v, &bits, false);
+    if (s != SPH_OK) return s;
+    if (bits & SPH_DEV_TIMEOUT) return SPH_E_TIMEOUT;
+    return bits ? SPH_E_DEVICE : SPH_OK;
+}
+
+sph_status sph_view_status(sph_view v, uint32_t *bits, int32_t clear)
+{
+    if (!v || !bits) return SPH_E_INVAL;
+    return read_status(v, bits, clear != 0);
+}
+
+sph_status sph_view_soa(sph_view v, int32_t field, int32_t comp, void **dev_ptr)
+{
+    if (!v || !dev_ptr || field < 0 || field >= SPH_NFIELDS || comp < 0 || comp >= kNcomp[field]) return SPH_E_INVAL;
+    if (!(v->present & SPH_BIT(field))) return SPH_E_INVAL;
+    *dev_ptr = v->soa.p[field][comp];
+    return SPH_OK;
+}
+
+sph_status sph_view_index(sph_view v, int32_t which, void **dev_ptr)
+{
+    if (!v || !dev_ptr) return SPH_E_INVAL;
+    switch (which) {
+    case 0: *dev_ptr = v->perm; return SPH_OK;
+    case 1: *dev_ptr = v->cell_start; return SPH_OK;
+    case 2: *dev_ptr = v->cell_of_slot; return SPH_OK;
+    default: return SPH_E_INVAL;
+    }
+}
+
+sph_status sph_view_export(sph_view v, int32_t field, int32_t comp, void *dst, int64_t count)
+{
+    void *src = nullptr;
+    sph_status s = sph_view_soa(v, field, comp, &src);
+    if (s != SPH_OK) return s;
+    if (!dst || count < 0 || count > v->n_max) return SPH_E_INVAL;
+    if (count && cudaMemcpyAsync(dst, src, (size_t)count * v->esz, cudaMemcpyDefault, v->st) != cudaSuccess)
+        return SPH_E_CUDA;
+    return cudaStreamSynchronize(v->st) == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+sph_status sph_view_export_index(sph_view v, int32_t which, void *dst, int64_t count)
+{
+    void *src = nullptr;
+    sph_status s = sph_view_index(v, which, &src);
+    if (s != SPH_OK) return s;
+    const int64_t cap = which == 1 ? (int64_t)v->ncells + 1 : v->n_max;
+    if (!dst || count < 0 || count > cap) return SPH_E_INVAL;
+    if (count && cudaMemcpyAsync(dst, src, (size_t)count * 4, cudaMemcpyDefault, v->st) != cudaSuccess)
+        return SPH_E_CUDA;
+    return cudaStreamSynchronize(v->st) == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+sph_status sph_view_info(sph_view v, int64_t *n, int64_t *ncells)
+{
+    if (!v) return SPH_E_INVAL;
+    if (n) *n = v->n;
+    if (ncells) *ncells = v->ncells;
+    return SPH_OK;
+}
+
+sph_status sph_pair_counts(sph_view v, uint64_t counts[4], int32_t reset)
+{
+    if (!v || !counts) return SPH_E_INVAL;
+    cudaError_t e = cudaMemcpyAsync(v->h_counters, v->counters, sizeof(sphk::Counters), cudaMemcpyDeviceToHost, v->st);
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    if (reset && cudaMemsetAsync(v->counters, 0, sizeof(sphk::Counters), v->st) != cudaSuccess) return SPH_E_CUDA;
+    if (cudaStreamSynchronize(v->st) != cudaSuccess) return SPH_E_CUDA;
+    counts[0] = v->h_counters->dens_cand;
+    counts[1] = v->h_counters->dens_pairs;
+    counts[2] = v->h_counters->force_pairs;
+    counts[3] = v->h_counters->force_cand;
+    return SPH_OK;
+}
+
+sph_status sph_view_timing(sph_view v, int32_t enable)
+{
+    if (!v) return SPH_E_INVAL;
+    v->timing = enable != 0;
+    return SPH_OK;
+}
+
+sph_status sph_view_phase_times(sph_view v, double ms[SPH_NPHASES], int64_t launches[SPH_NPHASES], int32_t reset)
+{
+    if (!v) return SPH_E_INVAL;
+    sph_status s = drain_timings(v);
+    if (s != SPH_OK) return s;
+    for (int p = 0; p < SPH_NPHASES; ++p) {
+        if (ms) ms[p] = v->phase_ms[p];
+        if (launches) launches[p] = v->launches[p];
+        if (reset) {
+            v->phase_ms[p] = 0.0;
+            v->launches[p] = 0;
+        }
+    }
+    return SPH_OK;
+}
+
+const char *sph_strerror(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_E_INVAL: return "invalid argument";
+    case SPH_E_NOMEM: return "out of memory";
+    case SPH_E_CUDA: return "CUDA error";
+    case SPH_E_DEVICE: return "device status word set";
+    case SPH_E_TIMEOUT: return "bounded device wait timed out";
+    case SPH_E_NOTCONV: return "iteration did not converge";
+    case SPH_E_STATE: return "call order (view member not resident or not binned)";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

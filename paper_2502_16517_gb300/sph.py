@@ -1,0 +1,271 @@
+"""ctypes binding of libsph (include/sph.h).
+
+Same names as the C ABI, argument marshalling only: every step of the path runs in the library's CUDA kernels.
+Device buffers may be passed as torch CUDA tensors (their data pointer is used) or as raw integer addresses.
+Each call raises SphError when the library returns a status other than SPH_OK.  Loading fails loudly when the
+compiled library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsph.so")
+
+# ---- constants (mirror include/sph.h) ----
+SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_DEVICE, SPH_E_TIMEOUT, SPH_E_NOTCONV, SPH_E_STATE = range(8)
+SPH_F64, SPH_F32 = 0, 1
+SPH_X, SPH_V, SPH_A, SPH_MASS, SPH_H, SPH_RHO, SPH_P, SPH_U, SPH_DUDT, SPH_CS = range(10)
+SPH_NFIELDS = 10
+FIELD_NAMES = ("x", "v", "a", "mass", "h", "rho", "P", "u", "dudt", "cs")
+NCOMP = (3, 3, 3, 1, 1, 1, 1, 1, 1, 1)
+
+
+def SPH_BIT(f):
+    return 1 << f
+
+
+SPH_DENSITY_IN = SPH_BIT(SPH_X) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_U)
+SPH_DENSITY_OUT = SPH_BIT(SPH_RHO) | SPH_BIT(SPH_P) | SPH_BIT(SPH_CS)
+SPH_FORCE_IN = (SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_RHO)
+                | SPH_BIT(SPH_P) | SPH_BIT(SPH_CS))
+SPH_FORCE_OUT = SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT)
+SPH_ALL_FIELDS = (1 << SPH_NFIELDS) - 1
+SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 0x2, 0x4, 0x8
+(SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
+ SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
+SPH_NPHASES = 9
+PHASE_NAMES = ("bin", "gather", "density_prep", "density", "scatter", "force_prep", "force", "reduce", "kdk")
+
+
+class sph_layout(ctypes.Structure):
+    _fields_ = [("stride", ctypes.c_int64), ("off", ctypes.c_int32 * SPH_NFIELDS)]
+
+
+class sph_domain(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double * 3), ("ncell", ctypes.c_int32 * 3), ("periodic", ctypes.c_int32)]
+
+
+class sph_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class SphError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = int(status)
+        super().__init__(f"{fn}: {strerror(status)} ({status})")
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SIGS = {
+    "sph_view_create": [ctypes.POINTER(sph_layout), ctypes.c_int, _I64, ctypes.POINTER(sph_domain), _VP,
+                        ctypes.POINTER(_VP)],
+    "sph_view_destroy": [_VP],
+    "sph_bin": [_VP, _VP, _I64],
+    "sph_aos_to_soa": [_VP, _VP, _I64, ctypes.c_uint32],
+    "sph_density": [_VP, ctypes.POINTER(sph_params)],
+    "sph_force": [_VP, ctypes.POINTER(sph_params)],
+    "sph_soa_to_aos": [_VP, _VP, _I64, ctypes.c_uint32],
+    "sph_step": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.c_double, _I32, ctypes.POINTER(ctypes.c_double)],
+    "sph_step_host": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.c_double, _I32,
+                      ctypes.POINTER(ctypes.c_double)],
+    "sph_reduce": [_VP, ctypes.POINTER(ctypes.c_double)],
+    "sph_view_sync": [_VP],
+    "sph_view_status": [_VP, ctypes.POINTER(ctypes.c_uint32), _I32],
+    "sph_view_soa": [_VP, _I32, _I32, ctypes.POINTER(_VP)],
+    "sph_view_index": [_VP, _I32, ctypes.POINTER(_VP)],
+    "sph_view_export": [_VP, _I32, _I32, _VP, _I64],
+    "sph_view_export_index": [_VP, _I32, _VP, _I64],
+    "sph_view_info": [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "sph_pair_counts": [_VP, ctypes.POINTER(ctypes.c_uint64), _I32],
+    "sph_view_timing": [_VP, _I32],
+    "sph_view_phase_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
+}
+EXPORTED = tuple(_SIGS) + ("sph_strerror",)
+
+
+def lib():
+    """Load libsph.so (built in-tree by paper_2502_16517_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsph is not built ({LIB_PATH} missing): run paper_2502_16517_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sph_strerror.argtypes = [ctypes.c_int]
+        L.sph_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().sph_strerror(int(status)).decode()
+
+
+def _check(fn, status):
+    if status != SPH_OK:
+        raise SphError(fn, status)
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+# ---- struct helpers ----
+def make_layout(layout: dict) -> sph_layout:
+    """sph_layout from {"stride": s, "offsets": {name: byte offset}}; absent members get -1."""
+    L = sph_layout()
+    L.stride = int(layout["stride"])
+    for f, name in enumerate(FIELD_NAMES):
+        L.off[f] = int(layout["offsets"].get(name, -1))
+    return L
+
+
+def make_domain(box, ncell, periodic=True) -> sph_domain:
+    D = sph_domain()
+    for a in range(3):
+        D.box[a] = float(box[a])
+        D.ncell[a] = int(ncell[a])
+    D.periodic = 1 if periodic else 0
+    return D
+
+
+def make_params(p: dict) -> sph_params:
+    return sph_params(float(p["gamma"]), float(p["alpha"]), float(p["beta"]), float(p["eps"]))
+
+
+# ---- the C ABI ----
+def sph_view_create(layout, prec, n_max, domain, stream=None):
+    """Returns the view handle (an int).  layout/domain may be dicts/tuples or ctypes structs."""
+    L = layout if isinstance(layout, sph_layout) else make_layout(layout)
+    D = domain if isinstance(domain, sph_domain) else make_domain(*domain)
+    out = _VP()
+    st = _addr(stream) if stream is not None else None
+    _check("sph_view_create", lib().sph_view_create(ctypes.byref(L), int(prec), int(n_max), ctypes.byref(D),
+                                                    st, ctypes.byref(out)))
+    return out.value
+
+
+def sph_view_destroy(view):
+    _check("sph_view_destroy", lib().sph_view_destroy(view))
+
+
+def sph_bin(view, aos_dev, n):
+    _check("sph_bin", lib().sph_bin(view, _addr(aos_dev), int(n)))
+
+
+def sph_aos_to_soa(view, aos_dev, n, in_mask):
+    _check("sph_aos_to_soa", lib().sph_aos_to_soa(view, _addr(aos_dev), int(n), int(in_mask)))
+
+
+def sph_density(view, params):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    _check("sph_density", lib().sph_density(view, ctypes.byref(P)))
+
+
+def sph_force(view, params):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    _check("sph_force", lib().sph_force(view, ctypes.byref(P)))
+
+
+def sph_soa_to_aos(view, aos_dev, n, out_mask):
+    _check("sph_soa_to_aos", lib().sph_soa_to_aos(view, _addr(aos_dev), int(n), int(out_mask)))
+
+
+def sph_step(view, aos_dev, n, params, dt=0.0, nsteps=0, want_stats=False):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    stats = (ctypes.c_double * 8)() if want_stats else None
+    _check("sph_step", lib().sph_step(view, _addr(aos_dev), int(n), ctypes.byref(P), float(dt), int(nsteps),
+                                      stats))
+    return np.array(stats[:]) if want_stats else None
+
+
+def sph_step_host(view, aos_host, n, params, dt=0.0, nsteps=0, want_stats=False):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    stats = (ctypes.c_double * 8)() if want_stats else None
+    _check("sph_step_host", lib().sph_step_host(view, _addr(aos_host), int(n), ctypes.byref(P), float(dt),
+                                                int(nsteps), stats))
+    return np.array(stats[:]) if want_stats else None
+
+
+def sph_reduce(view):
+    out = (ctypes.c_double * 8)()
+    _check("sph_reduce", lib().sph_reduce(view, out))
+    return np.array(out[:])
+
+
+def sph_view_sync(view):
+    _check("sph_view_sync", lib().sph_view_sync(view))
+
+
+def sph_view_status(view, clear=False):
+    bits = ctypes.c_uint32()
+    _check("sph_view_status", lib().sph_view_status(view, ctypes.byref(bits), 1 if clear else 0))
+    return bits.value
+
+
+def sph_view_soa(view, field, comp=0):
+    p = _VP()
+    _check("sph_view_soa", lib().sph_view_soa(view, int(field), int(comp), ctypes.byref(p)))
+    return p.value
+
+
+def sph_view_index(view, which):
+    p = _VP()
+    _check("sph_view_index", lib().sph_view_index(view, int(which), ctypes.byref(p)))
+    return p.value
+
+
+def sph_view_export(view, field, comp, count, prec):
+    """SoA member `field`/`comp` as a host numpy array of `count` elements (float64 or float32 by prec)."""
+    out = np.empty(int(count), np.float64 if prec == SPH_F64 else np.float32)
+    _check("sph_view_export", lib().sph_view_export(view, int(field), int(comp), out.ctypes.data, int(count)))
+    return out
+
+
+def sph_view_export_index(view, which, count):
+    out = np.empty(int(count), np.int32)
+    _check("sph_view_export_index", lib().sph_view_export_index(view, int(which), out.ctypes.data, int(count)))
+    return out
+
+
+def sph_view_info(view):
+    n, nc = _I64(), _I64()
+    _check("sph_view_info", lib().sph_view_info(view, ctypes.byref(n), ctypes.byref(nc)))
+    return n.value, nc.value
+
+
+def sph_pair_counts(view, reset=False):
+    out = (ctypes.c_uint64 * 4)()
+    _check("sph_pair_counts", lib().sph_pair_counts(view, out, 1 if reset else 0))
+    return [int(v) for v in out]
+
+
+def sph_view_timing(view, enable=True):
+    _check("sph_view_timing", lib().sph_view_timing(view, 1 if enable else 0))
+
+
+def sph_view_phase_times(view, reset=False):
+    """(ms per phase, kernel launches per phase) as numpy arrays of SPH_NPHASES entries."""
+    ms = (ctypes.c_double * SPH_NPHASES)()
+    nl = (_I64 * SPH_NPHASES)()
+    _check("sph_view_phase_times", lib().sph_view_phase_times(view, ms, nl, 1 if reset else 0))
+    return np.array(ms[:]), np.array(nl[:], np.int64)

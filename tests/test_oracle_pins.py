@@ -364,3 +364,22 @@ def test_sampled_pass_equals_full_pass(oracle):
     smp = oracle.step_sampled(aos, lay, f["box"], wl.SPH_PARAMS, tg)
     for k in ("rho", "P", "cs", "a", "dudt"):
         np.testing.assert_array_equal(smp[k], full[k][tg])
+
+
+def test_fp32_position_round_trip_within_float_rounding(oracle):
+    lay = wl.default_layout()
+    f = wl.jittered_lattice(9, jitter=0.45, seed=13)
+    aos, _ = wl.pack_aos(f, lay)
+    nc = np.array([4, 3, 5], np.int32)
+    x = oracle.unpack(aos, lay)["x"]
+    _, _, perm, cos, _ = oracle.bin_cells(x, f["box"], nc)
+    rel = oracle.gather_pos_f32(aos, lay["stride"], perm, lay["offsets"]["x"], cos, f["box"], nc)
+    out = aos.copy()
+    oracle.scatter_pos_f32(out, lay["stride"], perm, lay["offsets"]["x"], cos, f["box"], nc, rel)
+    back = oracle.unpack(out, lay)["x"]
+    edge = f["box"] / nc
+    # |rel| <= edge, so the float rounding error is at most half an ulp of the edge (2^-24 relative)
+    assert np.all(np.abs(back - x) <= edge * 2.0 ** -24 + 1e-17)
+    changed = np.any(out != aos, axis=0)
+    o = lay["offsets"]["x"]
+    assert not changed[:o].any() and not changed[o + 24:].any()
