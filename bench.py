@@ -326,6 +326,9 @@ def main():
     ap.add_argument("--cpu-block", type=int, default=10, help="oracle sample cube (lattice spacings) for cpu_baseline")
     ap.add_argument("--ref-block", type=int, default=4, help="oracle sample cube per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--only", choices=["f64", "f32"], default=None,
+                    help="run one form only (profiling runs); the JSON line then carries that form's numbers")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -346,18 +349,26 @@ def main():
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if \
         os.environ.get("CUDA_VISIBLE_DEVICES") else local
 
-    r64 = run_form(0, steps, warmup, dev, aos_h, lay, f["box"], ncell, clocks_gpu=gpu_index)
-    r32 = run_form(1, steps, warmup, dev, aos_h, lay, f["box"], ncell)
+    forms = ["f64", "f32"] if args.only is None else [args.only]
+    runs = {}
+    for k, form in enumerate(forms):
+        runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
+                              clocks_gpu=gpu_index if k == 0 else None)
     # max over ranks of the summed step time
-    tot = torch.tensor([float(np.sum(r64["step_ms"])), float(np.sum(r32["step_ms"]))], device=dev)
+    tot = torch.tensor([float(np.sum(runs[fm]["step_ms"])) for fm in forms], device=dev)
     if world > 1:
         torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    r64["step_ms"] = [tot[0].item() / steps] * steps
-    r32["step_ms"] = [tot[1].item() / steps] * steps
-    s64 = summarize_form(0, r64, n, steps, world)
-    s32 = summarize_form(1, r32, n, steps, world)
-    e2e = run_e2e(0, max(steps // 2, 3), 2, dev, aos_h, lay, f["box"], ncell)
-    e2e["value"] *= world
+    summ = {}
+    for k, fm in enumerate(forms):
+        runs[fm]["step_ms"] = [tot[k].item() / steps] * steps
+        summ[fm] = summarize_form(0 if fm == "f64" else 1, runs[fm], n, steps, world)
+    main_form = forms[0]
+    s64, r64 = summ[main_form], runs[main_form]
+    s32 = summ.get("f32") if main_form == "f64" else None
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(0 if main_form == "f64" else 1, max(steps // 2, 3), 2, dev, aos_h, lay, f["box"], ncell)
+        e2e["value"] *= world
     peaks = measured_peaks()
     if rank != 0:
         torch.distributed.destroy_process_group()
@@ -371,16 +382,17 @@ def main():
         conv["hbm_peak_GBps"] = hbm
         conv["gather_frac"] = conv["gather_GBps"] / hbm if conv["gather_GBps"] else None
         conv["scatter_frac"] = conv["scatter_GBps"] / hbm if conv["scatter_GBps"] else None
+    prec_main = 0 if main_form == "f64" else 1
     line = {
         "metric": METRIC, "value": s64["value"], "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": s64["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": main_form, "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": n, "cells": int(np.prod(ncell)), "record_bytes": lay["stride"],
                    "l2": "256 MB buffer written between timed steps (outside the step events)",
                    "step": "sph_step: bin + gather + density + scatter + gather + force + scatter",
                    "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": roofline_of(0, s64, steps, peaks),
+        "roofline": roofline_of(prec_main, s64, steps, peaks),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(s64["launches"].values())),
@@ -389,11 +401,11 @@ def main():
         "pairs_per_step": s64["pairs_per_step"],
         "candidates_per_step": s64["candidates_per_step"],
         "conversion": conv,
-        "forms": {"f32": {"value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
-                          "speedup_vs_f64": s32["value"] / s64["value"],
-                          "phases_ms_per_step": s32["phases_ms_per_step"],
-                          "roofline": roofline_of(1, s32, steps, peaks), "conversion": s32["conversion"],
-                          "gpu_launches": int(sum(s32["launches"].values()))}},
+        "forms": {} if s32 is None else {"f32": {
+            "value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
+            "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
+            "roofline": roofline_of(1, s32, steps, peaks), "conversion": s32["conversion"],
+            "gpu_launches": int(sum(s32["launches"].values()))}},
         "wall_s_timed_bracket": r64["wall_s"],
     }
     print(json.dumps(line))

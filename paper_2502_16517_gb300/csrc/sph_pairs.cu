@@ -361,7 +361,8 @@ struct DensF32 {
         A.cs[i] = cs;
         unsigned bits = 0;
         if (!(rho > 0.0f) || !isfinite(rho) || !isfinite(P) || !isfinite(cs)) bits |= SPH_DEV_NONFINITE;
-        if (!(2.0 * (double)h <= A.cm.g.min_edge)) bits |= SPH_DEV_H_TOO_BIG;
+        // h is the float cast of the record's h (at most half an ulp above it): allow that rounding
+        if (!(2.0 * (double)h <= A.cm.g.min_edge * (1.0 + 2.4e-7))) bits |= SPH_DEV_H_TOO_BIG;
         if (bits) atomicOr(A.cm.status, bits);
     }
     static __device__ __forceinline__ void count(const Args &A, unsigned long long cand,

@@ -161,7 +161,7 @@ def pack_aos(fields, layout=None, order="shuffled", seed=SEED + 1, canary=True):
     for name in FIELDS:
         if name not in fields or name not in offs:
             continue
-        val = np.asarray(fields[name], np.float64).reshape(n, NCOMP[name])
+        val = np.ascontiguousarray(np.asarray(fields[name], np.float64).reshape(n, NCOMP[name]))
         o = int(offs[name])
         rec[:, o:o + 8 * NCOMP[name]] = val.view(np.uint8).reshape(n, 8 * NCOMP[name])
     if layout["offsets"] == RECORD_OFFSETS and stride >= ID_OFFSET + 8:

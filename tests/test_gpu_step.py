@@ -55,14 +55,18 @@ def test_step_host_equals_step(sph, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_reduce_matches_oracle_sums(sph, oracle, prec):
+    """The FP64 sums run over the view's values: FP64 views hold the records' values, FP32 views their
+    round-to-nearest casts (numpy's float32 cast), so the oracle sums those."""
     f, lay, aos_h, ncell = _tiny_aos()
     out, info = H.run_step(aos_h, lay, f["box"], ncell, prec)
     g = oracle.unpack(out, lay)
+    if prec == 1:
+        g = {k: v.astype(np.float32).astype(np.float64) for k, v in g.items()}
     ref = oracle.reduce_sums(g["mass"], g["v"], g["a"], g["u"], g["dudt"])
     red = info["reduce"]
-    # the GPU sums the view's values (FP32 views: the float values, widened) in a tree order
-    scale = np.array([np.sum(g["mass"][:, None] * np.abs(g["v"]))] * 3 + [np.sum(g["mass"][:, None] * np.abs(g["a"]))] * 3
-                     + [abs(ref[6]), np.sum(g["mass"] * (np.abs((g["v"] * g["a"]).sum(1)) + np.abs(g["dudt"])))])
+    m = g["mass"]
+    scale = np.array([np.sum(m[:, None] * np.abs(g["v"]))] * 3 + [np.sum(m[:, None] * np.abs(g["a"]))] * 3
+                     + [abs(ref[6]), np.sum(m * (np.abs((g["v"] * g["a"]).sum(1)) + np.abs(g["dudt"])))])
     assert np.all(np.abs(red - ref) <= 1e-12 * scale)
 
 
