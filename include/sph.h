@@ -228,6 +228,35 @@ SPH_API sph_status sph_view_timing(sph_view view, int32_t enable);
 SPH_API sph_status sph_view_phase_times(sph_view view, double ms[SPH_NPHASES], int64_t launches[SPH_NPHASES],
                                         int32_t reset);
 
+/* Capacity of sph_bin_static's fixed scratch. */
+#define SPH_BIN_STATIC_MAX_PARTICLES 262144
+#define SPH_BIN_STATIC_MAX_CELLS 65536
+
+/* Cell bucketing that allocates nothing.  The paper has no counterpart: this entry point exists for callers
+ * that may not allocate device memory, such as code running inside an allocator or memory-pool callback, a
+ * plug-in whose host framework owns all device allocations, or a loop with a strict no-allocation rule.  Those
+ * callers cannot create a view, because sph_view_create allocates.
+ * It computes what sph_bin computes, for the records [0, n) of aos_dev (positions at layout->off[SPH_X]) in
+ * `domain`, into the caller's device arrays:
+ *   perm_dev[n]                record held by each slot;
+ *   cell_start_dev[ncells + 1] CSR offsets of the cells;
+ *   cell_of_slot_dev[n]        cell of each slot.
+ * Inside a cell the slots hold ascending record indices.  status_dev, if not NULL, is a device word into which
+ * SPH_DEV_POS_RANGE is OR-ed when a position lies outside the box; the caller clears it.
+ * Work is enqueued on cuda_stream; the call does not wait.
+ * Intermediate arrays live in one fixed device array of 2.5 MB inside the library.  It exists once per GPU that
+ * loads the library and stays allocated until the process exits.  No call allocates or frees memory.  All calls
+ * on a device share that array, so calls whose work can overlap on the GPU (other streams, other host threads)
+ * race on it and must be ordered by the caller.  Each call clears what must start at zero.
+ * The first call on a device looks up the array's address with that device current; make that first call
+ * before any stream capture.
+ * Errors: SPH_E_INVAL for a null pointer, a bad layout or domain, or a size beyond the fixed capacity
+ * (n > SPH_BIN_STATIC_MAX_PARTICLES or more than SPH_BIN_STATIC_MAX_CELLS cells); SPH_E_CUDA if the address
+ * lookup or a launch fails. */
+SPH_API sph_status sph_bin_static(const sph_layout *layout, const sph_domain *domain, const void *aos_dev, int64_t n,
+                                  int32_t *perm_dev, int32_t *cell_start_dev, int32_t *cell_of_slot_dev,
+                                  uint32_t *status_dev, void *cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 SPH_API const char *sph_strerror(sph_status status);
 

@@ -38,6 +38,8 @@ SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 
 (SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
  SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
 SPH_NPHASES = 9
+SPH_BIN_STATIC_MAX_PARTICLES = 262144
+SPH_BIN_STATIC_MAX_CELLS = 65536
 PHASE_NAMES = ("bin", "gather", "density_prep", "density", "scatter", "force_prep", "force", "reduce", "kdk")
 
 
@@ -87,6 +89,7 @@ _SIGS = {
     "sph_pair_counts": [_VP, ctypes.POINTER(ctypes.c_uint64), _I32],
     "sph_view_timing": [_VP, _I32],
     "sph_view_phase_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
+    "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
 EXPORTED = tuple(_SIGS) + ("sph_strerror",)
 
@@ -269,3 +272,14 @@ def sph_view_phase_times(view, reset=False):
     nl = (_I64 * SPH_NPHASES)()
     _check("sph_view_phase_times", lib().sph_view_phase_times(view, ms, nl, 1 if reset else 0))
     return np.array(ms[:]), np.array(nl[:], np.int64)
+
+
+def sph_bin_static(layout, domain, aos_dev, n, perm_dev, cell_start_dev, cell_of_slot_dev, status_dev=None,
+                   stream=None):
+    """Cell bucketing into caller-owned device arrays with no allocation (see include/sph.h)."""
+    L = layout if isinstance(layout, sph_layout) else make_layout(layout)
+    D = domain if isinstance(domain, sph_domain) else make_domain(*domain)
+    st = _addr(stream) if stream is not None else None
+    _check("sph_bin_static", lib().sph_bin_static(ctypes.byref(L), ctypes.byref(D), _addr(aos_dev), int(n),
+                                                  _addr(perm_dev), _addr(cell_start_dev), _addr(cell_of_slot_dev),
+                                                  _addr(status_dev), st))
