@@ -229,7 +229,7 @@ def summarize_form(prec, r, n, steps, world):
             "launches": nl, "conversion": conv}
 
 
-def roofline_of(prec, s, steps, peaks):
+def roofline_of(prec, s, steps, peaks, measured=None):
     """Dominant kernel = the phase with the largest device time (the force pair kernel)."""
     ph = s["phases_ms_per_step"]
     dom = max(("density", "force"), key=lambda k: ph[k])
@@ -244,7 +244,8 @@ def roofline_of(prec, s, steps, peaks):
             "peak_source": ("derived: GB300 nominal FP64 1.25 TFLOP/s" if prec == 0 else
                             "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
             "algorithmic_flops_per_launch": flops, "flops_per_pair": FLOPS_FORCE_PAIR if dom == "force" else
-            FLOPS_DENSITY_PAIR, "launch_ms": ph[dom]}
+            FLOPS_DENSITY_PAIR, "launch_ms": ph[dom],
+            "measured_fma_peak_tflops": measured, "frac_of_measured_fma_peak": (achieved / measured) if measured else None}
 
 
 # ----------------------------------------------------------------------------------------------------------
@@ -370,6 +371,8 @@ def main():
         e2e = run_e2e(0 if main_form == "f64" else 1, max(steps // 2, 3), 2, dev, aos_h, lay, f["box"], ncell)
         e2e["value"] *= world
     peaks = measured_peaks()
+    from paper_2502_16517_gb300 import sph as _sph
+    fma_peak = {"f64": _sph.sph_probe_fma_rate(_sph.SPH_F64) / 1e12, "f32": _sph.sph_probe_fma_rate(_sph.SPH_F32) / 1e12}
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
@@ -392,7 +395,8 @@ def main():
                    "step": "sph_step: bin + gather + density + scatter + gather + force + scatter",
                    "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": roofline_of(prec_main, s64, steps, peaks),
+        "roofline": roofline_of(prec_main, s64, steps, peaks, fma_peak[main_form]),
+        "measured_fma_peak_tflops": fma_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(s64["launches"].values())),
@@ -404,7 +408,7 @@ def main():
         "forms": {} if s32 is None else {"f32": {
             "value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
-            "roofline": roofline_of(1, s32, steps, peaks), "conversion": s32["conversion"],
+            "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
             "gpu_launches": int(sum(s32["launches"].values()))}},
         "wall_s_timed_bracket": r64["wall_s"],
     }

@@ -228,6 +228,12 @@ SPH_API sph_status sph_view_timing(sph_view view, int32_t enable);
 SPH_API sph_status sph_view_phase_times(sph_view view, double ms[SPH_NPHASES], int64_t launches[SPH_NPHASES],
                                         int32_t reset);
 
+/* Measured fused multiply-add throughput of the current device, in flops/s (an FMA counts 2): prec SPH_F64 or
+ * SPH_F32.  Runs 8 independent FMA chains per thread on 8 CTAs of 256 threads per SM, on a private stream, and
+ * waits.  This is the arithmetic peak that the pair kernels' pipe fractions are compared with.  The paper has no
+ * counterpart; it reports no hardware peaks. */
+SPH_API sph_status sph_probe_fma_rate(int32_t prec, double *flops_per_s);
+
 /* Capacity of sph_bin_static's fixed scratch. */
 #define SPH_BIN_STATIC_MAX_PARTICLES 262144
 #define SPH_BIN_STATIC_MAX_CELLS 65536

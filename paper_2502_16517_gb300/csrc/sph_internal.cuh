@@ -50,10 +50,15 @@ struct SoaPtrs {
 struct Scratch {
     float *xf, *yf, *zf;  // FP64 views: cell-relative float copies of the positions (input of the FP32 filter)
     float *hf;            // FP64 views: (float) h, rounded up (filter radius)
-    void *hinv;           // force loop, view precision: 1/h
-    void *k5;             // force loop, view precision: 1/(pi h^5), so grad W(r,h) = k5 g(q) r_vec, g = f'(q)/q
-    void *A;              // force loop, view precision: P / rho^2
+    // Per-particle values of the pair loops, in the view's precision.
+    //   FP64 density: d[0..4] the cubic-in-r spline coefficients -3/(2h^2), 3/(4h^3), -3/h, 3/(2h^2), -1/(4h^3)
+    //   FP64 force: d[0] h/2, d[1] -3/(pi h^4), d[2] 3/(pi h^5), d[3] 9/(4 pi h^6), d[4] -3/(4 pi h^6), d[5] P/rho^2,
+    //         d[6] alpha c / 2
+    //   FP32: d[0] 1/h, d[1] 1/(pi h^5), d[2] P/rho^2
+    void *d[8];
 };
+constexpr int kDerivedF64 = 7;
+constexpr int kDerivedF32 = 3;
 
 struct Counters {
     unsigned long long dens_cand, dens_pairs, force_pairs, force_cand;
@@ -77,7 +82,7 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
                                 const Grid &g, cudaStream_t st, int *nl);
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const Grid &g, cudaStream_t st, int *nl);
+                              const Grid &g, double alpha, cudaStream_t st, int *nl);
 
 // The pair kernels.  tj: active particles staged per shared-memory tile (0 = default of the path).
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,

@@ -7,21 +7,24 @@
 //
 // Per CTA:
 //   1. a 27-entry neighbour table (first slot, count, running prefix, periodic shift) in shared memory;
-//   2. the active set is staged through shared memory in tiles of TJ particles (only the SoA members the
-//      loop body reads);
-//   3. each warp takes one local particle i at a time: its 32 lanes sweep the staged tile with a cheap FP32
-//      distance test, the survivors are compacted into a per-warp queue (ballot + popc), and whenever 32 are
-//      queued the lanes evaluate the full pair term in the path's precision, one pair per lane, with the exact
-//      support test applied as a mask (the neutral-element formulation of Section 5.6: out-of-support pairs
-//      contribute zero, no per-pair branch decides whether a term is summed);
-//   4. the warp's per-lane partial sums are combined by a shuffle tree and added to the particle's
-//      shared-memory accumulator; after the last tile each accumulator is finalised and written to the SoA.
-// The compaction keeps the expensive pair evaluation at ~90 % lane occupancy although only ~14 % of the
+//   2. the active set is staged through shared memory in tiles of TJ particles holding only the SoA members the
+//      loop body reads, plus one float4 per particle for the distance filter; each tile is padded to a multiple
+//      of 64 with sentinel particles that no filter accepts;
+//   3. each warp takes one local particle i at a time: its 32 lanes sweep the tile 64 candidates per step with
+//      the FP32 distance filter, the survivors are compacted (ballot + popc) into a per-warp ring of 128 slots,
+//      and whenever 32 are queued the lanes evaluate the full pair term in the path's precision, one pair per
+//      lane.  Inside the term the support is applied as a mask (the neutral-element formulation of Section 5.6:
+//      out-of-support coefficients are zero, no branch decides whether a term is summed);
+//   4. the per-lane partial sums are combined by shuffles and added to the particle's shared-memory
+//      accumulator; after the last tile each accumulator is finalised and written to the SoA arrays.
+// The compaction keeps the expensive evaluation at ~97 % lane occupancy although only ~15 % of the
 // 3^3-stencil candidates lie inside the support (cell edge 2h).
 //
 // FP64 path: positions are the FP64 members; x_i - x_j gets the periodic shift (+-box) of j's cell exactly as a
-// minimum-image wrap would.  The FP32 filter uses cell-relative float copies of the positions (k_pos32) with a
-// conservative radius, so it never drops a pair the FP64 test keeps.
+// minimum-image wrap would.  The FP32 filter uses cell-relative float copies of the positions with a conservative
+// radius, so it never drops a pair the FP64 test keeps.  The FP64 pipe (1/64 of the FP32 rate on this part) is
+// the bound, so every per-pair FP64 instruction is counted: piece selection and masks run on the integer pipe,
+// reciprocals are FP32-seeded Newton iterations, per-particle factors are precomputed.
 // FP32 path: positions are cell-relative floats (the FP32 view), so x_i - x_j = r_i - (r_j + d * edge) with d the
 // neighbour cell offset; the filter is the exact test; all sums are Kahan-compensated.
 #include <math.h>
@@ -36,6 +39,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPairThreads = 128;
 constexpr int kPairWarps = kPairThreads / 32;
 constexpr int kMaxLocal = 128;
+constexpr int kRing = 128;   // per-warp queue slots (at most 31 + 64 pending)
+constexpr int kStep = 64;    // candidates per filter step (two per lane)
+constexpr float kFar = 1e30f;  // sentinel coordinate: its squared distance overflows to +inf
 
 struct NbrTable {
     int start[27];
@@ -148,32 +154,105 @@ struct Kahan {
 };
 
 // ------------------------------------------------------------------------------------------------------------
-// Loop bodies
+// Pair-term arithmetic.
+//
+// The cubic spline is piecewise cubic in q = r/h.  Instead of evaluating both pieces and selecting, the
+// coefficients of the one piece that applies are selected and a single polynomial is evaluated:
+//   f(q)     = d0 + d1 q + d2 q^2 + d3 q^3     inner (q < 1): (1, 0, -3/2, 3/4), outer (1 <= q < 2): (2, -3, 3/2, -1/4)
+//   f'(q)/q  = c0/q + c1 + c2 q                inner: (0, -3, 9/4),             outer: (-3, 3, -3/4)
+// with every coefficient 0 for q >= 2 (outside the support): the masking of Section 5.6.  The FP64 loop bodies
+// scale these coefficients by powers of 1/h per particle (so the polynomials run in r) and choose the piece by
+// integer compares of bit patterns: for doubles >= 0 the bit patterns order like the values.
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float spline_w(float q)
+{
+    const bool in1 = q < 1.0f, in2 = q < 2.0f;
+    const float d0 = in1 ? 1.0f : (in2 ? 2.0f : 0.0f);
+    const float d1 = in1 ? 0.0f : (in2 ? -3.0f : 0.0f);
+    const float d2 = in1 ? -1.5f : (in2 ? 1.5f : 0.0f);
+    const float d3 = in1 ? 0.75f : (in2 ? -0.25f : 0.0f);
+    return fmaf(fmaf(fmaf(d3, q, d2), q, d1), q, d0);
+}
+
+__device__ __forceinline__ float spline_g(float q, float inv_q)
+{
+    const bool in1 = q < 1.0f, in2 = q < 2.0f;
+    const float c0 = in1 ? 0.0f : (in2 ? -3.0f : 0.0f);
+    const float c1 = in1 ? -3.0f : (in2 ? 3.0f : 0.0f);
+    const float c2 = in1 ? 2.25f : (in2 ? -0.75f : 0.0f);
+    return fmaf(c0, inv_q, fmaf(c2, q, c1));
+}
+
+// FP32 approximation of a positive double by bit manipulation on the integer pipe (exponent re-bias, mantissa
+// truncated to 23 bits; the input is first clamped into the float normal range), and the exact reverse.
+__device__ __forceinline__ float dbl_to_flt_bits(double x)
+{
+    unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    hi = min(max(hi, 0x38100000u), 0x47EFFFFFu);
+    return __uint_as_float(((hi - 0x38000000u) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double flt_to_dbl_bits(float y)
+{
+    const unsigned f = __float_as_uint(y);
+    return __hiloint2double((int)((f >> 3) + 0x38000000u), (int)(f << 29));
+}
+
+// 1/sqrt(x), x >= 0: FP32 seed (no conversion instructions), then two Newton-Raphson steps
+// y <- y (3/2 - x y^2 / 2) in FP64 (quadratic convergence: ~2^-22 -> ~2^-44 -> below FP64 rounding).  For x = 0
+// (or x below the float range) the result is large but finite, so r = x / sqrt(x) comes out 0 (or tiny).
+__device__ __forceinline__ double rsqrt_seeded(double x)
+{
+    double y = flt_to_dbl_bits(rsqrtf(dbl_to_flt_bits(x)));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
+// 1/x, x > 0 within the float range: FP32 seed, then two Newton-Raphson steps y <- y + y (1 - x y) in FP64.
+__device__ __forceinline__ double rcp_seeded(double x)
+{
+    double y = flt_to_dbl_bits(__frcp_rn(dbl_to_flt_bits(x)));
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Loop bodies.  Each provides: Args, Tile (carve / stage / sentinel), Lhs (load), filter, eval, Part (per-lane
+// partial sums, reduce), Acc (shared accumulator), accumulate, finish, count.
 // ------------------------------------------------------------------------------------------------------------
 struct PairCommon {
     const int *cell_start;
     Grid g;
     unsigned *status;
     Counters *counters;
-    int tj;  // staged particles per tile
+    int tj;  // staged particles per tile (a multiple of kStep)
 };
 
 // ---- density, FP64 ----
+// Per pair: r from one reciprocal square root, the piece of the spline chosen by integer compares of the bit
+// patterns of r against h_i and 2 h_i, and f evaluated as a cubic in r whose coefficients d_k h_i^-k come from
+// the per-particle set-up kernel.
 struct DensF64 {
     struct Args {
         PairCommon cm;
         const double *x, *y, *z, *m, *h, *u;
-        const float *xf, *yf, *zf;  // cell-relative float positions (filter only)
+        const float *xf, *yf, *zf;             // cell-relative float positions (filter only)
+        const double *e2, *e3, *o1, *o2, *o3;  // per particle (k_density_prep_f64)
         double *rho, *P, *cs;
         double gamma;
     };
     struct Tile {
         double *x, *y, *z, *m;
-        float *fx, *fy, *fz;
+        float4 *f4;  // filter: cell-relative position seen from the local cell, unused
         unsigned char *q;
     };
     struct Lhs {
-        double x, y, z, h, hinv;
+        double x, y, z;
+        long long hb1, hb2;  // bit patterns of h and 2h (r < h  <=>  bits(r) < hb1 for r >= 0)
+        double e2, e3, o1, o2, o3;
         float fx, fy, fz, b2;
     };
     struct Part {
@@ -182,7 +261,7 @@ struct DensF64 {
         __device__ __forceinline__ void reduce() { rho = warp_sum(rho); }
     };
     using Acc = double;
-    static constexpr int kStageBytes = 4 * 8 + 3 * 4 + 1;
+    static constexpr int kStageBytes = 4 * 8 + 16 + 1;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
@@ -191,10 +270,8 @@ struct DensF64 {
         t.y = t.x + tj;
         t.z = t.y + tj;
         t.m = t.z + tj;
-        t.fx = reinterpret_cast<float *>(t.m + tj);
-        t.fy = t.fx + tj;
-        t.fz = t.fy + tj;
-        t.q = reinterpret_cast<unsigned char *>(t.fz + tj);
+        t.f4 = reinterpret_cast<float4 *>(t.m + tj);
+        t.q = reinterpret_cast<unsigned char *>(t.f4 + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
@@ -204,30 +281,37 @@ struct DensF64 {
         T.y[t] = A.y[slot];
         T.z[t] = A.z[slot];
         T.m[t] = A.m[slot];
-        T.fx[t] = A.xf[slot] + nb.offf[q][0];
-        T.fy[t] = A.yf[slot] + nb.offf[q][1];
-        T.fz[t] = A.zf[slot] + nb.offf[q][2];
+        T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
+                              0.0f);
         T.q[t] = (unsigned char)q;
     }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
     {
         Lhs L;
         L.x = A.x[i];
         L.y = A.y[i];
         L.z = A.z[i];
-        L.h = A.h[i];
-        L.hinv = 1.0 / L.h;
+        const double h = A.h[i];
+        L.hb1 = __double_as_longlong(h);
+        L.hb2 = L.hb1 + (1LL << 52);  // bits of 2h (exponent + 1)
+        L.e2 = A.e2[i];
+        L.e3 = A.e3[i];
+        L.o1 = A.o1[i];
+        L.o2 = A.o2[i];
+        L.o3 = A.o3[i];
         L.fx = A.xf[i];
         L.fy = A.yf[i];
         L.fz = A.zf[i];
-        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), __double2float_ru(L.h), margin);
+        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), __double2float_ru(h), margin);
         L.b2 = __fmul_ru(rf, rf);
         return L;
     }
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
-        const float dx = L.fx - T.fx[k], dy = L.fy - T.fy[k], dz = L.fz - T.fz[k];
-        return dx * dx + dy * dy + dz * dz < L.b2;
+        const float4 p = T.f4[k];
+        const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < L.b2;
     }
     static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int, int k, Part &P)
@@ -239,16 +323,22 @@ struct DensF64 {
             dy += nb.shift[q][1];
             dz += nb.shift[q][2];
         }
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double q = sqrt(r2) * L.hinv;
-        const double w1 = fma(q * q, fma(0.75, q, -1.5), 1.0);
-        const double t = 2.0 - q;
-        const double w2 = 0.25 * (t * t * t);
-        const double w = (q < 1.0) ? w1 : ((q < 2.0) ? w2 : 0.0);
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double r = r2 * rsqrt_seeded(r2);
+        const long long rb = __double_as_longlong(r);
+        const bool inner = rb < L.hb1, supp = rb < L.hb2;
+        const double c0 = inner ? 1.0 : (supp ? 2.0 : 0.0);
+        const double c1 = inner ? 0.0 : (supp ? L.o1 : 0.0);
+        const double c2 = inner ? L.e2 : (supp ? L.o2 : 0.0);
+        const double c3 = inner ? L.e3 : (supp ? L.o3 : 0.0);
+        const double w = fma(fma(fma(c3, r, c2), r, c1), r, c0);
         P.rho = fma(T.m[k], w, P.rho);
-        return q < 2.0;
+        return supp;
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P) { a += P.rho; }
+    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
+    {
+        if (lane == 0) a += P.rho;
+    }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
         const double h = A.h[i];
@@ -281,10 +371,10 @@ struct DensF32 {
         float gamma;
     };
     struct Tile {
-        float *x, *y, *z, *m;
+        float4 *p4;  // position seen from the local cell, mass
     };
     struct Lhs {
-        float x, y, z, h, hinv, b2;
+        float x, y, z, hinv, b2;
     };
     struct Part {
         Kahan rho;
@@ -292,56 +382,51 @@ struct DensF32 {
         __device__ __forceinline__ void reduce() { rho.warp_reduce(); }
     };
     using Acc = float2;  // (s, c)
-    static constexpr int kStageBytes = 4 * 4;
+    static constexpr int kStageBytes = 16;
 
-    static __device__ Tile carve(unsigned char *s, int tj)
+    static __device__ Tile carve(unsigned char *s, int)
     {
         Tile t;
-        t.x = reinterpret_cast<float *>(s);
-        t.y = t.x + tj;
-        t.z = t.y + tj;
-        t.m = t.z + tj;
+        t.p4 = reinterpret_cast<float4 *>(s);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
-        T.x[t] = A.x[slot] + nb.offf[q][0];
-        T.y[t] = A.y[slot] + nb.offf[q][1];
-        T.z[t] = A.z[slot] + nb.offf[q][2];
-        T.m[t] = A.m[slot];
+        T.p4[t] = make_float4(A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2],
+                              A.m[slot]);
     }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.p4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
     {
         Lhs L;
         L.x = A.x[i];
         L.y = A.y[i];
         L.z = A.z[i];
-        L.h = A.h[i];
-        L.hinv = __frcp_rn(L.h);
-        L.b2 = 4.0f * L.h * L.h;
+        const float h = A.h[i];
+        L.hinv = __frcp_rn(h);
+        L.b2 = 4.0f * h * h;
         return L;
     }
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
-        const float dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        return dx * dx + dy * dy + dz * dz < L.b2;
+        const float4 p = T.p4[k];
+        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < L.b2;
     }
     static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &,
                                                 bool, int, int k, Part &P)
     {
-        const float dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float q = sqrtf(r2) * L.hinv;
-        const float w1 = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-        const float t = 2.0f - q;
-        const float w2 = 0.25f * (t * t * t);
-        const float w = (q < 1.0f) ? w1 : ((q < 2.0f) ? w2 : 0.0f);
-        P.rho.add(T.m[k] * w);
+        const float4 p = T.p4[k];
+        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float q = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * L.hinv;
+        P.rho.add(p.w * spline_w(q));
         return q < 2.0f;
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P)
+    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
     {
+        if (lane != 0) return;
         Kahan k;
         k.s = a.x;
         k.c = a.y;
@@ -374,64 +459,70 @@ struct DensF32 {
 };
 
 // ---- force, FP64 ----
+// Per particle (k_force_prep_f64): hh = h/2, the gradient coefficients S0 = -3/(pi h^4), K1 = 3/(pi h^5),
+// K2i = 2.25/(pi h^6), K2o = -0.75/(pi h^6) so that grad_i W(r_ij, h) = F r_ij with
+//   F = K2i r - K1                  (r < h)
+//   F = S0 / r + K2o r + K1         (h <= r < 2h),   0 beyond,
+// A = P / rho^2 and ach = alpha c / 2.  Per pair the piece of each side is chosen by integer compares of
+// bits(r) - 2^52 (= bits(r/2)) and bits(r) - 2^53 (= bits(r/4)) against bits(hh); F then costs two FMAs.
 struct ForceF64 {
     struct Args {
         PairCommon cm;
-        const double *x, *y, *z, *vx, *vy, *vz, *m, *h, *rho, *cs;
-        const double *hinv, *k5, *A;      // derived per particle (k_force_prep)
-        const float *xf, *yf, *zf, *hf;  // filter copies
+        const double *x, *y, *z, *vx, *vy, *vz, *m, *rho;
+        const double *hh, *S0, *K1, *K2i, *K2o, *A, *ach;  // per particle (k_force_prep_f64)
+        const float *xf, *yf, *zf, *hf;                    // filter copies
         double *ax, *ay, *az, *dudt;
-        double alpha, beta, eps;
+        double beta, eps;
     };
     struct Tile {
-        double *x, *y, *z, *vx, *vy, *vz, *m, *h, *hinv, *k5, *A, *c, *rho;
-        float *fx, *fy, *fz, *fh;
+        double *x, *y, *z, *vx, *vy, *vz, *m, *hh, *S0, *K1, *K2i, *K2o, *A, *ach, *rho;
+        float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
         int *slot;
         unsigned char *q;
     };
     struct Lhs {
-        double x, y, z, vx, vy, vz, h, hinv, k5, A, c, rho;
+        double x, y, z, vx, vy, vz, hh, S0, K1, K2i, K2o, A, ach, rho;
+        long long hb;  // bit pattern of hh
         float fx, fy, fz, fh, margin;
     };
     struct Part {
         double ax, ay, az, du;
         __device__ __forceinline__ void zero() { ax = ay = az = du = 0.0; }
+        // Reduce-scatter over the warp: afterwards lane 0 holds sum ax, lane 8 sum ay, lane 16 sum az and lane 24
+        // sum du (6 additions per lane instead of 20 for four butterflies).
         __device__ __forceinline__ void reduce()
         {
-            ax = warp_sum(ax);
-            ay = warp_sum(ay);
-            az = warp_sum(az);
-            du = warp_sum(du);
+            const int lane = threadIdx.x & 31;
+            const bool up16 = (lane & 16) != 0;
+            double s0 = up16 ? az : ax, s1 = up16 ? du : ay;
+            const double o0 = up16 ? ax : az, o1 = up16 ? ay : du;
+            s0 += __shfl_xor_sync(kFull, o0, 16);
+            s1 += __shfl_xor_sync(kFull, o1, 16);
+            const bool up8 = (lane & 8) != 0;
+            double t = up8 ? s1 : s0;
+            const double o = up8 ? s0 : s1;
+            t += __shfl_xor_sync(kFull, o, 8);
+            t += __shfl_xor_sync(kFull, t, 4);
+            t += __shfl_xor_sync(kFull, t, 2);
+            t += __shfl_xor_sync(kFull, t, 1);
+            ax = t;  // the sum this lane's group of 8 holds (see accumulate)
         }
     };
     struct Acc {
         double ax, ay, az, du;
     };
-    static constexpr int kStageBytes = 13 * 8 + 4 * 4 + 4 + 1;
+    static constexpr int kStageBytes = 15 * 8 + 16 + 4 + 1;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
         Tile t;
         double *d = reinterpret_cast<double *>(s);
-        t.x = d;
-        t.y = d + tj;
-        t.z = d + 2 * tj;
-        t.vx = d + 3 * tj;
-        t.vy = d + 4 * tj;
-        t.vz = d + 5 * tj;
-        t.m = d + 6 * tj;
-        t.h = d + 7 * tj;
-        t.hinv = d + 8 * tj;
-        t.k5 = d + 9 * tj;
-        t.A = d + 10 * tj;
-        t.c = d + 11 * tj;
-        t.rho = d + 12 * tj;
-        float *f = reinterpret_cast<float *>(d + 13 * tj);
-        t.fx = f;
-        t.fy = f + tj;
-        t.fz = f + 2 * tj;
-        t.fh = f + 3 * tj;
-        t.slot = reinterpret_cast<int *>(f + 4 * tj);
+        double **dst[15] = {&t.x, &t.y, &t.z, &t.vx, &t.vy, &t.vz, &t.m, &t.hh, &t.S0, &t.K1, &t.K2i, &t.K2o,
+                            &t.A, &t.ach, &t.rho};
+#pragma unroll
+        for (int a = 0; a < 15; ++a) *dst[a] = d + a * tj;
+        t.f4 = reinterpret_cast<float4 *>(d + 15 * tj);
+        t.slot = reinterpret_cast<int *>(t.f4 + tj);
         t.q = reinterpret_cast<unsigned char *>(t.slot + tj);
         return t;
     }
@@ -445,19 +536,20 @@ struct ForceF64 {
         T.vy[t] = A.vy[slot];
         T.vz[t] = A.vz[slot];
         T.m[t] = A.m[slot];
-        T.h[t] = A.h[slot];
-        T.hinv[t] = A.hinv[slot];
-        T.k5[t] = A.k5[slot];
+        T.hh[t] = A.hh[slot];
+        T.S0[t] = A.S0[slot];
+        T.K1[t] = A.K1[slot];
+        T.K2i[t] = A.K2i[slot];
+        T.K2o[t] = A.K2o[slot];
         T.A[t] = A.A[slot];
-        T.c[t] = A.cs[slot];
+        T.ach[t] = A.ach[slot];
         T.rho[t] = A.rho[slot];
-        T.fx[t] = A.xf[slot] + nb.offf[q][0];
-        T.fy[t] = A.yf[slot] + nb.offf[q][1];
-        T.fz[t] = A.zf[slot] + nb.offf[q][2];
-        T.fh[t] = A.hf[slot];
+        T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
+                              A.hf[slot]);
         T.slot[t] = slot;
         T.q[t] = (unsigned char)q;
     }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
     {
         Lhs L;
@@ -467,12 +559,15 @@ struct ForceF64 {
         L.vx = A.vx[i];
         L.vy = A.vy[i];
         L.vz = A.vz[i];
-        L.h = A.h[i];
-        L.hinv = A.hinv[i];
-        L.k5 = A.k5[i];
+        L.hh = A.hh[i];
+        L.S0 = A.S0[i];
+        L.K1 = A.K1[i];
+        L.K2i = A.K2i[i];
+        L.K2o = A.K2o[i];
         L.A = A.A[i];
-        L.c = A.cs[i];
+        L.ach = A.ach[i];
         L.rho = A.rho[i];
+        L.hb = __double_as_longlong(L.hh);
         L.fx = A.xf[i];
         L.fy = A.yf[i];
         L.fz = A.zf[i];
@@ -482,9 +577,10 @@ struct ForceF64 {
     }
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
-        const float dx = L.fx - T.fx[k], dy = L.fy - T.fy[k], dz = L.fz - T.fz[k];
-        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), fmaxf(L.fh, T.fh[k]), L.margin);
-        return dx * dx + dy * dy + dz * dz < __fmul_ru(rf, rf);
+        const float4 p = T.f4[k];
+        const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
+        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), fmaxf(L.fh, p.w), L.margin);
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < __fmul_ru(rf, rf);
     }
     static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int i, int k, Part &P)
@@ -496,36 +592,38 @@ struct ForceF64 {
             dy += nb.shift[q][1];
             dz += nb.shift[q][2];
         }
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double hj = T.h[k];
-        const double hm = fmax(L.h, hj);
-        const bool in = (r2 < 4.0 * hm * hm) && (T.slot[k] != i) && (r2 > 0.0);
-        const double rinv = rsqrt(in ? r2 : 1.0);
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double rinv = rsqrt_seeded(r2);
         const double r = r2 * rinv;
-        const double qi = r * L.hinv, qj = r * T.hinv[k];
-        const double ti = 2.0 - qi, tj = 2.0 - qj;
-        // g(q) = f'(q)/q; on the outer piece 1/q = h/r
-        const double gi = (qi < 1.0) ? fma(2.25, qi, -3.0) : ((qi < 2.0) ? (-0.75 * ti * ti) * (L.h * rinv) : 0.0);
-        const double gj = (qj < 1.0) ? fma(2.25, qj, -3.0) : ((qj < 2.0) ? (-0.75 * tj * tj) * (hj * rinv) : 0.0);
-        const double Fi = L.k5 * gi, Fj = T.k5[k] * gj;  // grad_i W(r_ij, h) = F r_ij
+        const long long rb = __double_as_longlong(r);
+        const long long rh = rb - (1LL << 52), rq = rb - (2LL << 52);  // bits of r/2 and r/4
+        const long long hbj = __double_as_longlong(T.hh[k]);
+        const bool ii = rh < L.hb, io = rq < L.hb;  // r < h_i, r < 2 h_i
+        const bool ji = rh < hbj, jo = rq < hbj;    // r < h_j, r < 2 h_j
+        const double Fi = fma(ii ? 0.0 : (io ? L.S0 : 0.0), rinv,
+                              fma(ii ? L.K2i : (io ? L.K2o : 0.0), r, ii ? -L.K1 : (io ? L.K1 : 0.0)));
+        const double K1j = T.K1[k];
+        const double Fj = fma(ji ? 0.0 : (jo ? T.S0[k] : 0.0), rinv,
+                              fma(ji ? T.K2i[k] : (jo ? T.K2o[k] : 0.0), r, ji ? -K1j : (jo ? K1j : 0.0)));
         const double dvx = L.vx - T.vx[k], dvy = L.vy - T.vy[k], dvz = L.vz - T.vz[k];
-        const double vdotr = dvx * dx + dvy * dy + dvz * dz;
-        double visc = 0.0;
-        if (in && vdotr < 0.0) {
-            const double hb = 0.5 * (L.h + hj);
-            const double D1 = fma(A.eps * hb, hb, r2);   // r^2 + eps hbar^2
-            const double D2 = 0.5 * (L.rho + T.rho[k]);  // rhobar
-            const double rr = 1.0 / (D1 * D2);
-            const double mu = hb * vdotr * (D2 * rr);
-            const double cb = 0.5 * (L.c + T.c[k]);
-            visc = mu * fma(A.beta, mu, -A.alpha * cb) * (D1 * rr);
-        }
-        const double Fb = 0.5 * (Fi + Fj);
-        const double mj = T.m[k];
+        const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
+        // Monaghan viscosity, Ph = Pi / 2 = mu (beta mu - alpha cbar) / (rho_i + rho_j) with
+        // mu = hbar v.r / (r^2 + eps hbar^2): one reciprocal R = 1 / (D1 D2) serves both quotients.
+        const double hb = L.hh + T.hh[k];
+        const double D1 = fma(A.eps * hb, hb, r2);
+        const double D2 = L.rho + T.rho[k];
+        const double R = rcp_seeded(D1 * D2);
+        const double mu = (hb * vdotr) * (D2 * R);
+        const double t = fma(A.beta, mu, -(L.ach + T.ach[k]));
+        double Ph = (mu * t) * (D1 * R);
+        if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
+        const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
         const double aF = L.A * Fi;
-        double coef = mj * (aF + T.A[k] * Fj + visc * Fb);
-        double dcoef = mj * (aF + 0.5 * visc * Fb) * vdotr;
-        if (!in) {
+        const double mj = T.m[k];
+        double coef = mj * fma(T.A[k], Fj, aF + V);
+        double dcoef = (mj * vdotr) * fma(0.5, V, aF);
+        const bool self = T.slot[k] == i;
+        if (self) {
             coef = 0.0;
             dcoef = 0.0;
         }
@@ -533,14 +631,15 @@ struct ForceF64 {
         P.ay = fma(-coef, dy, P.ay);
         P.az = fma(-coef, dz, P.az);
         P.du += dcoef;
-        return in;
+        return !self && (io || jo);
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P)
+    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
     {
-        a.ax += P.ax;
-        a.ay += P.ay;
-        a.az += P.az;
-        a.du += P.du;
+        // after the reduce-scatter: lane 0 -> ax, 8 -> ay, 16 -> az, 24 -> du
+        if (lane == 0) a.ax += P.ax;
+        if (lane == 8) a.ay += P.ax;
+        if (lane == 16) a.az += P.ax;
+        if (lane == 24) a.du += P.ax;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
@@ -569,7 +668,8 @@ struct ForceF32 {
         float alpha, beta, eps;
     };
     struct Tile {
-        float *x, *y, *z, *vx, *vy, *vz, *m, *h, *hinv, *k5, *A, *c, *rho;
+        float4 *p4;  // position seen from the local cell, h
+        float *vx, *vy, *vz, *m, *hinv, *k5, *A, *c, *rho;
         int *slot;
     };
     struct Lhs {
@@ -595,39 +695,28 @@ struct ForceF32 {
     struct Acc {
         float2 ax, ay, az, du;
     };
-    static constexpr int kStageBytes = 13 * 4 + 4;
+    static constexpr int kStageBytes = 16 + 9 * 4 + 4;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
         Tile t;
-        float *f = reinterpret_cast<float *>(s);
-        t.x = f;
-        t.y = f + tj;
-        t.z = f + 2 * tj;
-        t.vx = f + 3 * tj;
-        t.vy = f + 4 * tj;
-        t.vz = f + 5 * tj;
-        t.m = f + 6 * tj;
-        t.h = f + 7 * tj;
-        t.hinv = f + 8 * tj;
-        t.k5 = f + 9 * tj;
-        t.A = f + 10 * tj;
-        t.c = f + 11 * tj;
-        t.rho = f + 12 * tj;
-        t.slot = reinterpret_cast<int *>(f + 13 * tj);
+        t.p4 = reinterpret_cast<float4 *>(s);
+        float *f = reinterpret_cast<float *>(t.p4 + tj);
+        float **dst[9] = {&t.vx, &t.vy, &t.vz, &t.m, &t.hinv, &t.k5, &t.A, &t.c, &t.rho};
+#pragma unroll
+        for (int a = 0; a < 9; ++a) *dst[a] = f + a * tj;
+        t.slot = reinterpret_cast<int *>(f + 9 * tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
-        T.x[t] = A.x[slot] + nb.offf[q][0];
-        T.y[t] = A.y[slot] + nb.offf[q][1];
-        T.z[t] = A.z[slot] + nb.offf[q][2];
+        T.p4[t] = make_float4(A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2],
+                              A.h[slot]);
         T.vx[t] = A.vx[slot];
         T.vy[t] = A.vy[slot];
         T.vz[t] = A.vz[slot];
         T.m[t] = A.m[slot];
-        T.h[t] = A.h[slot];
         T.hinv[t] = A.hinv[slot];
         T.k5[t] = A.k5[slot];
         T.A[t] = A.A[slot];
@@ -635,6 +724,7 @@ struct ForceF32 {
         T.rho[t] = A.rho[slot];
         T.slot[t] = slot;
     }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.p4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
     {
         Lhs L;
@@ -654,43 +744,41 @@ struct ForceF32 {
     }
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
-        const float dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        const float hm = fmaxf(L.h, T.h[k]);
-        return dx * dx + dy * dy + dz * dz < 4.0f * hm * hm;
+        const float4 p = T.p4[k];
+        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
+        const float hm = fmaxf(L.h, p.w);
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0f * hm * hm;
     }
     static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &,
                                                 bool, int i, int k, Part &P)
     {
-        const float dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float hj = T.h[k];
-        const float hm = fmaxf(L.h, hj);
-        const bool in = (r2 < 4.0f * hm * hm) && (T.slot[k] != i) && (r2 > 0.0f);
-        const float rinv = rsqrtf(in ? r2 : 1.0f);
+        const float4 p = T.p4[k];
+        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float hj = p.w;
+        const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
         const float r = r2 * rinv;
         const float qi = r * L.hinv, qj = r * T.hinv[k];
-        const float ti = 2.0f - qi, tj = 2.0f - qj;
-        const float gi = (qi < 1.0f) ? fmaf(2.25f, qi, -3.0f) : ((qi < 2.0f) ? (-0.75f * ti * ti) * (L.h * rinv) : 0.0f);
-        const float gj = (qj < 1.0f) ? fmaf(2.25f, qj, -3.0f) : ((qj < 2.0f) ? (-0.75f * tj * tj) * (hj * rinv) : 0.0f);
-        const float Fi = L.k5 * gi, Fj = T.k5[k] * gj;
+        const float Fi = L.k5 * spline_g(qi, L.h * rinv);
+        const float Fj = T.k5[k] * spline_g(qj, hj * rinv);
         const float dvx = L.vx - T.vx[k], dvy = L.vy - T.vy[k], dvz = L.vz - T.vz[k];
-        const float vdotr = dvx * dx + dvy * dy + dvz * dz;
-        float visc = 0.0f;
-        if (in && vdotr < 0.0f) {
-            const float hb = 0.5f * (L.h + hj);
-            const float D1 = fmaf(A.eps * hb, hb, r2);
-            const float D2 = 0.5f * (L.rho + T.rho[k]);
-            const float rr = __frcp_rn(D1 * D2);
-            const float mu = hb * vdotr * (D2 * rr);
-            const float cb = 0.5f * (L.c + T.c[k]);
-            visc = mu * fmaf(A.beta, mu, -A.alpha * cb) * (D1 * rr);
-        }
-        const float Fb = 0.5f * (Fi + Fj);
-        const float mj = T.m[k];
+        const float vdotr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
+        const float hb = 0.5f * (L.h + hj);
+        const float D1 = fmaf(A.eps * hb, hb, r2);
+        const float D2 = L.rho + T.rho[k];
+        const float R = __frcp_rn(D1 * D2);
+        const float mu = (hb * vdotr) * (D2 * R);
+        const float cb = 0.5f * (L.c + T.c[k]);
+        float Ph = (mu * fmaf(A.beta, mu, -A.alpha * cb)) * (D1 * R);
+        if (!(vdotr < 0.0f)) Ph = 0.0f;
+        const float Fs = Fi + Fj;
         const float aF = L.A * Fi;
-        float coef = mj * (aF + T.A[k] * Fj + visc * Fb);
-        float dcoef = mj * (aF + 0.5f * visc * Fb) * vdotr;
-        if (!in) {
+        const float mj = T.m[k];
+        const bool self = T.slot[k] == i;
+        const bool in = !self && (qi < 2.0f || qj < 2.0f);
+        float coef = mj * fmaf(Ph, Fs, fmaf(T.A[k], Fj, aF));
+        float dcoef = (mj * vdotr) * fmaf(0.5f * Ph, Fs, aF);
+        if (self) {
             coef = 0.0f;
             dcoef = 0.0f;
         }
@@ -709,8 +797,9 @@ struct ForceF32 {
         a.x = k.s;
         a.y = k.c;
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P)
+    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
     {
+        if (lane != 0) return;
         merge2(a.ax, P.ax);
         merge2(a.ay, P.ay);
         merge2(a.az, P.az);
@@ -757,7 +846,7 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ NbrTable nb;
     __shared__ typename K::Acc acc[kMaxLocal];
-    __shared__ int queue[kPairWarps][64];
+    __shared__ int ring[kPairWarps][kRing];
     __shared__ unsigned long long sh_pairs;
 
     const int c = blockIdx.x;
@@ -767,6 +856,7 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
     const unsigned lt_mask = (1u << lane) - 1u;
     const int tj = A.cm.tj;
     const typename K::Tile T = K::carve(smem, tj);
+    int *q = ring[warp];
     if (tid == 0) sh_pairs = 0ull;
     build_nbr_table(nb, c, A.cm.g, A.cm.cell_start);
     const int NJ = nb.pref[27];
@@ -780,12 +870,16 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
         for (int t = tid; t < nloc; t += kPairThreads) zero_acc<K>(acc[t]);
         for (int tb = 0; tb < NJ; tb += tj) {
             const int tn = min(tj, NJ - tb);
+            const int tnp = (tn + kStep - 1) / kStep * kStep;  // padded to whole filter steps (<= tj)
             __syncthreads();  // accumulators zeroed, previous tile consumed
-            for (int t = tid; t < tn; t += kPairThreads) {
-                const int jj = tb + t;
-                const int q = find_nbr(nb, jj);
-                const int slot = nb.start[q] + (jj - nb.pref[q]);
-                K::stage(A, T, nb, t, slot, q);
+            for (int t = tid; t < tnp; t += kPairThreads) {
+                if (t < tn) {
+                    const int jj = tb + t;
+                    const int nq = find_nbr(nb, jj);
+                    K::stage(A, T, nb, t, nb.start[nq] + (jj - nb.pref[nq]), nq);
+                } else {
+                    K::sentinel(T, t);
+                }
             }
             __syncthreads();
             for (int li = warp; li < nloc; li += kPairWarps) {
@@ -793,33 +887,36 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
                 const typename K::Lhs L = K::load(A, i, margin);
                 typename K::Part P;
                 P.zero();
-                int nq = 0;
-                for (int jb = 0; jb < tn; jb += 32) {
-                    const int k = jb + lane;
-                    const bool p = (k < tn) && K::filter(L, T, k);
-                    const unsigned bal = __ballot_sync(kFull, p);
-                    if (p) queue[warp][nq + __popc(bal & lt_mask)] = k;
-                    nq += __popc(bal);
-                    __syncwarp();
-                    if (nq >= 32) {
-                        const bool in = K::eval(A, L, T, nb, wrap, i, queue[warp][lane], P);
+                int head = 0, tail = 0;  // warp-uniform ring cursors; tail - head <= 31 + kStep
+                for (int jb = 0; jb < tnp; jb += kStep) {
+                    const int k0 = jb + lane, k1 = k0 + 32;
+                    const bool p0 = K::filter(L, T, k0);
+                    const bool p1 = K::filter(L, T, k1);
+                    const unsigned b0 = __ballot_sync(kFull, p0);
+                    const unsigned b1 = __ballot_sync(kFull, p1);
+                    const int c0 = __popc(b0);
+                    if (p0) q[(tail + __popc(b0 & lt_mask)) & (kRing - 1)] = k0;
+                    if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & (kRing - 1)] = k1;
+                    tail += c0 + __popc(b1);
+                    while (tail - head >= 32) {
+                        __syncwarp();
+                        const bool in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
                         const unsigned bin = __ballot_sync(kFull, in);  // every lane votes
                         if (lane == 0) my_pairs += __popc(bin);
-                        __syncwarp();
-                        if (lane < nq - 32) queue[warp][lane] = queue[warp][lane + 32];
-                        nq -= 32;
-                        __syncwarp();
+                        head += 32;
                     }
                 }
-                if (nq > 0) {
+                const int rem = tail - head;
+                if (rem > 0) {
+                    __syncwarp();
                     bool in = false;
-                    if (lane < nq) in = K::eval(A, L, T, nb, wrap, i, queue[warp][lane], P);
+                    if (lane < rem) in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
                     const unsigned b = __ballot_sync(kFull, in);
                     if (lane == 0) my_pairs += __popc(b);
                 }
-                __syncwarp();
+                __syncwarp();  // the ring is reused by the next local particle
                 P.reduce();
-                if (lane == 0) K::accumulate(acc[li], P);
+                K::accumulate(acc[li], P, lane);
             }
         }
         __syncthreads();
@@ -830,7 +927,7 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
     if (tid == 0) K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, sh_pairs);
 }
 
-// FP32 cell-relative copies of FP64 positions (filter input of the FP64 path), plus (float) h.
+// FP32 cell-relative copies of FP64 positions and (float) h rounded up: the filter inputs of the FP64 force loop.
 __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                         const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, Grid g,
                         float *__restrict__ xf, float *__restrict__ yf, float *__restrict__ zf,
@@ -843,22 +940,68 @@ __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__
     xf[s] = __double2float_rn(x[s] - (double)kx * g.edge[0]);
     yf[s] = __double2float_rn(y[s] - (double)ky * g.edge[1]);
     zf[s] = __double2float_rn(z[s] - (double)kz * g.edge[2]);
-    if (hf) hf[s] = __double2float_ru(h[s]);
+    hf[s] = __double2float_ru(h[s]);
 }
 
-// Per-particle quantities of the force loop: 1/h, 1/(pi h^5), P/rho^2.
-template <typename T>
-__global__ void k_force_prep(const T *__restrict__ h, const T *__restrict__ P, const T *__restrict__ rho, int n,
-                             T *__restrict__ hinv, T *__restrict__ k5, T *__restrict__ A)
+// Per-particle set-up of the FP64 density loop: cell-relative float positions (filter) and f(r/h) of the cubic
+// spline as a cubic in r: inner piece 1 - 3/2 (r/h)^2 + 3/4 (r/h)^3, outer 2 - 3 (r/h) + 3/2 (r/h)^2 - 1/4 (r/h)^3.
+__global__ void k_density_prep_f64(const double *__restrict__ x, const double *__restrict__ y,
+                                   const double *__restrict__ z, const double *__restrict__ h,
+                                   const int *__restrict__ cell_of_slot, int n, Grid g, float *__restrict__ xf,
+                                   float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2,
+                                   double *__restrict__ e3, double *__restrict__ o1, double *__restrict__ o2,
+                                   double *__restrict__ o3)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const T hi = T(1) / h[s];
-    const T h2 = hi * hi;
+    const int c = cell_of_slot[s];
+    const int kx = c % g.n[0], ky = (c / g.n[0]) % g.n[1], kz = c / (g.n[0] * g.n[1]);
+    xf[s] = __double2float_rn(x[s] - (double)kx * g.edge[0]);
+    yf[s] = __double2float_rn(y[s] - (double)ky * g.edge[1]);
+    zf[s] = __double2float_rn(z[s] - (double)kz * g.edge[2]);
+    const double hi = 1.0 / h[s], h2 = hi * hi, h3 = h2 * hi;
+    e2[s] = -1.5 * h2;
+    e3[s] = 0.75 * h3;
+    o1[s] = -3.0 * hi;
+    o2[s] = 1.5 * h2;
+    o3[s] = -0.25 * h3;
+}
+
+// Per-particle quantities of the FP32 force loop: 1/h, 1/(pi h^5), P/rho^2.
+__global__ void k_force_prep_f32(const float *__restrict__ h, const float *__restrict__ P,
+                                 const float *__restrict__ rho, int n, float *__restrict__ hinv,
+                                 float *__restrict__ k5, float *__restrict__ A)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float hi = 1.0f / h[s];
+    const float h2 = hi * hi;
     hinv[s] = hi;
-    k5[s] = T(kInvPi) * h2 * h2 * hi;
-    const T r = rho[s];
+    k5[s] = (float)kInvPi * h2 * h2 * hi;
+    const float r = rho[s];
     A[s] = P[s] / (r * r);
+}
+
+// Per-particle quantities of the FP64 force loop (see ForceF64).
+__global__ void k_force_prep_f64(const double *__restrict__ h, const double *__restrict__ P,
+                                 const double *__restrict__ rho, const double *__restrict__ cs, double alpha, int n,
+                                 double *__restrict__ hh, double *__restrict__ S0, double *__restrict__ K1,
+                                 double *__restrict__ K2i, double *__restrict__ K2o, double *__restrict__ A,
+                                 double *__restrict__ ach)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double hv = h[s];
+    const double hi = 1.0 / hv, h2 = hi * hi;
+    const double s4 = kInvPi * h2 * h2;  // 1/(pi h^4)
+    hh[s] = 0.5 * hv;
+    S0[s] = -3.0 * s4;
+    K1[s] = 3.0 * s4 * hi;
+    K2i[s] = 2.25 * s4 * h2;
+    K2o[s] = -0.75 * s4 * h2;
+    const double r = rho[s];
+    A[s] = P[s] / (r * r);
+    ach[s] = 0.5 * alpha * cs[s];
 }
 
 template <class K>
@@ -875,21 +1018,28 @@ cudaError_t run_cells(const typename K::Args &A, int ncells, cudaStream_t st)
     return cudaGetLastError();
 }
 
+int tile_or_default(int tj, int dflt)
+{
+    const int t = tj > 0 ? tj : dflt;
+    return (t + kStep - 1) / kStep * kStep;
+}
+
 }  // namespace
 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
                                 const Grid &g, cudaStream_t st, int *nl)
 {
     if (n <= 0 || f32) return cudaSuccess;  // FP32 views are already cell-relative floats
-    k_pos32<<<(n + 255) / 256, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
-                                             (const double *)soa.p[SPH_X][2], nullptr, cell_of_slot, n, g, scr.xf,
-                                             scr.yf, scr.zf, nullptr);
+    k_density_prep_f64<<<(n + 255) / 256, 256, 0, st>>>(
+        (const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1], (const double *)soa.p[SPH_X][2],
+        (const double *)soa.p[SPH_H][0], cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, (double *)scr.d[0],
+        (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3], (double *)scr.d[4]);
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const Grid &g, cudaStream_t st, int *nl)
+                              const Grid &g, double alpha, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     const int nb = (n + 255) / 256;
@@ -897,14 +1047,16 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
         k_pos32<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
                                     (const double *)soa.p[SPH_X][2], (const double *)soa.p[SPH_H][0], cell_of_slot,
                                     n, g, scr.xf, scr.yf, scr.zf, scr.hf);
-        k_force_prep<double><<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
-                                                 (const double *)soa.p[SPH_RHO][0], n, (double *)scr.hinv,
-                                                 (double *)scr.k5, (double *)scr.A);
+        k_force_prep_f64<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
+                                             (const double *)soa.p[SPH_RHO][0], (const double *)soa.p[SPH_CS][0],
+                                             alpha, n, (double *)scr.d[0], (double *)scr.d[1], (double *)scr.d[2],
+                                             (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
+                                             (double *)scr.d[6]);
         *nl += 2;
     } else {
-        k_force_prep<float><<<nb, 256, 0, st>>>((const float *)soa.p[SPH_H][0], (const float *)soa.p[SPH_P][0],
-                                                (const float *)soa.p[SPH_RHO][0], n, (float *)scr.hinv,
-                                                (float *)scr.k5, (float *)scr.A);
+        k_force_prep_f32<<<nb, 256, 0, st>>>((const float *)soa.p[SPH_H][0], (const float *)soa.p[SPH_P][0],
+                                             (const float *)soa.p[SPH_RHO][0], n, (float *)scr.d[0],
+                                             (float *)scr.d[1], (float *)scr.d[2]);
         *nl += 1;
     }
     return cudaGetLastError();
@@ -919,7 +1071,7 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
     PairCommon cm{cell_start, g, status, counters, 0};
     if (!f32) {
         DensF64::Args A;
-        cm.tj = tj > 0 ? tj : 512;
+        cm.tj = tile_or_default(tj, 512);
         A.cm = cm;
         A.x = (const double *)soa.p[SPH_X][0];
         A.y = (const double *)soa.p[SPH_X][1];
@@ -930,6 +1082,11 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
         A.xf = scr.xf;
         A.yf = scr.yf;
         A.zf = scr.zf;
+        A.e2 = (const double *)scr.d[0];
+        A.e3 = (const double *)scr.d[1];
+        A.o1 = (const double *)scr.d[2];
+        A.o2 = (const double *)scr.d[3];
+        A.o3 = (const double *)scr.d[4];
         A.rho = (double *)soa.p[SPH_RHO][0];
         A.P = (double *)soa.p[SPH_P][0];
         A.cs = (double *)soa.p[SPH_CS][0];
@@ -937,7 +1094,7 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
         return run_cells<DensF64>(A, ncells, st);
     }
     DensF32::Args A;
-    cm.tj = tj > 0 ? tj : 1024;
+    cm.tj = tile_or_default(tj, 1024);
     A.cm = cm;
     A.x = (const float *)soa.p[SPH_X][0];
     A.y = (const float *)soa.p[SPH_X][1];
@@ -961,7 +1118,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     PairCommon cm{cell_start, g, status, counters, 0};
     if (!f32) {
         ForceF64::Args A;
-        cm.tj = tj > 0 ? tj : 512;
+        cm.tj = tile_or_default(tj, 384);
         A.cm = cm;
         A.x = (const double *)soa.p[SPH_X][0];
         A.y = (const double *)soa.p[SPH_X][1];
@@ -970,12 +1127,14 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
         A.vy = (const double *)soa.p[SPH_V][1];
         A.vz = (const double *)soa.p[SPH_V][2];
         A.m = (const double *)soa.p[SPH_MASS][0];
-        A.h = (const double *)soa.p[SPH_H][0];
         A.rho = (const double *)soa.p[SPH_RHO][0];
-        A.cs = (const double *)soa.p[SPH_CS][0];
-        A.hinv = (const double *)scr.hinv;
-        A.k5 = (const double *)scr.k5;
-        A.A = (const double *)scr.A;
+        A.hh = (const double *)scr.d[0];
+        A.S0 = (const double *)scr.d[1];
+        A.K1 = (const double *)scr.d[2];
+        A.K2i = (const double *)scr.d[3];
+        A.K2o = (const double *)scr.d[4];
+        A.A = (const double *)scr.d[5];
+        A.ach = (const double *)scr.d[6];
         A.xf = scr.xf;
         A.yf = scr.yf;
         A.zf = scr.zf;
@@ -984,13 +1143,12 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
         A.ay = (double *)soa.p[SPH_A][1];
         A.az = (double *)soa.p[SPH_A][2];
         A.dudt = (double *)soa.p[SPH_DUDT][0];
-        A.alpha = prm.alpha;
         A.beta = prm.beta;
         A.eps = prm.eps;
         return run_cells<ForceF64>(A, ncells, st);
     }
     ForceF32::Args A;
-    cm.tj = tj > 0 ? tj : 512;
+    cm.tj = tile_or_default(tj, 512);
     A.cm = cm;
     A.x = (const float *)soa.p[SPH_X][0];
     A.y = (const float *)soa.p[SPH_X][1];
@@ -1002,9 +1160,9 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     A.h = (const float *)soa.p[SPH_H][0];
     A.rho = (const float *)soa.p[SPH_RHO][0];
     A.cs = (const float *)soa.p[SPH_CS][0];
-    A.hinv = (const float *)scr.hinv;
-    A.k5 = (const float *)scr.k5;
-    A.A = (const float *)scr.A;
+    A.hinv = (const float *)scr.d[0];
+    A.k5 = (const float *)scr.d[1];
+    A.A = (const float *)scr.d[2];
     A.ax = (float *)soa.p[SPH_A][0];
     A.ay = (float *)soa.p[SPH_A][1];
     A.az = (float *)soa.p[SPH_A][2];

@@ -187,9 +187,8 @@ void carve(sph_view_s *v, Bump &b)
         v->scr.zf = (float *)b.take(nm * 4);
         v->scr.hf = (float *)b.take(nm * 4);
     }
-    v->scr.hinv = b.take(nm * v->esz);
-    v->scr.k5 = b.take(nm * v->esz);
-    v->scr.A = b.take(nm * v->esz);
+    const int nd = v->prec == SPH_F64 ? sphk::kDerivedF64 : sphk::kDerivedF32;
+    for (int k = 0; k < nd; ++k) v->scr.d[k] = b.take(nm * v->esz);
     const size_t nc = (size_t)v->ncells;
     v->cell_of = (int *)b.take(nm * 4);
     v->count = (int *)b.take(nc * 4);
@@ -350,7 +349,7 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_FORCE_PREP);
-        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, v->st, &ph.nl);
+        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, p->alpha, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {

@@ -89,6 +89,7 @@ _SIGS = {
     "sph_pair_counts": [_VP, ctypes.POINTER(ctypes.c_uint64), _I32],
     "sph_view_timing": [_VP, _I32],
     "sph_view_phase_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
+    "sph_probe_fma_rate": [_I32, ctypes.POINTER(ctypes.c_double)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
 EXPORTED = tuple(_SIGS) + ("sph_strerror",)
@@ -283,3 +284,10 @@ def sph_bin_static(layout, domain, aos_dev, n, perm_dev, cell_start_dev, cell_of
     _check("sph_bin_static", lib().sph_bin_static(ctypes.byref(L), ctypes.byref(D), _addr(aos_dev), int(n),
                                                   _addr(perm_dev), _addr(cell_start_dev), _addr(cell_of_slot_dev),
                                                   _addr(status_dev), st))
+
+
+def sph_probe_fma_rate(prec):
+    """Measured FMA throughput of the current device in flops/s (FP64 for SPH_F64, FP32 for SPH_F32)."""
+    out = ctypes.c_double()
+    _check("sph_probe_fma_rate", lib().sph_probe_fma_rate(int(prec), ctypes.byref(out)))
+    return out.value
