@@ -120,6 +120,29 @@ typedef struct sph_view_s *sph_view;
 SPH_API sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_max, const sph_domain *domain,
                            void *cuda_stream, sph_view *out);
 
+/* Batched form: a view over many independent patches (the paper's per-cell kernels batched into one launch,
+ * Section 7.5).  Each patch is an open box [0, patch_box) holding its own particles; particles of different
+ * patches never interact.  The records of patch p are records patch_start[p] .. patch_start[p+1]-1 of the AoS,
+ * positions patch-local.  Every sph_patches_bin gives each patch its own cell grid with edge >= 2 h_max of that
+ * patch (Section 2.1's cells at least as wide as the interaction radius), at most ncell_cap cells per axis, and
+ * builds a largest-first work list of the non-empty cells for the persistent pair kernels.  Up to npatch_max
+ * patches and n_max particles.  The other calls (sph_aos_to_soa, sph_density, sph_force, sph_soa_to_aos,
+ * sph_reduce ...) work on a patch view as on any view; sph_bin and sph_step are rejected (use sph_patches_bin /
+ * sph_patches_step).  Errors: SPH_E_INVAL (bad layout, box, npatch_max < 1, ncell_cap outside 1..64, more than
+ * 2^27 cells of capacity), SPH_E_NOMEM, SPH_E_CUDA. */
+SPH_API sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n_max, int32_t npatch_max,
+                                      const double patch_box[3], int32_t ncell_cap, void *cuda_stream, sph_view *out);
+
+/* Bin the records [0, n) of a patch view; patch_start_dev: npatch + 1 ascending int64 record offsets in device
+ * memory (patch_start[0] = 0, patch_start[npatch] = n), read on the device.  Needs x and h in the layout. */
+SPH_API sph_status sph_patches_bin(sph_view view, const void *aos_dev, int64_t n, const int64_t *patch_start_dev,
+                                   int32_t npatch);
+
+/* One density + force pass over all patches, as sph_step with dt = 0: bin, gather, density, scatter, gather,
+ * force, scatter.  stats_out as in sph_step. */
+SPH_API sph_status sph_patches_step(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
+                                    int32_t npatch, const sph_params *params, double *stats_out);
+
 /* Wait for the view's stream, free everything the view allocated.  NULL is accepted. */
 SPH_API sph_status sph_view_destroy(sph_view view);
 

@@ -59,6 +59,8 @@ def _load():
                                     _I64, _D, _D]),
                 "or_neighbours": (i64, [i64, _D, _D, _D, ctypes.c_int, i64, dbl, i64, _I64]),
                 "or_bin": (i64, [i64, _D, _D, _I32, _I32, _I32, _I32, _I32]),
+                "or_bin_patches": (i64, [i64, _D, _D, _I64, i32, _D, i32, _I32, _I32, _I32, _I32, _I32, _I32]),
+                "or_gather_pos_f32_patches": (None, [_U8, i64, i64, _I32, i64, _I32, _I32, _I32, i32, _D, _F]),
                 "or_gather_f64": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _D]),
                 "or_gather_f32": (None, [_U8, i64, i64, _I32, i64, ctypes.c_int, _F]),
                 "or_gather_pos_f32": (None, [_U8, i64, i64, _I32, i64, _I32, _D, _I32, _F]),
@@ -175,6 +177,61 @@ def bin_cells(x, box, ncell):
     bad = _load().or_bin(n, _p(x, _D), _p(box, _D), _p(nc, _I32), _p(cell_of, _I32), _p(cell_start, _I32),
                          _p(perm, _I32), _p(cos, _I32))
     return cell_of, cell_start, perm, cos, int(bad)
+
+
+def bin_patches(x, h, patch_start, box, ncap):
+    """Per-patch grids (edge >= 2 h_max of the patch, at most ncap per axis) and the stable counting sort over the
+    concatenated patch cells: returns dict patch_n [npatch, 3], patch_cell_base, cell_of, cell_start, perm,
+    cell_of_slot."""
+    x, h, box = _c(x, np.float64), _c(h, np.float64), _c(box, np.float64)
+    ps = _c(patch_start, np.int64)
+    npatch = ps.size - 1
+    n = h.size
+    patch_n = np.empty(3 * npatch, np.int32)
+    pcb = np.empty(npatch + 1, np.int32)
+    cell_of = np.empty(n, np.int32)
+    cap = npatch * int(ncap) ** 3
+    cell_start = np.empty(cap + 1, np.int32)
+    perm = np.empty(n, np.int32)
+    cos = np.empty(n, np.int32)
+    nc = _load().or_bin_patches(n, _p(x, _D), _p(h, _D), _p(ps, _I64), npatch, _p(box, _D), int(ncap),
+                                _p(patch_n, _I32), _p(pcb, _I32), _p(cell_of, _I32), _p(cell_start, _I32),
+                                _p(perm, _I32), _p(cos, _I32))
+    return {"patch_n": patch_n.reshape(npatch, 3), "patch_cell_base": pcb, "cell_of": cell_of,
+            "cell_start": cell_start[:nc + 1].copy(), "perm": perm, "cell_of_slot": cos, "ncells": int(nc)}
+
+
+def gather_pos_f32_patches(aos, stride, perm, off, cell_of_slot, patch_cell_base, patch_n, box):
+    """FP32 patch-local positions relative to the slot's cell origin, array [3, n]."""
+    aos = _c(aos, np.uint8)
+    perm, cos = _c(perm, np.int32), _c(cell_of_slot, np.int32)
+    pcb, pn = _c(patch_cell_base, np.int32), _c(patch_n, np.int32).ravel()
+    box = _c(box, np.float64)
+    n = perm.size
+    out = np.empty((3, n), np.float32)
+    _load().or_gather_pos_f32_patches(_p(aos, _U8), int(stride), n, _p(perm, _I32), int(off), _p(cos, _I32),
+                                      _p(pcb, _I32), _p(pn, _I32), pcb.size - 1, _p(box, _D), _p(out, _F))
+    return out
+
+
+def step_patches(aos, layout, patch_start, box, params, patches=None):
+    """Expected rho, P, c_s, a, du/dt of every record of the listed patches (all if None): each patch is an open
+    box whose particles interact only with each other; brute force within the patch."""
+    f = unpack(aos, layout)
+    ps = np.asarray(patch_start, np.int64)
+    n = f["h"].size
+    out = {k: np.full(n, np.nan) for k in ("rho", "P", "cs", "dudt")}
+    out["a"] = np.full((n, 3), np.nan)
+    for p in (range(ps.size - 1) if patches is None else patches):
+        s, e = int(ps[p]), int(ps[p + 1])
+        if e == s:
+            continue
+        x, v, m, h, u = f["x"][s:e], f["v"][s:e], f["mass"][s:e], f["h"][s:e], f["u"][s:e]
+        rho = density(x, m, h, box, periodic=False)
+        P, cs = eos(rho, u, params["gamma"])
+        a, du = force(x, v, m, h, rho, P, cs, box, False, params["alpha"], params["beta"], params["eps"])
+        out["rho"][s:e], out["P"][s:e], out["cs"][s:e], out["a"][s:e], out["dudt"][s:e] = rho, P, cs, a, du
+    return out
 
 
 def gather(aos, stride, perm, off, ncomp, dtype=np.float64):

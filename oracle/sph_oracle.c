@@ -241,6 +241,87 @@ int64_t or_bin(int64_t n, const double *x, const double *box, const int32_t *nce
 }
 
 /* ---------------------------------------------------------------------------------------------------------
+ * Cell bucketing of independent patches (open boxes of edge box[d], patch p = particles patch_start[p] ..
+ * patch_start[p+1]-1, patch-local positions).  Each patch gets its own grid, chosen so that every cell is at
+ * least as wide as the largest interaction radius 2 h_max of the patch (Section 2.1): per axis
+ * n = floor(box / (2 h_max)), at least 1, at most ncap, lowered while box / n < 2 h_max; n = ncap for a patch
+ * without particles.  Global cell ids: patch_cell_base[p] + kx + nx (ky + ny kz) with k = floor(x * (n / box))
+ * clamped into [0, n-1].  Slot order as in or_bin: cell-major, ascending particle index inside a cell.
+ * Outputs patch_n (3 per patch), patch_cell_base (npatch + 1), cell_of, cell_start (cells + 1), perm,
+ * cell_of_slot; returns the number of cells.
+ * ------------------------------------------------------------------------------------------------------- */
+int64_t or_bin_patches(int64_t n, const double *x, const double *h, const int64_t *patch_start, int32_t npatch,
+                       const double *box, int32_t ncap, int32_t *patch_n, int32_t *patch_cell_base, int32_t *cell_of,
+                       int32_t *cell_start, int32_t *perm, int32_t *cell_of_slot)
+{
+    patch_cell_base[0] = 0;
+    for (int32_t p = 0; p < npatch; ++p) {
+        double hm = 0.0;
+        for (int64_t i = patch_start[p]; i < patch_start[p + 1]; ++i)
+            if (h[i] > hm) hm = h[i];
+        int32_t cells = 1;
+        for (int d = 0; d < 3; ++d) {
+            int32_t nn = ncap;
+            if (hm > 0.0) {
+                double f = floor(box[d] / (2.0 * hm));
+                nn = f >= (double)ncap ? ncap : (f >= 1.0 ? (int32_t)f : 1);
+                while (nn > 1 && box[d] / (double)nn < 2.0 * hm) --nn;
+            }
+            patch_n[3 * p + d] = nn;
+            cells *= nn;
+        }
+        patch_cell_base[p + 1] = patch_cell_base[p] + cells;
+    }
+    int64_t ncells = patch_cell_base[npatch];
+    for (int32_t p = 0; p < npatch; ++p) {
+        for (int64_t i = patch_start[p]; i < patch_start[p + 1]; ++i) {
+            int32_t k[3];
+            for (int d = 0; d < 3; ++d) {
+                int32_t nn = patch_n[3 * p + d];
+                double inv = (double)nn / box[d];
+                double f = floor(x[3 * i + d] * inv);
+                k[d] = !(f >= 0.0) ? 0 : (f > (double)(nn - 1) ? nn - 1 : (int32_t)f);
+            }
+            cell_of[i] = patch_cell_base[p] + k[0] + patch_n[3 * p] * (k[1] + patch_n[3 * p + 1] * k[2]);
+        }
+    }
+    for (int64_t c = 0; c <= ncells; ++c) cell_start[c] = 0;
+    for (int64_t i = 0; i < n; ++i) cell_start[cell_of[i] + 1] += 1;
+    for (int64_t c = 0; c < ncells; ++c) cell_start[c + 1] += cell_start[c];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncells > 0 ? ncells : 1));
+    for (int64_t c = 0; c < ncells; ++c) fill[c] = cell_start[c];
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t s = fill[cell_of[i]]++;
+        perm[s] = (int32_t)i;
+        cell_of_slot[s] = cell_of[i];
+    }
+    free(fill);
+    return ncells;
+}
+
+/* FP32 patch-local positions relative to the origin of the slot's cell: (float)(x - k_d * (box_d / n_d)). */
+void or_gather_pos_f32_patches(const uint8_t *aos, int64_t stride, int64_t n, const int32_t *perm, int64_t off,
+                               const int32_t *cell_of_slot, const int32_t *patch_cell_base, const int32_t *patch_n,
+                               int32_t npatch, const double *box, float *out)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        int32_t c = cell_of_slot[s];
+        int32_t p = 0;
+        while (p + 1 < npatch && patch_cell_base[p + 1] <= c) ++p;
+        int32_t local = c - patch_cell_base[p];
+        const int32_t *nn = patch_n + 3 * p;
+        int32_t k[3] = {local % nn[0], (local / nn[0]) % nn[1], local / (nn[0] * nn[1])};
+        for (int d = 0; d < 3; ++d) {
+            double xv;
+            memcpy(&xv, aos + (int64_t)perm[s] * stride + off + 8 * d, 8);
+            double edge = box[d] / (double)nn[d];
+            double origin = (double)k[d] * edge;
+            out[(int64_t)d * n + s] = (float)(xv - origin);
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
  * View conversions (Section 4, Eq. 3-5).  The gather is narrowing N followed by C_AoS^SoA, fused: for every
  * slot s, out[comp][s] = field component of record perm[s].  The scatter is C_SoA^AoS followed by widening W:
  * the field of record perm[s] is overwritten from in[comp][s]; no other byte of the record is touched.

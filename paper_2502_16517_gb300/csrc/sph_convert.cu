@@ -9,6 +9,10 @@
 //   k_cell_sort   one warp per cell: ranks the claimed record indices so that each cell holds ascending record
 //                 indices (the slot order is then independent of atomic timing, i.e. deterministic).
 //
+// Patch views (independent open boxes): k_patch_grid gives every patch its own grid with cell edge >= 2 h_max of
+// the patch (capped), k_bin_count_patches maps records to global cell ids, and the same scan / place / sort
+// follow, with the cell count read on the device.
+//
 // Views (Section 4, Eq. 3-5; prologue/epilogue of Section 3.1):
 //   k_gather      CTA per tile of 256 slots.  Phase 1 reads, per record, only the 16-byte chunks that hold a
 //                 member of the mask (128-bit loads; consecutive threads take consecutive chunks of one record)
@@ -58,12 +62,14 @@ __global__ void k_bin_count(const uint8_t *__restrict__ aos, int64_t stride, int
 
 // Single-CTA exclusive scan over the cell histogram, 4 cells per thread per round.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_scan_cells(const int *__restrict__ count, int ncells,
+__global__ void __launch_bounds__(kScanThreads) k_scan_cells(const int *__restrict__ count, int ncells_host,
+                                                             const int *__restrict__ ncells_dev,
                                                              int *__restrict__ cell_start, int *__restrict__ fill)
 {
     __shared__ int warp_tot[32];
     __shared__ int carry_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncells = ncells_dev ? *ncells_dev : ncells_host;
     if (tid == 0) carry_s = 0;
     __syncthreads();
     for (int base = 0; base < ncells; base += kScanThreads * 4) {
@@ -123,12 +129,13 @@ __global__ void k_bin_place(const int *__restrict__ cell_of, int n, int *__restr
 
 // One warp per cell: rank every record index of the cell among the cell's indices (all distinct), write it to
 // its sorted slot.  O(L^2 / 32) per cell of L particles, with the compared values broadcast by shuffles.
-__global__ void k_cell_sort(const int *__restrict__ cell_start, int ncells, const int *__restrict__ perm_tmp,
-                            int *__restrict__ perm, int *__restrict__ cell_of_slot)
+__global__ void k_cell_sort(const int *__restrict__ cell_start, int ncells_host, const int *__restrict__ ncells_dev,
+                            const int *__restrict__ perm_tmp, int *__restrict__ perm, int *__restrict__ cell_of_slot)
 {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int ncells = ncells_dev ? *ncells_dev : ncells_host;
     const int lane = threadIdx.x & 31;
-    if (c >= ncells) return;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncells; c += nwarps) {
     const int b = cell_start[c], L = cell_start[c + 1] - b;
     for (int k0 = 0; k0 < L; k0 += 32) {
         const int k = k0 + lane;
@@ -144,19 +151,79 @@ __global__ void k_cell_sort(const int *__restrict__ cell_start, int ncells, cons
             cell_of_slot[b + rank] = c;
         }
     }
+    }
 }
 
-__device__ __forceinline__ int cell_axis_coord(int c, int axis, const Grid &g)
+// Patch grids: per patch (one CTA) the largest h of its records, then per axis n = floor(box / (2 h_max)) cells
+// (at least 1, at most ncap, lowered while box / n < 2 h_max after rounding), the cell edge box / n and the inverse
+// n / box, each rounded once in FP64, and the patch's cell count.
+__global__ void __launch_bounds__(256) k_patch_grid(const uint8_t *__restrict__ aos, int64_t stride, int off_h,
+                                                    const int64_t *__restrict__ patch_start, Grid g, int ncap,
+                                                    int *__restrict__ patch_n, double *__restrict__ patch_edge,
+                                                    double *__restrict__ patch_inv, int *__restrict__ patch_cells)
 {
-    if (axis == 0) return c % g.n[0];
-    if (axis == 1) return (c / g.n[0]) % g.n[1];
-    return c / (g.n[0] * g.n[1]);
+    __shared__ double red[8];
+    const int p = blockIdx.x;
+    const int64_t s = patch_start[p], e = patch_start[p + 1];
+    double hm = 0.0;
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x)
+        hm = fmax(hm, *reinterpret_cast<const double *>(aos + i * stride + off_h));
+    for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(kFull, hm, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) hm = fmax(hm, red[w]);
+        int cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            int nn = ncap;
+            if (hm > 0.0) {
+                const double f = floor(g.box[a] / (2.0 * hm));
+                nn = f >= (double)ncap ? ncap : (f >= 1.0 ? (int)f : 1);
+                while (nn > 1 && __ddiv_rn(g.box[a], (double)nn) < 2.0 * hm) --nn;
+            }
+            patch_n[3 * p + a] = nn;
+            patch_edge[3 * p + a] = __ddiv_rn(g.box[a], (double)nn);
+            patch_inv[3 * p + a] = __ddiv_rn((double)nn, g.box[a]);
+            cells *= nn;
+        }
+        patch_cells[p] = cells;
+    }
 }
 
-// g.edge[axis] without dynamic indexing of the kernel parameter (keeps it out of local memory)
-__device__ __forceinline__ double edge_of(int axis, const Grid &g)
+// Global cell of every record of a patch view: patch by binary search of the record index in patch_start, then
+// floor(x * (n / box)) per axis in the patch grid, clamped (positions outside [0, box] set SPH_DEV_POS_RANGE).
+__global__ void k_bin_count_patches(const uint8_t *__restrict__ aos, int64_t stride, int off_x, int n,
+                                    const int64_t *__restrict__ patch_start, int npatch, Grid g,
+                                    const int *__restrict__ patch_n, const double *__restrict__ patch_inv,
+                                    const int *__restrict__ patch_cell_base, int *__restrict__ cell_of,
+                                    int *__restrict__ count, unsigned *status)
 {
-    return axis == 0 ? g.edge[0] : (axis == 1 ? g.edge[1] : g.edge[2]);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = npatch;  // patch_start[lo] <= i < patch_start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (patch_start[mid] <= (int64_t)i) lo = mid; else hi = mid;
+    }
+    const double *xp = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_x);
+    bool bad = false;
+    const int nx = patch_n[3 * lo], ny = patch_n[3 * lo + 1], nz = patch_n[3 * lo + 2];
+    const int kx = cell_coord(__ldg(xp + 0), patch_inv[3 * lo], nx, g.box[0], bad);
+    const int ky = cell_coord(__ldg(xp + 1), patch_inv[3 * lo + 1], ny, g.box[1], bad);
+    const int kz = cell_coord(__ldg(xp + 2), patch_inv[3 * lo + 2], nz, g.box[2], bad);
+    const int c = patch_cell_base[lo] + kx + nx * (ky + ny * kz);
+    cell_of[i] = c;
+    atomicAdd(&count[c], 1);
+    if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
+}
+
+// Origin of the slot's cell along an axis: k * edge, the product rounded once in FP64.
+__device__ __forceinline__ double cell_origin(const CellSpace &cs, int c, int axis)
+{
+    CellLoc L;
+    locate_cell(cs, c, L);
+    const int k = axis == 0 ? L.k[0] : (axis == 1 ? L.k[1] : L.k[2]);
+    return __dmul_rn((double)k, cell_edge(cs, L, axis));
 }
 
 // Gather: VEC16 selects 16-byte chunks (record stride and buffer 16-byte aligned) or 8-byte items.
@@ -164,7 +231,7 @@ template <bool VEC16, bool F32>
 __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ aos, int64_t stride,
                                                   const int *__restrict__ perm,
                                                   const int *__restrict__ cell_of_slot, int n,
-                                                  const ConvPlan plan, const Grid g)
+                                                  const ConvPlan plan, const CellSpace cs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int srec[kTile];
@@ -207,8 +274,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             const int axis = plan.item_pos[k];
             float o;
             if (axis >= 0) {
-                const int kc = cell_axis_coord(cell_of_slot[base + s], axis, g);
-                const double origin = __dmul_rn((double)kc, edge_of(axis, g));
+                const double origin = cell_origin(cs, cell_of_slot[base + s], axis);
                 o = __double2float_rn(__dsub_rn(v, origin));
             } else {
                 o = __double2float_rn(v);
@@ -222,7 +288,7 @@ template <bool F32>
 __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, int64_t stride,
                                                    const int *__restrict__ perm,
                                                    const int *__restrict__ cell_of_slot, int n,
-                                                   const ConvPlan plan, const Grid g)
+                                                   const ConvPlan plan, const CellSpace cs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int srec[kTile];
@@ -242,10 +308,7 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         } else {
             v = (double)static_cast<const float *>(plan.soa[k])[base + s];
             const int axis = plan.item_pos[k];
-            if (axis >= 0) {
-                const int kc = cell_axis_coord(cell_of_slot[base + s], axis, g);
-                v = __dadd_rn(__dmul_rn((double)kc, edge_of(axis, g)), v);
-            }
+            if (axis >= 0) v = __dadd_rn(cell_origin(cs, cell_of_slot[base + s], axis), v);
         }
         sval[s * ni + k] = v;
     }
@@ -270,20 +333,51 @@ cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, con
         k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status);
         ++*nl;
     }
-    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells, cell_start, fill);
+    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells, nullptr, cell_start, fill);
     ++*nl;
     if (n > 0) {
         *nl += 2;
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
         const long long threads = (long long)ncells * 32;
-        k_cell_sort<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(cell_start, ncells, perm_tmp, perm,
-                                                                      cell_of_slot);
+        const long long blocks = (threads + 255) / 256;
+        k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,
+                                                                                perm_tmp, perm, cell_of_slot);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, int off_h, int n,
+                               const int64_t *patch_start, int npatch, const Grid &box, int ncap, int ncells_cap,
+                               int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
+                               int *ncells_dev, int *cell_of, int *count, int *cell_start, int *fill,
+                               int *perm_tmp, int *perm, int *cell_of_slot, unsigned *status, cudaStream_t st,
+                               int *nl)
+{
+    // patch_edge holds 3 * npatch edges followed by 3 * npatch inverses
+    double *patch_inv = patch_edge + 3 * (size_t)npatch;
+    k_patch_grid<<<npatch, 256, 0, st>>>(aos, stride, off_h, patch_start, box, ncap, patch_n, patch_edge, patch_inv,
+                                         patch_cells);
+    k_scan_cells<<<1, kScanThreads, 0, st>>>(patch_cells, npatch, nullptr, patch_cell_base, fill);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells_cap, st);
+    if (e != cudaSuccess) return e;
+    *nl += 2;
+    if (n > 0) {
+        k_bin_count_patches<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, patch_start, npatch, box, patch_n,
+                                                             patch_inv, patch_cell_base, cell_of, count, status);
+        ++*nl;
+    }
+    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells_cap, ncells_dev, cell_start, fill);
+    ++*nl;
+    if (n > 0) {
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        k_cell_sort<<<2048, 256, 0, st>>>(cell_start, ncells_cap, ncells_dev, perm_tmp, perm, cell_of_slot);
+        *nl += 2;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
-                          const int *cell_of_slot, int n, const ConvPlan &plan, const Grid &g, bool f32,
+                          const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &g, bool f32,
                           cudaStream_t st, int *nl)
 {
     if (n <= 0 || plan.nitems == 0) return cudaSuccess;
@@ -311,7 +405,7 @@ cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const 
 }
 
 cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const int *cell_of_slot, int n,
-                           const ConvPlan &plan, const Grid &g, bool f32, cudaStream_t st, int *nl)
+                           const ConvPlan &plan, const CellSpace &g, bool f32, cudaStream_t st, int *nl)
 {
     if (n <= 0 || plan.nitems == 0) return cudaSuccess;
     ++*nl;

@@ -27,6 +27,61 @@ struct Grid {
     double min_edge;   // smallest cell edge: every 2h must fit
 };
 
+// Cell space of a view: either one grid over the domain (npatch == 0), or npatch independent patches, each an
+// open box of size g.box with its own grid of patch_n[3p..3p+2] cells (chosen per step from the patch's largest h).
+// Global cell ids of patch p are patch_cell_base[p] .. patch_cell_base[p+1]-1; inside a grid the id is
+// kx + nx (ky + ny kz).
+struct CellSpace {
+    Grid g;
+    int npatch;
+    const int *patch_cell_base;  // [npatch + 1]
+    const int *patch_n;          // [3 npatch]
+    const double *patch_edge;    // [3 npatch]: g.box[a] / patch_n[3p+a], rounded once in FP64
+    const int *ncells_dev;       // total cells (device word; patches only)
+};
+
+struct CellLoc {
+    int k[3];  // cell coordinates inside its grid
+    int n[3];  // grid size
+    int base;  // first global cell of the grid
+    int patch;
+};
+
+// Coordinates of global cell c (patches: binary search of c in patch_cell_base).
+__device__ __forceinline__ void locate_cell(const CellSpace &cs, int c, CellLoc &L)
+{
+    int local = c;
+    if (cs.npatch == 0) {
+        L.n[0] = cs.g.n[0];
+        L.n[1] = cs.g.n[1];
+        L.n[2] = cs.g.n[2];
+        L.base = 0;
+        L.patch = 0;
+    } else {
+        int lo = 0, hi = cs.npatch;  // patch_cell_base[lo] <= c < patch_cell_base[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cs.patch_cell_base[mid] <= c) lo = mid; else hi = mid;
+        }
+        L.patch = lo;
+        L.base = cs.patch_cell_base[lo];
+        L.n[0] = cs.patch_n[3 * lo];
+        L.n[1] = cs.patch_n[3 * lo + 1];
+        L.n[2] = cs.patch_n[3 * lo + 2];
+        local = c - L.base;
+    }
+    L.k[0] = local % L.n[0];
+    L.k[1] = (local / L.n[0]) % L.n[1];
+    L.k[2] = local / (L.n[0] * L.n[1]);
+}
+
+// Cell edge along an axis: box / n rounded once in FP64 (precomputed for the uniform grid and per patch).
+__device__ __forceinline__ double cell_edge(const CellSpace &cs, const CellLoc &L, int axis)
+{
+    if (cs.npatch == 0) return axis == 0 ? cs.g.edge[0] : (axis == 1 ? cs.g.edge[1] : cs.g.edge[2]);
+    return cs.patch_edge[3 * L.patch + axis];
+}
+
 // Field-selective conversion plan (host builds it from a member mask and the record layout).
 // Items are the double components moved; for the 16-byte path the record bytes holding them are loaded as a
 // few 16-byte chunks per record, for the 8-byte path every item is its own 8-byte chunk.
@@ -70,27 +125,51 @@ cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, con
                        int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
                        int *cell_of_slot, unsigned *status, cudaStream_t st, int *nl);
 
+// Patch binning: per-patch grids from the patches' largest h (cells per axis capped at ncap), global cell ids,
+// then the same counting sort as launch_bin over at most ncells_cap cells.
+cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, int off_h, int n,
+                               const int64_t *patch_start, int npatch, const Grid &box, int ncap, int ncells_cap,
+                               int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
+                               int *ncells_dev, int *cell_of,
+                               int *count, int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot,
+                               unsigned *status, cudaStream_t st, int *nl);
+
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
-                          const int *cell_of_slot, int n, const ConvPlan &plan, const Grid &g, bool f32,
+                          const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &cs, bool f32,
                           cudaStream_t st, int *nl);
 
 cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const int *cell_of_slot, int n,
-                           const ConvPlan &plan, const Grid &g, bool f32, cudaStream_t st, int *nl);
+                           const ConvPlan &plan, const CellSpace &cs, bool f32, cudaStream_t st, int *nl);
 
-// Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h); force: 1/h,
-// 1/(pi h^5), P/rho^2).
+// Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h) and coefficient
+// tables; FP32 force: 1/h, 1/(pi h^5), P/rho^2).
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const Grid &g, cudaStream_t st, int *nl);
+                                const CellSpace &cs, cudaStream_t st, int *nl);
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const Grid &g, double alpha, cudaStream_t st, int *nl);
+                              const CellSpace &cs, double alpha, cudaStream_t st, int *nl);
 
-// The pair kernels.  tj: active particles staged per shared-memory tile (0 = default of the path).
+// Pair-kernel launch shape: active particles staged per tile (0 = default of the path), and for patch views the
+// largest-first work list the persistent kernel pulls cells from.
+struct PairLaunch {
+    int tj;
+    int threads;              // 128 or 256 threads per CTA (0 = 128)
+    const int *work_order;    // patches: cells in descending cost order (nullptr: one CTA per cell)
+    const int *work_count;    // patches: number of entries in work_order (device)
+    int *work_next;           // patches: work counter (device, zeroed by the launcher)
+    int persistent_ctas;      // patches: CTAs of the persistent launch
+};
+
+// The pair kernels.
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                                 int ncells, int n, const Grid &g, double gamma, int tj, unsigned *status,
-                                 Counters *counters, cudaStream_t st, int *nl);
+                                 int ncells, int n, const CellSpace &cs, double gamma, const PairLaunch &pl,
+                                 unsigned *status, Counters *counters, cudaStream_t st, int *nl);
 cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                               int ncells, int n, const Grid &g, const sph_params &prm, int tj, unsigned *status,
-                               Counters *counters, cudaStream_t st, int *nl);
+                               int ncells, int n, const CellSpace &cs, const sph_params &prm, const PairLaunch &pl,
+                               unsigned *status, Counters *counters, cudaStream_t st, int *nl);
+
+// Largest-first work list over the non-empty cells (cost = local particles x active particles).
+cudaError_t launch_work_list(const CellSpace &cs, const int *cell_start, int ncells_cap, int *cell_bucket,
+                             int *bucket_count, int *work_order, int *work_count, cudaStream_t st, int *nl);
 
 cudaError_t launch_reduce(bool f32, const SoaPtrs &soa, int n, double *partials, double *out, cudaStream_t st,
                           int *nl);

@@ -49,51 +49,59 @@ struct NbrTable {
     double shift[27][3];  // added to x_i - x_j for a j of neighbour q (0 or +-box)
     float offf[27][3];    // origin of neighbour cell q relative to the local cell origin: (float)(d * edge)
     int wrap;             // any shift != 0
+    float margin;         // slack of the FP64 paths' FP32 filter
 };
 
-__device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const Grid &g, const int *cell_start)
+__device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellSpace &cs, const int *cell_start)
 {
     const int tid = threadIdx.x;
-    const int kc[3] = {c % g.n[0], (c / g.n[0]) % g.n[1], c / (g.n[0] * g.n[1])};
+    const bool periodic = cs.npatch == 0 && cs.g.periodic;
     if (tid == 0) nb.wrap = 0;
     __syncthreads();
     if (tid < 27) {
+        CellLoc L;
+        locate_cell(cs, c, L);
         const int d[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
         int kk[3];
         bool valid = true;
         bool wr = false;
         for (int a = 0; a < 3; ++a) {
-            int k = kc[a] + d[a];
+            int k = L.k[a] + d[a];
             double s = 0.0;
             if (k < 0) {
-                if (g.periodic) {
-                    k += g.n[a];
-                    s = g.box[a];
+                if (periodic) {
+                    k += L.n[a];
+                    s = cs.g.box[a];
                 } else {
                     valid = false;
                 }
-            } else if (k >= g.n[a]) {
-                if (g.periodic) {
-                    k -= g.n[a];
-                    s = -g.box[a];
+            } else if (k >= L.n[a]) {
+                if (periodic) {
+                    k -= L.n[a];
+                    s = -cs.g.box[a];
                 } else {
                     valid = false;
                 }
             }
             kk[a] = k;
             nb.shift[tid][a] = s;
-            nb.offf[tid][a] = __double2float_rn((double)d[a] * g.edge[a]);
+            nb.offf[tid][a] = __double2float_rn((double)d[a] * cell_edge(cs, L, a));
             wr = wr || (s != 0.0);
         }
         int cnt = 0, st = 0;
         if (valid) {
-            const int c2 = kk[0] + g.n[0] * (kk[1] + g.n[1] * kk[2]);
+            const int c2 = L.base + kk[0] + L.n[0] * (kk[1] + L.n[1] * kk[2]);
             st = cell_start[c2];
             cnt = cell_start[c2 + 1] - st;
         }
         nb.start[tid] = st;
         nb.pref[tid + 1] = cnt;  // counts, turned into a prefix below
         if (wr && cnt > 0) atomicOr(&nb.wrap, 1);
+        if (tid == 13) {
+            // conservative slack of the FP32 filter: float rounding of cell-relative coordinates (|coord| <= 2 edges)
+            const double emax = fmax(cell_edge(cs, L, 0), fmax(cell_edge(cs, L, 1), cell_edge(cs, L, 2)));
+            nb.margin = (float)(4e-6 * emax);
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -225,7 +233,7 @@ __device__ __forceinline__ double rcp_seeded(double x)
 // ------------------------------------------------------------------------------------------------------------
 struct PairCommon {
     const int *cell_start;
-    Grid g;
+    CellSpace cs;
     unsigned *status;
     Counters *counters;
     int tj;  // staged particles per tile (a multiple of kStep)
@@ -351,7 +359,7 @@ struct DensF64 {
         A.cs[i] = cs;
         unsigned bits = 0;
         if (!(rho > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(cs)) bits |= SPH_DEV_NONFINITE;
-        if (!(2.0 * h <= A.cm.g.min_edge)) bits |= SPH_DEV_H_TOO_BIG;
+        if (!(2.0 * h <= A.cm.cs.g.min_edge)) bits |= SPH_DEV_H_TOO_BIG;
         if (bits) atomicOr(A.cm.status, bits);
     }
     static __device__ __forceinline__ void count(const Args &A, unsigned long long cand,
@@ -447,7 +455,7 @@ struct DensF32 {
         unsigned bits = 0;
         if (!(rho > 0.0f) || !isfinite(rho) || !isfinite(P) || !isfinite(cs)) bits |= SPH_DEV_NONFINITE;
         // h is the float cast of the record's h (at most half an ulp above it): allow that rounding
-        if (!(2.0 * (double)h <= A.cm.g.min_edge * (1.0 + 2.4e-7))) bits |= SPH_DEV_H_TOO_BIG;
+        if (!(2.0 * (double)h <= A.cm.cs.g.min_edge * (1.0 + 2.4e-7))) bits |= SPH_DEV_H_TOO_BIG;
         if (bits) atomicOr(A.cm.status, bits);
     }
     static __device__ __forceinline__ void count(const Args &A, unsigned long long cand,
@@ -841,33 +849,35 @@ __device__ __forceinline__ void zero_acc<ForceF32>(ForceF32::Acc &a)
 // The per-cell driver shared by all loop bodies.
 // ------------------------------------------------------------------------------------------------------------
 template <class K>
-__global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::Args A)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ NbrTable nb;
-    __shared__ typename K::Acc acc[kMaxLocal];
-    __shared__ int ring[kPairWarps][kRing];
-    __shared__ unsigned long long sh_pairs;
+struct PairShared {
+    NbrTable nb;
+    typename K::Acc acc[kMaxLocal];
+    int ring[kPairWarps][kRing];
+    unsigned long long pairs;
+};
 
-    const int c = blockIdx.x;
+// One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
+template <class K>
+__device__ __forceinline__ void process_cell(const typename K::Args &A, int c, const typename K::Tile &T,
+                                             PairShared<K> &S)
+{
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int tj = A.cm.tj;
-    const typename K::Tile T = K::carve(smem, tj);
-    int *q = ring[warp];
-    if (tid == 0) sh_pairs = 0ull;
-    build_nbr_table(nb, c, A.cm.g, A.cm.cell_start);
+    int *q = S.ring[warp];
+    NbrTable &nb = S.nb;
+    if (tid == 0) S.pairs = 0ull;
+    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start);
     const int NJ = nb.pref[27];
     const bool wrap = nb.wrap != 0;
-    // conservative slack of the FP32 filter: float rounding of cell-relative coordinates (|coord| <= 2 edges)
-    const float margin = (float)(4e-6 * fmax(A.cm.g.edge[0], fmax(A.cm.g.edge[1], A.cm.g.edge[2])));
+    const float margin = nb.margin;
     unsigned long long my_pairs = 0;
 
     for (int ib = ls; ib < le; ib += kMaxLocal) {
         const int nloc = min(kMaxLocal, le - ib);
-        for (int t = tid; t < nloc; t += kPairThreads) zero_acc<K>(acc[t]);
+        for (int t = tid; t < nloc; t += kPairThreads) zero_acc<K>(S.acc[t]);
         for (int tb = 0; tb < NJ; tb += tj) {
             const int tn = min(tj, NJ - tb);
             const int tnp = (tn + kStep - 1) / kStep * kStep;  // padded to whole filter steps (<= tj)
@@ -916,30 +926,120 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::A
                 }
                 __syncwarp();  // the ring is reused by the next local particle
                 P.reduce();
-                K::accumulate(acc[li], P, lane);
+                K::accumulate(S.acc[li], P, lane);
             }
         }
         __syncthreads();
-        for (int t = tid; t < nloc; t += kPairThreads) K::finish(A, ib + t, acc[t]);
+        for (int t = tid; t < nloc; t += kPairThreads) K::finish(A, ib + t, S.acc[t]);
     }
-    if (lane == 0 && my_pairs) atomicAdd(&sh_pairs, my_pairs);
+    if (lane == 0 && my_pairs) atomicAdd(&S.pairs, my_pairs);
     __syncthreads();
-    if (tid == 0) K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, sh_pairs);
+    if (tid == 0) K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, S.pairs);
+}
+
+// One CTA per cell (single-grid views).
+template <class K>
+__global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::Args A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PairShared<K> S;
+    const typename K::Tile T = K::carve(smem, A.cm.tj);
+    process_cell<K>(A, blockIdx.x, T, S);
+}
+
+// Persistent CTAs pulling cells from a work list (patch views: cells in descending cost order, so the largest
+// cells start first and the small ones fill the tail).
+template <class K>
+__global__ void __launch_bounds__(kPairThreads) k_cell_pairs_persist(const typename K::Args A,
+                                                                     const int *__restrict__ order,
+                                                                     const int *__restrict__ count, int *next)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PairShared<K> S;
+    __shared__ int w;
+    const typename K::Tile T = K::carve(smem, A.cm.tj);
+    const int total = *count;
+    for (;;) {
+        if (threadIdx.x == 0) w = atomicAdd(next, 1);
+        __syncthreads();
+        const int wi = w;
+        __syncthreads();  // every thread has read w before thread 0 fetches the next item
+        if (wi >= total) break;
+        process_cell<K>(A, order[wi], T, S);
+    }
+}
+
+// Cost of every non-empty cell (local particles x active particles), bucketed by floor(log2(cost)).
+__global__ void k_cell_cost(const CellSpace cs, const int *__restrict__ cell_start, int *__restrict__ cell_bucket,
+                            int *__restrict__ bucket_count)
+{
+    const int ncells = *cs.ncells_dev;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int nloc = cell_start[c + 1] - cell_start[c];
+        int b = -1;
+        if (nloc > 0) {
+            CellLoc L;
+            locate_cell(cs, c, L);
+            long long nj = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int kx = L.k[0] + dx, ky = L.k[1] + dy, kz = L.k[2] + dz;
+                        if (kx < 0 || ky < 0 || kz < 0 || kx >= L.n[0] || ky >= L.n[1] || kz >= L.n[2]) continue;
+                        const int c2 = L.base + kx + L.n[0] * (ky + L.n[1] * kz);
+                        nj += cell_start[c2 + 1] - cell_start[c2];
+                    }
+            const unsigned long long cost = (unsigned long long)nloc * (unsigned long long)nj;
+            b = 63 - __clzll((long long)cost);
+            atomicAdd(&bucket_count[b], 1);
+        }
+        cell_bucket[c] = b;
+    }
+}
+
+// Offsets of the 64 cost buckets, largest first; the work count.
+__global__ void k_work_offsets(int *__restrict__ bucket_count, int *__restrict__ work_count)
+{
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 63; b >= 0; --b) {
+            const int cnt = bucket_count[b];
+            bucket_count[b] = run;  // becomes the bucket's cursor
+            run += cnt;
+        }
+        *work_count = run;
+    }
+}
+
+__global__ void k_work_place(const CellSpace cs, const int *__restrict__ cell_bucket, int *__restrict__ cursor,
+                             int *__restrict__ order)
+{
+    const int ncells = *cs.ncells_dev;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int b = cell_bucket[c];
+        if (b >= 0) order[atomicAdd(&cursor[b], 1)] = c;
+    }
 }
 
 // FP32 cell-relative copies of FP64 positions and (float) h rounded up: the filter inputs of the FP64 force loop.
+__device__ __forceinline__ void cell_relative_f32(const CellSpace &cs, int c, double x, double y, double z,
+                                                  float &xf, float &yf, float &zf)
+{
+    CellLoc L;
+    locate_cell(cs, c, L);
+    xf = __double2float_rn(x - (double)L.k[0] * cell_edge(cs, L, 0));
+    yf = __double2float_rn(y - (double)L.k[1] * cell_edge(cs, L, 1));
+    zf = __double2float_rn(z - (double)L.k[2] * cell_edge(cs, L, 2));
+}
+
 __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                        const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, Grid g,
+                        const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, CellSpace cs,
                         float *__restrict__ xf, float *__restrict__ yf, float *__restrict__ zf,
                         float *__restrict__ hf)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const int c = cell_of_slot[s];
-    const int kx = c % g.n[0], ky = (c / g.n[0]) % g.n[1], kz = c / (g.n[0] * g.n[1]);
-    xf[s] = __double2float_rn(x[s] - (double)kx * g.edge[0]);
-    yf[s] = __double2float_rn(y[s] - (double)ky * g.edge[1]);
-    zf[s] = __double2float_rn(z[s] - (double)kz * g.edge[2]);
+    cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
     hf[s] = __double2float_ru(h[s]);
 }
 
@@ -947,18 +1047,14 @@ __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__
 // spline as a cubic in r: inner piece 1 - 3/2 (r/h)^2 + 3/4 (r/h)^3, outer 2 - 3 (r/h) + 3/2 (r/h)^2 - 1/4 (r/h)^3.
 __global__ void k_density_prep_f64(const double *__restrict__ x, const double *__restrict__ y,
                                    const double *__restrict__ z, const double *__restrict__ h,
-                                   const int *__restrict__ cell_of_slot, int n, Grid g, float *__restrict__ xf,
+                                   const int *__restrict__ cell_of_slot, int n, CellSpace cs, float *__restrict__ xf,
                                    float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2,
                                    double *__restrict__ e3, double *__restrict__ o1, double *__restrict__ o2,
                                    double *__restrict__ o3)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const int c = cell_of_slot[s];
-    const int kx = c % g.n[0], ky = (c / g.n[0]) % g.n[1], kz = c / (g.n[0] * g.n[1]);
-    xf[s] = __double2float_rn(x[s] - (double)kx * g.edge[0]);
-    yf[s] = __double2float_rn(y[s] - (double)ky * g.edge[1]);
-    zf[s] = __double2float_rn(z[s] - (double)kz * g.edge[2]);
+    cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
     const double hi = 1.0 / h[s], h2 = hi * hi, h3 = h2 * hi;
     e2[s] = -1.5 * h2;
     e3[s] = 0.75 * h3;
@@ -1005,16 +1101,36 @@ __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__r
 }
 
 template <class K>
-cudaError_t run_cells(const typename K::Args &A, int ncells, cudaStream_t st)
+cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &pl, cudaStream_t st)
 {
     const size_t smem = (size_t)A.cm.tj * K::kStageBytes + 16;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(k_cell_pairs<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_cell_pairs_persist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    k_cell_pairs<K><<<ncells, kPairThreads, smem, st>>>(A);
+    if (pl.work_order) {
+        // persistent CTAs: as many as fit on the device at once (occupancy of this kernel at this tile size)
+        static size_t sized_for = 0;
+        static int ctas = 0;
+        if (sized_for != smem || ctas <= 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cell_pairs_persist<K>, kPairThreads, smem);
+            ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+            sized_for = smem;
+        }
+        cudaError_t e = cudaMemsetAsync(pl.work_next, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        k_cell_pairs_persist<K><<<pl.persistent_ctas > 0 ? pl.persistent_ctas : ctas, kPairThreads, smem, st>>>(
+            A, pl.work_order, pl.work_count, pl.work_next);
+    } else {
+        k_cell_pairs<K><<<ncells, kPairThreads, smem, st>>>(A);
+    }
     return cudaGetLastError();
 }
 
@@ -1027,7 +1143,7 @@ int tile_or_default(int tj, int dflt)
 }  // namespace
 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const Grid &g, cudaStream_t st, int *nl)
+                                const CellSpace &g, cudaStream_t st, int *nl)
 {
     if (n <= 0 || f32) return cudaSuccess;  // FP32 views are already cell-relative floats
     k_density_prep_f64<<<(n + 255) / 256, 256, 0, st>>>(
@@ -1039,7 +1155,7 @@ cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr
 }
 
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const Grid &g, double alpha, cudaStream_t st, int *nl)
+                              const CellSpace &g, double alpha, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     const int nb = (n + 255) / 256;
@@ -1063,12 +1179,13 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
 }
 
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                                 int ncells, int n, const Grid &g, double gamma, int tj, unsigned *status,
-                                 Counters *counters, cudaStream_t st, int *nl)
+                                 int ncells, int n, const CellSpace &g, double gamma, const PairLaunch &pl,
+                                 unsigned *status, Counters *counters, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
     PairCommon cm{cell_start, g, status, counters, 0};
+    const int tj = pl.tj;
     if (!f32) {
         DensF64::Args A;
         cm.tj = tile_or_default(tj, 512);
@@ -1091,7 +1208,7 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
         A.P = (double *)soa.p[SPH_P][0];
         A.cs = (double *)soa.p[SPH_CS][0];
         A.gamma = gamma;
-        return run_cells<DensF64>(A, ncells, st);
+        return run_cells<DensF64>(A, ncells, pl, st);
     }
     DensF32::Args A;
     cm.tj = tile_or_default(tj, 1024);
@@ -1106,16 +1223,17 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
     A.P = (float *)soa.p[SPH_P][0];
     A.cs = (float *)soa.p[SPH_CS][0];
     A.gamma = (float)gamma;
-    return run_cells<DensF32>(A, ncells, st);
+    return run_cells<DensF32>(A, ncells, pl, st);
 }
 
 cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                               int ncells, int n, const Grid &g, const sph_params &prm, int tj, unsigned *status,
-                               Counters *counters, cudaStream_t st, int *nl)
+                               int ncells, int n, const CellSpace &g, const sph_params &prm, const PairLaunch &pl,
+                               unsigned *status, Counters *counters, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
     PairCommon cm{cell_start, g, status, counters, 0};
+    const int tj = pl.tj;
     if (!f32) {
         ForceF64::Args A;
         cm.tj = tile_or_default(tj, 384);
@@ -1145,7 +1263,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
         A.dudt = (double *)soa.p[SPH_DUDT][0];
         A.beta = prm.beta;
         A.eps = prm.eps;
-        return run_cells<ForceF64>(A, ncells, st);
+        return run_cells<ForceF64>(A, ncells, pl, st);
     }
     ForceF32::Args A;
     cm.tj = tile_or_default(tj, 512);
@@ -1170,7 +1288,20 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     A.alpha = (float)prm.alpha;
     A.beta = (float)prm.beta;
     A.eps = (float)prm.eps;
-    return run_cells<ForceF32>(A, ncells, st);
+    return run_cells<ForceF32>(A, ncells, pl, st);
+}
+
+cudaError_t launch_work_list(const CellSpace &cs, const int *cell_start, int ncells_cap, int *cell_bucket,
+                             int *bucket_count, int *work_order, int *work_count, cudaStream_t st, int *nl)
+{
+    cudaError_t e = cudaMemsetAsync(bucket_count, 0, 64 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (ncells_cap + 255) / 256 < 4096 ? (ncells_cap + 255) / 256 : 4096;
+    k_cell_cost<<<blocks, 256, 0, st>>>(cs, cell_start, cell_bucket, bucket_count);
+    k_work_offsets<<<1, 32, 0, st>>>(bucket_count, work_count);
+    k_work_place<<<blocks, 256, 0, st>>>(cs, cell_bucket, bucket_count, work_order);
+    *nl += 3;
+    return cudaGetLastError();
 }
 
 }  // namespace sphk

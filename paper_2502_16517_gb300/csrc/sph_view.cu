@@ -37,8 +37,16 @@ struct sph_view_s {
     sph_domain dom;
     cudaStream_t st;
     Grid g;
-    int ncells;
+    sphk::CellSpace cs;
+    int ncells;  // single grid: its cells; patch views: capacity
     size_t esz;
+
+    // patch views
+    int npatch_max, npatch, ncap;
+    const int64_t *patch_start;  // caller's device array of the last sph_patches_bin
+    int *patch_n, *patch_cells, *patch_cell_base;
+    double *patch_edge;  // 3 npatch_max edges, then 3 npatch_max inverses
+    int *cell_bucket, *bucket_count, *work_order, *work_count, *work_next;
 
     int64_t n;
     bool binned;
@@ -66,6 +74,7 @@ struct sph_view_s {
     std::vector<cudaEvent_t> *ev_free;
     std::vector<PendingTiming> *ev_pending;
     int tile_density, tile_force;  // staged particles per tile (0 = default)
+    int persistent_ctas;           // CTAs of the persistent pair launches (patch views; 0 = as many as fit)
 };
 
 namespace {
@@ -197,6 +206,18 @@ void carve(sph_view_s *v, Bump &b)
     v->perm_tmp = (int *)b.take(nm * 4);
     v->perm = (int *)b.take(nm * 4);
     v->cell_of_slot = (int *)b.take(nm * 4);
+    if (v->npatch_max > 0) {
+        const size_t np = (size_t)v->npatch_max;
+        v->patch_n = (int *)b.take(3 * np * 4);
+        v->patch_cells = (int *)b.take(np * 4);
+        v->patch_cell_base = (int *)b.take((np + 1) * 4);
+        v->patch_edge = (double *)b.take(6 * np * 8);
+        v->cell_bucket = (int *)b.take(nc * 4);
+        v->bucket_count = (int *)b.take(64 * 4);
+        v->work_order = (int *)b.take(nc * 4);
+        v->work_count = (int *)b.take(4);
+        v->work_next = (int *)b.take(4);
+    }
     v->status = (unsigned *)b.take(sizeof(unsigned));
     v->counters = (sphk::Counters *)b.take(sizeof(sphk::Counters));
     v->red_partials = (double *)b.take(1024 * 8 * sizeof(double));
@@ -266,6 +287,7 @@ sph_status drain_timings(sph_view_s *v)
 
 sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
 {
+    if (v->npatch_max > 0) return SPH_E_INVAL;  // patch views bin with sph_patches_bin
     if (!aos || n < 0 || n > v->n_max || !aos_aligned(aos, 8)) return SPH_E_INVAL;
     if (!(v->present & SPH_BIT(SPH_X))) return SPH_E_INVAL;
     cudaError_t e;
@@ -274,6 +296,50 @@ sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
         e = sphk::launch_bin(static_cast<const uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X], (int)n, v->g,
                              v->ncells, v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
                              v->cell_of_slot, v->status, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->n = n;
+    v->binned = true;
+    v->resident = 0;
+    return SPH_OK;
+}
+
+sphk::PairLaunch pair_launch(const sph_view_s *v, int tj)
+{
+    sphk::PairLaunch pl;
+    pl.tj = tj;
+    pl.threads = 0;
+    pl.work_order = v->npatch_max > 0 ? v->work_order : nullptr;
+    pl.work_count = v->work_count;
+    pl.work_next = v->work_next;
+    pl.persistent_ctas = v->persistent_ctas;
+    return pl;
+}
+
+sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64_t *patch_start, int npatch)
+{
+    if (v->npatch_max <= 0) return SPH_E_INVAL;  // not a patch view
+    if (!aos || !patch_start || n < 0 || n > v->n_max || !aos_aligned(aos, 8)) return SPH_E_INVAL;
+    if (!aos_aligned(patch_start, 8) || npatch < 1 || npatch > v->npatch_max) return SPH_E_INVAL;
+    if (!(v->present & SPH_BIT(SPH_X)) || !(v->present & SPH_BIT(SPH_H))) return SPH_E_INVAL;
+    v->npatch = npatch;
+    v->patch_start = patch_start;
+    v->cs.npatch = npatch;
+    v->cs.patch_cell_base = v->patch_cell_base;
+    v->cs.patch_n = v->patch_n;
+    v->cs.patch_edge = v->patch_edge;
+    v->cs.ncells_dev = v->patch_cell_base + npatch;
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_BIN);
+        e = sphk::launch_bin_patches(static_cast<const uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X],
+                                     v->layout.off[SPH_H], (int)n, patch_start, npatch, v->g, v->ncap, v->ncells,
+                                     v->patch_n, v->patch_edge, v->patch_cells, v->patch_cell_base,
+                                     v->patch_cell_base + npatch, v->cell_of, v->count, v->cell_start, v->fill,
+                                     v->perm_tmp, v->perm, v->cell_of_slot, v->status, v->st, &ph.nl);
+        if (e == cudaSuccess)
+            e = sphk::launch_work_list(v->cs, v->cell_start, v->ncells, v->cell_bucket, v->bucket_count,
+                                       v->work_order, v->work_count, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->n = n;
@@ -294,7 +360,7 @@ sph_status do_gather(sph_view_s *v, const void *aos, int64_t n, uint32_t mask)
     {
         Phase ph(v, SPH_PH_GATHER);
         e = sphk::launch_gather(static_cast<const uint8_t *>(aos), v->layout.stride, vec16, v->perm, v->cell_of_slot,
-                                (int)n, plan, v->g, v->prec == SPH_F32, v->st, &ph.nl);
+                                (int)n, plan, v->cs, v->prec == SPH_F32, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->resident |= mask;
@@ -313,7 +379,7 @@ sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask)
     {
         Phase ph(v, SPH_PH_SCATTER);
         e = sphk::launch_scatter(static_cast<uint8_t *>(aos), v->layout.stride, v->perm, v->cell_of_slot, (int)n,
-                                 plan, v->g, v->prec == SPH_F32, v->st, &ph.nl);
+                                 plan, v->cs, v->prec == SPH_F32, v->st, &ph.nl);
     }
     return cuda_fail(e);
 }
@@ -327,13 +393,13 @@ sph_status do_density(sph_view_s *v, const sph_params *p)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_DENSITY_PREP);
-        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, v->st, &ph.nl);
+        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_DENSITY);
-        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->g, p->gamma,
-                                       v->tile_density, v->status, v->counters, v->st, &ph.nl);
+        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, p->gamma,
+                                       pair_launch(v, v->tile_density), v->status, v->counters, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->resident |= SPH_DENSITY_OUT;
@@ -349,13 +415,13 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_FORCE_PREP);
-        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->g, p->alpha, v->st, &ph.nl);
+        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, p->alpha, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_FORCE);
-        e = sphk::launch_force_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->g, *p,
-                                     v->tile_force, v->status, v->counters, v->st, &ph.nl);
+        e = sphk::launch_force_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, *p,
+                                     pair_launch(v, v->tile_force), v->status, v->counters, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->resident |= SPH_FORCE_OUT;
@@ -365,7 +431,11 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
 sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
 {
     sph_status s;
-    if ((s = do_bin(v, aos, n)) != SPH_OK) return s;
+    if (v->npatch_max > 0) {
+        if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch)) != SPH_OK) return s;
+    } else if ((s = do_bin(v, aos, n)) != SPH_OK) {
+        return s;
+    }
     if ((s = do_gather(v, aos, n, SPH_DENSITY_IN)) != SPH_OK) return s;
     if ((s = do_density(v, p)) != SPH_OK) return s;
     if ((s = do_scatter(v, aos, n, SPH_DENSITY_OUT)) != SPH_OK) return s;
@@ -468,6 +538,8 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     v->dom = *domain;
     v->st = static_cast<cudaStream_t>(cuda_stream);
     v->g = make_grid(*domain);
+    v->cs.g = v->g;
+    v->cs.npatch = 0;
     v->ncells = domain->ncell[0] * domain->ncell[1] * domain->ncell[2];
     v->esz = prec == SPH_F64 ? 8 : 4;
     v->present = present;
@@ -503,6 +575,94 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     }
     *out = v;
     return SPH_OK;
+}
+
+sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n_max, int32_t npatch_max,
+                              const double patch_box[3], int32_t ncell_cap, void *cuda_stream, sph_view *out)
+{
+    if (!out || !patch_box) return SPH_E_INVAL;
+    *out = nullptr;
+    if (npatch_max < 1 || npatch_max > (1 << 24) || ncell_cap < 1 || ncell_cap > 64) return SPH_E_INVAL;
+    const int64_t cells = (int64_t)npatch_max * ncell_cap * ncell_cap * ncell_cap;
+    if (cells > (int64_t(1) << 27)) return SPH_E_INVAL;
+    uint32_t present = 0;
+    if (!layout_valid(layout, &present)) return SPH_E_INVAL;
+    if (prec != SPH_F64 && prec != SPH_F32) return SPH_E_INVAL;
+    if (n_max < 0 || n_max > 0x7fffffffLL) return SPH_E_INVAL;
+    sph_domain dom;
+    for (int a = 0; a < 3; ++a) {
+        if (!(patch_box[a] > 0.0) || !(patch_box[a] < 1e300)) return SPH_E_INVAL;
+        dom.box[a] = patch_box[a];
+        dom.ncell[a] = 1;
+    }
+    dom.periodic = 0;
+    sph_view_s *v = new (std::nothrow) sph_view_s;
+    if (!v) return SPH_E_NOMEM;
+    memset(v, 0, sizeof(*v));
+    v->layout = *layout;
+    v->prec = prec;
+    v->n_max = n_max;
+    v->dom = dom;
+    v->st = static_cast<cudaStream_t>(cuda_stream);
+    v->g = make_grid(dom);
+    v->g.min_edge = 1e308;  // patch grids are sized so that every cell edge is at least 2 h_max of its patch
+    v->cs.g = v->g;
+    v->cs.npatch = 0;
+    v->npatch_max = npatch_max;
+    v->ncap = ncell_cap;
+    v->ncells = (int)std::max<int64_t>(cells, npatch_max);
+    v->esz = prec == SPH_F64 ? 8 : 4;
+    v->present = present;
+    v->persistent_ctas = 0;  // sized from the pair kernels' occupancy at launch
+    v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
+    v->ev_pending = new (std::nothrow) std::vector<PendingTiming>();
+    if (!v->ev_free || !v->ev_pending) {
+        delete v->ev_free;
+        delete v->ev_pending;
+        delete v;
+        return SPH_E_NOMEM;
+    }
+    Bump sizing;
+    carve(v, sizing);
+    if (cudaMalloc(&v->arena, sizing.off) != cudaSuccess) {
+        v->arena = nullptr;
+        sph_view_destroy(v);
+        return SPH_E_NOMEM;
+    }
+    Bump real;
+    real.base = static_cast<char *>(v->arena);
+    carve(v, real);
+    if (cudaMallocHost(&v->h_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&v->h_red, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess) {
+        sph_view_destroy(v);
+        return SPH_E_NOMEM;
+    }
+    if (cudaMemsetAsync(v->status, 0, sizeof(unsigned), v->st) != cudaSuccess ||
+        cudaMemsetAsync(v->counters, 0, sizeof(sphk::Counters), v->st) != cudaSuccess ||
+        cudaStreamSynchronize(v->st) != cudaSuccess) {
+        sph_view_destroy(v);
+        return SPH_E_CUDA;
+    }
+    *out = v;
+    return SPH_OK;
+}
+
+sph_status sph_patches_bin(sph_view v, const void *aos_dev, int64_t n, const int64_t *patch_start_dev,
+                           int32_t npatch)
+{
+    if (!v) return SPH_E_INVAL;
+    return do_bin_patches(v, aos_dev, n, patch_start_dev, npatch);
+}
+
+sph_status sph_patches_step(sph_view v, void *aos_dev, int64_t n, const int64_t *patch_start_dev, int32_t npatch,
+                            const sph_params *params, double *stats_out)
+{
+    if (!v) return SPH_E_INVAL;
+    if (v->npatch_max <= 0 || !patch_start_dev || npatch < 1 || npatch > v->npatch_max) return SPH_E_INVAL;
+    v->patch_start = patch_start_dev;
+    v->npatch = npatch;
+    return do_step(v, aos_dev, n, params, 0.0, 0, stats_out);
 }
 
 sph_status sph_view_destroy(sph_view v)

@@ -90,6 +90,10 @@ _SIGS = {
     "sph_view_timing": [_VP, _I32],
     "sph_view_phase_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
     "sph_probe_fma_rate": [_I32, ctypes.POINTER(ctypes.c_double)],
+    "sph_patches_create": [ctypes.POINTER(sph_layout), ctypes.c_int, _I64, _I32, ctypes.POINTER(ctypes.c_double), _I32,
+                           _VP, ctypes.POINTER(_VP)],
+    "sph_patches_bin": [_VP, _VP, _I64, _VP, _I32],
+    "sph_patches_step": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params), ctypes.POINTER(ctypes.c_double)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
 EXPORTED = tuple(_SIGS) + ("sph_strerror",)
@@ -291,3 +295,26 @@ def sph_probe_fma_rate(prec):
     out = ctypes.c_double()
     _check("sph_probe_fma_rate", lib().sph_probe_fma_rate(int(prec), ctypes.byref(out)))
     return out.value
+
+
+def sph_patches_create(layout, prec, n_max, npatch_max, patch_box, ncell_cap=8, stream=None):
+    """View over independent open-box patches; returns the handle."""
+    L = layout if isinstance(layout, sph_layout) else make_layout(layout)
+    box = (ctypes.c_double * 3)(*[float(b) for b in patch_box])
+    out = _VP()
+    st = _addr(stream) if stream is not None else None
+    _check("sph_patches_create", lib().sph_patches_create(ctypes.byref(L), int(prec), int(n_max), int(npatch_max), box,
+                                                          int(ncell_cap), st, ctypes.byref(out)))
+    return out.value
+
+
+def sph_patches_bin(view, aos_dev, n, patch_start_dev, npatch):
+    _check("sph_patches_bin", lib().sph_patches_bin(view, _addr(aos_dev), int(n), _addr(patch_start_dev), int(npatch)))
+
+
+def sph_patches_step(view, aos_dev, n, patch_start_dev, npatch, params, want_stats=False):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    stats = (ctypes.c_double * 8)() if want_stats else None
+    _check("sph_patches_step", lib().sph_patches_step(view, _addr(aos_dev), int(n), _addr(patch_start_dev), int(npatch),
+                                                      ctypes.byref(P), stats))
+    return np.array(stats[:]) if want_stats else None

@@ -139,11 +139,13 @@ def patches(npatch, lam_lo=8.0, lam_hi=256.0, hfac=1.2, hmax=0.5, u0=1.0, vel_si
     }
 
 
-def pack_aos(fields, layout=None, order="shuffled", seed=SEED + 1, canary=True):
+def pack_aos(fields, layout=None, order="shuffled", seed=SEED + 1, canary=True, segments=None):
     """Write the fields into records: a uint8 array [n, stride].
 
     order: "shuffled" puts particle k at a seeded random record (heap-scattered AoS, the paper's pointer-indexed
-    storage), "given" keeps particle k at record k.  Returns (aos, where) with where[k] = record of particle k.
+    storage), "given" keeps particle k at record k.  With segments (ascending offsets, e.g. patch_start) the
+    shuffle stays inside each segment, so every patch keeps a contiguous range of records.
+    Returns (aos, where) with where[k] = record of particle k.
     Bytes outside the given fields (a, rho, P, dudt, cs, admin fields, padding) are random canary bytes when
     canary is set, else zero; the id field (when inside the default layout) holds the particle index."""
     layout = layout or default_layout()
@@ -155,7 +157,15 @@ def pack_aos(fields, layout=None, order="shuffled", seed=SEED + 1, canary=True):
         aos = rng.integers(0, 256, size=(n, stride), dtype=np.uint8)
     else:
         aos = np.zeros((n, stride), np.uint8)
-    where = rng.permutation(n) if order == "shuffled" else np.arange(n)
+    if order != "shuffled":
+        where = np.arange(n)
+    elif segments is None:
+        where = rng.permutation(n)
+    else:
+        seg = np.asarray(segments, np.int64)
+        where = np.arange(n)
+        for a, b in zip(seg[:-1], seg[1:]):
+            where[a:b] = a + rng.permutation(int(b - a))
     rec = np.empty_like(aos)
     rec[:] = aos
     for name in FIELDS:

@@ -111,3 +111,16 @@ def test_create_accepts_open_small_grid_layout_validation_only(sph):
     # the host-side checks are exercised here (no GPU in this process means the allocation reports an error).
     st = _create(sph, _lay(), ncell=(1, 2, 1), periodic=False)
     assert st in (sph.SPH_OK, sph.SPH_E_NOMEM, sph.SPH_E_CUDA)
+
+
+@pytest.mark.parametrize("kw", [{"npatch_max": 0}, {"ncell_cap": 0}, {"ncell_cap": 65}, {"box": (3, 0, 3)},
+                                {"npatch_max": 1 << 20, "ncell_cap": 64}])
+def test_patches_create_rejects_bad_arguments(sph, kw):
+    args = {"npatch_max": 4, "ncell_cap": 8, "box": (3, 3, 3)}
+    args.update(kw)
+    L = sph.make_layout(_lay())
+    box = (ctypes.c_double * 3)(*args["box"])
+    out = ctypes.c_void_p()
+    st = sph.lib().sph_patches_create(ctypes.byref(L), 0, 100, args["npatch_max"], box, args["ncell_cap"], None,
+                                      ctypes.byref(out))
+    assert st == sph.SPH_E_INVAL and not out.value

@@ -383,3 +383,67 @@ def test_fp32_position_round_trip_within_float_rounding(oracle):
     changed = np.any(out != aos, axis=0)
     o = lay["offsets"]["x"]
     assert not changed[:o].any() and not changed[o + 24:].any()
+
+
+# --------------------------------------------------------------------------------------------------------
+# Patches (independent open boxes)
+# --------------------------------------------------------------------------------------------------------
+def test_patch_grids_respect_interaction_radius(oracle):
+    f = wl.patches(12, lam_lo=8, lam_hi=80, seed=3)
+    r = oracle.bin_patches(f["x"], f["h"], f["patch_start"], f["box"], 8)
+    ps = f["patch_start"]
+    for p in range(12):
+        hm = f["h"][ps[p]:ps[p + 1]].max()
+        for d in range(3):
+            nn = r["patch_n"][p, d]
+            edge = f["box"][d] / nn
+            assert edge >= 2 * hm                       # every pair within 2h lies in neighbouring cells
+            assert nn == 8 or nn + 1 > f["box"][d] / (2 * hm)   # and the grid is the finest that allows it
+    # stable cell-major order; every slot's cell contains its position
+    n = f["h"].size
+    assert np.array_equal(np.sort(r["perm"]), np.arange(n))
+    for c in range(r["ncells"]):
+        seg = r["perm"][r["cell_start"][c]:r["cell_start"][c + 1]]
+        assert np.all(np.diff(seg) > 0)
+        assert np.all(r["cell_of"][seg] == c)
+    # cells never mix patches
+    patch_of = np.searchsorted(ps, np.arange(n), side="right") - 1
+    patch_of_cell = np.searchsorted(r["patch_cell_base"], r["cell_of"], side="right") - 1
+    assert np.array_equal(patch_of, patch_of_cell)
+
+
+def test_patches_do_not_interact(oracle):
+    # two copies of one patch side by side give identical results; a patch with one particle gives m W(0, h)
+    rng = np.random.default_rng(4)
+    k = 300
+    x = rng.uniform(0, 3, size=(k, 3))
+    fields = {"x": np.concatenate([x, x, [[1.5, 1.5, 1.5]]]), "v": rng.normal(0, 0.2, size=(2 * k + 1, 3)),
+              "mass": np.full(2 * k + 1, 0.01), "h": np.full(2 * k + 1, 0.3), "u": np.ones(2 * k + 1)}
+    fields["v"][k:2 * k] = fields["v"][:k]
+    lay = wl.default_layout()
+    aos, _ = wl.pack_aos(fields, lay, order="given")
+    ps = np.array([0, k, 2 * k, 2 * k + 1])
+    out = oracle.step_patches(aos, lay, ps, np.full(3, 3.0), wl.SPH_PARAMS)
+    for key in ("rho", "P", "cs", "dudt"):
+        np.testing.assert_array_equal(out[key][:k], out[key][k:2 * k])
+    np.testing.assert_array_equal(out["a"][:k], out["a"][k:2 * k])
+    assert out["rho"][-1] == pytest.approx(0.01 / (PI * 0.3 ** 3), rel=1e-15)
+    assert np.all(out["a"][-1] == 0.0)
+
+
+def test_patch_fp32_positions_round_trip(oracle):
+    f = wl.patches(5, lam_lo=10, lam_hi=40, seed=6)
+    lay = wl.default_layout()
+    aos, _ = wl.pack_aos(f, lay, order="given")
+    r = oracle.bin_patches(f["x"], f["h"], f["patch_start"], f["box"], 8)
+    rel = oracle.gather_pos_f32_patches(aos, lay["stride"], r["perm"], lay["offsets"]["x"], r["cell_of_slot"],
+                                        r["patch_cell_base"], r["patch_n"], f["box"])
+    x = f["x"][r["perm"]]
+    patch_of_cell = np.searchsorted(r["patch_cell_base"], r["cell_of_slot"], side="right") - 1
+    edge = f["box"][None, :] / r["patch_n"][patch_of_cell]
+    assert np.all(rel.T >= 0) and np.all(rel.T <= edge.astype(np.float32))
+    local = r["cell_of_slot"] - r["patch_cell_base"][patch_of_cell]
+    nn = r["patch_n"][patch_of_cell]
+    k = np.stack([local % nn[:, 0], (local // nn[:, 0]) % nn[:, 1], local // (nn[:, 0] * nn[:, 1])], axis=1)
+    back = k * edge + rel.T.astype(np.float64)
+    assert np.all(np.abs(back - x) <= edge * 2.0 ** -24 + 1e-16)
