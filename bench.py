@@ -69,7 +69,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
@@ -120,16 +120,20 @@ def _inputs():
     return f, lay, aos_h, ncell
 
 
-def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None):
+def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None):
     import torch
-    from paper_2502_16517_gb300 import sph
+    from paper_2502_16517_gb300 import autotune, sph
     from paper_2502_16517_gb300 import workloads as wl
     n = aos_h.shape[0]
     aos = torch.from_numpy(aos_h).to(dev)
     stream = torch.cuda.current_stream(dev)
     view = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
+    tiles = None
     try:
+        if tune_cache:
+            key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, "grid", n / float(np.prod(ncell)))
+            tiles = autotune.tuned_tiles(view, aos, n, wl.SPH_PARAMS, key, tune_cache)
         for _ in range(max(warmup, 0)):
             flush.zero_()
             sph.sph_step(view, aos, n, wl.SPH_PARAMS)
@@ -167,8 +171,70 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None):
         sph.sph_view_destroy(view)
     return {
         "step_ms": step_ms, "wall_s": wall, "counts": counts, "phase_ms": phase_ms, "launches": launches,
-        "clocks": sampler.summary() if sampler else None,
+        "clocks": sampler.summary() if sampler else None, "tiles": tiles,
     }
+
+
+def batched_inputs():
+    """The batched workload: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8, 256)) particles per cell
+    (records grouped by patch, scattered inside each patch)."""
+    from paper_2502_16517_gb300 import workloads as wl
+    fp = wl.patches(4096, seed=wl.SEED)
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(fp, lay, order="shuffled", segments=fp["patch_start"], canary=False)
+    return fp, lay, aos_h
+
+
+def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=8):
+    """Graph-captured steps over all patches (one graph launch per step); per-phase times from one extra
+    un-captured step with event timing."""
+    import torch
+    from paper_2502_16517_gb300 import autotune, sph
+    from paper_2502_16517_gb300 import workloads as wl
+    n = aos_h.shape[0]
+    npatch = len(fp["patch_start"]) - 1
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        aos = torch.from_numpy(aos_h).to(dev)
+        ps = torch.tensor(fp["patch_start"], dtype=torch.int64, device=dev)
+        view = sph.sph_patches_create(lay, prec, n, npatch, fp["box"], ncap, stream.cuda_stream)
+        try:
+            sph.sph_patches_bin(view, aos, n, ps, npatch)
+            tiles = None
+            if tune_cache:
+                key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, "patches", float(fp["lam"].mean()))
+                tiles = autotune.tuned_tiles(view, aos, n, wl.SPH_PARAMS, key, tune_cache)
+            for _ in range(max(warmup, 1)):
+                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+            sph.sph_view_sync(view)
+            sph.sph_pair_counts(view, reset=True)
+            sph.sph_view_phase_times(view, reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize(dev)
+            for k in range(steps):
+                ev[k][0].record(stream)
+                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            sph.sph_view_sync(view)
+            step_ms = [a.elapsed_time(b) for a, b in ev]
+            counts = sph.sph_pair_counts(view, reset=True)
+            _, launches = sph.sph_view_phase_times(view, reset=True)
+            # phase breakdown (outside the timed region)
+            sph.sph_view_timing(view, True)
+            sph.sph_patches_step(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+            phase_ms, _ = sph.sph_view_phase_times(view, reset=True)
+            sph.sph_view_timing(view, False)
+            sph.sph_view_sync(view)
+        finally:
+            sph.sph_view_destroy(view)
+    ms = float(np.sum(step_ms))
+    pairs_step = (counts[1] + counts[2]) / steps
+    return {"value": pairs_step * steps / (ms / 1e3), "ms_per_step": ms / steps, "pairs_per_step": pairs_step,
+            "particles": int(n), "patches": int(npatch),
+            "phases_ms": {nm: float(phase_ms[i]) for i, nm in enumerate(sph.PHASE_NAMES)},
+            "gpu_launches": int(launches.sum()), "tiles": tiles, "dtype": "f64" if prec == 0 else "f32",
+            "graph": "one CUDA graph launch per step (bin, work list, gathers, density, force, scatters)"}
 
 
 def run_e2e(prec, steps, warmup, dev, aos_h, lay, box, ncell):
@@ -328,6 +394,8 @@ def main():
     ap.add_argument("--ref-block", type=int, default=4, help="oracle sample cube per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tiles (no autotuning)")
+    ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the batched (patches) forms")
     ap.add_argument("--only", choices=["f64", "f32"], default=None,
                     help="run one form only (profiling runs); the JSON line then carries that form's numbers")
     args = ap.parse_args()
@@ -350,11 +418,26 @@ def main():
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if \
         os.environ.get("CUDA_VISIBLE_DEVICES") else local
 
+    import tempfile
+    tune_cache = os.path.join(tempfile.mkdtemp(prefix="sph_tiles_"), "tiles.json") if not args.no_tune else None
     forms = ["f64", "f32"] if args.only is None else [args.only]
     runs = {}
-    for k, form in enumerate(forms):
-        runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
-                              clocks_gpu=gpu_index if k == 0 else None)
+    sampler = ClockSampler(gpu_index)
+    sampler.__enter__()
+    try:
+        for k, form in enumerate(forms):
+            runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
+                                  tune_cache=tune_cache)
+        batched = {}
+        if args.batched and args.only is None:
+            fp, lay_b, aos_b = batched_inputs()
+            for form in ("f32", "f64"):
+                batched[form] = run_batched(0 if form == "f64" else 1, max(steps // 3, 3), 2, dev, fp, lay_b, aos_b,
+                                            tune_cache=tune_cache)
+            del aos_b
+    finally:
+        sampler.__exit__(None, None, None)
+    clocks = sampler.summary()
     # max over ranks of the summed step time
     tot = torch.tensor([float(np.sum(runs[fm]["step_ms"])) for fm in forms], device=dev)
     if world > 1:
@@ -400,18 +483,29 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(s64["launches"].values())),
-        "clocks": r64["clocks"],
+        "clocks": clocks,
+        "tiles": r64["tiles"],
         "phases_ms_per_step": s64["phases_ms_per_step"],
         "pairs_per_step": s64["pairs_per_step"],
         "candidates_per_step": s64["candidates_per_step"],
         "conversion": conv,
-        "forms": {} if s32 is None else {"f32": {
+        "forms": {},
+        "wall_s_timed_bracket": r64["wall_s"],
+    }
+    if s32 is not None:
+        line["forms"]["f32"] = {
+            "workload": "FP32 precision form: the same 262,144-particle input, FP32 views, Kahan sums",
             "value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
             "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
-            "gpu_launches": int(sum(s32["launches"].values()))}},
-        "wall_s_timed_bracket": r64["wall_s"],
-    }
+            "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"]}
+    for form, b in batched.items():
+        b = dict(b)
+        b["workload"] = ("batched form: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8,256)) per cell, "
+                         f"{b['particles']} particles, inputs larger than L2 (no flush)")
+        b["value"] *= world
+        b["speedup_vs_plain_f64"] = b["value"] / s64["value"]
+        line["forms"][f"batched_{form}"] = b
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -143,6 +143,28 @@ SPH_API sph_status sph_patches_bin(sph_view view, const void *aos_dev, int64_t n
 SPH_API sph_status sph_patches_step(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
                                     int32_t npatch, const sph_params *params, double *stats_out);
 
+/* sph_step / sph_patches_step through a CUDA graph.  A call with a new argument set (aos_dev, n, params, dt,
+ * nsteps, patch_start_dev, npatch) runs the step normally, then captures the same launch sequence into a graph;
+ * a call repeating the previous argument set replays that graph (one launch for the whole step).  The records'
+ * contents may change between calls; the pointers and sizes may not without a new capture.  The view's stream
+ * must not be the legacy default stream (SPH_E_INVAL).  Per-phase event timing is not recorded in replays.  Not
+ * on patch views (sph_step_graph) / only on patch views (sph_patches_step_graph). */
+SPH_API sph_status sph_step_graph(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt,
+                                  int32_t nsteps);
+SPH_API sph_status sph_patches_step_graph(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
+                                          int32_t npatch, const sph_params *params);
+
+/* Staged particles per shared-memory tile of the density and force pair loops (multiples of 64; 0 = the
+ * defaults).  Larger tiles stage more neighbours per barrier, smaller ones leave room for more CTAs per SM. */
+SPH_API sph_status sph_view_set_tiles(sph_view view, int32_t tile_density, int32_t tile_force);
+
+/* Autotuner: runs one pass on the records (as sph_step / sph_patches_step with the last bin's arguments would,
+ * leaving the same outputs in the records), then times the density and the force pair loops at each candidate
+ * tile size on this data and keeps the fastest of each in the view.  chosen (may be NULL) receives the two tile
+ * sizes, best_ms (may be NULL) their kernel times.  Waits.  For a patch view, call sph_patches_bin first. */
+SPH_API sph_status sph_autotune(sph_view view, void *aos_dev, int64_t n, const sph_params *params, int32_t chosen[2],
+                                float best_ms[2]);
+
 /* Wait for the view's stream, free everything the view allocated.  NULL is accepted. */
 SPH_API sph_status sph_view_destroy(sph_view view);
 

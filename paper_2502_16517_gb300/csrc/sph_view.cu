@@ -74,6 +74,18 @@ struct sph_view_s {
     std::vector<cudaEvent_t> *ev_free;
     std::vector<PendingTiming> *ev_pending;
     int tile_density, tile_force;  // staged particles per tile (0 = default)
+
+    // graph-captured step: the arguments it was captured for, the executable graph, its kernel launches
+    bool graph_valid;
+    void *g_aos;
+    int64_t g_n;
+    sph_params g_p;
+    double g_dt;
+    int32_t g_nsteps;
+    const int64_t *g_ps;
+    int32_t g_npatch;
+    cudaGraphExec_t g_exec;
+    int64_t g_launches[SPH_NPHASES];
     int persistent_ctas;           // CTAs of the persistent pair launches (patch views; 0 = as many as fit)
 };
 
@@ -516,9 +528,173 @@ sph_status do_step(sph_view_s *v, void *aos, int64_t n, const sph_params *p, dou
     return SPH_OK;
 }
 
+void graph_drop(sph_view_s *v)
+{
+    if (v->graph_valid && v->g_exec) cudaGraphExecDestroy(v->g_exec);
+    v->g_exec = nullptr;
+    v->graph_valid = false;
+}
+
+// One step through a CUDA graph: on a new argument set, run the step normally (this call's result), then capture
+// the same sequence into a graph; on a repeated argument set, replay the graph.  The host-side view state after a
+// replay is the state the captured run left.
+sph_status do_step_graph(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double dt, int32_t nsteps)
+{
+    if (!p || !aos) return SPH_E_INVAL;
+    if (v->st == nullptr) return SPH_E_INVAL;  // the legacy default stream cannot be captured
+    const bool same = v->graph_valid && v->g_aos == aos && v->g_n == n && memcmp(&v->g_p, p, sizeof(*p)) == 0 &&
+                      v->g_dt == dt && v->g_nsteps == nsteps && v->g_ps == v->patch_start &&
+                      v->g_npatch == v->npatch;
+    if (same) {
+        if (cudaGraphLaunch(v->g_exec, v->st) != cudaSuccess) return SPH_E_CUDA;
+        for (int k = 0; k < SPH_NPHASES; ++k) v->launches[k] += v->g_launches[k];
+        return SPH_OK;
+    }
+    graph_drop(v);
+    sph_status s = do_step(v, aos, n, p, dt, nsteps, nullptr);  // this call's step, uncaptured
+    if (s != SPH_OK) return s;
+    const bool timing = v->timing;
+    v->timing = false;  // no event nodes in the graph
+    int64_t before[SPH_NPHASES];
+    memcpy(before, v->launches, sizeof(before));
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(v->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        v->timing = timing;
+        return SPH_E_CUDA;
+    }
+    s = do_step(v, aos, n, p, dt, nsteps, nullptr);
+    const cudaError_t ec = cudaStreamEndCapture(v->st, &graph);
+    v->timing = timing;
+    for (int k = 0; k < SPH_NPHASES; ++k) {
+        v->g_launches[k] = v->launches[k] - before[k];
+        v->launches[k] = before[k];  // captured, not executed
+    }
+    if (s != SPH_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        return s != SPH_OK ? s : SPH_E_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&v->g_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        v->g_exec = nullptr;
+        return SPH_E_CUDA;
+    }
+    v->graph_valid = true;
+    v->g_aos = aos;
+    v->g_n = n;
+    v->g_p = *p;
+    v->g_dt = dt;
+    v->g_nsteps = nsteps;
+    v->g_ps = v->patch_start;
+    v->g_npatch = v->npatch;
+    return SPH_OK;
+}
+
+// Median-free minimum of a few timed repetitions of one pair loop at one tile size.
+float time_loop(sph_view_s *v, const sph_params *p, bool force, int tj, int reps, cudaEvent_t e0, cudaEvent_t e1)
+{
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        if (force) v->tile_force = tj; else v->tile_density = tj;
+        cudaEventRecord(e0, v->st);
+        const sph_status s = force ? do_force(v, p) : do_density(v, p);
+        cudaEventRecord(e1, v->st);
+        if (s != SPH_OK || cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best) best = ms;  // the first repetition warms up
+    }
+    return best;
+}
+
 }  // namespace
 
 extern "C" {
+
+sph_status sph_step_graph(sph_view v, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps)
+{
+    if (!v || v->npatch_max > 0) return SPH_E_INVAL;
+    return do_step_graph(v, aos_dev, n, params, dt, nsteps);
+}
+
+sph_status sph_patches_step_graph(sph_view v, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
+                                  int32_t npatch, const sph_params *params)
+{
+    if (!v || v->npatch_max <= 0 || !patch_start_dev || npatch < 1 || npatch > v->npatch_max) return SPH_E_INVAL;
+    v->patch_start = patch_start_dev;
+    v->npatch = npatch;
+    return do_step_graph(v, aos_dev, n, params, 0.0, 0);
+}
+
+sph_status sph_view_set_tiles(sph_view v, int32_t tile_density, int32_t tile_force)
+{
+    if (!v || tile_density < 0 || tile_force < 0 || tile_density > 4096 || tile_force > 4096) return SPH_E_INVAL;
+    if (tile_density % 64 != 0 || tile_force % 64 != 0) return SPH_E_INVAL;
+    const size_t esz = v->esz;
+    // shared memory per staged particle of each loop (FP64: 49 / 141 bytes, FP32: 16 / 56 bytes)
+    const size_t dens_b = esz == 8 ? 49 : 16, force_b = esz == 8 ? 141 : 56;
+    if (tile_density * dens_b > 200 * 1024 || tile_force * force_b > 200 * 1024) return SPH_E_INVAL;
+    v->tile_density = tile_density;
+    v->tile_force = tile_force;
+    graph_drop(v);
+    return SPH_OK;
+}
+
+sph_status sph_autotune(sph_view v, void *aos_dev, int64_t n, const sph_params *params, int32_t chosen[2],
+                        float best_ms[2])
+{
+    if (!v || !params || !aos_dev) return SPH_E_INVAL;
+    // a full pass first: every member the loops read becomes resident (the records get this pass's outputs)
+    sph_status s = do_pass(v, aos_dev, n, params);
+    if (s != SPH_OK) return s;
+    static const int cand_d64[] = {256, 384, 512, 768, 1024, 1536};
+    static const int cand_f64[] = {128, 192, 256, 384, 512, 768};
+    static const int cand_d32[] = {256, 512, 1024, 2048, 4096};
+    static const int cand_f32[] = {256, 384, 512, 1024, 2048};
+    const bool f32 = v->prec == SPH_F32;
+    const int *cd = f32 ? cand_d32 : cand_d64;
+    const int *cf = f32 ? cand_f32 : cand_f64;
+    const int nd = f32 ? 5 : 6, nf = f32 ? 5 : 6;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool timing = v->timing;
+    v->timing = false;
+    int bd = 0, bf = 0;
+    float td = 1e30f, tf = 1e30f;
+    for (int k = 0; k < nd; ++k) {
+        const float t = time_loop(v, params, false, cd[k], 4, e0, e1);
+        if (t < td) {
+            td = t;
+            bd = cd[k];
+        }
+    }
+    v->tile_density = bd;
+    for (int k = 0; k < nf; ++k) {
+        const float t = time_loop(v, params, true, cf[k], 4, e0, e1);
+        if (t < tf) {
+            tf = t;
+            bf = cf[k];
+        }
+    }
+    v->tile_force = bf;
+    v->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    graph_drop(v);
+    if (bd == 0 || bf == 0) return SPH_E_CUDA;
+    // leave the records as one pass leaves them: the timed loops rewrote only SoA members, so scatter them again
+    if ((s = do_scatter(v, aos_dev, n, SPH_FORCE_OUT)) != SPH_OK) return s;
+    if (chosen) {
+        chosen[0] = bd;
+        chosen[1] = bf;
+    }
+    if (best_ms) {
+        best_ms[0] = td;
+        best_ms[1] = tf;
+    }
+    return sph_view_sync(v);
+}
 
 sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_max, const sph_domain *domain,
                            void *cuda_stream, sph_view *out)
@@ -674,6 +850,7 @@ sph_status sph_view_destroy(sph_view v)
     if (v->h_status) cudaFreeHost(v->h_status);
     if (v->h_red) cudaFreeHost(v->h_red);
     if (v->h_counters) cudaFreeHost(v->h_counters);
+    graph_drop(v);
     if (v->ev_pending) {
         for (const PendingTiming &p : *v->ev_pending) {
             cudaEventDestroy(p.e0);

@@ -94,6 +94,10 @@ _SIGS = {
                            _VP, ctypes.POINTER(_VP)],
     "sph_patches_bin": [_VP, _VP, _I64, _VP, _I32],
     "sph_patches_step": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params), ctypes.POINTER(ctypes.c_double)],
+    "sph_step_graph": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.c_double, _I32],
+    "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
+    "sph_view_set_tiles": [_VP, _I32, _I32],
+    "sph_autotune": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
 EXPORTED = tuple(_SIGS) + ("sph_strerror",)
@@ -318,3 +322,27 @@ def sph_patches_step(view, aos_dev, n, patch_start_dev, npatch, params, want_sta
     _check("sph_patches_step", lib().sph_patches_step(view, _addr(aos_dev), int(n), _addr(patch_start_dev), int(npatch),
                                                       ctypes.byref(P), stats))
     return np.array(stats[:]) if want_stats else None
+
+
+def sph_step_graph(view, aos_dev, n, params, dt=0.0, nsteps=0):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    _check("sph_step_graph", lib().sph_step_graph(view, _addr(aos_dev), int(n), ctypes.byref(P), float(dt), int(nsteps)))
+
+
+def sph_patches_step_graph(view, aos_dev, n, patch_start_dev, npatch, params):
+    P = params if isinstance(params, sph_params) else make_params(params)
+    _check("sph_patches_step_graph", lib().sph_patches_step_graph(view, _addr(aos_dev), int(n), _addr(patch_start_dev),
+                                                                  int(npatch), ctypes.byref(P)))
+
+
+def sph_view_set_tiles(view, tile_density, tile_force):
+    _check("sph_view_set_tiles", lib().sph_view_set_tiles(view, int(tile_density), int(tile_force)))
+
+
+def sph_autotune(view, aos_dev, n, params):
+    """Returns ((tile_density, tile_force), (ms_density, ms_force))."""
+    P = params if isinstance(params, sph_params) else make_params(params)
+    chosen = (_I32 * 2)()
+    ms = (ctypes.c_float * 2)()
+    _check("sph_autotune", lib().sph_autotune(view, _addr(aos_dev), int(n), ctypes.byref(P), chosen, ms))
+    return (chosen[0], chosen[1]), (ms[0], ms[1])
