@@ -185,6 +185,67 @@ def batched_inputs():
     return fp, lay, aos_h
 
 
+def large_inputs():
+    """The large-run workload: 2,097,152 clustered particles (8 Gaussian overdensities, sigma 0.05, peak 4x),
+    h = 1.2/128, 53^3 periodic cells, v = 0, u = 1."""
+    from paper_2502_16517_gb300 import workloads as wl
+    f = wl.large()
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled", canary=False)
+    return f, lay, aos_h, wl.ncell_for(f["box"], f["h"].max())
+
+
+def run_large(prec, reps, dev, f, lay, aos_h, ncell, dt=None, nsteps=10, tune_cache=None):
+    """Ten kick-drift-kick steps (initial pass + per step: kick, drift, re-bin, gather, density, scatter, gather,
+    force, scatter, kick) as ONE CUDA graph launch per run; each timed run starts from the same initial records
+    (restored outside the timed region).  dt = 0.3 min h / max(c_s + |v|) from the initial pass, in FP64."""
+    import torch
+    from paper_2502_16517_gb300 import autotune, sph
+    from paper_2502_16517_gb300 import workloads as wl
+    n = aos_h.shape[0]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        aos0 = torch.from_numpy(aos_h).to(dev)
+        aos = aos0.clone()
+        view = sph.sph_view_create(lay, prec, n, (f["box"], ncell, True), stream.cuda_stream)
+        try:
+            stats0 = sph.sph_step(view, aos, n, wl.SPH_PARAMS, want_stats=True)
+            if dt is None:
+                rec = aos.cpu().numpy()
+                hv = rec[:, 80:88].copy().view(np.float64)[:, 0]
+                cs = rec[:, 120:128].copy().view(np.float64)[:, 0]
+                vv = rec[:, 24:48].copy().view(np.float64)
+                dt = 0.3 * hv.min() / np.max(cs + np.linalg.norm(vv, axis=1))
+            tiles = None
+            if tune_cache:
+                key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, "grid", n / float(np.prod(ncell)))
+                tiles = autotune.tuned_tiles(view, aos, n, wl.SPH_PARAMS, key, tune_cache)
+            aos.copy_(aos0)
+            sph.sph_step_graph(view, aos, n, wl.SPH_PARAMS, dt=dt, nsteps=nsteps)  # capture (and one run)
+            sph.sph_view_sync(view)
+            sph.sph_pair_counts(view, reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            stats1 = None
+            for k in range(reps):
+                aos.copy_(aos0)
+                ev[k][0].record(stream)
+                sph.sph_step_graph(view, aos, n, wl.SPH_PARAMS, dt=dt, nsteps=nsteps)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            stats1 = sph.sph_reduce(view)
+            counts = sph.sph_pair_counts(view, reset=True)
+            out = aos.cpu().numpy()
+        finally:
+            sph.sph_view_destroy(view)
+    ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    pairs_run = (counts[1] + counts[2]) / reps
+    return {"value": pairs_run * reps / (ms / 1e3), "ms_per_run": ms / reps, "pairs_per_run": pairs_run,
+            "steps_per_run": nsteps, "passes_per_run": nsteps + 1, "dt": dt, "particles": int(n),
+            "energy_rel_drift": float((stats1[6] - stats0[6]) / stats0[6]),
+            "momentum_abs": [float(x) for x in stats1[0:3]], "tiles": tiles, "dtype": "f64" if prec == 0 else "f32",
+            "graph": "one CUDA graph launch per ten-step run"}, out
+
+
 def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=8):
     """Graph-captured steps over all patches (one graph launch per step); per-phase times from one extra
     un-captured step with event timing."""
@@ -396,6 +457,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tiles (no autotuning)")
     ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the batched (patches) forms")
+    ap.add_argument("--no-large", dest="large", action="store_false", help="skip the large ten-step run forms")
     ap.add_argument("--only", choices=["f64", "f32"], default=None,
                     help="run one form only (profiling runs); the JSON line then carries that form's numbers")
     args = ap.parse_args()
@@ -435,6 +497,22 @@ def main():
                 batched[form] = run_batched(0 if form == "f64" else 1, max(steps // 3, 3), 2, dev, fp, lay_b, aos_b,
                                             tune_cache=tune_cache)
             del aos_b
+        large = {}
+        if args.large and args.only is None:
+            fl, lay_l, aos_l, ncell_l = large_inputs()
+            large["f64"], out64 = run_large(0, 3, dev, fl, lay_l, aos_l, ncell_l, tune_cache=tune_cache)
+            large["f32"], out32 = run_large(1, 3, dev, fl, lay_l, aos_l, ncell_l, dt=large["f64"]["dt"],
+                                            tune_cache=tune_cache)
+            x64 = out64[:, 0:24].copy().view(np.float64)
+            x32 = out32[:, 0:24].copy().view(np.float64)
+            d = x32 - x64
+            d -= np.round(d)
+            rho64 = out64[:, 88:96].copy().view(np.float64)[:, 0]
+            rho32 = out32[:, 88:96].copy().view(np.float64)[:, 0]
+            large["f32"]["vs_f64_after_10_steps"] = {
+                "max_position_diff_over_h": float(np.max(np.abs(d)) / fl["h"][0]),
+                "max_rel_density_diff": float(np.max(np.abs(rho32 - rho64) / rho64))}
+            del aos_l, out64, out32
     finally:
         sampler.__exit__(None, None, None)
     clocks = sampler.summary()
@@ -499,6 +577,12 @@ def main():
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
             "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
             "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"]}
+    for form, b in large.items():
+        b = dict(b)
+        b["workload"] = ("large run: 2,097,152 particles, 8 Gaussian overdensities (sigma 0.05, 4x) on a uniform "
+                         "background, 53^3 periodic cells, 10 KDK steps with per-step conversion and re-binning")
+        b["value"] *= world
+        line["forms"][f"large_{form}"] = b
     for form, b in batched.items():
         b = dict(b)
         b["workload"] = ("batched form: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8,256)) per cell, "

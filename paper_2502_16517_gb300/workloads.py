@@ -195,6 +195,13 @@ def plain(seed=SEED):
     return jittered_lattice(64, jitter=0.1, vel_sigma=0.1, seed=seed)
 
 
+def large(n_side=128, seed=SEED):
+    """2,097,152 particles (n_side = 128) drawn iid from a uniform background plus 8 Gaussian overdensities
+    (sigma 0.05, peak 4x the background), periodic unit box, m = 1/N, h = 1.2 / n_side for every particle, u = 1,
+    v = 0.  The lattice size only sets N and the background spacing."""
+    return clustered(n_side ** 3, nclusters=8, sigma=0.05, peak=4.0, hfac=1.2, n_side_equiv=n_side, seed=seed)
+
+
 def ncell_for(box, hmax):
     """Largest cell count per axis with cell edge >= 2 h_max (and at least 3 for the periodic stencil)."""
     box = np.asarray(box, np.float64)

@@ -1,0 +1,143 @@
+"""The large-run form: clustered particles, ten leapfrog kick-drift-kick steps with per-step conversion and
+re-binning, each ten-step run one CUDA graph launch.
+
+Parity: a 4096-particle clustered set through the same ten steps against the oracle's composition of the steps
+(FP64 within 1e-10 normwise after ten steps: round-off grows through the steps, so the single-pass 1e-12 bar is
+not kept; FP32 within 1e-3).  Full size (2,097,152 particles): properties that hold at any size -- momentum
+conserved, the semi-discrete energy rate zero, the integrator's energy drift first order in dt -- and the FP32
+path stays close to the FP64 path."""
+import numpy as np
+import pytest
+
+import helpers as H
+from paper_2502_16517_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_16517_gb300 import build as b
+    b.build()
+    from paper_2502_16517_gb300 import sph as s
+    return s
+
+
+@pytest.fixture
+def side_stream():
+    import torch
+    s = torch.cuda.Stream(device=H.device())
+    with torch.cuda.stream(s):
+        yield s
+
+
+def cfl_dt(out, lay, courant=0.3):
+    """dt = courant * min h / max(c_s + |v|), in FP64 from the records after the initial pass."""
+    import oracle
+    st = oracle.unpack(out, lay)
+    return courant * st["h"].min() / np.max(st["cs"] + np.linalg.norm(st["v"], axis=1))
+
+
+def _oracle_kdk(oracle, st, box, dt, nsteps, p):
+    x, v, u = st["x"], st["v"], st["u"]
+
+    def forces(x, v, u):
+        rho = oracle.density(x, st["mass"], st["h"], box)
+        P, cs = oracle.eos(rho, u, p["gamma"])
+        a, du = oracle.force(x, v, st["mass"], st["h"], rho, P, cs, box, True, p["alpha"], p["beta"], p["eps"])
+        return rho, a, du
+    rho, a, du = forces(x, v, u)
+    for _ in range(nsteps):
+        v, u = oracle.kick(0.5 * dt, a, du, v, u)
+        x = oracle.drift(dt, v, x, box)
+        rho, a, du = forces(x, v, u)
+        v, u = oracle.kick(0.5 * dt, a, du, v, u)
+    return {"x": x, "v": v, "u": u, "rho": rho, "a": a}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ten_kdk_steps_small_clustered_parity(sph, oracle, side_stream, prec):
+    f = wl.clustered(4096, sigma=0.05, peak=4.0, n_side_equiv=16, seed=8)
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay)
+    n = aos_h.shape[0]
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    p = wl.SPH_PARAMS
+    first = oracle.step_all(aos_h, lay, f["box"], p)
+    dt = 0.3 * f["h"].min() / np.max(first["cs"])
+    aos = H.to_dev(aos_h)
+    v = sph.sph_view_create(lay, prec, n, (f["box"], ncell, True), side_stream.cuda_stream)
+    try:
+        sph.sph_step_graph(v, aos, n, p, dt=dt, nsteps=10)
+        sph.sph_view_sync(v)
+        out = aos.cpu().numpy()
+    finally:
+        sph.sph_view_destroy(v)
+    ref = _oracle_kdk(oracle, oracle.unpack(aos_h, lay), f["box"], dt, 10, p)
+    got = oracle.unpack(out, lay)
+    tol = 1e-10 if prec == 0 else 1e-3
+    d = got["x"] - ref["x"]
+    d -= np.round(d)                              # periodic distance
+    assert np.max(np.abs(d)) / f["h"][0] <= tol * 10
+    assert H.normwise(got["v"], ref["v"]) <= tol
+    assert H.rel_max(got["u"], ref["u"]) <= tol
+    assert H.rel_max(got["rho"], ref["rho"]) <= tol
+    assert H.normwise(got["a"], ref["a"]) <= tol
+
+
+def _large_run(sph, aos_h, lay, box, ncell, prec, stream, dt=None, nsteps=10):
+    """Initial pass, then nsteps KDK steps as one graph launch, then one more pass so that the force sees the
+    final velocities.  Returns (stats after the initial pass, stats after the final pass, final records, dt)."""
+    n = aos_h.shape[0]
+    p = wl.SPH_PARAMS
+    aos = H.to_dev(aos_h)
+    v = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
+    try:
+        s0 = sph.sph_step(v, aos, n, p, want_stats=True)          # initial pass: rho, P, c_s, a, du/dt
+        if dt is None:
+            dt = cfl_dt(aos.cpu().numpy(), lay)
+        sph.sph_step_graph(v, aos, n, p, dt=dt, nsteps=nsteps)
+        s1 = sph.sph_step(v, aos, n, p, want_stats=True)          # a, du/dt at the final x, v, u
+        out = aos.cpu().numpy()
+    finally:
+        sph.sph_view_destroy(v)
+    return s0, s1, out, dt
+
+
+def test_large_run_full_size_properties(sph, oracle, side_stream):
+    """Full size, 2,097,152 particles, FP64 and FP32.
+
+    - Momentum: zero initially (v = 0) and conserved exactly by the pairwise-antisymmetric force (FP64).
+    - Energy rate: the semi-discrete equations conserve sum m (|v|^2/2 + u) exactly, so sum m (v.a + du/dt)
+      vanishes up to round-off when a and du/dt are evaluated with the same v (the final pass).
+    - Energy drift of the leapfrog as read here is first order in dt: the force at t_{n+1} sees the half-step
+      velocity, so the ten-step drift halves when dt halves (twenty steps of dt/2).
+    - The FP32 path follows the FP64 path over the ten steps."""
+    f = wl.large()
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay, canary=False)
+    n = aos_h.shape[0]
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    assert n == 2097152 and tuple(ncell) == (53, 53, 53)
+    s0, s1, out64, dt = _large_run(sph, aos_h, lay, f["box"], ncell, 0, side_stream)
+    st64 = oracle.unpack(out64, lay)
+    m = st64["mass"]
+    assert np.all(np.abs(s1[0:3]) <= 1e-12 * np.sum(m[:, None] * np.abs(st64["v"])))
+    scale = np.sum(m * (np.abs(np.sum(st64["v"] * st64["a"], axis=1)) + np.abs(st64["dudt"])))
+    assert scale > 0 and abs(s1[7]) <= 1e-10 * scale
+    drift1 = (s1[6] - s0[6]) / s0[6]
+    h0, h1, _, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 0, side_stream, dt=0.5 * dt, nsteps=20)
+    drift2 = (h1[6] - h0[6]) / h0[6]
+    assert 0 < drift1 < 0.1 and 1.6 < drift1 / drift2 < 2.5
+    t0, t1, out32, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 1, side_stream, dt=dt)
+    st32 = oracle.unpack(out32, lay)
+    assert abs(t1[7]) <= 1e-4 * scale
+    d = st32["x"] - st64["x"]
+    d -= np.round(d)
+    assert np.max(np.abs(d)) / f["h"][0] < 1e-3
+    assert H.rel_max(st32["rho"], st64["rho"]) < 1e-3
+    assert abs((t1[6] - t0[6]) / t0[6] - drift1) < 1e-3 * abs(drift1)
+    assert np.all(np.isfinite(st64["a"])) and np.all(np.isfinite(st32["a"]))
