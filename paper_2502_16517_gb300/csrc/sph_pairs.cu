@@ -5,7 +5,7 @@
 // local-active (Section 5.4): every local particle gathers its sum, so there are no atomics on results.  Pair
 // symmetry is not exploited (Section 5.3): every ordered pair is evaluated once from each side.
 //
-// Per CTA:
+// Per CTA (FP64 loop bodies):
 //   1. a 27-entry neighbour table (first slot, count, running prefix, periodic shift) in shared memory;
 //   2. the active set is staged through shared memory in tiles of TJ particles holding only the SoA members the
 //      loop body reads, plus one float4 per particle for the distance filter; each tile is padded to a multiple
@@ -26,7 +26,11 @@
 // the bound, so every per-pair FP64 instruction is counted: piece selection and masks run on the integer pipe,
 // reciprocals are FP32-seeded Newton iterations, per-particle factors are precomputed.
 // FP32 path: positions are cell-relative floats (the FP32 view), so x_i - x_j = r_i - (r_j + d * edge) with d the
-// neighbour cell offset; the filter is the exact test; all sums are Kahan-compensated.
+// neighbour cell offset; the filter is the exact test; all sums are Kahan-compensated.  The FP32 loop bodies run
+// under the lane driver (process_cell_lanes below): each thread owns one (local particle, candidate stream) pair
+// and keeps its sums in registers over all tiles.  Their arithmetic is written for the FMA pipe: clamps are
+// saturating adds, the spline pieces are combined arithmetically rather than selected, the viscosity switch is
+// min(v.r, 0) = (v.r - |v.r|) / 2, so the half-rate ALU pipe carries almost no per-pair work.
 #include <math.h>
 
 #include "sph_internal.cuh"
@@ -150,47 +154,20 @@ struct Kahan {
         c = __fsub_rn(__fadd_rn(c, c2), err);
         s = t;
     }
-    __device__ __forceinline__ void warp_reduce()
-    {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float s2 = __shfl_xor_sync(kFull, s, o);
-            const float c2 = __shfl_xor_sync(kFull, c, o);
-            merge(s2, c2);
-        }
-    }
 };
 
 // ------------------------------------------------------------------------------------------------------------
-// Pair-term arithmetic.
+// Pair-term arithmetic of the FP64 loop bodies.
 //
 // The cubic spline is piecewise cubic in q = r/h.  Instead of evaluating both pieces and selecting, the
 // coefficients of the one piece that applies are selected and a single polynomial is evaluated:
 //   f(q)     = d0 + d1 q + d2 q^2 + d3 q^3     inner (q < 1): (1, 0, -3/2, 3/4), outer (1 <= q < 2): (2, -3, 3/2, -1/4)
 //   f'(q)/q  = c0/q + c1 + c2 q                inner: (0, -3, 9/4),             outer: (-3, 3, -3/4)
-// with every coefficient 0 for q >= 2 (outside the support): the masking of Section 5.6.  The FP64 loop bodies
-// scale these coefficients by powers of 1/h per particle (so the polynomials run in r) and choose the piece by
-// integer compares of bit patterns: for doubles >= 0 the bit patterns order like the values.
+// with every coefficient 0 for q >= 2 (outside the support): the masking of Section 5.6.  The coefficients are
+// scaled by powers of 1/h per particle (so the polynomials run in r) and the piece is chosen by integer compares
+// of bit patterns: for doubles >= 0 the bit patterns order like the values.  (The FP32 bodies use another form
+// of the same spline, suited to the FP32 pipes; see DensF32.)
 // ------------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ float spline_w(float q)
-{
-    const bool in1 = q < 1.0f, in2 = q < 2.0f;
-    const float d0 = in1 ? 1.0f : (in2 ? 2.0f : 0.0f);
-    const float d1 = in1 ? 0.0f : (in2 ? -3.0f : 0.0f);
-    const float d2 = in1 ? -1.5f : (in2 ? 1.5f : 0.0f);
-    const float d3 = in1 ? 0.75f : (in2 ? -0.25f : 0.0f);
-    return fmaf(fmaf(fmaf(d3, q, d2), q, d1), q, d0);
-}
-
-__device__ __forceinline__ float spline_g(float q, float inv_q)
-{
-    const bool in1 = q < 1.0f, in2 = q < 2.0f;
-    const float c0 = in1 ? 0.0f : (in2 ? -3.0f : 0.0f);
-    const float c1 = in1 ? -3.0f : (in2 ? 3.0f : 0.0f);
-    const float c2 = in1 ? 2.25f : (in2 ? -0.75f : 0.0f);
-    return fmaf(c0, inv_q, fmaf(c2, q, c1));
-}
-
 // FP32 approximation of a positive double by bit manipulation on the integer pipe (exponent re-bias, mantissa
 // truncated to 23 bits; the input is first clamped into the float normal range), and the exact reverse.
 __device__ __forceinline__ float dbl_to_flt_bits(double x)
@@ -370,8 +347,13 @@ struct DensF64 {
     }
 };
 
-// ---- density, FP32 (cell-relative float positions, Kahan sums) ----
+// ---- density, FP32 (cell-relative float positions, Kahan sums; lane driver, every candidate evaluated) ----
+// f(q) = 2 s^3 - t^3 with s = sat(1 - q/2), t = sat(1 - q): the outer piece 1/4 (2-q)^3 = 2 s^3, and for q < 1 the
+// inner piece 1 - 3/2 q^2 + 3/4 q^3 = 1/4 (2-q)^3 - (1-q)^3; beyond q = 2 both clamps are 0 (the support mask).
+// The self term (r = 0) is included, as in the definition of rho_i.  s > 0 exactly when q < 2 and then
+// s >= 2^-24, so sat(2^24 s) counts the pairs in the support.
 struct DensF32 {
+    static constexpr bool kMasked = true;
     struct Args {
         PairCommon cm;
         const float *x, *y, *z, *m, *h, *u;
@@ -382,12 +364,16 @@ struct DensF32 {
         float4 *p4;  // position seen from the local cell, mass
     };
     struct Lhs {
-        float x, y, z, hinv, b2;
+        float x, y, z, hinv;
     };
     struct Part {
         Kahan rho;
-        __device__ __forceinline__ void zero() { rho.zero(); }
-        __device__ __forceinline__ void reduce() { rho.warp_reduce(); }
+        float npair;
+        __device__ __forceinline__ void zero()
+        {
+            rho.zero();
+            npair = 0.f;
+        }
     };
     using Acc = float2;  // (s, c)
     static constexpr int kStageBytes = 16;
@@ -404,37 +390,40 @@ struct DensF32 {
         T.p4[t] = make_float4(A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2],
                               A.m[slot]);
     }
-    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.p4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
     {
         Lhs L;
         L.x = A.x[i];
         L.y = A.y[i];
         L.z = A.z[i];
-        const float h = A.h[i];
-        L.hinv = __frcp_rn(h);
-        L.b2 = 4.0f * h * h;
+        L.hinv = __frcp_rn(A.h[i]);
         return L;
     }
-    static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
-    {
-        const float4 p = T.p4[k];
-        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
-        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < L.b2;
-    }
-    static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &,
-                                                bool, int, int k, Part &P)
+    // m_j f(q_ij) of one candidate; counts it if it lies in the support.
+    static __device__ __forceinline__ float term(const Lhs &L, const Tile &T, int k, float &npair)
     {
         const float4 p = T.p4[k];
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float q = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * L.hinv;
-        P.rho.add(p.w * spline_w(q));
-        return q < 2.0f;
+        const float q = r2 * rsqrtf(r2 + 1e-30f) * L.hinv;
+        const float sq = __saturatef(fmaf(-0.5f, q, 1.0f));
+        const float t = __saturatef(1.0f - q);
+        const float s2 = sq * sq, t2 = t * t;
+        npair += __saturatef(sq * 16777216.0f);
+        return p.w * fmaf(s2 + s2, sq, -(t2 * t));
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
+    // Candidates k, k + ns, ... < tn: four terms summed plainly, then added to the compensated sum.
+    static __device__ __forceinline__ void sweep(const Lhs &L, const Tile &T, int k, int ns, int tn, Part &P)
     {
-        if (lane != 0) return;
+        for (; k + 3 * ns < tn; k += 4 * ns) {
+            const float a = term(L, T, k, P.npair), b = term(L, T, k + ns, P.npair);
+            const float c = term(L, T, k + 2 * ns, P.npair), d = term(L, T, k + 3 * ns, P.npair);
+            P.rho.add((a + b) + (c + d));
+        }
+        for (; k < tn; k += ns) P.rho.add(term(L, T, k, P.npair));
+    }
+    static __device__ __forceinline__ void merge_part(Acc &a, const Part &P)
+    {
         Kahan k;
         k.s = a.x;
         k.c = a.y;
@@ -442,6 +431,7 @@ struct DensF32 {
         a.x = k.s;
         a.y = k.c;
     }
+    static __device__ __forceinline__ unsigned pairs_of(const Part &P) { return (unsigned)P.npair; }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
         const float h = A.h[i];
@@ -666,22 +656,30 @@ struct ForceF64 {
     }
 };
 
-// ---- force, FP32 ----
+// ---- force, FP32 (lane driver: candidates filtered into a per-lane hit mask, only hits evaluated) ----
+// grad_i W(r_ij, h) = F r_ij with F = 3 (t^2 - s^2) / (pi h^4 r), s = sat(1 - q/2), t = sat(1 - q) (the derivative
+// of f = 2 s^3 - t^3); 3/(pi h^4) comes per particle from k_force_prep_f32.  The viscosity uses
+// min(v_ij . r_ij, 0), which makes Pi_ij vanish for receding pairs without a branch.  A pair at r = 0 (the self
+// pair, or two coincident particles) contributes exactly 0: q = 0 gives F = 0, and r_ij = 0.  The pairs counted
+// are the filter's hits, r^2 < 4 max(h_i, h_j)^2, minus the self pair of every local particle.
 struct ForceF32 {
+    static constexpr bool kMasked = false;
     struct Args {
         PairCommon cm;
         const float *x, *y, *z, *vx, *vy, *vz, *m, *h, *rho, *cs;
-        const float *hinv, *k5, *A;
+        const float *hinv, *k4, *A;
         float *ax, *ay, *az, *dudt;
         float alpha, beta, eps;
     };
+    // Staged members in four float4 groups (one 16-byte shared load each): the filter reads only p4.
     struct Tile {
-        float4 *p4;  // position seen from the local cell, h
-        float *vx, *vy, *vz, *m, *hinv, *k5, *A, *c, *rho;
-        int *slot;
+        float4 *p4;  // position seen from the local cell, 4 h^2
+        float4 *v4;  // velocity, mass
+        float4 *g4;  // h, 1/h, 3/(pi h^4), P/rho^2
+        float2 *c2;  // c_s, rho
     };
     struct Lhs {
-        float x, y, z, vx, vy, vz, h, hinv, k5, A, c, rho;
+        float x, y, z, vx, vy, vz, h, hinv, k4, A, c, rho, b2;
     };
     struct Part {
         Kahan ax, ay, az, du;
@@ -692,47 +690,31 @@ struct ForceF32 {
             az.zero();
             du.zero();
         }
-        __device__ __forceinline__ void reduce()
-        {
-            ax.warp_reduce();
-            ay.warp_reduce();
-            az.warp_reduce();
-            du.warp_reduce();
-        }
     };
     struct Acc {
         float2 ax, ay, az, du;
     };
-    static constexpr int kStageBytes = 16 + 9 * 4 + 4;
+    static constexpr int kStageBytes = 3 * 16 + 8;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
         Tile t;
         t.p4 = reinterpret_cast<float4 *>(s);
-        float *f = reinterpret_cast<float *>(t.p4 + tj);
-        float **dst[9] = {&t.vx, &t.vy, &t.vz, &t.m, &t.hinv, &t.k5, &t.A, &t.c, &t.rho};
-#pragma unroll
-        for (int a = 0; a < 9; ++a) *dst[a] = f + a * tj;
-        t.slot = reinterpret_cast<int *>(f + 9 * tj);
+        t.v4 = t.p4 + tj;
+        t.g4 = t.v4 + tj;
+        t.c2 = reinterpret_cast<float2 *>(t.g4 + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
+        const float h = A.h[slot];
         T.p4[t] = make_float4(A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2],
-                              A.h[slot]);
-        T.vx[t] = A.vx[slot];
-        T.vy[t] = A.vy[slot];
-        T.vz[t] = A.vz[slot];
-        T.m[t] = A.m[slot];
-        T.hinv[t] = A.hinv[slot];
-        T.k5[t] = A.k5[slot];
-        T.A[t] = A.A[slot];
-        T.c[t] = A.cs[slot];
-        T.rho[t] = A.rho[slot];
-        T.slot[t] = slot;
+                              4.0f * h * h);
+        T.v4[t] = make_float4(A.vx[slot], A.vy[slot], A.vz[slot], A.m[slot]);
+        T.g4[t] = make_float4(h, A.hinv[slot], A.k4[slot], A.A[slot]);
+        T.c2[t] = make_float2(A.cs[slot], A.rho[slot]);
     }
-    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.p4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
     {
         Lhs L;
@@ -744,57 +726,54 @@ struct ForceF32 {
         L.vz = A.vz[i];
         L.h = A.h[i];
         L.hinv = A.hinv[i];
-        L.k5 = A.k5[i];
+        L.k4 = A.k4[i];
         L.A = A.A[i];
         L.c = A.cs[i];
         L.rho = A.rho[i];
+        L.b2 = 4.0f * L.h * L.h;
         return L;
     }
+    // r < 2 max(h_i, h_j), as r^2 < max(4 h_i^2, 4 h_j^2) (the same float products the staging formed).
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
         const float4 p = T.p4[k];
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
-        const float hm = fmaxf(L.h, p.w);
-        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0f * hm * hm;
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < fmaxf(L.b2, p.w);
     }
-    static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &,
-                                                bool, int i, int k, Part &P)
+    static __device__ __forceinline__ void eval(const Args &A, const Lhs &L, const Tile &T, int k, Part &P)
     {
         const float4 p = T.p4[k];
+        const float4 vm = T.v4[k];
+        const float4 g = T.g4[k];
+        const float2 cr = T.c2[k];
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float hj = p.w;
-        const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+        const float rinv = rsqrtf(r2 + 1e-30f);
         const float r = r2 * rinv;
-        const float qi = r * L.hinv, qj = r * T.hinv[k];
-        const float Fi = L.k5 * spline_g(qi, L.h * rinv);
-        const float Fj = T.k5[k] * spline_g(qj, hj * rinv);
-        const float dvx = L.vx - T.vx[k], dvy = L.vy - T.vy[k], dvz = L.vz - T.vz[k];
+        const float qi = r * L.hinv, qj = r * g.y;
+        const float si = __saturatef(fmaf(-0.5f, qi, 1.0f)), ti = __saturatef(1.0f - qi);
+        const float sj = __saturatef(fmaf(-0.5f, qj, 1.0f)), tj = __saturatef(1.0f - qj);
+        const float Fi = (L.k4 * rinv) * ((ti - si) * (ti + si));
+        const float Fj = (g.z * rinv) * ((tj - sj) * (tj + sj));
+        const float dvx = L.vx - vm.x, dvy = L.vy - vm.y, dvz = L.vz - vm.z;
         const float vdotr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
-        const float hb = 0.5f * (L.h + hj);
+        const float vneg = 0.5f * (vdotr - fabsf(vdotr));  // min(v_ij . r_ij, 0)
+        const float hb = 0.5f * (L.h + g.x);
         const float D1 = fmaf(A.eps * hb, hb, r2);
-        const float D2 = L.rho + T.rho[k];
-        const float R = __frcp_rn(D1 * D2);
-        const float mu = (hb * vdotr) * (D2 * R);
-        const float cb = 0.5f * (L.c + T.c[k]);
-        float Ph = (mu * fmaf(A.beta, mu, -A.alpha * cb)) * (D1 * R);
-        if (!(vdotr < 0.0f)) Ph = 0.0f;
+        const float D2 = L.rho + cr.y;
+        const float R = __fdividef(1.0f, D1 * D2);
+        const float mu = (hb * vneg) * (D2 * R);
+        const float cb = 0.5f * (L.c + cr.x);
+        const float Ph = (mu * fmaf(A.beta, mu, -A.alpha * cb)) * (D1 * R);
         const float Fs = Fi + Fj;
         const float aF = L.A * Fi;
-        const float mj = T.m[k];
-        const bool self = T.slot[k] == i;
-        const bool in = !self && (qi < 2.0f || qj < 2.0f);
-        float coef = mj * fmaf(Ph, Fs, fmaf(T.A[k], Fj, aF));
-        float dcoef = (mj * vdotr) * fmaf(0.5f * Ph, Fs, aF);
-        if (self) {
-            coef = 0.0f;
-            dcoef = 0.0f;
-        }
+        const float mj = vm.w;
+        const float coef = mj * fmaf(Ph, Fs, fmaf(g.w, Fj, aF));
+        const float dcoef = (mj * vdotr) * fmaf(0.5f * Ph, Fs, aF);
         P.ax.add(-coef * dx);
         P.ay.add(-coef * dy);
         P.az.add(-coef * dz);
         P.du.add(dcoef);
-        return in;
     }
     static __device__ __forceinline__ void merge2(float2 &a, const Kahan &p)
     {
@@ -805,9 +784,8 @@ struct ForceF32 {
         a.x = k.s;
         a.y = k.c;
     }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
+    static __device__ __forceinline__ void merge_part(Acc &a, const Part &P)
     {
-        if (lane != 0) return;
         merge2(a.ax, P.ax);
         merge2(a.ay, P.ay);
         merge2(a.az, P.az);
@@ -937,6 +915,150 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
     if (tid == 0) K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, S.pairs);
 }
 
+// Lane driver of the FP32 loop bodies: each of the CTA's threads owns one (local particle, candidate stream)
+// pair.  With nloc local particles, ns = min(32, 128 / nloc) threads share a particle; thread t takes particle
+// t / ns and the candidates s, s + ns, s + 2 ns, ... of every tile (s = t mod ns).  The thread's partial sums
+// live in registers across all tiles; at the end the ns partials of a particle are merged in stream order
+// (deterministic) through shared memory and finalised.  Two sweeps:
+//   K::kMasked:  every candidate is evaluated, the support acting only as a mask (Section 5.6) -- the density,
+//                whose term is barely dearer than the distance test;
+//   otherwise:   the lane tests 32 of its candidates into a bit mask, then evaluates its hits -- the force,
+//                whose term costs several times the test and covers ~15 % of the candidates.
+template <class K>
+struct LaneShared {
+    NbrTable nb;
+    unsigned long long pairs;
+};
+
+template <class K>
+__device__ __forceinline__ unsigned hit_sweep(const typename K::Args &A, const typename K::Lhs &L,
+                                              const typename K::Tile &T, int s, int ns, int tn,
+                                              typename K::Part &P)
+{
+    unsigned nhit = 0;
+    int k0 = s;
+    for (; k0 + 31 * ns < tn; k0 += 32 * ns) {  // whole windows: no bounds test per candidate
+        unsigned hits = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b)
+            if (K::filter(L, T, k0 + b * ns)) hits |= 1u << b;
+        nhit += __popc(hits);
+        while (hits) {
+            const int b = __ffs(hits) - 1;
+            hits &= hits - 1u;
+            K::eval(A, L, T, k0 + b * ns, P);
+        }
+    }
+    if (k0 < tn) {  // the last, partial window
+        unsigned hits = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const int k = k0 + b * ns;
+            if (k < tn && K::filter(L, T, k)) hits |= 1u << b;
+        }
+        nhit += __popc(hits);
+        while (hits) {
+            const int b = __ffs(hits) - 1;
+            hits &= hits - 1u;
+            K::eval(A, L, T, k0 + b * ns, P);
+        }
+    }
+    return nhit;
+}
+
+template <class K>
+__device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, int c, const typename K::Tile &T,
+                                                   LaneShared<K> &S, unsigned char *smem)
+{
+    const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
+    if (ls >= le) return;  // CTA-uniform
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tj = A.cm.tj;
+    NbrTable &nb = S.nb;
+    if (tid == 0) S.pairs = 0ull;
+    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start);
+    const int NJ = nb.pref[27];
+    unsigned my_pairs = 0;
+    typename K::Part *part = reinterpret_cast<typename K::Part *>(smem);  // reuses the tile after the last one
+
+    for (int ib = ls; ib < le; ib += kPairThreads) {
+        const int nloc = min(kPairThreads, le - ib);
+        const int ns = min(32, kPairThreads / nloc);  // lanes per local particle
+        const int li = tid / ns, s = tid - li * ns;
+        const bool active = li < nloc;
+        const int i = ib + (active ? li : 0);
+        const typename K::Lhs L = K::load(A, i, 0.f);
+        typename K::Part P;
+        P.zero();
+        for (int tb = 0; tb < NJ; tb += tj) {
+            const int tn = min(tj, NJ - tb);
+            __syncthreads();  // previous tile consumed
+            for (int t = tid; t < tn; t += kPairThreads) {
+                const int jj = tb + t;
+                const int nq = find_nbr(nb, jj);
+                K::stage(A, T, nb, t, nb.start[nq] + (jj - nb.pref[nq]), nq);
+            }
+            __syncthreads();
+            if (active) {
+                if constexpr (K::kMasked) {
+                    K::sweep(L, T, s, ns, tn, P);
+                } else {
+                    my_pairs += hit_sweep<K>(A, L, T, s, ns, tn, P);
+                }
+            }
+        }
+        if constexpr (K::kMasked) {
+            if (active) my_pairs += K::pairs_of(P);
+        }
+        __syncthreads();  // last tile consumed: its space holds the partials now
+        part[tid] = P;
+        __syncthreads();
+        if (tid < nloc) {
+            typename K::Acc acc;
+            zero_acc<K>(acc);
+            for (int q = 0; q < ns; ++q) K::merge_part(acc, part[tid * ns + q]);
+            K::finish(A, ib + tid, acc);
+        }
+    }
+    const unsigned long long wp = warp_sum((unsigned long long)my_pairs);
+    if (lane == 0 && wp) atomicAdd(&S.pairs, wp);
+    __syncthreads();
+    if (tid == 0) {
+        // the hit count of the filtered sweep includes every local particle's self pair
+        const unsigned long long self = K::kMasked ? 0ull : (unsigned long long)(le - ls);
+        K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, S.pairs - self);
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(kPairThreads) k_cell_lanes(const typename K::Args A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LaneShared<K> S;
+    const typename K::Tile T = K::carve(smem, A.cm.tj);
+    process_cell_lanes<K>(A, blockIdx.x, T, S, smem);
+}
+
+template <class K>
+__global__ void __launch_bounds__(kPairThreads) k_cell_lanes_persist(const typename K::Args A,
+                                                                     const int *__restrict__ order,
+                                                                     const int *__restrict__ count, int *next)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LaneShared<K> S;
+    __shared__ int w;
+    const typename K::Tile T = K::carve(smem, A.cm.tj);
+    const int total = *count;
+    for (;;) {
+        if (threadIdx.x == 0) w = atomicAdd(next, 1);
+        __syncthreads();
+        const int wi = w;
+        __syncthreads();
+        if (wi >= total) break;
+        process_cell_lanes<K>(A, order[wi], T, S, smem);
+    }
+}
+
 // One CTA per cell (single-grid views).
 template <class K>
 __global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::Args A)
@@ -1063,17 +1185,17 @@ __global__ void k_density_prep_f64(const double *__restrict__ x, const double *_
     o3[s] = -0.25 * h3;
 }
 
-// Per-particle quantities of the FP32 force loop: 1/h, 1/(pi h^5), P/rho^2.
+// Per-particle quantities of the FP32 force loop: 1/h, 3/(pi h^4), P/rho^2.
 __global__ void k_force_prep_f32(const float *__restrict__ h, const float *__restrict__ P,
                                  const float *__restrict__ rho, int n, float *__restrict__ hinv,
-                                 float *__restrict__ k5, float *__restrict__ A)
+                                 float *__restrict__ k4, float *__restrict__ A)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const float hi = 1.0f / h[s];
     const float h2 = hi * hi;
     hinv[s] = hi;
-    k5[s] = (float)kInvPi * h2 * h2 * hi;
+    k4[s] = (float)(3.0 * kInvPi) * h2 * h2;
     const float r = rho[s];
     A[s] = P[s] / (r * r);
 }
@@ -1101,14 +1223,41 @@ __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__r
 }
 
 template <class K>
+struct UsesLanes {
+    static constexpr bool value = false;
+};
+template <>
+struct UsesLanes<DensF32> {
+    static constexpr bool value = true;
+};
+template <>
+struct UsesLanes<ForceF32> {
+    static constexpr bool value = true;
+};
+
+template <class K, bool Lanes>
+struct CellKernels {
+    static auto grid() { return k_cell_pairs<K>; }
+    static auto persist() { return k_cell_pairs_persist<K>; }
+};
+template <class K>
+struct CellKernels<K, true> {
+    static auto grid() { return k_cell_lanes<K>; }
+    static auto persist() { return k_cell_lanes_persist<K>; }
+};
+
+template <class K>
 cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &pl, cudaStream_t st)
 {
+    void (*const kgrid)(const typename K::Args) = CellKernels<K, UsesLanes<K>::value>::grid();
+    void (*const kpers)(const typename K::Args, const int *, const int *, int *) =
+        CellKernels<K, UsesLanes<K>::value>::persist();
     const size_t smem = (size_t)A.cm.tj * K::kStageBytes + 16;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_cell_pairs<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kgrid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_cell_pairs_persist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(kpers, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
@@ -1120,16 +1269,16 @@ cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &p
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cell_pairs_persist<K>, kPairThreads, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpers, kPairThreads, smem);
             ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
             sized_for = smem;
         }
         cudaError_t e = cudaMemsetAsync(pl.work_next, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
-        k_cell_pairs_persist<K><<<pl.persistent_ctas > 0 ? pl.persistent_ctas : ctas, kPairThreads, smem, st>>>(
+        kpers<<<pl.persistent_ctas > 0 ? pl.persistent_ctas : ctas, kPairThreads, smem, st>>>(
             A, pl.work_order, pl.work_count, pl.work_next);
     } else {
-        k_cell_pairs<K><<<ncells, kPairThreads, smem, st>>>(A);
+        kgrid<<<ncells, kPairThreads, smem, st>>>(A);
     }
     return cudaGetLastError();
 }
@@ -1279,7 +1428,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     A.rho = (const float *)soa.p[SPH_RHO][0];
     A.cs = (const float *)soa.p[SPH_CS][0];
     A.hinv = (const float *)scr.d[0];
-    A.k5 = (const float *)scr.d[1];
+    A.k4 = (const float *)scr.d[1];
     A.A = (const float *)scr.d[2];
     A.ax = (float *)soa.p[SPH_A][0];
     A.ay = (float *)soa.p[SPH_A][1];
