@@ -58,59 +58,69 @@ struct NbrTable {
 
 __device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellSpace &cs, const int *cell_start)
 {
+    // one warp: lane q < 27 fills neighbour q, then the counts are prefix-summed with shuffles
     const int tid = threadIdx.x;
-    const bool periodic = cs.npatch == 0 && cs.g.periodic;
-    if (tid == 0) nb.wrap = 0;
-    __syncthreads();
-    if (tid < 27) {
+    if (tid < 32) {
+        const bool periodic = cs.npatch == 0 && cs.g.periodic;
         CellLoc L;
         locate_cell(cs, c, L);
-        const int d[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
-        int kk[3];
-        bool valid = true;
+        int cnt = 0;
         bool wr = false;
-        for (int a = 0; a < 3; ++a) {
-            int k = L.k[a] + d[a];
-            double s = 0.0;
-            if (k < 0) {
-                if (periodic) {
-                    k += L.n[a];
-                    s = cs.g.box[a];
-                } else {
-                    valid = false;
+        if (tid < 27) {
+            const int d[3] = {tid % 3 - 1, (tid / 3) % 3 - 1, tid / 9 - 1};
+            int kk[3];
+            bool valid = true;
+            for (int a = 0; a < 3; ++a) {
+                int k = L.k[a] + d[a];
+                double sh = 0.0;
+                if (k < 0) {
+                    if (periodic) {
+                        k += L.n[a];
+                        sh = cs.g.box[a];
+                    } else {
+                        valid = false;
+                    }
+                } else if (k >= L.n[a]) {
+                    if (periodic) {
+                        k -= L.n[a];
+                        sh = -cs.g.box[a];
+                    } else {
+                        valid = false;
+                    }
                 }
-            } else if (k >= L.n[a]) {
-                if (periodic) {
-                    k -= L.n[a];
-                    s = -cs.g.box[a];
-                } else {
-                    valid = false;
-                }
+                kk[a] = k;
+                nb.shift[tid][a] = sh;
+                // (float)(d edge) for d in {-1, 0, 1} is d (float)edge exactly
+                const float ef = cs.npatch == 0 ? cs.g.edgef[a] : __double2float_rn(cell_edge(cs, L, a));
+                nb.offf[tid][a] = (float)d[a] * ef;
+                wr = wr || (sh != 0.0);
             }
-            kk[a] = k;
-            nb.shift[tid][a] = s;
-            nb.offf[tid][a] = __double2float_rn((double)d[a] * cell_edge(cs, L, a));
-            wr = wr || (s != 0.0);
+            int st = 0;
+            if (valid) {
+                const int c2 = L.base + kk[0] + L.n[0] * (kk[1] + L.n[1] * kk[2]);
+                st = cell_start[c2];
+                cnt = cell_start[c2 + 1] - st;
+            }
+            nb.start[tid] = st;
         }
-        int cnt = 0, st = 0;
-        if (valid) {
-            const int c2 = L.base + kk[0] + L.n[0] * (kk[1] + L.n[1] * kk[2]);
-            st = cell_start[c2];
-            cnt = cell_start[c2 + 1] - st;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int up = __shfl_up_sync(kFull, incl, o);
+            if (tid >= o) incl += up;
         }
-        nb.start[tid] = st;
-        nb.pref[tid + 1] = cnt;  // counts, turned into a prefix below
-        if (wr && cnt > 0) atomicOr(&nb.wrap, 1);
-        if (tid == 13) {
+        if (tid < 27) nb.pref[tid + 1] = incl;
+        const bool any_wrap = __any_sync(kFull, wr && cnt > 0);
+        if (tid == 0) {
+            nb.pref[0] = 0;
+            nb.wrap = any_wrap ? 1 : 0;
             // conservative slack of the FP32 filter: float rounding of cell-relative coordinates (|coord| <= 2 edges)
-            const double emax = fmax(cell_edge(cs, L, 0), fmax(cell_edge(cs, L, 1), cell_edge(cs, L, 2)));
-            nb.margin = (float)(4e-6 * emax);
+            const float emax = cs.npatch == 0
+                                   ? fmaxf(cs.g.edgef[0], fmaxf(cs.g.edgef[1], cs.g.edgef[2]))
+                                   : __double2float_rn(fmax(cell_edge(cs, L, 0),
+                                                            fmax(cell_edge(cs, L, 1), cell_edge(cs, L, 2))));
+            nb.margin = 4e-6f * emax;
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        nb.pref[0] = 0;
-        for (int q = 0; q < 27; ++q) nb.pref[q + 1] += nb.pref[q];
     }
     __syncthreads();
 }
@@ -132,6 +142,35 @@ __device__ __forceinline__ T warp_sum(T v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
+}
+
+// Single-instruction FP32 forms (PTX): approximate reciprocal square root and reciprocal, and saturating
+// (clamped to [0, 1]) multiply-add / add / multiply.  Subnormal inputs and results flush to zero; the FP32
+// pair terms stay far above the subnormal range, so this changes no result and saves the subnormal fix-up
+// sequences of the default forms.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float fma_sat(float a, float b, float c)
+{
+    float y;
+    asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+    return y;
+}
+__device__ __forceinline__ float mul_sat(float a, float b)
+{
+    float y;
+    asm("mul.rn.ftz.sat.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+    return y;
 }
 
 // Kahan accumulator (FP32 path): value = s - c.
@@ -188,7 +227,7 @@ __device__ __forceinline__ double flt_to_dbl_bits(float y)
 // (or x below the float range) the result is large but finite, so r = x / sqrt(x) comes out 0 (or tiny).
 __device__ __forceinline__ double rsqrt_seeded(double x)
 {
-    double y = flt_to_dbl_bits(rsqrtf(dbl_to_flt_bits(x)));
+    double y = flt_to_dbl_bits(rsqrt_ftz(dbl_to_flt_bits(x)));
     const double hx = 0.5 * x;
     y = y * fma(-hx * y, y, 1.5);
     y = y * fma(-hx * y, y, 1.5);
@@ -198,7 +237,7 @@ __device__ __forceinline__ double rsqrt_seeded(double x)
 // 1/x, x > 0 within the float range: FP32 seed, then two Newton-Raphson steps y <- y + y (1 - x y) in FP64.
 __device__ __forceinline__ double rcp_seeded(double x)
 {
-    double y = flt_to_dbl_bits(__frcp_rn(dbl_to_flt_bits(x)));
+    double y = flt_to_dbl_bits(rcp_ftz(dbl_to_flt_bits(x)));
     y = fma(y, fma(-x, y, 1.0), y);
     y = fma(y, fma(-x, y, 1.0), y);
     return y;
@@ -405,11 +444,11 @@ struct DensF32 {
         const float4 p = T.p4[k];
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float q = r2 * rsqrtf(r2 + 1e-30f) * L.hinv;
-        const float sq = __saturatef(fmaf(-0.5f, q, 1.0f));
-        const float t = __saturatef(1.0f - q);
+        const float q = r2 * rsqrt_ftz(r2 + 1e-30f) * L.hinv;
+        const float sq = fma_sat(-0.5f, q, 1.0f);
+        const float t = fma_sat(-1.0f, q, 1.0f);
         const float s2 = sq * sq, t2 = t * t;
-        npair += __saturatef(sq * 16777216.0f);
+        npair += mul_sat(sq, 16777216.0f);
         return p.w * fmaf(s2 + s2, sq, -(t2 * t));
     }
     // Candidates k, k + ns, ... < tn: four terms summed plainly, then added to the compensated sum.
@@ -748,11 +787,11 @@ struct ForceF32 {
         const float2 cr = T.c2[k];
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rinv = rsqrtf(r2 + 1e-30f);
+        const float rinv = rsqrt_ftz(r2 + 1e-30f);
         const float r = r2 * rinv;
         const float qi = r * L.hinv, qj = r * g.y;
-        const float si = __saturatef(fmaf(-0.5f, qi, 1.0f)), ti = __saturatef(1.0f - qi);
-        const float sj = __saturatef(fmaf(-0.5f, qj, 1.0f)), tj = __saturatef(1.0f - qj);
+        const float si = fma_sat(-0.5f, qi, 1.0f), ti = fma_sat(-1.0f, qi, 1.0f);
+        const float sj = fma_sat(-0.5f, qj, 1.0f), tj = fma_sat(-1.0f, qj, 1.0f);
         const float Fi = (L.k4 * rinv) * ((ti - si) * (ti + si));
         const float Fj = (g.z * rinv) * ((tj - sj) * (tj + sj));
         const float dvx = L.vx - vm.x, dvy = L.vy - vm.y, dvz = L.vz - vm.z;
@@ -761,7 +800,7 @@ struct ForceF32 {
         const float hb = 0.5f * (L.h + g.x);
         const float D1 = fmaf(A.eps * hb, hb, r2);
         const float D2 = L.rho + cr.y;
-        const float R = __fdividef(1.0f, D1 * D2);
+        const float R = rcp_ftz(D1 * D2);
         const float mu = (hb * vneg) * (D2 * R);
         const float cb = 0.5f * (L.c + cr.x);
         const float Ph = (mu * fmaf(A.beta, mu, -A.alpha * cb)) * (D1 * R);
