@@ -120,7 +120,7 @@ def _inputs():
     return f, lay, aos_h, ncell
 
 
-def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None):
+def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None, union=True):
     import torch
     from paper_2502_16517_gb300 import autotune, sph
     from paper_2502_16517_gb300 import workloads as wl
@@ -128,6 +128,8 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
     aos = torch.from_numpy(aos_h).to(dev)
     stream = torch.cuda.current_stream(dev)
     view = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
+    if not union:
+        sph.sph_view_set_union(view, False)
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
     tiles = None
     try:
@@ -171,7 +173,7 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
         sph.sph_view_destroy(view)
     return {
         "step_ms": step_ms, "wall_s": wall, "counts": counts, "phase_ms": phase_ms, "launches": launches,
-        "clocks": sampler.summary() if sampler else None, "tiles": tiles,
+        "clocks": sampler.summary() if sampler else None, "tiles": tiles, "union": union,
     }
 
 
@@ -325,12 +327,16 @@ def run_e2e(prec, steps, warmup, dev, aos_h, lay, box, ncell):
             "d2h_bytes_per_step": int(n * lay["stride"]), "ms_per_step": wall * 1e3 / steps}
 
 
-def conversion_bytes(prec, n):
-    """Algorithmic bytes of the four view conversions of one pass (read + written, incl. the 4-byte perm read;
-    FP32 positions also read the 4-byte cell of the slot)."""
+def conversion_bytes(prec, n, union=True):
+    """Algorithmic bytes of the view conversions of one pass (read + written, incl. the 4-byte perm read; FP32
+    positions also read the 4-byte cell of the slot).  Union view: gather {x,m,h,u} and {v}, one scatter of
+    {rho,P,cs,a,dudt}; per-loop views: gather {x,m,h,u} and {x,v,m,h,rho,P,cs}, scatter {rho,P,cs} and {a,dudt}."""
     e = 8 if prec == 0 else 4
     pos_extra = 0 if prec == 0 else 4
     gather_d = n * (6 * 8 + 6 * e + 4 + pos_extra)
+    if union:
+        gather_f = n * (3 * 8 + 3 * e + 4)
+        return gather_d + gather_f, n * (7 * 8 + 7 * e + 4)
     gather_f = n * (11 * 8 + 11 * e + 4 + pos_extra)
     scatter_d = n * (3 * 8 + 3 * e + 4)
     scatter_f = n * (4 * 8 + 4 * e + 4)
@@ -344,7 +350,7 @@ def summarize_form(prec, r, n, steps, world):
     value = world * pairs_step * steps / (ms / 1e3)
     ph = {name: float(r["phase_ms"][i]) / steps for i, name in enumerate(sph.PHASE_NAMES)}
     nl = {name: int(r["launches"][i]) for i, name in enumerate(sph.PHASE_NAMES)}
-    g_bytes, s_bytes = conversion_bytes(prec, n)
+    g_bytes, s_bytes = conversion_bytes(prec, n, r.get("union", True))
     conv = {
         "gather_GBps": g_bytes / (ph["gather"] * 1e-3) / 1e9 if ph["gather"] > 0 else None,
         "scatter_GBps": s_bytes / (ph["scatter"] * 1e-3) / 1e9 if ph["scatter"] > 0 else None,
@@ -490,6 +496,11 @@ def main():
         for k, form in enumerate(forms):
             runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
                                   tune_cache=tune_cache)
+        per_loop = None
+        if args.only is None:
+            # the paper's conversion pattern: one view per loop, converted forth and back around each
+            per_loop = run_form(0, steps, warmup, dev, aos_h, lay, f["box"], ncell, tune_cache=tune_cache,
+                                union=False)
         batched = {}
         if args.batched and args.only is None:
             fp, lay_b, aos_b = batched_inputs()
@@ -553,7 +564,8 @@ def main():
         "dtype": main_form, "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": n, "cells": int(np.prod(ncell)), "record_bytes": lay["stride"],
                    "l2": "256 MB buffer written between timed steps (outside the step events)",
-                   "step": "sph_step: bin + gather + density + scatter + gather + force + scatter",
+                   "step": ("sph_step with one view for both loops: bin + gather {x,m,h,u} + density + gather {v} "
+                            "+ force + one scatter of {rho,P,cs,a,dudt}"),
                    "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline_of(prec_main, s64, steps, peaks, fma_peak[main_form]),
@@ -577,6 +589,16 @@ def main():
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
             "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
             "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"]}
+    if per_loop is not None:
+        per_loop["step_ms"] = list(per_loop["step_ms"])
+        sp = summarize_form(0, per_loop, n, steps, world)
+        line["forms"]["f64_per_loop_views"] = {
+            "workload": ("the plain FP64 input, one view per loop converted forth and back around each: bin + "
+                         "gather {x,m,h,u} + density + scatter {rho,P,cs} + gather {x,v,m,h,rho,P,cs} + force + "
+                         "scatter {a,dudt}"),
+            "value": sp["value"], "ms_per_step": sp["ms_per_step"], "dtype": "f64",
+            "phases_ms_per_step": sp["phases_ms_per_step"], "conversion": sp["conversion"],
+            "gpu_launches": int(sum(sp["launches"].values()))}
     for form, b in large.items():
         b = dict(b)
         b["workload"] = ("large run: 2,097,152 particles, 8 Gaussian overdensities (sigma 0.05, 4x) on a uniform "

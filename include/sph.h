@@ -154,6 +154,14 @@ SPH_API sph_status sph_step_graph(sph_view view, void *aos_dev, int64_t n, const
 SPH_API sph_status sph_patches_step_graph(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
                                           int32_t npatch, const sph_params *params);
 
+/* How sph_step / sph_patches_step convert (Section 8, future work: keep the SoA across loops).  on = 1 (the
+ * default): one view serves both loops -- the density view's members and outputs stay in SoA for the force, only
+ * the members the force adds (v) are gathered, and rho, P, c_s, a, du/dt are scattered together after the force.
+ * on = 0: one view per loop, converted forth and back around each (scatter the density outputs, gather the full
+ * force view), as the paper's annotated loops do.  The records end up byte-identical either way.  Errors:
+ * SPH_E_INVAL (on not 0 or 1). */
+SPH_API sph_status sph_view_set_union(sph_view view, int32_t on);
+
 /* Staged particles per shared-memory tile of the density and force pair loops (multiples of 64; 0 = the
  * defaults).  Larger tiles stage more neighbours per barrier, smaller ones leave room for more CTAs per SM. */
 SPH_API sph_status sph_view_set_tiles(sph_view view, int32_t tile_density, int32_t tile_force);

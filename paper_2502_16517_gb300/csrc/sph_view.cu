@@ -87,6 +87,7 @@ struct sph_view_s {
     cudaGraphExec_t g_exec;
     int64_t g_launches[SPH_NPHASES];
     int persistent_ctas;           // CTAs of the persistent pair launches (patch views; 0 = as many as fit)
+    bool union_view;               // one gather per member and one scatter per pass (sph_view_set_union)
 };
 
 namespace {
@@ -450,10 +451,19 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     }
     if ((s = do_gather(v, aos, n, SPH_DENSITY_IN)) != SPH_OK) return s;
     if ((s = do_density(v, p)) != SPH_OK) return s;
-    if ((s = do_scatter(v, aos, n, SPH_DENSITY_OUT)) != SPH_OK) return s;
-    if ((s = do_gather(v, aos, n, SPH_FORCE_IN)) != SPH_OK) return s;
+    if (!v->union_view) {
+        // one view per loop, converted forth and back around each (the paper's prologue / epilogue per loop)
+        if ((s = do_scatter(v, aos, n, SPH_DENSITY_OUT)) != SPH_OK) return s;
+        if ((s = do_gather(v, aos, n, SPH_FORCE_IN)) != SPH_OK) return s;
+        if ((s = do_force(v, p)) != SPH_OK) return s;
+        return do_scatter(v, aos, n, SPH_FORCE_OUT);
+    }
+    // union view: the force reads the density view's members and outputs where they are, in SoA; only the
+    // members it adds are gathered, and every written member is scattered once at the end
+    const uint32_t more = SPH_FORCE_IN & ~v->resident;
+    if (more && (s = do_gather(v, aos, n, more)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;
-    return do_scatter(v, aos, n, SPH_FORCE_OUT);
+    return do_scatter(v, aos, n, SPH_DENSITY_OUT | SPH_FORCE_OUT);
 }
 
 // Half kick on the view (v += a dt/2, u += du/dt dt/2), then write v and u back into the records.
@@ -626,6 +636,14 @@ sph_status sph_patches_step_graph(sph_view v, void *aos_dev, int64_t n, const in
     return do_step_graph(v, aos_dev, n, params, 0.0, 0);
 }
 
+sph_status sph_view_set_union(sph_view v, int32_t on)
+{
+    if (!v || (on != 0 && on != 1)) return SPH_E_INVAL;
+    v->union_view = on != 0;
+    graph_drop(v);
+    return SPH_OK;
+}
+
 sph_status sph_view_set_tiles(sph_view v, int32_t tile_density, int32_t tile_force)
 {
     if (!v || tile_density < 0 || tile_force < 0 || tile_density > 4096 || tile_force > 4096) return SPH_E_INVAL;
@@ -790,6 +808,7 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     v->esz = prec == SPH_F64 ? 8 : 4;
     v->present = present;
     v->persistent_ctas = 0;  // sized from the pair kernels' occupancy at launch
+    v->union_view = true;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
     v->ev_pending = new (std::nothrow) std::vector<PendingTiming>();
     if (!v->ev_free || !v->ev_pending) {

@@ -97,6 +97,7 @@ _SIGS = {
     "sph_step_graph": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.c_double, _I32],
     "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
     "sph_view_set_tiles": [_VP, _I32, _I32],
+    "sph_view_set_union": [_VP, _I32],
     "sph_autotune": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
@@ -333,6 +334,10 @@ def sph_patches_step_graph(view, aos_dev, n, patch_start_dev, npatch, params):
     P = params if isinstance(params, sph_params) else make_params(params)
     _check("sph_patches_step_graph", lib().sph_patches_step_graph(view, _addr(aos_dev), int(n), _addr(patch_start_dev),
                                                                   int(npatch), ctypes.byref(P)))
+
+
+def sph_view_set_union(view, on=True):
+    _check("sph_view_set_union", lib().sph_view_set_union(view, 1 if on else 0))
 
 
 def sph_view_set_tiles(view, tile_density, tile_force):

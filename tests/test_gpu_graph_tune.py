@@ -154,3 +154,47 @@ def test_set_tiles_validates(sph):
             assert e.value.status == sph.SPH_E_INVAL
     finally:
         sph.sph_view_destroy(v)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kdk", [False, True])
+def test_union_view_equals_per_loop_views(sph, side_stream, prec, kdk):
+    """One view for both loops (the force reads the density view's members and outputs in SoA, one scatter at the
+    end) leaves exactly the records that a view per loop, converted forth and back around each, leaves."""
+    f = wl.jittered_lattice(12, jitter=0.1, vel_sigma=0.2, seed=6)
+    lay = wl.shuffled_layout(seed=5, stride=200)
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled")
+    n = aos_h.shape[0]
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    outs, launches = [], []
+    for union in (True, False):
+        aos = H.to_dev(aos_h)
+        v = sph.sph_view_create(lay, prec, n, (f["box"], ncell, True), side_stream.cuda_stream)
+        try:
+            if not union:
+                sph.sph_view_set_union(v, False)
+            if kdk:
+                sph.sph_step(v, aos, n, wl.SPH_PARAMS, dt=1e-3, nsteps=2)
+            else:
+                sph.sph_step(v, aos, n, wl.SPH_PARAMS)
+            sph.sph_view_sync(v)
+            _, nl = sph.sph_view_phase_times(v)
+            outs.append(aos.cpu().numpy())
+            launches.append(nl)
+        finally:
+            sph.sph_view_destroy(v)
+    assert np.array_equal(outs[0], outs[1])
+    gi, si = sph.PHASE_NAMES.index("gather"), sph.PHASE_NAMES.index("scatter")
+    # the same number of gathers (the union form's second one moves only v), one scatter per pass instead of two
+    assert launches[0][gi] == launches[1][gi] and launches[0][si] < launches[1][si]
+
+
+def test_set_union_validates(sph):
+    f, lay, aos_h, ncell = _tiny()
+    v = H.new_view(lay, 0, aos_h.shape[0], f["box"], ncell)
+    try:
+        for bad in (2, -1):
+            assert sph.lib().sph_view_set_union(v, bad) == sph.SPH_E_INVAL
+        assert sph.lib().sph_view_set_union(v, 0) == sph.SPH_OK
+    finally:
+        sph.sph_view_destroy(v)
