@@ -70,6 +70,7 @@ def _load():
                 "or_reduce": (None, [i64, _D, _D, _D, _D, _D, _D]),
                 "or_kick": (None, [i64, dbl, _D, _D, _D, _D]),
                 "or_drift": (None, [i64, dbl, _D, _D, ctypes.c_int, _D]),
+                "or_h_iterate": (i64, [i64, _D, _D, _D, _D, ctypes.c_int, dbl, dbl, i32, _D, _I32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -299,6 +300,18 @@ def reduce_sums(m, v, a, u, dudt):
     return out
 
 
+def h_iterate(x, m, h, box, periodic=True, eta=1.2, tol=1e-6, max_iter=30):
+    """Smoothing-length iteration: returns (h, rho, rounds run, particles not converged)."""
+    x, m, box = _c(x, np.float64), _c(m, np.float64), _c(box, np.float64)
+    h = np.array(h, np.float64, copy=True, order="C")
+    n = m.size
+    rho = np.empty(n, np.float64)
+    it = np.zeros(1, np.int32)
+    left = _load().or_h_iterate(n, _p(x, _D), _p(m, _D), _p(h, _D), _p(box, _D), int(bool(periodic)), float(eta),
+                                float(tol), int(max_iter), _p(rho, _D), _p(it, _I32))
+    return h, rho, int(it[0]), int(left)
+
+
 def kick(dtk, a, dudt, v, u):
     """v += a dtk, u += du/dt dtk, in place on copies; returns (v, u)."""
     a, dudt = _c(a, np.float64), _c(dudt, np.float64)
@@ -339,6 +352,14 @@ def density_pass(aos, layout, box, gamma, periodic=True, targets=None):
     u = f["u"] if targets is None else f["u"][np.asarray(targets)]
     P, cs = eos(rho, u, gamma)
     return rho, P, cs
+
+
+def density_h_pass(aos, layout, box, params, eta=1.2, tol=1e-6, max_iter=30, periodic=True):
+    """Expected results of the smoothing-length iteration on the AoS state: dict h, rho, P, cs, iters, left."""
+    f = unpack(aos, layout)
+    h, rho, it, left = h_iterate(f["x"], f["mass"], f["h"], box, periodic, eta, tol, max_iter)
+    P, cs = eos(rho, f["u"], params["gamma"])
+    return {"h": h, "rho": rho, "P": P, "cs": cs, "iters": it, "left": left}
 
 
 def step_all(aos, layout, box, params, periodic=True):

@@ -18,6 +18,8 @@
  *     symmetrised momentum / energy equations of Price (2012);  or_density / or_eos / or_force;
  *   - the FP64 global momentum and energy sums; or_reduce.
  *   - the leapfrog kick-drift-kick of Section 2.1 (steps 3-5); or_kick / or_drift.
+ *   - the smoothing-length iteration of Section 2.1 step 1 (density, grow or shrink h, repeat until every
+ *     particle meets its termination test); or_h_iterate.
  *
  * Compile with -ffp-contract=off: every product and sum below is rounded on its own, exactly as written.
  */
@@ -461,4 +463,49 @@ void or_drift(int64_t n, double dt, const double *v, const double *box, int peri
             x[3 * i + d] = xn;
         }
     }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Smoothing-length iteration (Section 2.1, step 1: compute the density, decide to grow or shrink the
+ * interaction radius, recompute, until every particle meets its termination criterion).  The paper gives no
+ * update rule; the one used is h <- eta (m_i / rho_i)^(1/3), which at uniform density rho = m / s^3 gives
+ * h = eta s, with the termination test |h_new - h| < tol h, in FP64.  A particle that passes is frozen at
+ * h_new.  Every round recomputes the densities of the particles not yet frozen (rho_i depends on h_i only);
+ * after the last round the densities of all particles are recomputed at their final h.
+ * h is updated in place; rho_out receives the final densities; *iters_out the number of rounds run (at most
+ * max_iter).  Returns the number of particles still not frozen after the last round (0 = converged).
+ * ------------------------------------------------------------------------------------------------------- */
+int64_t or_h_iterate(int64_t n, const double *x, const double *m, double *h, const double *box, int periodic,
+                     double eta, double tol, int32_t max_iter, double *rho_out, int32_t *iters_out)
+{
+    unsigned char *done = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t *targets = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double *rho_t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *h_new = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int64_t undone = n;
+    int32_t it = 0;
+    while (undone > 0 && it < max_iter) {
+        ++it;
+        int64_t nt = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!done[i]) targets[nt++] = i;
+        }
+        or_density(n, x, m, h, box, periodic, nt, targets, rho_t);
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t i = targets[t];
+            h_new[t] = eta * cbrt(m[i] / rho_t[t]);
+            if (fabs(h_new[t] - h[i]) < tol * h[i]) done[i] = 1;
+        }
+        for (int64_t t = 0; t < nt; ++t) h[targets[t]] = h_new[t];
+        undone = 0;
+        for (int64_t i = 0; i < n; ++i) undone += done[i] ? 0 : 1;
+    }
+    for (int64_t i = 0; i < n; ++i) targets[i] = i;
+    or_density(n, x, m, h, box, periodic, n, targets, rho_out);
+    *iters_out = it;
+    free(done);
+    free(targets);
+    free(rho_t);
+    free(h_new);
+    return undone;
 }

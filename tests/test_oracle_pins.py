@@ -447,3 +447,57 @@ def test_patch_fp32_positions_round_trip(oracle):
     k = np.stack([local % nn[:, 0], (local // nn[:, 0]) % nn[:, 1], local // (nn[:, 0] * nn[:, 1])], axis=1)
     back = k * edge + rel.T.astype(np.float64)
     assert np.all(np.abs(back - x) <= edge * 2.0 ** -24 + 1e-16)
+
+
+# ---- smoothing-length iteration (Section 2.1, step 1) ----
+def test_h_iteration_isolated_particles_closed_form(oracle):
+    """A particle with no neighbour has rho = m W(0, h) = m / (pi h^3), so every round multiplies h by
+    eta pi^(1/3) exactly and the iteration never terminates."""
+    x = np.array([[1.0, 1.0, 1.0], [20.0, 1.0, 1.0], [1.0, 40.0, 60.0]])
+    m = np.array([1.0, 2.0, 0.5])
+    h0 = np.array([0.1, 0.2, 0.05])
+    eta = 1.2
+    h, rho, it, left = oracle.h_iterate(x, m, h0, np.full(3, 100.0), periodic=False, eta=eta, tol=1e-6, max_iter=3)
+    g = eta * np.pi ** (1.0 / 3.0)
+    np.testing.assert_allclose(h, h0 * g ** 3, rtol=1e-13)
+    np.testing.assert_allclose(rho, m / (np.pi * h ** 3), rtol=1e-13)
+    assert it == 3 and left == 3
+
+
+def test_h_iteration_scale_invariance(oracle):
+    """x -> 2x, box -> 2 box, h -> 2h, m -> 8m leaves every density unchanged, so the iteration must return 2h
+    after the same number of rounds: this fixes the exponent 1/3 and the m / rho ratio of the update."""
+    f = wl.clustered(400, sigma=0.08, peak=4.0, n_side_equiv=8, seed=4)
+    h1, rho1, it1, left1 = oracle.h_iterate(f["x"], f["mass"], f["h"], f["box"], eta=1.2, tol=1e-6, max_iter=30)
+    h2, rho2, it2, left2 = oracle.h_iterate(2 * f["x"], 8 * f["mass"], 2 * f["h"], 2 * f["box"], eta=1.2,
+                                            tol=1e-6, max_iter=30)
+    assert it1 == it2 and left1 == left2 == 0
+    np.testing.assert_allclose(h2, 2 * h1, rtol=1e-13)
+    np.testing.assert_allclose(rho2, rho1, rtol=1e-12)
+
+
+def test_h_iteration_perfect_lattice_fixed_point(oracle):
+    """On a perfect periodic lattice every particle sees the same neighbourhood, so all converge to one h; that h
+    solves h = eta (m / rho(h))^(1/3) to within the termination tolerance, and sits near eta s (the update is
+    exact at uniform density)."""
+    ns = 8
+    s = 1.0 / ns
+    idx = np.indices((ns, ns, ns)).reshape(3, -1).T.astype(np.float64)
+    x = (idx + 0.5) * s
+    n = ns ** 3
+    m = np.full(n, 1.0 / n)
+    tol = 1e-8
+    h, rho, it, left = oracle.h_iterate(x, m, np.full(n, 1.05 * s), np.ones(3), eta=1.2, tol=tol, max_iter=50)
+    assert left == 0 and 1 < it < 50
+    assert np.ptp(h) <= 1e-12 * h[0]
+    assert 1.1 < h[0] / s < 1.3
+    resid = 1.2 * np.cbrt(m / rho) - h
+    assert np.max(np.abs(resid)) <= 2 * tol * h[0]
+
+
+def test_h_iteration_stops_at_max_iter(oracle):
+    f = wl.tiny()
+    h, rho, it, left = oracle.h_iterate(f["x"], f["mass"], f["h"], f["box"], max_iter=1)
+    assert it == 1 and 0 < left <= len(h)
+    h_full, _, it_full, left_full = oracle.h_iterate(f["x"], f["mass"], f["h"], f["box"], max_iter=30)
+    assert left_full == 0 and it_full > 1
