@@ -81,6 +81,7 @@ enum {
 #define SPH_DEV_H_TOO_BIG 0x2u  /* 2h exceeded the smallest cell edge: the 3^3 stencil may miss pairs      */
 #define SPH_DEV_NONFINITE 0x4u  /* a density, pressure or sound speed came out non-finite or <= 0           */
 #define SPH_DEV_TIMEOUT 0x8u    /* a bounded device-side wait gave up                                       */
+#define SPH_DEV_NOTCONV 0x10u   /* a smoothing-length iteration inside sph_step left particles unconverged   */
 
 /* Record layout: `stride` bytes per record (a multiple of 8, at most 65536); off[f] is the byte offset of
  * member f inside a record (a multiple of 8), or -1 if the record has no such member.  Present members must
@@ -153,6 +154,32 @@ SPH_API sph_status sph_step_graph(sph_view view, void *aos_dev, int64_t n, const
                                   int32_t nsteps);
 SPH_API sph_status sph_patches_step_graph(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
                                           int32_t npatch, const sph_params *params);
+
+/* Smoothing-length iteration (Section 2.1, step 1: compute the density, decide whether to grow or shrink the
+ * interaction radius, recompute, until every particle meets its termination criterion) on the resident density
+ * view.  The paper fixes no update rule; the one used is h_i <- eta (m_i / rho_i)^(1/3) (exact at uniform
+ * density rho = m / s^3, where it gives h = eta s) with the termination test |h_new - h| < tol h, evaluated in
+ * FP64 for both view precisions; a particle that passes keeps that h_new.  Each round recomputes the density at
+ * the current h; at most max_iter rounds run, then the density (and P, c_s) of every particle is recomputed at
+ * its final h.  The SoA members h, rho, P, c_s hold the result; scatter SPH_BIT(SPH_H) | SPH_DENSITY_OUT to
+ * write it into the records.  Rounds after convergence cost one near-empty launch each; nothing inside waits,
+ * then the call waits once and reports *rounds (rounds run) and *unconverged (particles not converged after the
+ * last round).  The new h must keep 2h within the view's cell edge (else SPH_E_DEVICE, SPH_DEV_H_TOO_BIG): create
+ * the view with room for h to grow.  Grid views only.  Errors: SPH_E_INVAL (eta <= 0, tol not in (0, 1),
+ * max_iter not in 1..1000, patch view), SPH_E_STATE (density view not resident), SPH_E_NOTCONV (particles left
+ * unconverged; results are still written), SPH_E_DEVICE. */
+SPH_API sph_status sph_density_h(sph_view view, const sph_params *params, double eta, double tol, int32_t max_iter,
+                                 int32_t *rounds, int64_t *unconverged);
+
+/* Run the smoothing-length iteration in place of the single density pass inside every sph_step pass
+ * (max_iter > 0; 0 switches it off, the default).  h is then scattered with the density outputs.  Nothing waits:
+ * a pass that leaves particles unconverged sets SPH_DEV_NOTCONV, and sph_view_h_rounds reports the last
+ * iteration.  Errors: SPH_E_INVAL (as sph_density_h, max_iter not in 0..1000). */
+SPH_API sph_status sph_view_set_h_iteration(sph_view view, double eta, double tol, int32_t max_iter);
+
+/* Rounds run and particles left unconverged by the view's last smoothing-length iteration.  Waits.  Returns
+ * SPH_E_NOTCONV if particles were left, SPH_E_DEVICE if other device status bits are set. */
+SPH_API sph_status sph_view_h_rounds(sph_view view, int32_t *rounds, int64_t *unconverged);
 
 /* How sph_step / sph_patches_step convert (Section 8, future work: keep the SoA across loops).  on = 1 (the
  * default): one view serves both loops -- the density view's members and outputs stay in SoA for the force, only

@@ -157,7 +157,13 @@ struct PairLaunch {
     const int *work_count;    // patches: number of entries in work_order (device)
     int *work_next;           // patches: work counter (device, zeroed by the launcher)
     int persistent_ctas;      // patches: CTAs of the persistent launch
+    const int *skip;          // device flag: when nonzero the pair kernel returns at once (nullptr: never)
 };
+
+// The smoothing-length iteration (sph_hiter.cu): one round's update + bookkeeping, and the final status check.
+cudaError_t launch_h_update(bool f32, const SoaPtrs &soa, int n, double eta, double tol, double h_limit,
+                            unsigned char *done, int *hstate, unsigned *status, cudaStream_t st, int *nl);
+cudaError_t launch_h_finish(const int *hstate, unsigned *status, cudaStream_t st, int *nl);
 
 // The pair kernels.
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,

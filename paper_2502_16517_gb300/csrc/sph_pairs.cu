@@ -252,7 +252,8 @@ struct PairCommon {
     CellSpace cs;
     unsigned *status;
     Counters *counters;
-    int tj;  // staged particles per tile (a multiple of kStep)
+    int tj;            // staged particles per tile (a multiple of kStep)
+    const int *skip;   // device flag: nonzero = return at once (a converged smoothing-length iteration)
 };
 
 // ---- density, FP64 ----
@@ -878,6 +879,7 @@ template <class K>
 __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, const typename K::Tile &T,
                                              PairShared<K> &S)
 {
+    if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1009,6 +1011,7 @@ template <class K>
 __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, int c, const typename K::Tile &T,
                                                    LaneShared<K> &S, unsigned char *smem)
 {
+    if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1372,7 +1375,7 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
-    PairCommon cm{cell_start, g, status, counters, 0};
+    PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
     const int tj = pl.tj;
     if (!f32) {
         DensF64::Args A;
@@ -1420,7 +1423,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
-    PairCommon cm{cell_start, g, status, counters, 0};
+    PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
     const int tj = pl.tj;
     if (!f32) {
         ForceF64::Args A;

@@ -88,6 +88,12 @@ struct sph_view_s {
     int64_t g_launches[SPH_NPHASES];
     int persistent_ctas;           // CTAs of the persistent pair launches (patch views; 0 = as many as fit)
     bool union_view;               // one gather per member and one scatter per pass (sph_view_set_union)
+    // smoothing-length iteration
+    unsigned char *hdone;          // per slot: converged
+    int *hstate;                   // [left this round, all converged, rounds run, left after the last round]
+    int *h_hstate;                 // pinned host copy of hstate
+    double h_eta, h_tol;
+    int h_max_iter;                // 0: sph_step runs one density pass
 };
 
 namespace {
@@ -231,6 +237,8 @@ void carve(sph_view_s *v, Bump &b)
         v->work_count = (int *)b.take(4);
         v->work_next = (int *)b.take(4);
     }
+    v->hdone = (unsigned char *)b.take(nm);
+    v->hstate = (int *)b.take(4 * sizeof(int));
     v->status = (unsigned *)b.take(sizeof(unsigned));
     v->counters = (sphk::Counters *)b.take(sizeof(sphk::Counters));
     v->red_partials = (double *)b.take(1024 * 8 * sizeof(double));
@@ -326,6 +334,7 @@ sphk::PairLaunch pair_launch(const sph_view_s *v, int tj)
     pl.work_count = v->work_count;
     pl.work_next = v->work_next;
     pl.persistent_ctas = v->persistent_ctas;
+    pl.skip = nullptr;
     return pl;
 }
 
@@ -397,11 +406,9 @@ sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask)
     return cuda_fail(e);
 }
 
-sph_status do_density(sph_view_s *v, const sph_params *p)
+// One density pass; with `skip` (a device flag) every pair CTA returns at once while the flag is set.
+sph_status density_launch(sph_view_s *v, const sph_params *p, const int *skip)
 {
-    if (!p) return SPH_E_INVAL;
-    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
-    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
     const bool f32 = v->prec == SPH_F32;
     cudaError_t e;
     {
@@ -411,10 +418,54 @@ sph_status do_density(sph_view_s *v, const sph_params *p)
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_DENSITY);
-        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, p->gamma,
-                                       pair_launch(v, v->tile_density), v->status, v->counters, v->st, &ph.nl);
+        sphk::PairLaunch pl = pair_launch(v, v->tile_density);
+        pl.skip = skip;
+        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, p->gamma, pl,
+                                       v->status, v->counters, v->st, &ph.nl);
     }
+    return cuda_fail(e);
+}
+
+sph_status do_density(sph_view_s *v, const sph_params *p)
+{
+    if (!p) return SPH_E_INVAL;
+    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
+    sph_status s = density_launch(v, p, nullptr);
+    if (s != SPH_OK) return s;
+    v->resident |= SPH_DENSITY_OUT;
+    return SPH_OK;
+}
+
+// Smoothing-length iteration (Section 2.1, step 1) on the resident density view: max_iter rounds of density +
+// FP64 update / termination test, rounds after convergence returning at once on the device, then the density
+// of every particle at its final h.  Nothing waits.  With flag_status, particles left unconverged set
+// SPH_DEV_NOTCONV in the status word.
+sph_status do_density_h(sph_view_s *v, const sph_params *p, double eta, double tol, int max_iter, bool flag_status)
+{
+    if (!p || !(eta > 0.0) || !(eta < 1e6) || !(tol > 0.0) || !(tol < 1.0) || max_iter < 1 || max_iter > 1000)
+        return SPH_E_INVAL;
+    if (v->npatch_max > 0) return SPH_E_INVAL;  // patch grids are sized once per bin from the patch's h
+    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
+    const int n = (int)v->n;
+    cudaError_t e = cudaMemsetAsync(v->hdone, 0, (size_t)std::max(n, 1), v->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->hstate, 0, 4 * sizeof(int), v->st);
     if (e != cudaSuccess) return SPH_E_CUDA;
+    for (int r = 0; r < max_iter; ++r) {
+        sph_status s = density_launch(v, p, v->hstate + 1);
+        if (s != SPH_OK) return s;
+        Phase ph(v, SPH_PH_DENSITY);
+        e = sphk::launch_h_update(v->prec == SPH_F32, v->soa, n, eta, tol, 0.5 * v->g.min_edge, v->hdone, v->hstate,
+                                  v->status, v->st, &ph.nl);
+        if (e != cudaSuccess) return SPH_E_CUDA;
+    }
+    sph_status s = density_launch(v, p, nullptr);
+    if (s != SPH_OK) return s;
+    if (flag_status) {
+        Phase ph(v, SPH_PH_DENSITY);
+        if (sphk::launch_h_finish(v->hstate, v->status, v->st, &ph.nl) != cudaSuccess) return SPH_E_CUDA;
+    }
     v->resident |= SPH_DENSITY_OUT;
     return SPH_OK;
 }
@@ -450,10 +501,16 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
         return s;
     }
     if ((s = do_gather(v, aos, n, SPH_DENSITY_IN)) != SPH_OK) return s;
-    if ((s = do_density(v, p)) != SPH_OK) return s;
+    uint32_t dens_out = SPH_DENSITY_OUT;
+    if (v->h_max_iter > 0) {
+        if ((s = do_density_h(v, p, v->h_eta, v->h_tol, v->h_max_iter, true)) != SPH_OK) return s;
+        dens_out |= SPH_BIT(SPH_H);  // the iteration writes h as well
+    } else if ((s = do_density(v, p)) != SPH_OK) {
+        return s;
+    }
     if (!v->union_view) {
         // one view per loop, converted forth and back around each (the paper's prologue / epilogue per loop)
-        if ((s = do_scatter(v, aos, n, SPH_DENSITY_OUT)) != SPH_OK) return s;
+        if ((s = do_scatter(v, aos, n, dens_out)) != SPH_OK) return s;
         if ((s = do_gather(v, aos, n, SPH_FORCE_IN)) != SPH_OK) return s;
         if ((s = do_force(v, p)) != SPH_OK) return s;
         return do_scatter(v, aos, n, SPH_FORCE_OUT);
@@ -463,7 +520,7 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     const uint32_t more = SPH_FORCE_IN & ~v->resident;
     if (more && (s = do_gather(v, aos, n, more)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;
-    return do_scatter(v, aos, n, SPH_DENSITY_OUT | SPH_FORCE_OUT);
+    return do_scatter(v, aos, n, dens_out | SPH_FORCE_OUT);
 }
 
 // Half kick on the view (v += a dt/2, u += du/dt dt/2), then write v and u back into the records.
@@ -636,6 +693,41 @@ sph_status sph_patches_step_graph(sph_view v, void *aos_dev, int64_t n, const in
     return do_step_graph(v, aos_dev, n, params, 0.0, 0);
 }
 
+sph_status sph_density_h(sph_view v, const sph_params *params, double eta, double tol, int32_t max_iter,
+                         int32_t *rounds, int64_t *unconverged)
+{
+    if (!v) return SPH_E_INVAL;
+    sph_status s = do_density_h(v, params, eta, tol, max_iter, false);
+    if (s != SPH_OK) return s;
+    return sph_view_h_rounds(v, rounds, unconverged);
+}
+
+sph_status sph_view_h_rounds(sph_view v, int32_t *rounds, int64_t *unconverged)
+{
+    if (!v) return SPH_E_INVAL;
+    if (cudaMemcpyAsync(v->h_hstate, v->hstate, 4 * sizeof(int), cudaMemcpyDeviceToHost, v->st) != cudaSuccess)
+        return SPH_E_CUDA;
+    uint32_t bits = 0;
+    sph_status s = read_status(v, &bits, false);  // waits
+    if (s != SPH_OK) return s;
+    if (rounds) *rounds = v->h_hstate[2];
+    if (unconverged) *unconverged = v->h_hstate[3];
+    if (bits & ~SPH_DEV_NOTCONV) return SPH_E_DEVICE;
+    return v->h_hstate[3] > 0 ? SPH_E_NOTCONV : SPH_OK;
+}
+
+sph_status sph_view_set_h_iteration(sph_view v, double eta, double tol, int32_t max_iter)
+{
+    if (!v || max_iter < 0 || max_iter > 1000) return SPH_E_INVAL;
+    if (max_iter > 0 && (!(eta > 0.0) || !(eta < 1e6) || !(tol > 0.0) || !(tol < 1.0) || v->npatch_max > 0))
+        return SPH_E_INVAL;
+    v->h_eta = eta;
+    v->h_tol = tol;
+    v->h_max_iter = max_iter;
+    graph_drop(v);
+    return SPH_OK;
+}
+
 sph_status sph_view_set_union(sph_view v, int32_t on)
 {
     if (!v || (on != 0 && on != 1)) return SPH_E_INVAL;
@@ -737,6 +829,10 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     v->ncells = domain->ncell[0] * domain->ncell[1] * domain->ncell[2];
     v->esz = prec == SPH_F64 ? 8 : 4;
     v->present = present;
+    v->union_view = true;
+    v->h_max_iter = 0;
+    v->h_eta = 1.2;
+    v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
     v->ev_pending = new (std::nothrow) std::vector<PendingTiming>();
     if (!v->ev_free || !v->ev_pending) {
@@ -757,7 +853,8 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     carve(v, real);
     if (cudaMallocHost(&v->h_status, sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&v->h_red, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess) {
+        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess ||
+        cudaMallocHost(&v->h_hstate, 4 * sizeof(int)) != cudaSuccess) {
         sph_view_destroy(v);
         return SPH_E_NOMEM;
     }
@@ -809,6 +906,9 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     v->present = present;
     v->persistent_ctas = 0;  // sized from the pair kernels' occupancy at launch
     v->union_view = true;
+    v->h_max_iter = 0;
+    v->h_eta = 1.2;
+    v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
     v->ev_pending = new (std::nothrow) std::vector<PendingTiming>();
     if (!v->ev_free || !v->ev_pending) {
@@ -829,7 +929,8 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     carve(v, real);
     if (cudaMallocHost(&v->h_status, sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&v->h_red, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess) {
+        cudaMallocHost(&v->h_counters, sizeof(sphk::Counters)) != cudaSuccess ||
+        cudaMallocHost(&v->h_hstate, 4 * sizeof(int)) != cudaSuccess) {
         sph_view_destroy(v);
         return SPH_E_NOMEM;
     }
@@ -869,6 +970,7 @@ sph_status sph_view_destroy(sph_view v)
     if (v->h_status) cudaFreeHost(v->h_status);
     if (v->h_red) cudaFreeHost(v->h_red);
     if (v->h_counters) cudaFreeHost(v->h_counters);
+    if (v->h_hstate) cudaFreeHost(v->h_hstate);
     graph_drop(v);
     if (v->ev_pending) {
         for (const PendingTiming &p : *v->ev_pending) {

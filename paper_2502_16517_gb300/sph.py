@@ -35,6 +35,7 @@ SPH_FORCE_IN = (SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_MASS) | SPH_BIT(SP
 SPH_FORCE_OUT = SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT)
 SPH_ALL_FIELDS = (1 << SPH_NFIELDS) - 1
 SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 0x2, 0x4, 0x8
+SPH_DEV_NOTCONV = 0x10
 (SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
  SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
 SPH_NPHASES = 9
@@ -98,6 +99,9 @@ _SIGS = {
     "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
     "sph_view_set_tiles": [_VP, _I32, _I32],
     "sph_view_set_union": [_VP, _I32],
+    "sph_density_h": [_VP, _VP, ctypes.c_double, ctypes.c_double, _I32, _VP, _VP],
+    "sph_view_set_h_iteration": [_VP, ctypes.c_double, ctypes.c_double, _I32],
+    "sph_view_h_rounds": [_VP, _VP, _VP],
     "sph_autotune": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
 }
@@ -334,6 +338,30 @@ def sph_patches_step_graph(view, aos_dev, n, patch_start_dev, npatch, params):
     P = params if isinstance(params, sph_params) else make_params(params)
     _check("sph_patches_step_graph", lib().sph_patches_step_graph(view, _addr(aos_dev), int(n), _addr(patch_start_dev),
                                                                   int(npatch), ctypes.byref(P)))
+
+
+def sph_density_h(view, params, eta=1.2, tol=1e-6, max_iter=30, allow_unconverged=False):
+    """Returns (rounds, unconverged).  Raises SphError(SPH_E_NOTCONV) if particles are left unconverged, unless
+    allow_unconverged."""
+    P = params if isinstance(params, sph_params) else make_params(params)
+    rounds, left = ctypes.c_int32(), ctypes.c_int64()
+    st = lib().sph_density_h(view, ctypes.byref(P), float(eta), float(tol), int(max_iter), ctypes.byref(rounds),
+                             ctypes.byref(left))
+    if not (st == SPH_OK or (allow_unconverged and st == SPH_E_NOTCONV)):
+        raise SphError("sph_density_h", st)
+    return rounds.value, left.value
+
+
+def sph_view_set_h_iteration(view, eta=1.2, tol=1e-6, max_iter=30):
+    _check("sph_view_set_h_iteration", lib().sph_view_set_h_iteration(view, float(eta), float(tol), int(max_iter)))
+
+
+def sph_view_h_rounds(view, allow_unconverged=True):
+    rounds, left = ctypes.c_int32(), ctypes.c_int64()
+    st = lib().sph_view_h_rounds(view, ctypes.byref(rounds), ctypes.byref(left))
+    if not (st == SPH_OK or (allow_unconverged and st == SPH_E_NOTCONV)):
+        raise SphError("sph_view_h_rounds", st)
+    return rounds.value, left.value
 
 
 def sph_view_set_union(view, on=True):
