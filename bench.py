@@ -329,14 +329,13 @@ def run_e2e(prec, steps, warmup, dev, aos_h, lay, box, ncell):
 
 def conversion_bytes(prec, n, union=True):
     """Algorithmic bytes of the view conversions of one pass (read + written, incl. the 4-byte perm read; FP32
-    positions also read the 4-byte cell of the slot).  Union view: gather {x,m,h,u} and {v}, one scatter of
+    positions also read the 4-byte cell of the slot).  Union view: one gather of {x,m,h,u,v}, one scatter of
     {rho,P,cs,a,dudt}; per-loop views: gather {x,m,h,u} and {x,v,m,h,rho,P,cs}, scatter {rho,P,cs} and {a,dudt}."""
     e = 8 if prec == 0 else 4
     pos_extra = 0 if prec == 0 else 4
-    gather_d = n * (6 * 8 + 6 * e + 4 + pos_extra)
     if union:
-        gather_f = n * (3 * 8 + 3 * e + 4)
-        return gather_d + gather_f, n * (7 * 8 + 7 * e + 4)
+        return n * (9 * 8 + 9 * e + 4 + pos_extra), n * (7 * 8 + 7 * e + 4)
+    gather_d = n * (6 * 8 + 6 * e + 4 + pos_extra)
     gather_f = n * (11 * 8 + 11 * e + 4 + pos_extra)
     scatter_d = n * (3 * 8 + 3 * e + 4)
     scatter_f = n * (4 * 8 + 4 * e + 4)
@@ -564,8 +563,8 @@ def main():
         "dtype": main_form, "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": n, "cells": int(np.prod(ncell)), "record_bytes": lay["stride"],
                    "l2": "256 MB buffer written between timed steps (outside the step events)",
-                   "step": ("sph_step with one view for both loops: bin + gather {x,m,h,u} + density + gather {v} "
-                            "+ force + one scatter of {rho,P,cs,a,dudt}"),
+                   "step": ("sph_step with one view for both loops: bin + one gather of {x,m,h,u,v} + density + "
+                            "force + one scatter of {rho,P,cs,a,dudt}"),
                    "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline_of(prec_main, s64, steps, peaks, fma_peak[main_form]),

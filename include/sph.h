@@ -182,8 +182,8 @@ SPH_API sph_status sph_view_set_h_iteration(sph_view view, double eta, double to
 SPH_API sph_status sph_view_h_rounds(sph_view view, int32_t *rounds, int64_t *unconverged);
 
 /* How sph_step / sph_patches_step convert (Section 8, future work: keep the SoA across loops).  on = 1 (the
- * default): one view serves both loops -- the density view's members and outputs stay in SoA for the force, only
- * the members the force adds (v) are gathered, and rho, P, c_s, a, du/dt are scattered together after the force.
+ * default): one view serves both loops -- one gather brings in every member either loop reads (x, m, h, u, v),
+ * the density outputs stay in SoA for the force, and rho, P, c_s, a, du/dt are scattered together after it.
  * on = 0: one view per loop, converted forth and back around each (scatter the density outputs, gather the full
  * force view), as the paper's annotated loops do.  The records end up byte-identical either way.  Errors:
  * SPH_E_INVAL (on not 0 or 1). */

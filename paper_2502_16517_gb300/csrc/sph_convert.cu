@@ -4,14 +4,15 @@
 // 2.2 / 5.2: the particles of a cell form one contiguous chunk indexed by a CSR-like list):
 //   k_bin_count   one thread per record: cell coordinate floor(x * n/box) per axis, clamped, linear cell id,
 //                 histogram by atomicAdd;
-//   k_scan_cells  one CTA: exclusive scan of the histogram into cell_start (CSR) and the fill cursors;
+//   k_scan_cells  one CTA: exclusive scan of the histogram into cell_start (CSR) and the fill cursors (small
+//                 grids); large grids use k_scan_block_sums + k_scan_cells over the block sums + k_scan_apply;
 //   k_bin_place   one thread per record: claims a slot of its cell (atomic cursor);
 //   k_cell_sort   one warp per cell: ranks the claimed record indices so that each cell holds ascending record
 //                 indices (the slot order is then independent of atomic timing, i.e. deterministic).
 //
 // Patch views (independent open boxes): k_patch_grid gives every patch its own grid with cell edge >= 2 h_max of
-// the patch (capped), k_bin_count_patches maps records to global cell ids, and the same scan / place / sort
-// follow, with the cell count read on the device.
+// the patch (capped), k_bin_count_patches (one CTA per patch) maps records to global cell ids, and the same scan
+// / place / sort follow, with the cell count read on the device.
 //
 // Views (Section 4, Eq. 3-5; prologue/epilogue of Section 3.1):
 //   k_gather      CTA per tile of 256 slots.  Phase 1 reads, per record, only the 16-byte chunks that hold a
@@ -118,6 +119,81 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_cells(const int *__restri
     if (tid == 0) cell_start[ncells] = carry_s;
 }
 
+// Multi-CTA exclusive scan for large grids, in three deterministic launches: every CTA sums its kScanChunk cells
+// (k_scan_block_sums), one CTA scans those sums (k_scan_cells on the block sums), every CTA rescans its chunk from
+// its block offset (k_scan_apply).  The cell count may live on the device (patch views); CTAs past it idle.
+constexpr int kScanChunk = kScanThreads * 4;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_block_sums(const int *__restrict__ count, int ncells_host,
+                                                                  const int *__restrict__ ncells_dev,
+                                                                  int *__restrict__ block_sum)
+{
+    __shared__ int warp_tot[32];
+    const int ncells = ncells_dev ? *ncells_dev : ncells_host;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int idx = blockIdx.x * kScanChunk + tid * 4;
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t += (idx + k < ncells) ? count[idx + k] : 0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (lane == 0) warp_tot[warp] = t;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+        if (lane == 0) block_sum[blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restrict__ count, int ncells_host,
+                                                             const int *__restrict__ ncells_dev,
+                                                             const int *__restrict__ block_off,
+                                                             int *__restrict__ cell_start, int *__restrict__ fill)
+{
+    __shared__ int warp_tot[32];
+    const int ncells = ncells_dev ? *ncells_dev : ncells_host;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && tid == 0) cell_start[ncells] = block_off[gridDim.x];  // the total
+    const int base = blockIdx.x * kScanChunk;
+    if (base >= ncells) return;  // CTA-uniform
+    const int idx = base + tid * 4;
+    int v[4];
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (idx + k < ncells) ? count[idx + k] : 0;
+        t += v[k];
+    }
+    int incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = warp_tot[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = block_off[blockIdx.x] + warp_tot[warp] + incl - t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (idx + k < ncells) {
+            cell_start[idx + k] = run;
+            fill[idx + k] = run;
+        }
+        run += v[k];
+    }
+}
+
 __global__ void k_bin_place(const int *__restrict__ cell_of, int n, int *__restrict__ fill,
                             int *__restrict__ perm_tmp)
 {
@@ -190,30 +266,31 @@ __global__ void __launch_bounds__(256) k_patch_grid(const uint8_t *__restrict__ 
     }
 }
 
-// Global cell of every record of a patch view: patch by binary search of the record index in patch_start, then
-// floor(x * (n / box)) per axis in the patch grid, clamped (positions outside [0, box] set SPH_DEV_POS_RANGE).
-__global__ void k_bin_count_patches(const uint8_t *__restrict__ aos, int64_t stride, int off_x, int n,
-                                    const int64_t *__restrict__ patch_start, int npatch, Grid g,
-                                    const int *__restrict__ patch_n, const double *__restrict__ patch_inv,
-                                    const int *__restrict__ patch_cell_base, int *__restrict__ cell_of,
-                                    int *__restrict__ count, unsigned *status)
+// Global cell of every record of a patch view, one CTA per patch: floor(x * (n / box)) per axis in the patch's
+// grid, clamped (positions outside [0, box] set SPH_DEV_POS_RANGE).
+__global__ void __launch_bounds__(256) k_bin_count_patches(const uint8_t *__restrict__ aos, int64_t stride, int off_x,
+                                                           const int64_t *__restrict__ patch_start, Grid g,
+                                                           const int *__restrict__ patch_n,
+                                                           const double *__restrict__ patch_inv,
+                                                           const int *__restrict__ patch_cell_base,
+                                                           int *__restrict__ cell_of, int *__restrict__ count,
+                                                           unsigned *status)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int lo = 0, hi = npatch;  // patch_start[lo] <= i < patch_start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (patch_start[mid] <= (int64_t)i) lo = mid; else hi = mid;
-    }
-    const double *xp = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_x);
+    const int p = blockIdx.x;
+    const int64_t s = patch_start[p], e = patch_start[p + 1];
+    const int nx = patch_n[3 * p], ny = patch_n[3 * p + 1], nz = patch_n[3 * p + 2];
+    const double ix = patch_inv[3 * p], iy = patch_inv[3 * p + 1], iz = patch_inv[3 * p + 2];
+    const int cb = patch_cell_base[p];
     bool bad = false;
-    const int nx = patch_n[3 * lo], ny = patch_n[3 * lo + 1], nz = patch_n[3 * lo + 2];
-    const int kx = cell_coord(__ldg(xp + 0), patch_inv[3 * lo], nx, g.box[0], bad);
-    const int ky = cell_coord(__ldg(xp + 1), patch_inv[3 * lo + 1], ny, g.box[1], bad);
-    const int kz = cell_coord(__ldg(xp + 2), patch_inv[3 * lo + 2], nz, g.box[2], bad);
-    const int c = patch_cell_base[lo] + kx + nx * (ky + ny * kz);
-    cell_of[i] = c;
-    atomicAdd(&count[c], 1);
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+        const double *xp = reinterpret_cast<const double *>(aos + i * stride + off_x);
+        const int kx = cell_coord(__ldg(xp + 0), ix, nx, g.box[0], bad);
+        const int ky = cell_coord(__ldg(xp + 1), iy, ny, g.box[1], bad);
+        const int kz = cell_coord(__ldg(xp + 2), iz, nz, g.box[2], bad);
+        const int c = cb + kx + nx * (ky + ny * kz);
+        cell_of[i] = c;
+        atomicAdd(&count[c], 1);
+    }
     if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
 }
 
@@ -235,11 +312,32 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int srec[kTile];
+    __shared__ double sorg[F32 ? 3 * kTile : 1];  // FP32 views: origin of each slot's cell
+    __shared__ int prange[2];
     const int base = blockIdx.x * kTile;
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
     for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    bool haspos = false;
+    if (F32) {
+        for (int k = 0; k < plan.nitems; ++k) haspos = haspos || plan.item_pos[k] >= 0;
+        if (haspos && cs.npatch > 0 && tid < 2) {
+            // the tile's slots are cell-ordered, so its cells lie in the patches between these two
+            CellLoc L;
+            locate_cell(cs, cell_of_slot[base + (tid == 0 ? 0 : cnt - 1)], L);
+            prange[tid] = L.patch;
+        }
+    }
     __syncthreads();
+    if (F32 && haspos) {
+        const int lo = cs.npatch > 0 ? prange[0] : 0, hi = cs.npatch > 0 ? prange[1] + 1 : 0;
+        for (int s = tid; s < cnt; s += kTile) {
+            CellLoc L;
+            locate_cell_in(cs, cell_of_slot[base + s], lo, hi, L);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sorg[3 * s + a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
+        }
+    }
     const int nch = plan.nchunks;
     const int nload = cnt * nch;
     if (VEC16) {
@@ -274,8 +372,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             const int axis = plan.item_pos[k];
             float o;
             if (axis >= 0) {
-                const double origin = cell_origin(cs, cell_of_slot[base + s], axis);
-                o = __double2float_rn(__dsub_rn(v, origin));
+                o = __double2float_rn(__dsub_rn(v, sorg[3 * s + axis]));
             } else {
                 o = __double2float_rn(v);
             }
@@ -323,9 +420,33 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
 
 }  // namespace
 
+int scan_tmp_ints(int ncells_cap) { return 3 * ((ncells_cap + kScanChunk - 1) / kScanChunk) + 4; }
+
+namespace {
+
+// Exclusive scan of count[0 .. ncells) into cell_start (ncells + 1 entries) and fill; ncells is ncells_dev's
+// value when given, else ncells_host, and at most ncells_cap.  Small capacities (or no scratch): one CTA.
+void launch_scan(const int *count, int ncells_host, const int *ncells_dev, int ncells_cap, int *cell_start, int *fill,
+                 int *scan_tmp, cudaStream_t st, int *nl)
+{
+    if (!scan_tmp || ncells_cap <= 4 * kScanChunk) {
+        k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells_host, ncells_dev, cell_start, fill);
+        ++*nl;
+        return;
+    }
+    const int nb = (ncells_cap + kScanChunk - 1) / kScanChunk;
+    int *block_sum = scan_tmp, *block_off = scan_tmp + nb, *block_fill = scan_tmp + 2 * nb + 1;
+    k_scan_block_sums<<<nb, kScanThreads, 0, st>>>(count, ncells_host, ncells_dev, block_sum);
+    k_scan_cells<<<1, kScanThreads, 0, st>>>(block_sum, nb, nullptr, block_off, block_fill);
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(count, ncells_host, ncells_dev, block_off, cell_start, fill);
+    *nl += 3;
+}
+
+}  // namespace
+
 cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
                        int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                       int *cell_of_slot, unsigned *status, cudaStream_t st, int *nl)
+                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl)
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells, st);
     if (e != cudaSuccess) return e;
@@ -333,8 +454,7 @@ cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, con
         k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status);
         ++*nl;
     }
-    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells, nullptr, cell_start, fill);
-    ++*nl;
+    launch_scan(count, ncells, nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
         *nl += 2;
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
@@ -350,8 +470,8 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
                                const int64_t *patch_start, int npatch, const Grid &box, int ncap, int ncells_cap,
                                int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
                                int *ncells_dev, int *cell_of, int *count, int *cell_start, int *fill,
-                               int *perm_tmp, int *perm, int *cell_of_slot, unsigned *status, cudaStream_t st,
-                               int *nl)
+                               int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp, unsigned *status,
+                               cudaStream_t st, int *nl)
 {
     // patch_edge holds 3 * npatch edges followed by 3 * npatch inverses
     double *patch_inv = patch_edge + 3 * (size_t)npatch;
@@ -362,12 +482,11 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
     if (e != cudaSuccess) return e;
     *nl += 2;
     if (n > 0) {
-        k_bin_count_patches<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, patch_start, npatch, box, patch_n,
-                                                             patch_inv, patch_cell_base, cell_of, count, status);
+        k_bin_count_patches<<<npatch, 256, 0, st>>>(aos, stride, off_x, patch_start, box, patch_n, patch_inv,
+                                                    patch_cell_base, cell_of, count, status);
         ++*nl;
     }
-    k_scan_cells<<<1, kScanThreads, 0, st>>>(count, ncells_cap, ncells_dev, cell_start, fill);
-    ++*nl;
+    launch_scan(count, ncells_cap, ncells_dev, ncells_cap, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
         k_cell_sort<<<2048, 256, 0, st>>>(cell_start, ncells_cap, ncells_dev, perm_tmp, perm, cell_of_slot);

@@ -47,8 +47,9 @@ struct CellLoc {
     int patch;
 };
 
-// Coordinates of global cell c (patches: binary search of c in patch_cell_base).
-__device__ __forceinline__ void locate_cell(const CellSpace &cs, int c, CellLoc &L)
+// Coordinates of global cell c.  Patches: binary search of c in patch_cell_base over the patches [lo, hi), which
+// must contain c's patch (locate_cell searches all of them).
+__device__ __forceinline__ void locate_cell_in(const CellSpace &cs, int c, int lo, int hi, CellLoc &L)
 {
     int local = c;
     if (cs.npatch == 0) {
@@ -58,8 +59,7 @@ __device__ __forceinline__ void locate_cell(const CellSpace &cs, int c, CellLoc 
         L.base = 0;
         L.patch = 0;
     } else {
-        int lo = 0, hi = cs.npatch;  // patch_cell_base[lo] <= c < patch_cell_base[hi]
-        while (hi - lo > 1) {
+        while (hi - lo > 1) {  // patch_cell_base[lo] <= c < patch_cell_base[hi]
             const int mid = (lo + hi) >> 1;
             if (cs.patch_cell_base[mid] <= c) lo = mid; else hi = mid;
         }
@@ -73,6 +73,11 @@ __device__ __forceinline__ void locate_cell(const CellSpace &cs, int c, CellLoc 
     L.k[0] = local % L.n[0];
     L.k[1] = (local / L.n[0]) % L.n[1];
     L.k[2] = local / (L.n[0] * L.n[1]);
+}
+
+__device__ __forceinline__ void locate_cell(const CellSpace &cs, int c, CellLoc &L)
+{
+    locate_cell_in(cs, c, 0, cs.npatch, L);
 }
 
 // Cell edge along an axis: box / n rounded once in FP64 (precomputed for the uniform grid and per patch).
@@ -121,9 +126,11 @@ struct Counters {
 
 // ---- launchers: each enqueues on `st`, adds the number of kernels it launched to *nl and returns the first
 // CUDA error (cudaGetLastError after the launches). ----
+// scan_tmp: scan_tmp_ints(cells) ints of scratch for the multi-CTA scan of large grids (nullptr: one-CTA scan).
+int scan_tmp_ints(int ncells_cap);
 cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
                        int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                       int *cell_of_slot, unsigned *status, cudaStream_t st, int *nl);
+                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
 
 // Patch binning: per-patch grids from the patches' largest h (cells per axis capped at ncap), global cell ids,
 // then the same counting sort as launch_bin over at most ncells_cap cells.
@@ -132,7 +139,7 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
                                int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
                                int *ncells_dev, int *cell_of,
                                int *count, int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot,
-                               unsigned *status, cudaStream_t st, int *nl);
+                               int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
 
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
                           const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &cs, bool f32,

@@ -23,11 +23,13 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-// Scratch layout (int32): cell_of[P] | perm_tmp[P] | count[C] | fill[C] | status[1], P = max particles,
-// C = max cells.  2 * 262,144 + 2 * 65,536 + 1 ints = 2.5 MB.
+// Scratch layout (int32): cell_of[P] | perm_tmp[P] | count[C] | fill[C] | status[1] | scan[64], P = max
+// particles, C = max cells; scan is the scratch of the multi-CTA scan.  2 * 262,144 + 2 * 65,536 + 65 ints =
+// 2.5 MB.
 constexpr int64_t kMaxP = SPH_BIN_STATIC_MAX_PARTICLES;
 constexpr int64_t kMaxC = SPH_BIN_STATIC_MAX_CELLS;
-constexpr int64_t kScratchInts = 2 * kMaxP + 2 * kMaxC + 1;
+constexpr int64_t kScanInts = 64;
+constexpr int64_t kScratchInts = 2 * kMaxP + 2 * kMaxC + 1 + kScanInts;
 
 static __device__ __align__(256) int g_bin_scratch[kScratchInts];
 
@@ -76,6 +78,8 @@ extern "C" sph_status sph_bin_static(const sph_layout *layout, const sph_domain 
     int *fill = s + 2 * kMaxP + kMaxC;
     unsigned *status = status_dev ? reinterpret_cast<unsigned *>(status_dev)
                                   : reinterpret_cast<unsigned *>(s + 2 * kMaxP + 2 * kMaxC);
+    int *scan_tmp = s + 2 * kMaxP + 2 * kMaxC + 1;
+    static_assert(kScanInts >= 3 * ((kMaxC + 4095) / 4096) + 4, "scan scratch too small");
 
     sphk::Grid g;
     g.periodic = domain->periodic ? 1 : 0;
@@ -94,6 +98,6 @@ extern "C" sph_status sph_bin_static(const sph_layout *layout, const sph_domain 
     // launch_bin clears the histogram (count) itself; fill, perm_tmp and cell_of are fully rewritten
     cudaError_t e = sphk::launch_bin(static_cast<const uint8_t *>(aos_dev), layout->stride, off_x, (int)n, g,
                                      (int)ncells, cell_of, count, cell_start_dev, fill, perm_tmp, perm_dev,
-                                     cell_of_slot_dev, status, st, &launched);
+                                     cell_of_slot_dev, scan_tmp, status, st, &launched);
     return e == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }

@@ -1133,32 +1133,40 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs_persist(const typen
     }
 }
 
-// Cost of every non-empty cell (local particles x active particles), bucketed by floor(log2(cost)).
-__global__ void k_cell_cost(const CellSpace cs, const int *__restrict__ cell_start, int *__restrict__ cell_bucket,
-                            int *__restrict__ bucket_count)
+// Cost of every non-empty cell (local particles x active particles), bucketed by floor(log2(cost)); one CTA per
+// patch (patch views only), the bucket histogram gathered in shared memory first.
+__global__ void __launch_bounds__(256) k_cell_cost(const CellSpace cs, const int *__restrict__ cell_start,
+                                                   int *__restrict__ cell_bucket, int *__restrict__ bucket_count)
 {
-    const int ncells = *cs.ncells_dev;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    __shared__ int hist[64];
+    const int p = blockIdx.x;
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = cs.patch_cell_base[p], nc = cs.patch_cell_base[p + 1] - base;
+    const int nx = cs.patch_n[3 * p], ny = cs.patch_n[3 * p + 1], nz = cs.patch_n[3 * p + 2];
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+        const int c = base + l;
         const int nloc = cell_start[c + 1] - cell_start[c];
         int b = -1;
         if (nloc > 0) {
-            CellLoc L;
-            locate_cell(cs, c, L);
+            const int k0 = l % nx, k1 = (l / nx) % ny, k2 = l / (nx * ny);
             long long nj = 0;
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const int kx = L.k[0] + dx, ky = L.k[1] + dy, kz = L.k[2] + dz;
-                        if (kx < 0 || ky < 0 || kz < 0 || kx >= L.n[0] || ky >= L.n[1] || kz >= L.n[2]) continue;
-                        const int c2 = L.base + kx + L.n[0] * (ky + L.n[1] * kz);
+                        const int kx = k0 + dx, ky = k1 + dy, kz = k2 + dz;
+                        if (kx < 0 || ky < 0 || kz < 0 || kx >= nx || ky >= ny || kz >= nz) continue;
+                        const int c2 = base + kx + nx * (ky + ny * kz);
                         nj += cell_start[c2 + 1] - cell_start[c2];
                     }
             const unsigned long long cost = (unsigned long long)nloc * (unsigned long long)nj;
             b = 63 - __clzll((long long)cost);
-            atomicAdd(&bucket_count[b], 1);
+            atomicAdd(&hist[b], 1);
         }
         cell_bucket[c] = b;
     }
+    __syncthreads();
+    if (threadIdx.x < 64 && hist[threadIdx.x]) atomicAdd(&bucket_count[threadIdx.x], hist[threadIdx.x]);
 }
 
 // Offsets of the 64 cost buckets, largest first; the work count.
@@ -1175,13 +1183,28 @@ __global__ void k_work_offsets(int *__restrict__ bucket_count, int *__restrict__
     }
 }
 
-__global__ void k_work_place(const CellSpace cs, const int *__restrict__ cell_bucket, int *__restrict__ cursor,
-                             int *__restrict__ order)
+// Work list: every non-empty cell takes a place in its bucket's range (order inside a bucket is immaterial: every
+// cell's result is independent of when it runs).  One CTA per patch: it counts its cells per bucket in shared
+// memory, reserves one range per bucket with a single global atomic each, then places its cells through
+// shared-memory cursors.
+__global__ void __launch_bounds__(256) k_work_place(const CellSpace cs, const int *__restrict__ cell_bucket,
+                                                    int *__restrict__ cursor, int *__restrict__ order)
 {
-    const int ncells = *cs.ncells_dev;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        const int b = cell_bucket[c];
-        if (b >= 0) order[atomicAdd(&cursor[b], 1)] = c;
+    __shared__ int cnt[64], at[64];
+    const int p = blockIdx.x;
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = cs.patch_cell_base[p], nc = cs.patch_cell_base[p + 1] - base;
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+        const int b = cell_bucket[base + l];
+        if (b >= 0) atomicAdd(&cnt[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) at[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&cursor[threadIdx.x], cnt[threadIdx.x]) : 0;
+    __syncthreads();
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+        const int b = cell_bucket[base + l];
+        if (b >= 0) order[atomicAdd(&at[b], 1)] = base + l;
     }
 }
 
@@ -1485,12 +1508,13 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
 cudaError_t launch_work_list(const CellSpace &cs, const int *cell_start, int ncells_cap, int *cell_bucket,
                              int *bucket_count, int *work_order, int *work_count, cudaStream_t st, int *nl)
 {
+    (void)ncells_cap;
+    if (cs.npatch <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(bucket_count, 0, 64 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    const int blocks = (ncells_cap + 255) / 256 < 4096 ? (ncells_cap + 255) / 256 : 4096;
-    k_cell_cost<<<blocks, 256, 0, st>>>(cs, cell_start, cell_bucket, bucket_count);
+    k_cell_cost<<<cs.npatch, 256, 0, st>>>(cs, cell_start, cell_bucket, bucket_count);
     k_work_offsets<<<1, 32, 0, st>>>(bucket_count, work_count);
-    k_work_place<<<blocks, 256, 0, st>>>(cs, cell_bucket, bucket_count, work_order);
+    k_work_place<<<cs.npatch, 256, 0, st>>>(cs, cell_bucket, bucket_count, work_order);
     *nl += 3;
     return cudaGetLastError();
 }

@@ -57,6 +57,7 @@ struct sph_view_s {
     sphk::SoaPtrs soa;
     sphk::Scratch scr;
     int *cell_of, *count, *cell_start, *fill, *perm_tmp, *perm, *cell_of_slot;
+    int *scan_tmp;  // multi-CTA scan scratch
     unsigned *status;
     sphk::Counters *counters;
     double *red_partials, *red_out;
@@ -225,6 +226,7 @@ void carve(sph_view_s *v, Bump &b)
     v->perm_tmp = (int *)b.take(nm * 4);
     v->perm = (int *)b.take(nm * 4);
     v->cell_of_slot = (int *)b.take(nm * 4);
+    v->scan_tmp = (int *)b.take((size_t)sphk::scan_tmp_ints((int)nc) * 4);
     if (v->npatch_max > 0) {
         const size_t np = (size_t)v->npatch_max;
         v->patch_n = (int *)b.take(3 * np * 4);
@@ -316,7 +318,7 @@ sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
         Phase ph(v, SPH_PH_BIN);
         e = sphk::launch_bin(static_cast<const uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X], (int)n, v->g,
                              v->ncells, v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
-                             v->cell_of_slot, v->status, v->st, &ph.nl);
+                             v->cell_of_slot, v->scan_tmp, v->status, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->n = n;
@@ -358,7 +360,8 @@ sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64
                                      v->layout.off[SPH_H], (int)n, patch_start, npatch, v->g, v->ncap, v->ncells,
                                      v->patch_n, v->patch_edge, v->patch_cells, v->patch_cell_base,
                                      v->patch_cell_base + npatch, v->cell_of, v->count, v->cell_start, v->fill,
-                                     v->perm_tmp, v->perm, v->cell_of_slot, v->status, v->st, &ph.nl);
+                                     v->perm_tmp, v->perm, v->cell_of_slot, v->scan_tmp, v->status, v->st,
+                                     &ph.nl);
         if (e == cudaSuccess)
             e = sphk::launch_work_list(v->cs, v->cell_start, v->ncells, v->cell_bucket, v->bucket_count,
                                        v->work_order, v->work_count, v->st, &ph.nl);
@@ -500,7 +503,10 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     } else if ((s = do_bin(v, aos, n)) != SPH_OK) {
         return s;
     }
-    if ((s = do_gather(v, aos, n, SPH_DENSITY_IN)) != SPH_OK) return s;
+    // union view: one gather of every member either loop reads (each record is read once: its bytes arrive in
+    // whole memory sectors, so a second pass for the force's extra member v would read the records again)
+    const uint32_t first = v->union_view ? ((SPH_DENSITY_IN | SPH_FORCE_IN) & ~SPH_DENSITY_OUT) : SPH_DENSITY_IN;
+    if ((s = do_gather(v, aos, n, first)) != SPH_OK) return s;
     uint32_t dens_out = SPH_DENSITY_OUT;
     if (v->h_max_iter > 0) {
         if ((s = do_density_h(v, p, v->h_eta, v->h_tol, v->h_max_iter, true)) != SPH_OK) return s;
@@ -515,8 +521,8 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
         if ((s = do_force(v, p)) != SPH_OK) return s;
         return do_scatter(v, aos, n, SPH_FORCE_OUT);
     }
-    // union view: the force reads the density view's members and outputs where they are, in SoA; only the
-    // members it adds are gathered, and every written member is scattered once at the end
+    // union view: the force reads its members and the density outputs where they are, in SoA, and every written
+    // member is scattered once at the end
     const uint32_t more = SPH_FORCE_IN & ~v->resident;
     if (more && (s = do_gather(v, aos, n, more)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;

@@ -185,8 +185,8 @@ def test_union_view_equals_per_loop_views(sph, side_stream, prec, kdk):
             sph.sph_view_destroy(v)
     assert np.array_equal(outs[0], outs[1])
     gi, si = sph.PHASE_NAMES.index("gather"), sph.PHASE_NAMES.index("scatter")
-    # the same number of gathers (the union form's second one moves only v), one scatter per pass instead of two
-    assert launches[0][gi] == launches[1][gi] and launches[0][si] < launches[1][si]
+    # one gather and one scatter per pass instead of two of each
+    assert launches[0][gi] < launches[1][gi] and launches[0][si] < launches[1][si]
 
 
 def test_set_union_validates(sph):
