@@ -222,25 +222,25 @@ __device__ __forceinline__ double flt_to_dbl_bits(float y)
     return __hiloint2double((int)((f >> 3) + 0x38000000u), (int)(f << 29));
 }
 
-// 1/sqrt(x), x >= 0: FP32 seed (no conversion instructions), then two Newton-Raphson steps
-// y <- y (3/2 - x y^2 / 2) in FP64 (quadratic convergence: ~2^-22 -> ~2^-44 -> below FP64 rounding).  For x = 0
-// (or x below the float range) the result is large but finite, so r = x / sqrt(x) comes out 0 (or tiny).
+// 1/sqrt(x), x >= 0: FP32 seed y0 (no conversion instructions, relative error e0 below ~2^-22), then one
+// third-order step in FP64: with e = 1 - x y0^2, x^(-1/2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + 5e^3/16 ...),
+// truncated after e^2, which leaves ~(5/16) e0^3 < 2^-66, below FP64 rounding -- five FP64 operations instead of
+// the seven of two Newton steps.  For x = 0 (or x below the float range) the result is large but finite, so
+// r = x / sqrt(x) comes out 0 (or tiny).
 __device__ __forceinline__ double rsqrt_seeded(double x)
 {
-    double y = flt_to_dbl_bits(rsqrt_ftz(dbl_to_flt_bits(x)));
-    const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
-    return y;
+    const double y = flt_to_dbl_bits(rsqrt_ftz(dbl_to_flt_bits(x)));
+    const double e = fma(-(x * y), y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
-// 1/x, x > 0 within the float range: FP32 seed, then two Newton-Raphson steps y <- y + y (1 - x y) in FP64.
+// 1/x, x > 0 within the float range: FP32 seed y0, then 1/x = y0 / (1 - e) = y0 (1 + e + e^2 ...) with
+// e = 1 - x y0, truncated after e^2 (remainder ~e0^3, below FP64 rounding): three FMAs.
 __device__ __forceinline__ double rcp_seeded(double x)
 {
-    double y = flt_to_dbl_bits(rcp_ftz(dbl_to_flt_bits(x)));
-    y = fma(y, fma(-x, y, 1.0), y);
-    y = fma(y, fma(-x, y, 1.0), y);
-    return y;
+    const double y = flt_to_dbl_bits(rcp_ftz(dbl_to_flt_bits(x)));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // ------------------------------------------------------------------------------------------------------------
