@@ -361,6 +361,31 @@ def summarize_form(prec, r, n, steps, world):
             "launches": nl, "conversion": conv}
 
 
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary under profiles/ (its 'traffic:' line), if
+    the kernel's source file still has the hash the counters were taken on; else (None, reason)."""
+    import glob
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    for path in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                if not line.startswith("traffic: "):
+                    continue
+                kv = dict(tok.split("=", 1) for tok in line.split()[1:] if "=" in tok)
+                if kv.get("kernel") != kernel:
+                    continue
+                src = os.path.join(here, kv.get("source", ""))
+                if not os.path.isfile(src):
+                    return None, f"{os.path.basename(path)}: source file missing"
+                with open(src, "rb") as fs:
+                    sha = hashlib.sha256(fs.read()).hexdigest()
+                if sha != kv.get("sha256"):
+                    return None, f"{os.path.basename(path)}: kernel source changed since the capture"
+                return int(kv["bytes_per_launch"]), os.path.relpath(path, here)
+    return None, "no ncu capture of this kernel under profiles/"
+
+
 def roofline_of(prec, s, steps, peaks, measured=None):
     """Dominant kernel = the phase with the largest device time (the force pair kernel)."""
     ph = s["phases_ms_per_step"]
@@ -370,9 +395,13 @@ def roofline_of(prec, s, steps, peaks, measured=None):
     dur = ph[dom] * 1e-3  # one launch of the pair kernel per step
     achieved = flops / dur / 1e12
     peak = PEAK_FP64_TFLOPS if prec == 0 else PEAK_FP32_TFLOPS
-    return {"kernel": f"k_cell_pairs<{'Force' if dom == 'force' else 'Dens'}{'F64' if prec == 0 else 'F32'}>",
+    kernel = (f"k_cell_pairs<{'Force' if dom == 'force' else 'Dens'}F64>" if prec == 0 else
+              f"k_cell_lanes<{'Force' if dom == 'force' else 'Dens'}F32>")
+    traffic, traffic_src = profiled_traffic(kernel)
+    return {"kernel": kernel,
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic, "traffic_unit": "bytes per launch (dram read + write, ncu)",
+            "traffic_source": traffic_src,
             "peak_source": ("derived: GB300 nominal FP64 1.25 TFLOP/s" if prec == 0 else
                             "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
             "algorithmic_flops_per_launch": flops, "flops_per_pair": FLOPS_FORCE_PAIR if dom == "force" else
@@ -463,7 +492,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tiles (no autotuning)")
     ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the batched (patches) forms")
     ap.add_argument("--no-large", dest="large", action="store_false", help="skip the large ten-step run forms")
-    ap.add_argument("--only", choices=["f64", "f32"], default=None,
+    ap.add_argument("--only", choices=["f64", "f32", "batched_f32", "batched_f64"], default=None,
                     help="run one form only (profiling runs); the JSON line then carries that form's numbers")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -487,6 +516,16 @@ def main():
 
     import tempfile
     tune_cache = os.path.join(tempfile.mkdtemp(prefix="sph_tiles_"), "tiles.json") if not args.no_tune else None
+    if args.only in ("batched_f32", "batched_f64"):
+        # profiling runs of one batched form: its graph-captured steps only
+        fp, lay_b, aos_b = batched_inputs()
+        b = run_batched(0 if args.only == "batched_f64" else 1, steps, warmup, dev, fp, lay_b, aos_b,
+                        tune_cache=tune_cache)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": b["value"] * world, "unit": UNIT, "n_gpus": world,
+                              "steps": steps, "warmup": warmup, "ms_per_step": b["ms_per_step"],
+                              "higher_is_better": True, "form": args.only, "details": b}))
+        return 0
     forms = ["f64", "f32"] if args.only is None else [args.only]
     runs = {}
     sampler = ClockSampler(gpu_index)
