@@ -193,10 +193,21 @@ SPH_API sph_status sph_view_set_union(sph_view view, int32_t on);
  * defaults).  Larger tiles stage more neighbours per barrier, smaller ones leave room for more CTAs per SM. */
 SPH_API sph_status sph_view_set_tiles(sph_view view, int32_t tile_density, int32_t tile_force);
 
+/* Warps per pair CTA ("warps per cell") of the density and force loops: 4 or 8 (0 = 4).  One CTA works on one
+ * cell at a time; 8 warps split the same staged tile among more local particles (or more candidate streams per
+ * particle) and keep more warps per SM resident when registers, not shared memory, bound the CTAs per SM. */
+SPH_API sph_status sph_view_set_warps(sph_view view, int32_t warps_density, int32_t warps_force);
+
+/* The view's current pair-loop shapes: out = {tile_density, tile_force, warps_density, warps_force} (tiles 0 =
+ * the defaults).  For caching the autotuner's choice and restoring it with sph_view_set_tiles /
+ * sph_view_set_warps. */
+SPH_API sph_status sph_view_get_tuning(sph_view view, int32_t out[4]);
+
 /* Autotuner: runs one pass on the records (as sph_step / sph_patches_step with the last bin's arguments would,
  * leaving the same outputs in the records), then times the density and the force pair loops at each candidate
- * tile size on this data and keeps the fastest of each in the view.  chosen (may be NULL) receives the two tile
- * sizes, best_ms (may be NULL) their kernel times.  Waits.  For a patch view, call sph_patches_bin first. */
+ * shape -- tile size x warps per cell (4, 8) -- on this data and keeps the fastest of each in the view.  chosen
+ * (may be NULL) receives the two tile sizes, best_ms (may be NULL) their kernel times; sph_view_get_tuning
+ * reports the warps as well.  Waits.  For a patch view, call sph_patches_bin first. */
 SPH_API sph_status sph_autotune(sph_view view, void *aos_dev, int64_t n, const sph_params *params, int32_t chosen[2],
                                 float best_ms[2]);
 

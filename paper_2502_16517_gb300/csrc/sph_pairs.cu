@@ -33,6 +33,8 @@
 // min(v.r, 0) = (v.r - |v.r|) / 2, so the half-rate ALU pipe carries almost no per-pair work.
 #include <math.h>
 
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sphk {
@@ -40,9 +42,8 @@ namespace sphk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPairThreads = 128;
-constexpr int kPairWarps = kPairThreads / 32;
-constexpr int kMaxLocal = 128;
+constexpr int kMaxLocal = 128;  // local particles per round of the FP64 driver (shared accumulators)
+// Threads per pair CTA ("warps per cell"): 128 or 256, chosen per loop by the view (autotuner).
 constexpr int kRing = 128;   // per-warp queue slots (at most 31 + 64 pending)
 constexpr int kStep = 64;    // candidates per filter step (two per lane)
 constexpr float kFar = 1e30f;  // sentinel coordinate: its squared distance overflows to +inf
@@ -866,18 +867,18 @@ __device__ __forceinline__ void zero_acc<ForceF32>(ForceF32::Acc &a)
 // ------------------------------------------------------------------------------------------------------------
 // The per-cell driver shared by all loop bodies.
 // ------------------------------------------------------------------------------------------------------------
-template <class K>
+template <class K, int NT>
 struct PairShared {
     NbrTable nb;
     typename K::Acc acc[kMaxLocal];
-    int ring[kPairWarps][kRing];
+    int ring[NT / 32][kRing];
     unsigned long long pairs;
 };
 
 // One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
-template <class K>
+template <class K, int NT>
 __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, const typename K::Tile &T,
-                                             PairShared<K> &S)
+                                             PairShared<K, NT> &S)
 {
     if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
@@ -896,12 +897,12 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
 
     for (int ib = ls; ib < le; ib += kMaxLocal) {
         const int nloc = min(kMaxLocal, le - ib);
-        for (int t = tid; t < nloc; t += kPairThreads) zero_acc<K>(S.acc[t]);
+        for (int t = tid; t < nloc; t += NT) zero_acc<K>(S.acc[t]);
         for (int tb = 0; tb < NJ; tb += tj) {
             const int tn = min(tj, NJ - tb);
             const int tnp = (tn + kStep - 1) / kStep * kStep;  // padded to whole filter steps (<= tj)
             __syncthreads();  // accumulators zeroed, previous tile consumed
-            for (int t = tid; t < tnp; t += kPairThreads) {
+            for (int t = tid; t < tnp; t += NT) {
                 if (t < tn) {
                     const int jj = tb + t;
                     const int nq = find_nbr(nb, jj);
@@ -911,7 +912,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            for (int li = warp; li < nloc; li += kPairWarps) {
+            for (int li = warp; li < nloc; li += NT / 32) {
                 const int i = ib + li;
                 const typename K::Lhs L = K::load(A, i, margin);
                 typename K::Part P;
@@ -949,7 +950,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
             }
         }
         __syncthreads();
-        for (int t = tid; t < nloc; t += kPairThreads) K::finish(A, ib + t, S.acc[t]);
+        for (int t = tid; t < nloc; t += NT) K::finish(A, ib + t, S.acc[t]);
     }
     if (lane == 0 && my_pairs) atomicAdd(&S.pairs, my_pairs);
     __syncthreads();
@@ -1007,7 +1008,7 @@ __device__ __forceinline__ unsigned hit_sweep(const typename K::Args &A, const t
     return nhit;
 }
 
-template <class K>
+template <class K, int NT>
 __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, int c, const typename K::Tile &T,
                                                    LaneShared<K> &S, unsigned char *smem)
 {
@@ -1023,9 +1024,9 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
     unsigned my_pairs = 0;
     typename K::Part *part = reinterpret_cast<typename K::Part *>(smem);  // reuses the tile after the last one
 
-    for (int ib = ls; ib < le; ib += kPairThreads) {
-        const int nloc = min(kPairThreads, le - ib);
-        const int ns = min(32, kPairThreads / nloc);  // lanes per local particle
+    for (int ib = ls; ib < le; ib += NT) {
+        const int nloc = min(NT, le - ib);
+        const int ns = min(32, NT / nloc);  // lanes per local particle
         const int li = tid / ns, s = tid - li * ns;
         const bool active = li < nloc;
         const int i = ib + (active ? li : 0);
@@ -1035,7 +1036,7 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
         for (int tb = 0; tb < NJ; tb += tj) {
             const int tn = min(tj, NJ - tb);
             __syncthreads();  // previous tile consumed
-            for (int t = tid; t < tn; t += kPairThreads) {
+            for (int t = tid; t < tn; t += NT) {
                 const int jj = tb + t;
                 const int nq = find_nbr(nb, jj);
                 K::stage(A, T, nb, t, nb.start[nq] + (jj - nb.pref[nq]), nq);
@@ -1072,17 +1073,17 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
     }
 }
 
-template <class K>
-__global__ void __launch_bounds__(kPairThreads) k_cell_lanes(const typename K::Args A)
+template <class K, int NT>
+__global__ void __launch_bounds__(NT) k_cell_lanes(const typename K::Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LaneShared<K> S;
     const typename K::Tile T = K::carve(smem, A.cm.tj);
-    process_cell_lanes<K>(A, blockIdx.x, T, S, smem);
+    process_cell_lanes<K, NT>(A, blockIdx.x, T, S, smem);
 }
 
-template <class K>
-__global__ void __launch_bounds__(kPairThreads) k_cell_lanes_persist(const typename K::Args A,
+template <class K, int NT>
+__global__ void __launch_bounds__(NT) k_cell_lanes_persist(const typename K::Args A,
                                                                      const int *__restrict__ order,
                                                                      const int *__restrict__ count, int *next)
 {
@@ -1097,29 +1098,29 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_lanes_persist(const typen
         const int wi = w;
         __syncthreads();
         if (wi >= total) break;
-        process_cell_lanes<K>(A, order[wi], T, S, smem);
+        process_cell_lanes<K, NT>(A, order[wi], T, S, smem);
     }
 }
 
 // One CTA per cell (single-grid views).
-template <class K>
-__global__ void __launch_bounds__(kPairThreads) k_cell_pairs(const typename K::Args A)
+template <class K, int NT>
+__global__ void __launch_bounds__(NT) k_cell_pairs(const typename K::Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PairShared<K> S;
+    __shared__ PairShared<K, NT> S;
     const typename K::Tile T = K::carve(smem, A.cm.tj);
-    process_cell<K>(A, blockIdx.x, T, S);
+    process_cell<K, NT>(A, blockIdx.x, T, S);
 }
 
 // Persistent CTAs pulling cells from a work list (patch views: cells in descending cost order, so the largest
 // cells start first and the small ones fill the tail).
-template <class K>
-__global__ void __launch_bounds__(kPairThreads) k_cell_pairs_persist(const typename K::Args A,
+template <class K, int NT>
+__global__ void __launch_bounds__(NT) k_cell_pairs_persist(const typename K::Args A,
                                                                      const int *__restrict__ order,
                                                                      const int *__restrict__ count, int *next)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PairShared<K> S;
+    __shared__ PairShared<K, NT> S;
     __shared__ int w;
     const typename K::Tile T = K::carve(smem, A.cm.tj);
     const int total = *count;
@@ -1129,7 +1130,7 @@ __global__ void __launch_bounds__(kPairThreads) k_cell_pairs_persist(const typen
         const int wi = w;
         __syncthreads();  // every thread has read w before thread 0 fetches the next item
         if (wi >= total) break;
-        process_cell<K>(A, order[wi], T, S);
+        process_cell<K, NT>(A, order[wi], T, S);
     }
 }
 
@@ -1300,24 +1301,33 @@ struct UsesLanes<ForceF32> {
     static constexpr bool value = true;
 };
 
-template <class K, bool Lanes>
+template <class K, bool Lanes, int NT>
 struct CellKernels {
-    static auto grid() { return k_cell_pairs<K>; }
-    static auto persist() { return k_cell_pairs_persist<K>; }
+    static auto grid() { return k_cell_pairs<K, NT>; }
+    static auto persist() { return k_cell_pairs_persist<K, NT>; }
 };
-template <class K>
-struct CellKernels<K, true> {
-    static auto grid() { return k_cell_lanes<K>; }
-    static auto persist() { return k_cell_lanes_persist<K>; }
+template <class K, int NT>
+struct CellKernels<K, true, NT> {
+    static auto grid() { return k_cell_lanes<K, NT>; }
+    static auto persist() { return k_cell_lanes_persist<K, NT>; }
 };
 
-template <class K>
-cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &pl, cudaStream_t st)
+// Shared memory of a pair CTA: the tile, or (lane driver) the lane partials merged after the last tile if larger.
+template <class K, int NT>
+size_t pair_smem(int tj)
 {
-    void (*const kgrid)(const typename K::Args) = CellKernels<K, UsesLanes<K>::value>::grid();
+    size_t b = (size_t)tj * K::kStageBytes;
+    if (UsesLanes<K>::value) b = std::max(b, (size_t)NT * sizeof(typename K::Part));
+    return b + 16;
+}
+
+template <class K, int NT>
+cudaError_t run_cells_nt(const typename K::Args &A, int ncells, const PairLaunch &pl, cudaStream_t st)
+{
+    void (*const kgrid)(const typename K::Args) = CellKernels<K, UsesLanes<K>::value, NT>::grid();
     void (*const kpers)(const typename K::Args, const int *, const int *, int *) =
-        CellKernels<K, UsesLanes<K>::value>::persist();
-    const size_t smem = (size_t)A.cm.tj * K::kStageBytes + 16;
+        CellKernels<K, UsesLanes<K>::value, NT>::persist();
+    const size_t smem = pair_smem<K, NT>(A.cm.tj);
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kgrid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1334,18 +1344,24 @@ cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &p
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpers, kPairThreads, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpers, NT, smem);
             ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
             sized_for = smem;
         }
         cudaError_t e = cudaMemsetAsync(pl.work_next, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
-        kpers<<<pl.persistent_ctas > 0 ? pl.persistent_ctas : ctas, kPairThreads, smem, st>>>(
-            A, pl.work_order, pl.work_count, pl.work_next);
+        kpers<<<pl.persistent_ctas > 0 ? pl.persistent_ctas : ctas, NT, smem, st>>>(A, pl.work_order, pl.work_count,
+                                                                                  pl.work_next);
     } else {
-        kgrid<<<ncells, kPairThreads, smem, st>>>(A);
+        kgrid<<<ncells, NT, smem, st>>>(A);
     }
     return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t run_cells(const typename K::Args &A, int ncells, const PairLaunch &pl, cudaStream_t st)
+{
+    return pl.threads == 256 ? run_cells_nt<K, 256>(A, ncells, pl, st) : run_cells_nt<K, 128>(A, ncells, pl, st);
 }
 
 int tile_or_default(int tj, int dflt)

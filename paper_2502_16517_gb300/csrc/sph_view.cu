@@ -75,6 +75,7 @@ struct sph_view_s {
     std::vector<cudaEvent_t> *ev_free;
     std::vector<PendingTiming> *ev_pending;
     int tile_density, tile_force;  // staged particles per tile (0 = default)
+    int warps_density, warps_force;  // warps per pair CTA: 4 or 8 (0 = 4)
 
     // graph-captured step: the arguments it was captured for, the executable graph, its kernel launches
     bool graph_valid;
@@ -327,11 +328,11 @@ sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
     return SPH_OK;
 }
 
-sphk::PairLaunch pair_launch(const sph_view_s *v, int tj)
+sphk::PairLaunch pair_launch(const sph_view_s *v, int tj, int warps)
 {
     sphk::PairLaunch pl;
     pl.tj = tj;
-    pl.threads = 0;
+    pl.threads = warps == 8 ? 256 : 128;
     pl.work_order = v->npatch_max > 0 ? v->work_order : nullptr;
     pl.work_count = v->work_count;
     pl.work_next = v->work_next;
@@ -421,7 +422,7 @@ sph_status density_launch(sph_view_s *v, const sph_params *p, const int *skip)
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_DENSITY);
-        sphk::PairLaunch pl = pair_launch(v, v->tile_density);
+        sphk::PairLaunch pl = pair_launch(v, v->tile_density, v->warps_density);
         pl.skip = skip;
         e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, p->gamma, pl,
                                        v->status, v->counters, v->st, &ph.nl);
@@ -488,7 +489,8 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     {
         Phase ph(v, SPH_PH_FORCE);
         e = sphk::launch_force_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, *p,
-                                     pair_launch(v, v->tile_force), v->status, v->counters, v->st, &ph.nl);
+                                     pair_launch(v, v->tile_force, v->warps_force), v->status, v->counters, v->st,
+                                     &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->resident |= SPH_FORCE_OUT;
@@ -664,11 +666,18 @@ sph_status do_step_graph(sph_view_s *v, void *aos, int64_t n, const sph_params *
 }
 
 // Median-free minimum of a few timed repetitions of one pair loop at one tile size.
-float time_loop(sph_view_s *v, const sph_params *p, bool force, int tj, int reps, cudaEvent_t e0, cudaEvent_t e1)
+float time_loop(sph_view_s *v, const sph_params *p, bool force, int tj, int warps, int reps, cudaEvent_t e0,
+                cudaEvent_t e1)
 {
     float best = 1e30f;
     for (int r = 0; r < reps; ++r) {
-        if (force) v->tile_force = tj; else v->tile_density = tj;
+        if (force) {
+            v->tile_force = tj;
+            v->warps_force = warps;
+        } else {
+            v->tile_density = tj;
+            v->warps_density = warps;
+        }
         cudaEventRecord(e0, v->st);
         const sph_status s = force ? do_force(v, p) : do_density(v, p);
         cudaEventRecord(e1, v->st);
@@ -734,6 +743,26 @@ sph_status sph_view_set_h_iteration(sph_view v, double eta, double tol, int32_t 
     return SPH_OK;
 }
 
+sph_status sph_view_set_warps(sph_view v, int32_t warps_density, int32_t warps_force)
+{
+    const auto ok = [](int32_t w) { return w == 0 || w == 4 || w == 8; };
+    if (!v || !ok(warps_density) || !ok(warps_force)) return SPH_E_INVAL;
+    v->warps_density = warps_density;
+    v->warps_force = warps_force;
+    graph_drop(v);
+    return SPH_OK;
+}
+
+sph_status sph_view_get_tuning(sph_view v, int32_t out[4])
+{
+    if (!v || !out) return SPH_E_INVAL;
+    out[0] = v->tile_density;
+    out[1] = v->tile_force;
+    out[2] = v->warps_density == 8 ? 8 : 4;
+    out[3] = v->warps_force == 8 ? 8 : 4;
+    return SPH_OK;
+}
+
 sph_status sph_view_set_union(sph_view v, int32_t on)
 {
     if (!v || (on != 0 && on != 1)) return SPH_E_INVAL;
@@ -776,24 +805,33 @@ sph_status sph_autotune(sph_view v, void *aos_dev, int64_t n, const sph_params *
     cudaEventCreate(&e1);
     const bool timing = v->timing;
     v->timing = false;
-    int bd = 0, bf = 0;
+    // tile size x warps per cell, each loop on its own
+    int bd = 0, bf = 0, wd = 4, wf = 4;
     float td = 1e30f, tf = 1e30f;
-    for (int k = 0; k < nd; ++k) {
-        const float t = time_loop(v, params, false, cd[k], 4, e0, e1);
-        if (t < td) {
-            td = t;
-            bd = cd[k];
+    for (int w = 4; w <= 8; w += 4) {
+        for (int k = 0; k < nd; ++k) {
+            const float t = time_loop(v, params, false, cd[k], w, 4, e0, e1);
+            if (t < td) {
+                td = t;
+                bd = cd[k];
+                wd = w;
+            }
         }
     }
     v->tile_density = bd;
-    for (int k = 0; k < nf; ++k) {
-        const float t = time_loop(v, params, true, cf[k], 4, e0, e1);
-        if (t < tf) {
-            tf = t;
-            bf = cf[k];
+    v->warps_density = wd;
+    for (int w = 4; w <= 8; w += 4) {
+        for (int k = 0; k < nf; ++k) {
+            const float t = time_loop(v, params, true, cf[k], w, 4, e0, e1);
+            if (t < tf) {
+                tf = t;
+                bf = cf[k];
+                wf = w;
+            }
         }
     }
     v->tile_force = bf;
+    v->warps_force = wf;
     v->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -99,6 +99,8 @@ _SIGS = {
     "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
     "sph_view_set_tiles": [_VP, _I32, _I32],
     "sph_view_set_union": [_VP, _I32],
+    "sph_view_set_warps": [_VP, _I32, _I32],
+    "sph_view_get_tuning": [_VP, _VP],
     "sph_density_h": [_VP, _VP, ctypes.c_double, ctypes.c_double, _I32, _VP, _VP],
     "sph_view_set_h_iteration": [_VP, ctypes.c_double, ctypes.c_double, _I32],
     "sph_view_h_rounds": [_VP, _VP, _VP],
@@ -362,6 +364,17 @@ def sph_view_h_rounds(view, allow_unconverged=True):
     if not (st == SPH_OK or (allow_unconverged and st == SPH_E_NOTCONV)):
         raise SphError("sph_view_h_rounds", st)
     return rounds.value, left.value
+
+
+def sph_view_set_warps(view, warps_density, warps_force):
+    _check("sph_view_set_warps", lib().sph_view_set_warps(view, int(warps_density), int(warps_force)))
+
+
+def sph_view_get_tuning(view):
+    """(tile_density, tile_force, warps_density, warps_force) of the view."""
+    out = (ctypes.c_int32 * 4)()
+    _check("sph_view_get_tuning", lib().sph_view_get_tuning(view, out))
+    return tuple(int(x) for x in out)
 
 
 def sph_view_set_union(view, on=True):

@@ -198,3 +198,64 @@ def test_set_union_validates(sph):
         assert sph.lib().sph_view_set_union(v, 0) == sph.SPH_OK
     finally:
         sph.sph_view_destroy(v)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warps_per_cell(sph, oracle, side_stream, prec):
+    """8 warps per cell: FP64 results bit-identical to 4 warps (each local particle keeps one warp and the same
+    queue order); FP32 within its bar of the oracle (the lanes split each particle's candidates differently)."""
+    f = wl.jittered_lattice(20, jitter=0.1, vel_sigma=0.1, seed=9)
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay)
+    n = aos_h.shape[0]
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    outs = []
+    for warps in (4, 8):
+        aos = H.to_dev(aos_h)
+        v = sph.sph_view_create(lay, prec, n, (f["box"], ncell, True), side_stream.cuda_stream)
+        try:
+            sph.sph_view_set_warps(v, warps, warps)
+            sph.sph_step(v, aos, n, wl.SPH_PARAMS)
+            sph.sph_view_sync(v)
+            assert sph.sph_view_get_tuning(v)[2:] == (warps, warps)
+            outs.append(aos.cpu().numpy())
+        finally:
+            sph.sph_view_destroy(v)
+    if prec == 0:
+        assert np.array_equal(outs[0], outs[1])
+    ref = oracle.step_all(aos_h, lay, f["box"], wl.SPH_PARAMS)
+    H.compare_fields(oracle.unpack(outs[1], lay), ref, prec, "8 warps")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warps_per_cell_patches(sph, oracle, side_stream, prec):
+    import torch
+    fp = wl.patches(12, lam_lo=8, lam_hi=150, seed=11, vel_sigma=0.2)
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(fp, lay, order="shuffled", segments=fp["patch_start"])
+    n = aos_h.shape[0]
+    ps = torch.tensor(fp["patch_start"], device=H.device())
+    aos = H.to_dev(aos_h)
+    v = sph.sph_patches_create(lay, prec, n, 12, fp["box"], 8, side_stream.cuda_stream)
+    try:
+        sph.sph_view_set_warps(v, 8, 8)
+        sph.sph_patches_step(v, aos, n, ps, 12, wl.SPH_PARAMS)
+        sph.sph_view_sync(v)
+        out = aos.cpu().numpy()
+    finally:
+        sph.sph_view_destroy(v)
+    ref = oracle.step_patches(aos_h, lay, fp["patch_start"], fp["box"], wl.SPH_PARAMS)
+    H.compare_fields(oracle.unpack(out, lay), ref, prec, "patches, 8 warps")
+
+
+def test_set_warps_validates(sph):
+    f, lay, aos_h, ncell = _tiny()
+    v = H.new_view(lay, 0, aos_h.shape[0], f["box"], ncell)
+    try:
+        for bad in ((2, 4), (4, 16), (-4, 4)):
+            with pytest.raises(sph.SphError) as e:
+                sph.sph_view_set_warps(v, *bad)
+            assert e.value.status == sph.SPH_E_INVAL
+        assert sph.sph_view_get_tuning(v) == (0, 0, 4, 4)
+    finally:
+        sph.sph_view_destroy(v)
