@@ -193,7 +193,8 @@ SPH_API sph_status sph_view_set_union(sph_view view, int32_t on);
  * defaults).  Larger tiles stage more neighbours per barrier, smaller ones leave room for more CTAs per SM. */
 SPH_API sph_status sph_view_set_tiles(sph_view view, int32_t tile_density, int32_t tile_force);
 
-/* Warps per pair CTA ("warps per cell") of the density and force loops: 4 or 8 (0 = 4).  One CTA works on one
+/* Warps per pair CTA ("warps per cell") of the density and force loops: 4 or 8 (0 = the default: 4, except 8
+ * for the FP64 force loop).  One CTA works on one
  * cell at a time; 8 warps split the same staged tile among more local particles (or more candidate streams per
  * particle) and keep more warps per SM resident when registers, not shared memory, bound the CTAs per SM. */
 SPH_API sph_status sph_view_set_warps(sph_view view, int32_t warps_density, int32_t warps_force);

@@ -1466,7 +1466,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     const int tj = pl.tj;
     if (!f32) {
         ForceF64::Args A;
-        cm.tj = tile_or_default(tj, 384);
+        cm.tj = tile_or_default(tj, 512);
         A.cm = cm;
         A.x = (const double *)soa.p[SPH_X][0];
         A.y = (const double *)soa.p[SPH_X][1];

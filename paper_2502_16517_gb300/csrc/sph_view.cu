@@ -328,6 +328,10 @@ sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
     return SPH_OK;
 }
 
+// Warps per CTA of the force loop: the view's choice, else 8 for FP64 (the register-bound FP64 force keeps more
+// warps resident with 256-thread CTAs) and 4 for FP32.
+int force_warps(const sph_view_s *v) { return v->warps_force ? v->warps_force : (v->prec == SPH_F64 ? 8 : 4); }
+
 sphk::PairLaunch pair_launch(const sph_view_s *v, int tj, int warps)
 {
     sphk::PairLaunch pl;
@@ -489,7 +493,7 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     {
         Phase ph(v, SPH_PH_FORCE);
         e = sphk::launch_force_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, *p,
-                                     pair_launch(v, v->tile_force, v->warps_force), v->status, v->counters, v->st,
+                                     pair_launch(v, v->tile_force, force_warps(v)), v->status, v->counters, v->st,
                                      &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
@@ -759,7 +763,7 @@ sph_status sph_view_get_tuning(sph_view v, int32_t out[4])
     out[0] = v->tile_density;
     out[1] = v->tile_force;
     out[2] = v->warps_density == 8 ? 8 : 4;
-    out[3] = v->warps_force == 8 ? 8 : 4;
+    out[3] = force_warps(v);
     return SPH_OK;
 }
 

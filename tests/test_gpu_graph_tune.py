@@ -256,6 +256,6 @@ def test_set_warps_validates(sph):
             with pytest.raises(sph.SphError) as e:
                 sph.sph_view_set_warps(v, *bad)
             assert e.value.status == sph.SPH_E_INVAL
-        assert sph.sph_view_get_tuning(v) == (0, 0, 4, 4)
+        assert sph.sph_view_get_tuning(v) == (0, 0, 4, 8)    # FP64 view: the force loop defaults to 8 warps
     finally:
         sph.sph_view_destroy(v)
