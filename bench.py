@@ -228,6 +228,8 @@ def run_large(prec, reps, dev, f, lay, aos_h, ncell, dt=None, nsteps=10, tune_ca
             sph.sph_pair_counts(view, reset=True)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
             stats1 = None
+            barrier()
+            torch.cuda.synchronize(dev)
             for k in range(reps):
                 aos.copy_(aos0)
                 ev[k][0].record(stream)
@@ -273,6 +275,7 @@ def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=
             sph.sph_pair_counts(view, reset=True)
             sph.sph_view_phase_times(view, reset=True)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            barrier()
             torch.cuda.synchronize(dev)
             for k in range(steps):
                 ev[k][0].record(stream)
@@ -359,6 +362,28 @@ def summarize_form(prec, r, n, steps, world):
             "density_pairs_per_step": r["counts"][1] / steps, "force_pairs_per_step": r["counts"][2] / steps,
             "candidates_per_step": (r["counts"][0] + r["counts"][3]) / steps, "phases_ms_per_step": ph,
             "launches": nl, "conversion": conv}
+
+
+def max_over_ranks(vals, device=None):
+    """Element-wise max of vals over all ranks of the default process group (the values unchanged when there is
+    none): the timing of a replica run is its slowest rank."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def barrier():
+    import torch
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second: every replica processes units_per_rank in at most `seconds`."""
+    return world * float(units_per_rank) / float(seconds)
 
 
 def profiled_traffic(kernel):
@@ -565,21 +590,27 @@ def main():
     finally:
         sampler.__exit__(None, None, None)
     clocks = sampler.summary()
-    # max over ranks of the summed step time
-    tot = torch.tensor([float(np.sum(runs[fm]["step_ms"])) for fm in forms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    # max over ranks of the summed step times; the batched / large forms' times likewise
+    tot = max_over_ranks([float(np.sum(runs[fm]["step_ms"])) for fm in forms], dev)
     summ = {}
     for k, fm in enumerate(forms):
-        runs[fm]["step_ms"] = [tot[k].item() / steps] * steps
+        runs[fm]["step_ms"] = [tot[k] / steps] * steps
         summ[fm] = summarize_form(0 if fm == "f64" else 1, runs[fm], n, steps, world)
+    for b in batched.values():
+        b["ms_per_step"] = max_over_ranks([b["ms_per_step"]], dev)[0]
+        b["value"] = whole_job_rate(b["pairs_per_step"], world, b["ms_per_step"] * 1e-3)
+    for b in large.values():
+        b["ms_per_run"] = max_over_ranks([b["ms_per_run"]], dev)[0]
+        b["value"] = whole_job_rate(b["pairs_per_run"], world, b["ms_per_run"] * 1e-3)
     main_form = forms[0]
     s64, r64 = summ[main_form], runs[main_form]
     s32 = summ.get("f32") if main_form == "f64" else None
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(0 if main_form == "f64" else 1, max(steps // 2, 3), 2, dev, aos_h, lay, f["box"], ncell)
-        e2e["value"] *= world
+        pairs_step = e2e["value"] * e2e["ms_per_step"] * 1e-3
+        e2e["ms_per_step"] = max_over_ranks([e2e["ms_per_step"]], dev)[0]
+        e2e["value"] = whole_job_rate(pairs_step, world, e2e["ms_per_step"] * 1e-3)
     peaks = measured_peaks()
     from paper_2502_16517_gb300 import sph as _sph
     fma_peak = {"f64": _sph.sph_probe_fma_rate(_sph.SPH_F64) / 1e12, "f32": _sph.sph_probe_fma_rate(_sph.SPH_F32) / 1e12}
@@ -641,13 +672,11 @@ def main():
         b = dict(b)
         b["workload"] = ("large run: 2,097,152 particles, 8 Gaussian overdensities (sigma 0.05, 4x) on a uniform "
                          "background, 53^3 periodic cells, 10 KDK steps with per-step conversion and re-binning")
-        b["value"] *= world
         line["forms"][f"large_{form}"] = b
     for form, b in batched.items():
         b = dict(b)
         b["workload"] = ("batched form: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8,256)) per cell, "
                          f"{b['particles']} particles, inputs larger than L2 (no flush)")
-        b["value"] *= world
         b["speedup_vs_plain_f64"] = b["value"] / s64["value"]
         line["forms"][f"batched_{form}"] = b
     print(json.dumps(line))
