@@ -401,8 +401,11 @@ struct DensF32 {
         float *rho, *P, *cs;
         float gamma;
     };
+    // Candidates stored pair-interleaved (candidates 2p and 2p+1 side by side), so that each 16-byte load gives
+    // two aligned float2 operands and the sweep runs two candidates per paired FP32 instruction.
     struct Tile {
-        float4 *p4;  // position seen from the local cell, mass
+        float4 *pa;  // pair p: x_2p, x_2p+1, y_2p, y_2p+1 (positions seen from the local cell)
+        float4 *pb;  // pair p: z_2p, z_2p+1, m_2p, m_2p+1
     };
     struct Lhs {
         float x, y, z, hinv;
@@ -419,18 +422,30 @@ struct DensF32 {
     using Acc = float2;  // (s, c)
     static constexpr int kStageBytes = 16;
 
-    static __device__ Tile carve(unsigned char *s, int)
+    static __device__ Tile carve(unsigned char *s, int tj)
     {
         Tile t;
-        t.p4 = reinterpret_cast<float4 *>(s);
+        t.pa = reinterpret_cast<float4 *>(s);
+        t.pb = t.pa + tj / 2;
         return t;
+    }
+    static __device__ __forceinline__ void put(const Tile &T, int t, float x, float y, float z, float m)
+    {
+        float *a = reinterpret_cast<float *>(T.pa + (t >> 1)) + (t & 1);
+        float *b = reinterpret_cast<float *>(T.pb + (t >> 1)) + (t & 1);
+        a[0] = x;
+        a[2] = y;
+        b[0] = z;
+        b[2] = m;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
-        T.p4[t] = make_float4(A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2],
-                              A.m[slot]);
+        put(T, t, A.x[slot] + nb.offf[q][0], A.y[slot] + nb.offf[q][1], A.z[slot] + nb.offf[q][2], A.m[slot]);
     }
+    // The partner of an odd last candidate: massless and far away (finite, so no inf * 0): it adds 0 and is
+    // never counted.
+    static __device__ __forceinline__ void pad(const Tile &T, int t) { put(T, t, 1e18f, 1e18f, 1e18f, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
     {
         Lhs L;
@@ -440,28 +455,41 @@ struct DensF32 {
         L.hinv = __frcp_rn(A.h[i]);
         return L;
     }
-    // m_j f(q_ij) of one candidate; counts it if it lies in the support.
-    static __device__ __forceinline__ float term(const Lhs &L, const Tile &T, int k, float &npair)
+    // m_j f(q_ij) of candidate pair p (two candidates at once); adds the pair's in-support count to cnt.
+    static __device__ __forceinline__ float2 term2(const Lhs &L, const Tile &T, int p, float2 &cnt)
     {
-        const float4 p = T.p4[k];
-        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float q = r2 * rsqrt_ftz(r2 + 1e-30f) * L.hinv;
-        const float sq = fma_sat(-0.5f, q, 1.0f);
-        const float t = fma_sat(-1.0f, q, 1.0f);
-        const float s2 = sq * sq, t2 = t * t;
-        npair += mul_sat(sq, 16777216.0f);
-        return p.w * fmaf(s2 + s2, sq, -(t2 * t));
+        const float4 a = T.pa[p], b = T.pb[p];
+        const float2 neg = make_float2(-1.0f, -1.0f);
+        const float2 dx = __ffma2_rn(make_float2(a.x, a.y), neg, make_float2(L.x, L.x));
+        const float2 dy = __ffma2_rn(make_float2(a.z, a.w), neg, make_float2(L.y, L.y));
+        const float2 dz = __ffma2_rn(make_float2(b.x, b.y), neg, make_float2(L.z, L.z));
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 r2e = __fadd2_rn(r2, make_float2(1e-30f, 1e-30f));
+        const float2 rs = make_float2(rsqrt_ftz(r2e.x), rsqrt_ftz(r2e.y));
+        const float2 q = __fmul2_rn(__fmul2_rn(r2, rs), make_float2(L.hinv, L.hinv));
+        const float2 sq = make_float2(fma_sat(-0.5f, q.x, 1.0f), fma_sat(-0.5f, q.y, 1.0f));
+        const float2 t = make_float2(fma_sat(-1.0f, q.x, 1.0f), fma_sat(-1.0f, q.y, 1.0f));
+        const float2 s3 = __fmul2_rn(__fmul2_rn(sq, sq), sq);
+        const float2 t3 = __fmul2_rn(__fmul2_rn(t, t), t);
+        const float2 w = __ffma2_rn(s3, make_float2(2.0f, 2.0f), make_float2(-t3.x, -t3.y));
+        cnt = __fadd2_rn(cnt, make_float2(mul_sat(sq.x, 16777216.0f), mul_sat(sq.y, 16777216.0f)));
+        return __fmul2_rn(make_float2(b.z, b.w), w);
     }
-    // Candidates k, k + ns, ... < tn: four terms summed plainly, then added to the compensated sum.
-    static __device__ __forceinline__ void sweep(const Lhs &L, const Tile &T, int k, int ns, int tn, Part &P)
+    // Candidate pairs p, p + ns, ... covering candidates < tn (an odd tail was padded): two pairs (four terms)
+    // summed plainly, then added to the compensated sum.
+    static __device__ __forceinline__ void sweep(const Lhs &L, const Tile &T, int p, int ns, int tn, Part &P)
     {
-        for (; k + 3 * ns < tn; k += 4 * ns) {
-            const float a = term(L, T, k, P.npair), b = term(L, T, k + ns, P.npair);
-            const float c = term(L, T, k + 2 * ns, P.npair), d = term(L, T, k + 3 * ns, P.npair);
-            P.rho.add((a + b) + (c + d));
+        const int np = (tn + 1) >> 1;
+        float2 cnt = make_float2(0.f, 0.f);
+        for (; p + ns < np; p += 2 * ns) {
+            const float2 u = term2(L, T, p, cnt), v = term2(L, T, p + ns, cnt);
+            P.rho.add((u.x + u.y) + (v.x + v.y));
         }
-        for (; k < tn; k += ns) P.rho.add(term(L, T, k, P.npair));
+        if (p < np) {
+            const float2 u = term2(L, T, p, cnt);
+            P.rho.add(u.x + u.y);
+        }
+        P.npair += cnt.x + cnt.y;
     }
     static __device__ __forceinline__ void merge_part(Acc &a, const Part &P)
     {
@@ -646,15 +674,17 @@ struct ForceF64 {
                               fma(ji ? T.K2i[k] : (jo ? T.K2o[k] : 0.0), r, ji ? -K1j : (jo ? K1j : 0.0)));
         const double dvx = L.vx - T.vx[k], dvy = L.vy - T.vy[k], dvz = L.vz - T.vz[k];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
-        // Monaghan viscosity, Ph = Pi / 2 = mu (beta mu - alpha cbar) / (rho_i + rho_j) with
-        // mu = hbar v.r / (r^2 + eps hbar^2): one reciprocal R = 1 / (D1 D2) serves both quotients.
+        // Monaghan viscosity, Ph = Pi / 2 = mu (beta mu - alpha cbar) / D2 with mu = w / D1, w = hbar v.r,
+        // D1 = r^2 + eps hbar^2, D2 = rho_i + rho_j: one reciprocal R = 1 / (D1 D2) gives 1 / D1 = D2 R, and
+        // Ph = w (beta mu - alpha cbar) R.
         const double hb = L.hh + T.hh[k];
         const double D1 = fma(A.eps * hb, hb, r2);
         const double D2 = L.rho + T.rho[k];
         const double R = rcp_seeded(D1 * D2);
-        const double mu = (hb * vdotr) * (D2 * R);
+        const double w = hb * vdotr;
+        const double mu = w * (D2 * R);
         const double t = fma(A.beta, mu, -(L.ach + T.ach[k]));
-        double Ph = (mu * t) * (D1 * R);
+        double Ph = (w * t) * R;
         if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
         const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
         const double aF = L.A * Fi;
@@ -1040,6 +1070,9 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
                 const int jj = tb + t;
                 const int nq = find_nbr(nb, jj);
                 K::stage(A, T, nb, t, nb.start[nq] + (jj - nb.pref[nq]), nq);
+            }
+            if constexpr (K::kMasked) {
+                if (tid == 0 && (tn & 1)) K::pad(T, tn);  // tn < tj here: tiles are multiples of 64
             }
             __syncthreads();
             if (active) {
