@@ -141,3 +141,40 @@ def test_large_run_full_size_properties(sph, oracle, side_stream):
     assert H.rel_max(st32["rho"], st64["rho"]) < 1e-3
     assert abs((t1[6] - t0[6]) / t0[6] - drift1) < 1e-3 * abs(drift1)
     assert np.all(np.isfinite(st64["a"])) and np.all(np.isfinite(st32["a"]))
+
+
+@pytest.fixture(scope="module")
+def large_sample(oracle):
+    """The large input, 12 sampled particles (3 at the centres of overdensities, 9 at random) and their oracle
+    values, computed once for both precisions."""
+    f = wl.large()
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled", canary=False)
+    n = aos_h.shape[0]
+    st = oracle.unpack(aos_h, lay)
+    dense = []
+    for c in f["centres"][:3]:
+        d = st["x"] - c
+        d -= np.round(d)
+        dense.append(int(np.argmin(np.sum(d * d, axis=1))))
+    rng = np.random.default_rng(21)
+    targets = np.unique(np.concatenate([dense, rng.choice(n, size=9, replace=False)]))
+    ref = oracle.step_sampled(aos_h, lay, f["box"], wl.SPH_PARAMS, targets)
+    return f, lay, aos_h, targets, ref
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_large_initial_pass_sampled(sph, oracle, large_sample, prec):
+    """Full size (2,097,152 clustered particles, 53^3 cells), one pass in the launch configuration the benchmark
+    uses; the sampled particles checked one by one against the brute-force oracle."""
+    f, lay, aos_h, targets, ref = large_sample
+    ncell = wl.ncell_for(f["box"], f["h"].max())
+    out, info = H.run_step(aos_h, lay, f["box"], ncell, prec, separate_calls=False)
+    got_all = oracle.unpack(out, lay)
+    got = {k: got_all[k][targets] for k in ("rho", "P", "cs", "a", "dudt")}
+    tol = H.TOL[prec]
+    for k in ("rho", "P", "cs"):
+        assert H.rel_max(got[k], ref[k]) <= tol, k
+    assert H.normwise(got["a"], ref["a"]) <= tol
+    assert H.normwise(got["dudt"], ref["dudt"]) <= tol
+    assert np.max(got["rho"]) > 2.0 * np.median(got_all["rho"])   # the sample reaches into an overdensity

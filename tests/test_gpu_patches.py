@@ -177,19 +177,20 @@ def test_sph_bin_and_patches_bin_reject_the_wrong_view(sph):
         sph.sph_view_destroy(u)
 
 
-def test_full_batched_workload_sampled_patches(sph, oracle):
-    """4096 patches, Poisson(lambda ~ U(8, 256)) per cell (~14.6 M particles), FP32 views, one pass in the launch
+@pytest.mark.parametrize("prec", [1, 0])
+def test_full_batched_workload_sampled_patches(sph, oracle, prec):
+    """4096 patches, Poisson(lambda ~ U(8, 256)) per cell (~14.6 M particles), one pass in the launch
     configuration the benchmark times; four patches checked record by record against the oracle."""
     f = wl.patches(4096, seed=wl.SEED)
     lay = wl.default_layout()
     aos_h, _ = wl.pack_aos(f, lay, order="shuffled", segments=f["patch_start"], canary=False)
     ps = f["patch_start"]
-    out, info = _run(sph, aos_h, lay, ps, f["box"], 1)
+    out, info = _run(sph, aos_h, lay, ps, f["box"], prec)
     lam = f["lam"]
     sample = [int(np.argmin(lam)), int(np.argmax(lam)), 1000, 3000]
     ref = oracle.step_patches(aos_h, lay, ps, f["box"], wl.SPH_PARAMS, patches=sample)
     got = oracle.unpack(out, lay)
     idx = np.concatenate([np.arange(ps[p], ps[p + 1]) for p in sample])
     sub = lambda d: {k: d[k][idx] for k in ("rho", "P", "cs", "a", "dudt")}
-    H.compare_fields(sub(got), sub(ref), 1, "batched sample")
+    H.compare_fields(sub(got), sub(ref), prec, "batched sample")
     assert np.all(np.isfinite(got["rho"])) and np.all(got["rho"] > 0)
