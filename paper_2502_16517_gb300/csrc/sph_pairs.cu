@@ -20,8 +20,9 @@
 // The compaction keeps the expensive evaluation at ~97 % lane occupancy although only ~15 % of the
 // 3^3-stencil candidates lie inside the support (cell edge 2h).
 //
-// FP64 path: positions are the FP64 members; x_i - x_j gets the periodic shift (+-box) of j's cell exactly as a
-// minimum-image wrap would.  The FP32 filter uses cell-relative float copies of the positions with a conservative
+// FP64 path: positions are the FP64 members; a neighbour across the periodic boundary is staged at its image
+// x_j -+ box, so x_i - x_j needs no wrap test in the pair term (the image differs from the minimum-image difference
+// by the rounding of one addition at the box scale).  The FP32 filter uses cell-relative float copies of the positions with a conservative
 // radius, so it never drops a pair the FP64 test keeps.  The FP64 pipe (1/64 of the FP32 rate on this part) is
 // the bound, so every per-pair FP64 instruction is counted: piece selection and masks run on the integer pipe,
 // reciprocals are FP32-seeded Newton iterations, per-particle factors are precomputed.
@@ -273,7 +274,6 @@ struct DensF64 {
     struct Tile {
         double *x, *y, *z, *m;
         float4 *f4;  // filter: cell-relative position seen from the local cell, unused
-        unsigned char *q;
     };
     struct Lhs {
         double x, y, z;
@@ -287,7 +287,7 @@ struct DensF64 {
         __device__ __forceinline__ void reduce() { rho = warp_sum(rho); }
     };
     using Acc = double;
-    static constexpr int kStageBytes = 4 * 8 + 16 + 1;
+    static constexpr int kStageBytes = 4 * 8 + 16;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
@@ -297,19 +297,25 @@ struct DensF64 {
         t.z = t.y + tj;
         t.m = t.z + tj;
         t.f4 = reinterpret_cast<float4 *>(t.m + tj);
-        t.q = reinterpret_cast<unsigned char *>(t.f4 + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
-        T.x[t] = A.x[slot];
-        T.y[t] = A.y[slot];
-        T.z[t] = A.z[slot];
+        // a neighbour across the periodic boundary is staged at its image position: shift is what the minimum image
+        // adds to x_i - x_j, so the image is x_j - shift (only cells next to the boundary have shifts)
+        double xs = A.x[slot], ys = A.y[slot], zs = A.z[slot];
+        if (nb.wrap) {
+            xs -= nb.shift[q][0];
+            ys -= nb.shift[q][1];
+            zs -= nb.shift[q][2];
+        }
+        T.x[t] = xs;
+        T.y[t] = ys;
+        T.z[t] = zs;
         T.m[t] = A.m[slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               0.0f);
-        T.q[t] = (unsigned char)q;
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
@@ -342,13 +348,7 @@ struct DensF64 {
     static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int, int k, Part &P)
     {
-        double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        if (wrap) {
-            const int q = T.q[k];
-            dx += nb.shift[q][0];
-            dy += nb.shift[q][1];
-            dz += nb.shift[q][2];
-        }
+        const double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double r = r2 * rsqrt_seeded(r2);
         const long long rb = __double_as_longlong(r);
@@ -545,7 +545,6 @@ struct ForceF64 {
         double *x, *y, *z, *vx, *vy, *vz, *m, *hh, *S0, *K1, *K2i, *K2o, *A, *ach, *rho;
         float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
         int *slot;
-        unsigned char *q;
     };
     struct Lhs {
         double x, y, z, vx, vy, vz, hh, S0, K1, K2i, K2o, A, ach, rho;
@@ -578,7 +577,7 @@ struct ForceF64 {
     struct Acc {
         double ax, ay, az, du;
     };
-    static constexpr int kStageBytes = 15 * 8 + 16 + 4 + 1;
+    static constexpr int kStageBytes = 15 * 8 + 16 + 4;
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
@@ -590,15 +589,22 @@ struct ForceF64 {
         for (int a = 0; a < 15; ++a) *dst[a] = d + a * tj;
         t.f4 = reinterpret_cast<float4 *>(d + 15 * tj);
         t.slot = reinterpret_cast<int *>(t.f4 + tj);
-        t.q = reinterpret_cast<unsigned char *>(t.slot + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
                                                  int slot, int q)
     {
-        T.x[t] = A.x[slot];
-        T.y[t] = A.y[slot];
-        T.z[t] = A.z[slot];
+        // a neighbour across the periodic boundary is staged at its image position: shift is what the minimum image
+        // adds to x_i - x_j, so the image is x_j - shift (only cells next to the boundary have shifts)
+        double xs = A.x[slot], ys = A.y[slot], zs = A.z[slot];
+        if (nb.wrap) {
+            xs -= nb.shift[q][0];
+            ys -= nb.shift[q][1];
+            zs -= nb.shift[q][2];
+        }
+        T.x[t] = xs;
+        T.y[t] = ys;
+        T.z[t] = zs;
         T.vx[t] = A.vx[slot];
         T.vy[t] = A.vy[slot];
         T.vz[t] = A.vz[slot];
@@ -614,7 +620,6 @@ struct ForceF64 {
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               A.hf[slot]);
         T.slot[t] = slot;
-        T.q[t] = (unsigned char)q;
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
@@ -652,13 +657,7 @@ struct ForceF64 {
     static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int i, int k, Part &P)
     {
-        double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
-        if (wrap) {
-            const int q = T.q[k];
-            dx += nb.shift[q][0];
-            dy += nb.shift[q][1];
-            dz += nb.shift[q][2];
-        }
+        const double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double rinv = rsqrt_seeded(r2);
         const double r = r2 * rinv;

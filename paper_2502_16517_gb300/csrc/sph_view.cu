@@ -780,8 +780,8 @@ sph_status sph_view_set_tiles(sph_view v, int32_t tile_density, int32_t tile_for
     if (!v || tile_density < 0 || tile_force < 0 || tile_density > 4096 || tile_force > 4096) return SPH_E_INVAL;
     if (tile_density % 64 != 0 || tile_force % 64 != 0) return SPH_E_INVAL;
     const size_t esz = v->esz;
-    // shared memory per staged particle of each loop (FP64: 49 / 141 bytes, FP32: 16 / 56 bytes)
-    const size_t dens_b = esz == 8 ? 49 : 16, force_b = esz == 8 ? 141 : 56;
+    // shared memory per staged particle of each loop (FP64: 48 / 140 bytes, FP32: 16 / 56 bytes)
+    const size_t dens_b = esz == 8 ? 48 : 16, force_b = esz == 8 ? 140 : 56;
     if (tile_density * dens_b > 200 * 1024 || tile_force * force_b > 200 * 1024) return SPH_E_INVAL;
     v->tile_density = tile_density;
     v->tile_force = tile_force;
