@@ -245,6 +245,15 @@ __device__ __forceinline__ double rcp_seeded(double x)
     return fma(y, fma(e, e, e), y);
 }
 
+// Shared-memory load the compiler may not hoist or merge (asm volatile): for values read again on purpose in
+// every round of a loop, so that they do not occupy registers across it.
+__device__ __forceinline__ double lds(const double *p)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Loop bodies.  Each provides: Args, Tile (carve / stage / sentinel), Lhs (load), filter, eval, Part (per-lane
 // partial sums, reduce), Acc (shared accumulator), accumulate, finish, count.
@@ -284,10 +293,45 @@ struct DensF64 {
     struct Part {
         double rho;
         __device__ __forceinline__ void zero() { rho = 0.0; }
-        __device__ __forceinline__ void reduce() { rho = warp_sum(rho); }
     };
     using Acc = double;
     static constexpr int kStageBytes = 4 * 8 + 16;
+    static constexpr int kSlotDoubles = 0;  // the local particle stays in registers
+    static constexpr int kJoint = 1;        // local particles a warp filters together
+    // A warp's lane partials of four consecutive local particles (u = 0..3) are reduced together: a
+    // reduce-scatter (xor 16 keeps two of the four sums per half-warp, xor 8 one per quarter, then xor 4, 2, 1)
+    // takes 6 additions per lane instead of 4 x 5.  Each particle's sum still runs over the same tree as a
+    // butterfly sum (xor 16, 8, 4, 2, 1), so the result does not depend on the grouping.
+    static constexpr int kGroup = 4;
+    struct Group {
+        double p0, p1, p2, p3;
+        __device__ __forceinline__ void zero() { p0 = p1 = p2 = p3 = 0.0; }
+        __device__ __forceinline__ void put(int u, const Part &P)
+        {
+            if (u == 0) p0 = P.rho;
+            else if (u == 1) p1 = P.rho;
+            else if (u == 2) p2 = P.rho;
+            else p3 = P.rho;
+        }
+        // Adds the four sums to acc[g0 + u * stride] (u < nu): lane 8u holds sum u.
+        __device__ __forceinline__ void accumulate(Acc *acc, int g0, int stride, int nu, int lane)
+        {
+            const bool up16 = (lane & 16) != 0;
+            double s0 = up16 ? p2 : p0, s1 = up16 ? p3 : p1;
+            const double o0 = up16 ? p0 : p2, o1 = up16 ? p1 : p3;
+            s0 += __shfl_xor_sync(kFull, o0, 16);
+            s1 += __shfl_xor_sync(kFull, o1, 16);
+            const bool up8 = (lane & 8) != 0;
+            double t = up8 ? s1 : s0;
+            const double o = up8 ? s0 : s1;
+            t += __shfl_xor_sync(kFull, o, 8);
+            t += __shfl_xor_sync(kFull, t, 4);
+            t += __shfl_xor_sync(kFull, t, 2);
+            t += __shfl_xor_sync(kFull, t, 1);
+            const int u = lane >> 3;
+            if ((lane & 7) == 0 && u < nu) acc[g0 + u * stride] += t;
+        }
+    };
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
@@ -318,7 +362,7 @@ struct DensF64 {
                               0.0f);
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
-    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *)
     {
         Lhs L;
         L.x = A.x[i];
@@ -360,10 +404,6 @@ struct DensF64 {
         const double w = fma(fma(fma(c3, r, c2), r, c1), r, c0);
         P.rho = fma(T.m[k], w, P.rho);
         return supp;
-    }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
-    {
-        if (lane == 0) a += P.rho;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
@@ -446,7 +486,7 @@ struct DensF32 {
     // The partner of an odd last candidate: massless and far away (finite, so no inf * 0): it adds 0 and is
     // never counted.
     static __device__ __forceinline__ void pad(const Tile &T, int t) { put(T, t, 1e18f, 1e18f, 1e18f, 0.f); }
-    static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float, double *)
     {
         Lhs L;
         L.x = A.x[i];
@@ -533,22 +573,27 @@ struct DensF32 {
 // A = P / rho^2 and ach = alpha c / 2.  Per pair the piece of each side is chosen by integer compares of
 // bits(r) - 2^52 (= bits(r/2)) and bits(r) - 2^53 (= bits(r/4)) against bits(hh); F then costs two FMAs.
 struct ForceF64 {
+    // The 15 FP64 members a pair term reads from either particle, in this order (per-particle arrays in Args,
+    // one row per candidate in the tile).
+    enum { X, Y, Z, VX, VY, VZ, M, HH, S0, K1, K2I, K2O, AP, ACH, RHO, NF };
     struct Args {
         PairCommon cm;
-        const double *x, *y, *z, *vx, *vy, *vz, *m, *rho;
-        const double *hh, *S0, *K1, *K2i, *K2o, *A, *ach;  // per particle (k_force_prep_f64)
-        const float *xf, *yf, *zf, *hf;                    // filter copies
+        const double *f[NF];                // x, y, z, v, m, rho and (k_force_prep_f64) hh .. ach
+        const float *xf, *yf, *zf, *hf;     // filter copies
         double *ax, *ay, *az, *dudt;
         double beta, eps;
     };
+    // Candidate k's members at d[k * NF + f]: one row address serves all fifteen loads (NF is odd, so 64-bit
+    // loads of 32 different rows hit distinct bank pairs).
     struct Tile {
-        double *x, *y, *z, *vx, *vy, *vz, *m, *hh, *S0, *K1, *K2i, *K2o, *A, *ach, *rho;
+        double *d;
         float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
         int *slot;
     };
+    // The local particle: its FP64 members sit in the warp's shared slot (s[f], read again in every evaluation
+    // round, which keeps them out of the registers); only the filter's FP32 copies stay in registers.
     struct Lhs {
-        double x, y, z, vx, vy, vz, hh, S0, K1, K2i, K2o, A, ach, rho;
-        long long hb;  // bit pattern of hh
+        const double *s;
         float fx, fy, fz, fh, margin;
     };
     struct Part {
@@ -577,17 +622,30 @@ struct ForceF64 {
     struct Acc {
         double ax, ay, az, du;
     };
-    static constexpr int kStageBytes = 15 * 8 + 16 + 4;
+    static constexpr int kStageBytes = NF * 8 + 16 + 4;
+    static constexpr int kSlotDoubles = 16;  // per-warp slot of the local particle's members
+    static constexpr int kJoint = 2;         // local particles a warp filters together (one queue, see process_cell)
+    // One local particle per reduction: its four sums already fill a reduce-scatter.
+    struct Group {
+        Part P;
+        __device__ __forceinline__ void put(int, const Part &Q) { P = Q; }
+        __device__ __forceinline__ void accumulate(Acc *acc, int g0, int, int, int lane)
+        {
+            P.reduce();
+            // after the reduce-scatter: lane 0 -> ax, 8 -> ay, 16 -> az, 24 -> du
+            Acc &a = acc[g0];
+            if (lane == 0) a.ax += P.ax;
+            if (lane == 8) a.ay += P.ax;
+            if (lane == 16) a.az += P.ax;
+            if (lane == 24) a.du += P.ax;
+        }
+    };
 
     static __device__ Tile carve(unsigned char *s, int tj)
     {
         Tile t;
-        double *d = reinterpret_cast<double *>(s);
-        double **dst[15] = {&t.x, &t.y, &t.z, &t.vx, &t.vy, &t.vz, &t.m, &t.hh, &t.S0, &t.K1, &t.K2i, &t.K2o,
-                            &t.A, &t.ach, &t.rho};
-#pragma unroll
-        for (int a = 0; a < 15; ++a) *dst[a] = d + a * tj;
-        t.f4 = reinterpret_cast<float4 *>(d + 15 * tj);
+        t.d = reinterpret_cast<double *>(s);
+        t.f4 = reinterpret_cast<float4 *>(t.d + NF * tj);
         t.slot = reinterpret_cast<int *>(t.f4 + tj);
         return t;
     }
@@ -596,50 +654,31 @@ struct ForceF64 {
     {
         // a neighbour across the periodic boundary is staged at its image position: shift is what the minimum image
         // adds to x_i - x_j, so the image is x_j - shift (only cells next to the boundary have shifts)
-        double xs = A.x[slot], ys = A.y[slot], zs = A.z[slot];
+        double *row = T.d + t * NF;
+        double xs = A.f[X][slot], ys = A.f[Y][slot], zs = A.f[Z][slot];
         if (nb.wrap) {
             xs -= nb.shift[q][0];
             ys -= nb.shift[q][1];
             zs -= nb.shift[q][2];
         }
-        T.x[t] = xs;
-        T.y[t] = ys;
-        T.z[t] = zs;
-        T.vx[t] = A.vx[slot];
-        T.vy[t] = A.vy[slot];
-        T.vz[t] = A.vz[slot];
-        T.m[t] = A.m[slot];
-        T.hh[t] = A.hh[slot];
-        T.S0[t] = A.S0[slot];
-        T.K1[t] = A.K1[slot];
-        T.K2i[t] = A.K2i[slot];
-        T.K2o[t] = A.K2o[slot];
-        T.A[t] = A.A[slot];
-        T.ach[t] = A.ach[slot];
-        T.rho[t] = A.rho[slot];
+        row[X] = xs;
+        row[Y] = ys;
+        row[Z] = zs;
+#pragma unroll
+        for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               A.hf[slot]);
         T.slot[t] = slot;
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
-    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin)
+    // Called by the whole warp; ws is the warp's slot (kSlotDoubles doubles of shared memory).
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *ws)
     {
+        const int lane = threadIdx.x & 31;
+        if (lane < NF) ws[lane] = A.f[lane][i];
+        __syncwarp();
         Lhs L;
-        L.x = A.x[i];
-        L.y = A.y[i];
-        L.z = A.z[i];
-        L.vx = A.vx[i];
-        L.vy = A.vy[i];
-        L.vz = A.vz[i];
-        L.hh = A.hh[i];
-        L.S0 = A.S0[i];
-        L.K1 = A.K1[i];
-        L.K2i = A.K2i[i];
-        L.K2o = A.K2o[i];
-        L.A = A.A[i];
-        L.ach = A.ach[i];
-        L.rho = A.rho[i];
-        L.hb = __double_as_longlong(L.hh);
+        L.s = ws;
         L.fx = A.xf[i];
         L.fy = A.yf[i];
         L.fz = A.zf[i];
@@ -657,38 +696,42 @@ struct ForceF64 {
     static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int i, int k, Part &P)
     {
-        const double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
+        const double *R_ = T.d + k * NF;
+        const double *L_ = L.s;
+        const double dx = lds(L_ + X) - R_[X], dy = lds(L_ + Y) - R_[Y], dz = lds(L_ + Z) - R_[Z];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double rinv = rsqrt_seeded(r2);
         const double r = r2 * rinv;
         const long long rb = __double_as_longlong(r);
         const long long rh = rb - (1LL << 52), rq = rb - (2LL << 52);  // bits of r/2 and r/4
-        const long long hbj = __double_as_longlong(T.hh[k]);
-        const bool ii = rh < L.hb, io = rq < L.hb;  // r < h_i, r < 2 h_i
-        const bool ji = rh < hbj, jo = rq < hbj;    // r < h_j, r < 2 h_j
-        const double Fi = fma(ii ? 0.0 : (io ? L.S0 : 0.0), rinv,
-                              fma(ii ? L.K2i : (io ? L.K2o : 0.0), r, ii ? -L.K1 : (io ? L.K1 : 0.0)));
-        const double K1j = T.K1[k];
-        const double Fj = fma(ji ? 0.0 : (jo ? T.S0[k] : 0.0), rinv,
-                              fma(ji ? T.K2i[k] : (jo ? T.K2o[k] : 0.0), r, ji ? -K1j : (jo ? K1j : 0.0)));
-        const double dvx = L.vx - T.vx[k], dvy = L.vy - T.vy[k], dvz = L.vz - T.vz[k];
+        const double hhi = lds(L_ + HH), hhj = R_[HH];
+        const long long hbi = __double_as_longlong(hhi), hbj = __double_as_longlong(hhj);
+        const bool ii = rh < hbi, io = rq < hbi;  // r < h_i, r < 2 h_i
+        const bool ji = rh < hbj, jo = rq < hbj;  // r < h_j, r < 2 h_j
+        const double K1i = lds(L_ + K1);
+        const double Fi = fma(ii ? 0.0 : (io ? lds(L_ + S0) : 0.0), rinv,
+                              fma(ii ? lds(L_ + K2I) : (io ? lds(L_ + K2O) : 0.0), r, ii ? -K1i : (io ? K1i : 0.0)));
+        const double K1j = R_[K1];
+        const double Fj = fma(ji ? 0.0 : (jo ? R_[S0] : 0.0), rinv,
+                              fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r, ji ? -K1j : (jo ? K1j : 0.0)));
+        const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
         // Monaghan viscosity, Ph = Pi / 2 = mu (beta mu - alpha cbar) / D2 with mu = w / D1, w = hbar v.r,
-        // D1 = r^2 + eps hbar^2, D2 = rho_i + rho_j: one reciprocal R = 1 / (D1 D2) gives 1 / D1 = D2 R, and
-        // Ph = w (beta mu - alpha cbar) R.
-        const double hb = L.hh + T.hh[k];
+        // D1 = r^2 + eps hbar^2, D2 = rho_i + rho_j: one reciprocal R = 1 / (D1 D2) gives g = w R = mu / D2,
+        // mu = g D2 and Ph = g (beta mu - alpha cbar).
+        const double hb = hhi + hhj;
         const double D1 = fma(A.eps * hb, hb, r2);
-        const double D2 = L.rho + T.rho[k];
+        const double D2 = lds(L_ + RHO) + R_[RHO];
         const double R = rcp_seeded(D1 * D2);
-        const double w = hb * vdotr;
-        const double mu = w * (D2 * R);
-        const double t = fma(A.beta, mu, -(L.ach + T.ach[k]));
-        double Ph = (w * t) * R;
+        const double g = (hb * vdotr) * R;
+        const double mu = g * D2;
+        const double t = fma(A.beta, mu, -(lds(L_ + ACH) + R_[ACH]));
+        double Ph = g * t;
         if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
         const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
-        const double aF = L.A * Fi;
-        const double mj = T.m[k];
-        double coef = mj * fma(T.A[k], Fj, aF + V);
+        const double aF = lds(L_ + AP) * Fi;
+        const double mj = R_[M];
+        double coef = mj * fma(R_[AP], Fj, aF + V);
         double dcoef = (mj * vdotr) * fma(0.5, V, aF);
         const bool self = T.slot[k] == i;
         if (self) {
@@ -700,14 +743,6 @@ struct ForceF64 {
         P.az = fma(-coef, dz, P.az);
         P.du += dcoef;
         return !self && (io || jo);
-    }
-    static __device__ __forceinline__ void accumulate(Acc &a, const Part &P, int lane)
-    {
-        // after the reduce-scatter: lane 0 -> ax, 8 -> ay, 16 -> az, 24 -> du
-        if (lane == 0) a.ax += P.ax;
-        if (lane == 8) a.ay += P.ax;
-        if (lane == 16) a.az += P.ax;
-        if (lane == 24) a.du += P.ax;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
@@ -785,7 +820,7 @@ struct ForceF32 {
         T.g4[t] = make_float4(h, A.hinv[slot], A.k4[slot], A.A[slot]);
         T.c2[t] = make_float2(A.cs[slot], A.rho[slot]);
     }
-    static __device__ __forceinline__ Lhs load(const Args &A, int i, float)
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float, double *)
     {
         Lhs L;
         L.x = A.x[i];
@@ -901,8 +936,79 @@ struct PairShared {
     NbrTable nb;
     typename K::Acc acc[kMaxLocal];
     int ring[NT / 32][kRing];
+    double lslot[NT / 32][2][K::kSlotDoubles > 0 ? K::kSlotDoubles : 1];  // per warp: its local particles (K::load)
     unsigned long long pairs;
 };
+
+// One staged tile against the local particles, two at a time per warp (particles 2m and 2m + 1 for m = warp,
+// warp + W, ...: the pairing does not depend on the warp count).  Both particles' filter hits go to the warp's one
+// queue, tagged with the particle, and every evaluation round takes 32 queue entries whichever particle they
+// belong to: only the last round of the pair of particles runs part-full, where one particle per warp would leave
+// a part-full round per particle.  Each lane evaluates with the members of its entry's particle (shared slot 0 or
+// 1) into that particle's partial sums.
+template <class K, int NT>
+__device__ __forceinline__ void tile_pairs_joint(const typename K::Args &A, const typename K::Tile &T,
+                                                 PairShared<K, NT> &S, int ib, int nloc, int tnp, float margin,
+                                                 bool wrap, unsigned long long &my_pairs)
+{
+    constexpr int W = NT / 32;
+    constexpr int kTag = 1 << 14;  // entry = candidate | kTag for the second particle (candidates < 4096)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int *q = S.ring[warp];
+    const NbrTable &nb = S.nb;
+    for (int li0 = 2 * warp; li0 < nloc; li0 += 2 * W) {
+        const bool two = li0 + 1 < nloc;  // warp-uniform
+        const int i0 = ib + li0, i1 = two ? i0 + 1 : i0;
+        const typename K::Lhs L0 = K::load(A, i0, margin, S.lslot[warp][0]);
+        const typename K::Lhs L1 = K::load(A, i1, margin, S.lslot[warp][1]);
+        typename K::Part P0, P1;
+        P0.zero();
+        P1.zero();
+        int head = 0, tail = 0;  // warp-uniform ring cursors; tail - head <= 31 + 64
+        auto round = [&](bool act) {
+            bool in = false;
+            if (act) {
+                const int e = q[(head + lane) & (kRing - 1)];
+                const bool tag = (e & kTag) != 0;
+                typename K::Part Pt = tag ? P1 : P0;
+                in = K::eval(A, tag ? L1 : L0, T, nb, wrap, tag ? i1 : i0, e & (kTag - 1), Pt);
+                if (tag) P1 = Pt; else P0 = Pt;
+            }
+            const unsigned b = __ballot_sync(kFull, in);  // every lane votes
+            if (lane == 0) my_pairs += __popc(b);
+        };
+        for (int jb = 0; jb < tnp; jb += 32) {
+            const int k = jb + lane;
+            const bool p0 = K::filter(L0, T, k);
+            const bool p1 = two && K::filter(L1, T, k);
+            const unsigned b0 = __ballot_sync(kFull, p0);
+            const unsigned b1 = __ballot_sync(kFull, p1);
+            const int c0 = __popc(b0);
+            if (p0) q[(tail + __popc(b0 & lt_mask)) & (kRing - 1)] = k;
+            if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & (kRing - 1)] = k | kTag;
+            tail += c0 + __popc(b1);
+            while (tail - head >= 32) {
+                __syncwarp();
+                round(true);
+                head += 32;
+            }
+        }
+        const int rem = tail - head;
+        if (rem > 0) {
+            __syncwarp();
+            round(lane < rem);
+        }
+        __syncwarp();  // the ring and the slots are reused by the next two particles
+        typename K::Group G;
+        G.put(0, P0);
+        G.accumulate(S.acc, li0, 0, 1, lane);
+        if (two) {
+            G.put(0, P1);
+            G.accumulate(S.acc, li0 + 1, 0, 1, lane);
+        }
+    }
+}
 
 // One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
 template <class K, int NT>
@@ -941,41 +1047,52 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            for (int li = warp; li < nloc; li += NT / 32) {
-                const int i = ib + li;
-                const typename K::Lhs L = K::load(A, i, margin);
-                typename K::Part P;
-                P.zero();
-                int head = 0, tail = 0;  // warp-uniform ring cursors; tail - head <= 31 + kStep
-                for (int jb = 0; jb < tnp; jb += kStep) {
-                    const int k0 = jb + lane, k1 = k0 + 32;
-                    const bool p0 = K::filter(L, T, k0);
-                    const bool p1 = K::filter(L, T, k1);
-                    const unsigned b0 = __ballot_sync(kFull, p0);
-                    const unsigned b1 = __ballot_sync(kFull, p1);
-                    const int c0 = __popc(b0);
-                    if (p0) q[(tail + __popc(b0 & lt_mask)) & (kRing - 1)] = k0;
-                    if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & (kRing - 1)] = k1;
-                    tail += c0 + __popc(b1);
-                    while (tail - head >= 32) {
-                        __syncwarp();
-                        const bool in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
-                        const unsigned bin = __ballot_sync(kFull, in);  // every lane votes
-                        if (lane == 0) my_pairs += __popc(bin);
-                        head += 32;
+            constexpr int W = NT / 32;
+            if constexpr (K::kJoint == 2) {
+                tile_pairs_joint<K, NT>(A, T, S, ib, nloc, tnp, margin, wrap, my_pairs);
+            } else {
+                for (int g0 = warp; g0 < nloc; g0 += K::kGroup * W) {
+                    typename K::Group G;
+                    G.zero();
+                    const int nu = min(K::kGroup, (nloc - g0 + W - 1) / W);  // particles g0 + u W < nloc
+                    for (int u = 0; u < nu; ++u) {
+                        const int li = g0 + u * W;
+                        const int i = ib + li;
+                        const typename K::Lhs L = K::load(A, i, margin, S.lslot[warp][0]);
+                        typename K::Part P;
+                        P.zero();
+                        int head = 0, tail = 0;  // warp-uniform ring cursors; tail - head <= 31 + kStep
+                        for (int jb = 0; jb < tnp; jb += kStep) {
+                            const int k0 = jb + lane, k1 = k0 + 32;
+                            const bool p0 = K::filter(L, T, k0);
+                            const bool p1 = K::filter(L, T, k1);
+                            const unsigned b0 = __ballot_sync(kFull, p0);
+                            const unsigned b1 = __ballot_sync(kFull, p1);
+                            const int c0 = __popc(b0);
+                            if (p0) q[(tail + __popc(b0 & lt_mask)) & (kRing - 1)] = k0;
+                            if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & (kRing - 1)] = k1;
+                            tail += c0 + __popc(b1);
+                            while (tail - head >= 32) {
+                                __syncwarp();
+                                const bool in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
+                                const unsigned bin = __ballot_sync(kFull, in);  // every lane votes
+                                if (lane == 0) my_pairs += __popc(bin);
+                                head += 32;
+                            }
+                        }
+                        const int rem = tail - head;
+                        if (rem > 0) {
+                            __syncwarp();
+                            bool in = false;
+                            if (lane < rem) in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
+                            const unsigned b = __ballot_sync(kFull, in);
+                            if (lane == 0) my_pairs += __popc(b);
+                        }
+                        __syncwarp();  // the ring is reused by the next local particle
+                        G.put(u, P);
                     }
+                    G.accumulate(S.acc, g0, W, nu, lane);
                 }
-                const int rem = tail - head;
-                if (rem > 0) {
-                    __syncwarp();
-                    bool in = false;
-                    if (lane < rem) in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
-                    const unsigned b = __ballot_sync(kFull, in);
-                    if (lane == 0) my_pairs += __popc(b);
-                }
-                __syncwarp();  // the ring is reused by the next local particle
-                P.reduce();
-                K::accumulate(S.acc[li], P, lane);
             }
         }
         __syncthreads();
@@ -1059,7 +1176,7 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
         const int li = tid / ns, s = tid - li * ns;
         const bool active = li < nloc;
         const int i = ib + (active ? li : 0);
-        const typename K::Lhs L = K::load(A, i, 0.f);
+        const typename K::Lhs L = K::load(A, i, 0.f, nullptr);
         typename K::Part P;
         P.zero();
         for (int tb = 0; tb < NJ; tb += tj) {
@@ -1498,23 +1615,24 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     const int tj = pl.tj;
     if (!f32) {
         ForceF64::Args A;
-        cm.tj = tile_or_default(tj, 512);
+        cm.tj = tile_or_default(tj, 448);  // 140 B per staged particle: three 256-thread CTAs per SM
         A.cm = cm;
-        A.x = (const double *)soa.p[SPH_X][0];
-        A.y = (const double *)soa.p[SPH_X][1];
-        A.z = (const double *)soa.p[SPH_X][2];
-        A.vx = (const double *)soa.p[SPH_V][0];
-        A.vy = (const double *)soa.p[SPH_V][1];
-        A.vz = (const double *)soa.p[SPH_V][2];
-        A.m = (const double *)soa.p[SPH_MASS][0];
-        A.rho = (const double *)soa.p[SPH_RHO][0];
-        A.hh = (const double *)scr.d[0];
-        A.S0 = (const double *)scr.d[1];
-        A.K1 = (const double *)scr.d[2];
-        A.K2i = (const double *)scr.d[3];
-        A.K2o = (const double *)scr.d[4];
-        A.A = (const double *)scr.d[5];
-        A.ach = (const double *)scr.d[6];
+        using F = ForceF64;
+        A.f[F::X] = (const double *)soa.p[SPH_X][0];
+        A.f[F::Y] = (const double *)soa.p[SPH_X][1];
+        A.f[F::Z] = (const double *)soa.p[SPH_X][2];
+        A.f[F::VX] = (const double *)soa.p[SPH_V][0];
+        A.f[F::VY] = (const double *)soa.p[SPH_V][1];
+        A.f[F::VZ] = (const double *)soa.p[SPH_V][2];
+        A.f[F::M] = (const double *)soa.p[SPH_MASS][0];
+        A.f[F::RHO] = (const double *)soa.p[SPH_RHO][0];
+        A.f[F::HH] = (const double *)scr.d[0];
+        A.f[F::S0] = (const double *)scr.d[1];
+        A.f[F::K1] = (const double *)scr.d[2];
+        A.f[F::K2I] = (const double *)scr.d[3];
+        A.f[F::K2O] = (const double *)scr.d[4];
+        A.f[F::AP] = (const double *)scr.d[5];
+        A.f[F::ACH] = (const double *)scr.d[6];
         A.xf = scr.xf;
         A.yf = scr.yf;
         A.zf = scr.zf;
