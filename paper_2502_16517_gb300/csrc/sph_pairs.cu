@@ -45,8 +45,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxLocal = 128;  // local particles per round of the FP64 driver (shared accumulators)
 // Threads per pair CTA ("warps per cell"): 128 or 256, chosen per loop by the view (autotuner).
-constexpr int kRing = 128;   // per-warp queue slots (at most 31 + 64 pending)
-constexpr int kStep = 64;    // candidates per filter step (two per lane)
+constexpr int kRing = 128;   // per-warp queue slots (at most 31 + 2 x 32 pending)
+constexpr int kStep = 64;    // tile granularity: a staged tile is padded to a multiple of kStep
 constexpr float kFar = 1e30f;  // sentinel coordinate: its squared distance overflows to +inf
 
 struct NbrTable {
@@ -272,11 +272,14 @@ struct PairCommon {
 // patterns of r against h_i and 2 h_i, and f evaluated as a cubic in r whose coefficients d_k h_i^-k come from
 // the per-particle set-up kernel.
 struct DensF64 {
+    // The FP64 members of the local particle a pair term reads (per-particle arrays in Args, the warp's shared
+    // slot in Lhs), in this order.
+    enum { X, Y, Z, H, E2, E3, O1, O2, O3, NF };
     struct Args {
         PairCommon cm;
-        const double *x, *y, *z, *m, *h, *u;
+        const double *f[NF];                   // x, y, z, h and (k_density_prep_f64) e2 .. o3
+        const double *m, *u;
         const float *xf, *yf, *zf;             // cell-relative float positions (filter only)
-        const double *e2, *e3, *o1, *o2, *o3;  // per particle (k_density_prep_f64)
         double *rho, *P, *cs;
         double gamma;
     };
@@ -284,10 +287,10 @@ struct DensF64 {
         double *x, *y, *z, *m;
         float4 *f4;  // filter: cell-relative position seen from the local cell, unused
     };
+    // The local particle: FP64 members in the warp's shared slot s (re-read every evaluation round), the
+    // filter's FP32 copies in registers.
     struct Lhs {
-        double x, y, z;
-        long long hb1, hb2;  // bit patterns of h and 2h (r < h  <=>  bits(r) < hb1 for r >= 0)
-        double e2, e3, o1, o2, o3;
+        const double *s;
         float fx, fy, fz, b2;
     };
     struct Part {
@@ -296,25 +299,25 @@ struct DensF64 {
     };
     using Acc = double;
     static constexpr int kStageBytes = 4 * 8 + 16;
-    static constexpr int kSlotDoubles = 0;  // the local particle stays in registers
-    static constexpr int kJoint = 1;        // local particles a warp filters together
-    // A warp's lane partials of four consecutive local particles (u = 0..3) are reduced together: a
-    // reduce-scatter (xor 16 keeps two of the four sums per half-warp, xor 8 one per quarter, then xor 4, 2, 1)
-    // takes 6 additions per lane instead of 4 x 5.  Each particle's sum still runs over the same tree as a
-    // butterfly sum (xor 16, 8, 4, 2, 1), so the result does not depend on the grouping.
+    static constexpr int kSlotDoubles = 16;  // per-warp slot of a local particle's members
+    // The warp's lane partials of four local particles (u = 0..3) are reduced together: a reduce-scatter (xor 16
+    // keeps two of the four sums per half-warp, xor 8 one per quarter, then xor 4, 2, 1) takes 6 additions per
+    // lane instead of 4 x 5.  Each particle's sum still runs over the same tree as a butterfly sum (xor 16, 8, 4,
+    // 2, 1), so the result does not depend on the grouping.
     static constexpr int kGroup = 4;
     struct Group {
         double p0, p1, p2, p3;
+        int l0, l1, l2, l3;
         __device__ __forceinline__ void zero() { p0 = p1 = p2 = p3 = 0.0; }
-        __device__ __forceinline__ void put(int u, const Part &P)
+        __device__ __forceinline__ void put(int u, const Part &P, int li)
         {
-            if (u == 0) p0 = P.rho;
-            else if (u == 1) p1 = P.rho;
-            else if (u == 2) p2 = P.rho;
-            else p3 = P.rho;
+            if (u == 0) { p0 = P.rho; l0 = li; }
+            else if (u == 1) { p1 = P.rho; l1 = li; }
+            else if (u == 2) { p2 = P.rho; l2 = li; }
+            else { p3 = P.rho; l3 = li; }
         }
-        // Adds the four sums to acc[g0 + u * stride] (u < nu): lane 8u holds sum u.
-        __device__ __forceinline__ void accumulate(Acc *acc, int g0, int stride, int nu, int lane)
+        // Adds sum u to acc[l_u] for u < nu (lane 8u holds sum u); called by the whole warp.
+        __device__ __forceinline__ void accumulate(Acc *acc, int nu, int lane)
         {
             const bool up16 = (lane & 16) != 0;
             double s0 = up16 ? p2 : p0, s1 = up16 ? p3 : p1;
@@ -329,7 +332,7 @@ struct DensF64 {
             t += __shfl_xor_sync(kFull, t, 2);
             t += __shfl_xor_sync(kFull, t, 1);
             const int u = lane >> 3;
-            if ((lane & 7) == 0 && u < nu) acc[g0 + u * stride] += t;
+            if ((lane & 7) == 0 && u < nu) acc[u == 0 ? l0 : u == 1 ? l1 : u == 2 ? l2 : l3] += t;
         }
     };
 
@@ -348,7 +351,7 @@ struct DensF64 {
     {
         // a neighbour across the periodic boundary is staged at its image position: shift is what the minimum image
         // adds to x_i - x_j, so the image is x_j - shift (only cells next to the boundary have shifts)
-        double xs = A.x[slot], ys = A.y[slot], zs = A.z[slot];
+        double xs = A.f[X][slot], ys = A.f[Y][slot], zs = A.f[Z][slot];
         if (nb.wrap) {
             xs -= nb.shift[q][0];
             ys -= nb.shift[q][1];
@@ -362,24 +365,18 @@ struct DensF64 {
                               0.0f);
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
-    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *)
+    // Called by the whole warp; ws is a slot of kSlotDoubles doubles of shared memory.
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *ws)
     {
+        const int lane = threadIdx.x & 31;
+        if (lane < NF) ws[lane] = A.f[lane][i];
+        __syncwarp();
         Lhs L;
-        L.x = A.x[i];
-        L.y = A.y[i];
-        L.z = A.z[i];
-        const double h = A.h[i];
-        L.hb1 = __double_as_longlong(h);
-        L.hb2 = L.hb1 + (1LL << 52);  // bits of 2h (exponent + 1)
-        L.e2 = A.e2[i];
-        L.e3 = A.e3[i];
-        L.o1 = A.o1[i];
-        L.o2 = A.o2[i];
-        L.o3 = A.o3[i];
+        L.s = ws;
         L.fx = A.xf[i];
         L.fy = A.yf[i];
         L.fz = A.zf[i];
-        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), __double2float_ru(h), margin);
+        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), __double2float_ru(A.f[H][i]), margin);
         L.b2 = __fmul_ru(rf, rf);
         return L;
     }
@@ -392,22 +389,25 @@ struct DensF64 {
     static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &nb,
                                                 bool wrap, int, int k, Part &P)
     {
-        const double dx = L.x - T.x[k], dy = L.y - T.y[k], dz = L.z - T.z[k];
+        const double *s = L.s;
+        const double dx = lds(s + X) - T.x[k], dy = lds(s + Y) - T.y[k], dz = lds(s + Z) - T.z[k];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double r = r2 * rsqrt_seeded(r2);
         const long long rb = __double_as_longlong(r);
-        const bool inner = rb < L.hb1, supp = rb < L.hb2;
+        // bit patterns of h and 2 h: for r >= 0, r < h exactly when bits(r) < bits(h)
+        const long long hb1 = __double_as_longlong(lds(s + H)), hb2 = hb1 + (1LL << 52);
+        const bool inner = rb < hb1, supp = rb < hb2;
         const double c0 = inner ? 1.0 : (supp ? 2.0 : 0.0);
-        const double c1 = inner ? 0.0 : (supp ? L.o1 : 0.0);
-        const double c2 = inner ? L.e2 : (supp ? L.o2 : 0.0);
-        const double c3 = inner ? L.e3 : (supp ? L.o3 : 0.0);
+        const double c1 = inner ? 0.0 : (supp ? lds(s + O1) : 0.0);
+        const double c2 = inner ? lds(s + E2) : (supp ? lds(s + O2) : 0.0);
+        const double c3 = inner ? lds(s + E3) : (supp ? lds(s + O3) : 0.0);
         const double w = fma(fma(fma(c3, r, c2), r, c1), r, c0);
         P.rho = fma(T.m[k], w, P.rho);
         return supp;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
-        const double h = A.h[i];
+        const double h = A.f[H][i];
         const double hinv = 1.0 / h;
         const double rho = a * (kInvPi * hinv * hinv * hinv);
         const double P = (A.gamma - 1.0) * rho * A.u[i];
@@ -624,16 +624,22 @@ struct ForceF64 {
     };
     static constexpr int kStageBytes = NF * 8 + 16 + 4;
     static constexpr int kSlotDoubles = 16;  // per-warp slot of the local particle's members
-    static constexpr int kJoint = 2;         // local particles a warp filters together (one queue, see process_cell)
     // One local particle per reduction: its four sums already fill a reduce-scatter.
+    static constexpr int kGroup = 1;
     struct Group {
         Part P;
-        __device__ __forceinline__ void put(int, const Part &Q) { P = Q; }
-        __device__ __forceinline__ void accumulate(Acc *acc, int g0, int, int, int lane)
+        int li;
+        __device__ __forceinline__ void zero() {}
+        __device__ __forceinline__ void put(int, const Part &Q, int l)
+        {
+            P = Q;
+            li = l;
+        }
+        __device__ __forceinline__ void accumulate(Acc *acc, int, int lane)
         {
             P.reduce();
             // after the reduce-scatter: lane 0 -> ax, 8 -> ay, 16 -> az, 24 -> du
-            Acc &a = acc[g0];
+            Acc &a = acc[li];
             if (lane == 0) a.ax += P.ax;
             if (lane == 8) a.ay += P.ax;
             if (lane == 16) a.az += P.ax;
@@ -929,14 +935,14 @@ __device__ __forceinline__ void zero_acc<ForceF32>(ForceF32::Acc &a)
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// The per-cell driver shared by all loop bodies.
+// The per-cell driver of the FP64 loop bodies.
 // ------------------------------------------------------------------------------------------------------------
 template <class K, int NT>
 struct PairShared {
     NbrTable nb;
     typename K::Acc acc[kMaxLocal];
     int ring[NT / 32][kRing];
-    double lslot[NT / 32][2][K::kSlotDoubles > 0 ? K::kSlotDoubles : 1];  // per warp: its local particles (K::load)
+    double lslot[NT / 32][2][K::kSlotDoubles];  // per warp: its two local particles (K::load)
     unsigned long long pairs;
 };
 
@@ -945,11 +951,11 @@ struct PairShared {
 // queue, tagged with the particle, and every evaluation round takes 32 queue entries whichever particle they
 // belong to: only the last round of the pair of particles runs part-full, where one particle per warp would leave
 // a part-full round per particle.  Each lane evaluates with the members of its entry's particle (shared slot 0 or
-// 1) into that particle's partial sums.
+// 1) into that particle's partial sums; the partials are reduced over the warp kGroup particles at a time.
 template <class K, int NT>
-__device__ __forceinline__ void tile_pairs_joint(const typename K::Args &A, const typename K::Tile &T,
-                                                 PairShared<K, NT> &S, int ib, int nloc, int tnp, float margin,
-                                                 bool wrap, unsigned long long &my_pairs)
+__device__ __forceinline__ void tile_pairs(const typename K::Args &A, const typename K::Tile &T,
+                                           PairShared<K, NT> &S, int ib, int nloc, int tnp, float margin, bool wrap,
+                                           unsigned long long &my_pairs)
 {
     constexpr int W = NT / 32;
     constexpr int kTag = 1 << 14;  // entry = candidate | kTag for the second particle (candidates < 4096)
@@ -957,6 +963,9 @@ __device__ __forceinline__ void tile_pairs_joint(const typename K::Args &A, cons
     const unsigned lt_mask = (1u << lane) - 1u;
     int *q = S.ring[warp];
     const NbrTable &nb = S.nb;
+    typename K::Group G;
+    G.zero();
+    int nu = 0;  // particles held by G (warp-uniform)
     for (int li0 = 2 * warp; li0 < nloc; li0 += 2 * W) {
         const bool two = li0 + 1 < nloc;  // warp-uniform
         const int i0 = ib + li0, i1 = two ? i0 + 1 : i0;
@@ -1000,14 +1009,22 @@ __device__ __forceinline__ void tile_pairs_joint(const typename K::Args &A, cons
             round(lane < rem);
         }
         __syncwarp();  // the ring and the slots are reused by the next two particles
-        typename K::Group G;
-        G.put(0, P0);
-        G.accumulate(S.acc, li0, 0, 1, lane);
+        G.put(nu++, P0, li0);
+        if (nu == K::kGroup) {
+            G.accumulate(S.acc, nu, lane);
+            G.zero();
+            nu = 0;
+        }
         if (two) {
-            G.put(0, P1);
-            G.accumulate(S.acc, li0 + 1, 0, 1, lane);
+            G.put(nu++, P1, li0 + 1);
+            if (nu == K::kGroup) {
+                G.accumulate(S.acc, nu, lane);
+                G.zero();
+                nu = 0;
+            }
         }
     }
+    if (nu > 0) G.accumulate(S.acc, nu, lane);
 }
 
 // One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
@@ -1018,10 +1035,8 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
     if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int tj = A.cm.tj;
-    int *q = S.ring[warp];
     NbrTable &nb = S.nb;
     if (tid == 0) S.pairs = 0ull;
     build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start);
@@ -1047,53 +1062,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            constexpr int W = NT / 32;
-            if constexpr (K::kJoint == 2) {
-                tile_pairs_joint<K, NT>(A, T, S, ib, nloc, tnp, margin, wrap, my_pairs);
-            } else {
-                for (int g0 = warp; g0 < nloc; g0 += K::kGroup * W) {
-                    typename K::Group G;
-                    G.zero();
-                    const int nu = min(K::kGroup, (nloc - g0 + W - 1) / W);  // particles g0 + u W < nloc
-                    for (int u = 0; u < nu; ++u) {
-                        const int li = g0 + u * W;
-                        const int i = ib + li;
-                        const typename K::Lhs L = K::load(A, i, margin, S.lslot[warp][0]);
-                        typename K::Part P;
-                        P.zero();
-                        int head = 0, tail = 0;  // warp-uniform ring cursors; tail - head <= 31 + kStep
-                        for (int jb = 0; jb < tnp; jb += kStep) {
-                            const int k0 = jb + lane, k1 = k0 + 32;
-                            const bool p0 = K::filter(L, T, k0);
-                            const bool p1 = K::filter(L, T, k1);
-                            const unsigned b0 = __ballot_sync(kFull, p0);
-                            const unsigned b1 = __ballot_sync(kFull, p1);
-                            const int c0 = __popc(b0);
-                            if (p0) q[(tail + __popc(b0 & lt_mask)) & (kRing - 1)] = k0;
-                            if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & (kRing - 1)] = k1;
-                            tail += c0 + __popc(b1);
-                            while (tail - head >= 32) {
-                                __syncwarp();
-                                const bool in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
-                                const unsigned bin = __ballot_sync(kFull, in);  // every lane votes
-                                if (lane == 0) my_pairs += __popc(bin);
-                                head += 32;
-                            }
-                        }
-                        const int rem = tail - head;
-                        if (rem > 0) {
-                            __syncwarp();
-                            bool in = false;
-                            if (lane < rem) in = K::eval(A, L, T, nb, wrap, i, q[(head + lane) & (kRing - 1)], P);
-                            const unsigned b = __ballot_sync(kFull, in);
-                            if (lane == 0) my_pairs += __popc(b);
-                        }
-                        __syncwarp();  // the ring is reused by the next local particle
-                        G.put(u, P);
-                    }
-                    G.accumulate(S.acc, g0, W, nu, lane);
-                }
-            }
+            tile_pairs<K, NT>(A, T, S, ib, nloc, tnp, margin, wrap, my_pairs);
         }
         __syncthreads();
         for (int t = tid; t < nloc; t += NT) K::finish(A, ib + t, S.acc[t]);
@@ -1569,20 +1538,21 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
         DensF64::Args A;
         cm.tj = tile_or_default(tj, 512);
         A.cm = cm;
-        A.x = (const double *)soa.p[SPH_X][0];
-        A.y = (const double *)soa.p[SPH_X][1];
-        A.z = (const double *)soa.p[SPH_X][2];
+        using D = DensF64;
+        A.f[D::X] = (const double *)soa.p[SPH_X][0];
+        A.f[D::Y] = (const double *)soa.p[SPH_X][1];
+        A.f[D::Z] = (const double *)soa.p[SPH_X][2];
+        A.f[D::H] = (const double *)soa.p[SPH_H][0];
+        A.f[D::E2] = (const double *)scr.d[0];
+        A.f[D::E3] = (const double *)scr.d[1];
+        A.f[D::O1] = (const double *)scr.d[2];
+        A.f[D::O2] = (const double *)scr.d[3];
+        A.f[D::O3] = (const double *)scr.d[4];
         A.m = (const double *)soa.p[SPH_MASS][0];
-        A.h = (const double *)soa.p[SPH_H][0];
         A.u = (const double *)soa.p[SPH_U][0];
         A.xf = scr.xf;
         A.yf = scr.yf;
         A.zf = scr.zf;
-        A.e2 = (const double *)scr.d[0];
-        A.e3 = (const double *)scr.d[1];
-        A.o1 = (const double *)scr.d[2];
-        A.o2 = (const double *)scr.d[3];
-        A.o3 = (const double *)scr.d[4];
         A.rho = (double *)soa.p[SPH_RHO][0];
         A.P = (double *)soa.p[SPH_P][0];
         A.cs = (double *)soa.p[SPH_CS][0];

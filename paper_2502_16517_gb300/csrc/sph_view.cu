@@ -796,14 +796,14 @@ sph_status sph_autotune(sph_view v, void *aos_dev, int64_t n, const sph_params *
     // a full pass first: every member the loops read becomes resident (the records get this pass's outputs)
     sph_status s = do_pass(v, aos_dev, n, params);
     if (s != SPH_OK) return s;
-    static const int cand_d64[] = {256, 384, 512, 768, 1024, 1536};
+    static const int cand_d64[] = {256, 384, 448, 512, 768, 1024, 1536};
     static const int cand_f64[] = {128, 192, 256, 384, 448, 512, 768};
     static const int cand_d32[] = {256, 512, 1024, 2048, 4096};
     static const int cand_f32[] = {256, 384, 512, 1024, 2048};
     const bool f32 = v->prec == SPH_F32;
     const int *cd = f32 ? cand_d32 : cand_d64;
     const int *cf = f32 ? cand_f32 : cand_f64;
-    const int nd = f32 ? 5 : 6, nf = f32 ? 5 : 7;
+    const int nd = f32 ? 5 : 7, nf = f32 ? 5 : 7;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

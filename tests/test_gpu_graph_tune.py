@@ -135,7 +135,7 @@ def test_autotune_picks_candidates_and_keeps_results(sph, oracle, side_stream, p
         tuned = aos.cpu().numpy()
     finally:
         sph.sph_view_destroy(v)
-    cands = {0: ([256, 384, 512, 768, 1024, 1536], [128, 192, 256, 384, 448, 512, 768]),
+    cands = {0: ([256, 384, 448, 512, 768, 1024, 1536], [128, 192, 256, 384, 448, 512, 768]),
              1: ([256, 512, 1024, 2048, 4096], [256, 384, 512, 1024, 2048])}[prec]
     assert td in cands[0] and tf in cands[1] and md > 0 and mf > 0
     ref = oracle.step_all(aos_h, lay, f["box"], wl.SPH_PARAMS)
