@@ -299,7 +299,9 @@ struct DensF64 {
     };
     using Acc = double;
     static constexpr int kStageBytes = 4 * 8 + 16;
-    static constexpr int kSlotDoubles = 16;  // per-warp slot of a local particle's members
+    static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
+    // CTAs per SM the register allocation must allow: shared memory allows seven of 128 threads at a 512 tile
+    static constexpr int min_ctas(int nt) { return nt == 128 ? 7 : 3; }
     // The warp's lane partials of four local particles (u = 0..3) are reduced together: a reduce-scatter (xor 16
     // keeps two of the four sums per half-warp, xor 8 one per quarter, then xor 4, 2, 1) takes 6 additions per
     // lane instead of 4 x 5.  Each particle's sum still runs over the same tree as a butterfly sum (xor 16, 8, 4,
@@ -599,51 +601,53 @@ struct ForceF64 {
     struct Part {
         double ax, ay, az, du;
         __device__ __forceinline__ void zero() { ax = ay = az = du = 0.0; }
-        // Reduce-scatter over the warp: afterwards lane 0 holds sum ax, lane 8 sum ay, lane 16 sum az and lane 24
-        // sum du (6 additions per lane instead of 20 for four butterflies).
-        __device__ __forceinline__ void reduce()
-        {
-            const int lane = threadIdx.x & 31;
-            const bool up16 = (lane & 16) != 0;
-            double s0 = up16 ? az : ax, s1 = up16 ? du : ay;
-            const double o0 = up16 ? ax : az, o1 = up16 ? ay : du;
-            s0 += __shfl_xor_sync(kFull, o0, 16);
-            s1 += __shfl_xor_sync(kFull, o1, 16);
-            const bool up8 = (lane & 8) != 0;
-            double t = up8 ? s1 : s0;
-            const double o = up8 ? s0 : s1;
-            t += __shfl_xor_sync(kFull, o, 8);
-            t += __shfl_xor_sync(kFull, t, 4);
-            t += __shfl_xor_sync(kFull, t, 2);
-            t += __shfl_xor_sync(kFull, t, 1);
-            ax = t;  // the sum this lane's group of 8 holds (see accumulate)
-        }
     };
     struct Acc {
         double ax, ay, az, du;
     };
     static constexpr int kStageBytes = NF * 8 + 16 + 4;
-    static constexpr int kSlotDoubles = 16;  // per-warp slot of the local particle's members
-    // One local particle per reduction: its four sums already fill a reduce-scatter.
-    static constexpr int kGroup = 1;
+    static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
+    // CTAs per SM the register allocation must allow: shared memory allows three at a 448 tile (85 registers
+    // at 256 threads)
+    static constexpr int min_ctas(int) { return 3; }
+    // The two local particles of a warp's queue are reduced together: one reduce-scatter of their eight sums
+    // (xor 16 keeps one particle per half-warp, xor 8 two of its sums, xor 4 one, then xor 2, 1) takes 9
+    // additions per lane instead of 2 x 6.  Every sum still runs over the butterfly tree (xor 16, 8, 4, 2, 1).
+    static constexpr int kGroup = 2;
     struct Group {
-        Part P;
-        int li;
+        Part P0, P1;
+        int l0, l1;
         __device__ __forceinline__ void zero() {}
-        __device__ __forceinline__ void put(int, const Part &Q, int l)
+        __device__ __forceinline__ void put(int u, const Part &P, int li)
         {
-            P = Q;
-            li = l;
+            if (u == 0) { P0 = P; l0 = li; }
+            else { P1 = P; l1 = li; }
         }
-        __device__ __forceinline__ void accumulate(Acc *acc, int, int lane)
+        // Adds the sums of particle u < nu to acc[l_u]; called by the whole warp.  Afterwards lanes 4g .. 4g + 3
+        // hold sum g = 4 u + c (c: 0 ax, 1 ay, 2 az, 3 du).
+        __device__ __forceinline__ void accumulate(Acc *acc, int nu, int lane)
         {
-            P.reduce();
-            // after the reduce-scatter: lane 0 -> ax, 8 -> ay, 16 -> az, 24 -> du
-            Acc &a = acc[li];
-            if (lane == 0) a.ax += P.ax;
-            if (lane == 8) a.ay += P.ax;
-            if (lane == 16) a.az += P.ax;
-            if (lane == 24) a.du += P.ax;
+            const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0, up4 = (lane & 4) != 0;
+            const Part &K = up16 ? P1 : P0, &O = up16 ? P0 : P1;
+            double a0 = K.ax + __shfl_xor_sync(kFull, O.ax, 16);
+            double a1 = K.ay + __shfl_xor_sync(kFull, O.ay, 16);
+            double a2 = K.az + __shfl_xor_sync(kFull, O.az, 16);
+            double a3 = K.du + __shfl_xor_sync(kFull, O.du, 16);
+            double b0 = up8 ? a2 : a0, b1 = up8 ? a3 : a1;
+            b0 += __shfl_xor_sync(kFull, up8 ? a0 : a2, 8);
+            b1 += __shfl_xor_sync(kFull, up8 ? a1 : a3, 8);
+            double t = up4 ? b1 : b0;
+            t += __shfl_xor_sync(kFull, up4 ? b0 : b1, 4);
+            t += __shfl_xor_sync(kFull, t, 2);
+            t += __shfl_xor_sync(kFull, t, 1);
+            const int u = lane >> 4, c = (lane >> 2) & 3;
+            if ((lane & 3) == 0 && u < nu) {
+                Acc &a = acc[u == 0 ? l0 : l1];
+                if (c == 0) a.ax += t;
+                else if (c == 1) a.ay += t;
+                else if (c == 2) a.az += t;
+                else a.du += t;
+            }
         }
     };
 
@@ -942,7 +946,9 @@ struct PairShared {
     NbrTable nb;
     typename K::Acc acc[kMaxLocal];
     int ring[NT / 32][kRing];
-    double lslot[NT / 32][2][K::kSlotDoubles];  // per warp: its two local particles (K::load)
+    // per warp: its two local particles (K::load); an odd slot length puts member f of the two slots in
+    // different banks, so a round that mixes the two particles reads both without a bank conflict
+    double lslot[NT / 32][2][K::kSlotDoubles];
     unsigned long long pairs;
 };
 
@@ -963,7 +969,7 @@ __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const type
     const unsigned lt_mask = (1u << lane) - 1u;
     int *q = S.ring[warp];
     const NbrTable &nb = S.nb;
-    typename K::Group G;
+    typename K::Group G;  // groups of kGroup > 2 particles span several pairs
     G.zero();
     int nu = 0;  // particles held by G (warp-uniform)
     for (int li0 = 2 * warp; li0 < nloc; li0 += 2 * W) {
@@ -1009,22 +1015,21 @@ __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const type
             round(lane < rem);
         }
         __syncwarp();  // the ring and the slots are reused by the next two particles
-        G.put(nu++, P0, li0);
-        if (nu == K::kGroup) {
-            G.accumulate(S.acc, nu, lane);
-            G.zero();
-            nu = 0;
-        }
-        if (two) {
-            G.put(nu++, P1, li0 + 1);
-            if (nu == K::kGroup) {
+        if constexpr (K::kGroup == 2) {  // one reduction per pair of particles
+            typename K::Group G2;
+            G2.put(0, P0, li0);
+            G2.put(1, P1, li0 + 1);  // (all zero when the warp has a single particle)
+            G2.accumulate(S.acc, two ? 2 : 1, lane);
+        } else {
+            G.put(nu++, P0, li0);
+            if (two) G.put(nu++, P1, li0 + 1);
+            if (nu == K::kGroup || li0 + 2 * W >= nloc) {
                 G.accumulate(S.acc, nu, lane);
                 G.zero();
                 nu = 0;
             }
         }
     }
-    if (nu > 0) G.accumulate(S.acc, nu, lane);
 }
 
 // One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
@@ -1222,7 +1227,7 @@ __global__ void __launch_bounds__(NT) k_cell_lanes_persist(const typename K::Arg
 
 // One CTA per cell (single-grid views).
 template <class K, int NT>
-__global__ void __launch_bounds__(NT) k_cell_pairs(const typename K::Args A)
+__global__ void __launch_bounds__(NT, K::min_ctas(NT)) k_cell_pairs(const typename K::Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PairShared<K, NT> S;
@@ -1233,7 +1238,7 @@ __global__ void __launch_bounds__(NT) k_cell_pairs(const typename K::Args A)
 // Persistent CTAs pulling cells from a work list (patch views: cells in descending cost order, so the largest
 // cells start first and the small ones fill the tail).
 template <class K, int NT>
-__global__ void __launch_bounds__(NT) k_cell_pairs_persist(const typename K::Args A,
+__global__ void __launch_bounds__(NT, K::min_ctas(NT)) k_cell_pairs_persist(const typename K::Args A,
                                                                      const int *__restrict__ order,
                                                                      const int *__restrict__ count, int *next)
 {
