@@ -197,6 +197,25 @@ struct Kahan {
     }
 };
 
+// Two Kahan accumulators side by side (value = s - c per component), updated with paired FP32 instructions: the
+// same IEEE operations, in the same order, as two Kahan::add.
+struct Kahan2 {
+    float2 s, c;
+    __device__ __forceinline__ void zero()
+    {
+        s = make_float2(0.f, 0.f);
+        c = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void add(float2 y)
+    {
+        const float2 neg = make_float2(-1.0f, -1.0f);
+        const float2 yy = __ffma2_rn(c, neg, y);  // y - c
+        const float2 t = __fadd2_rn(s, yy);
+        c = __ffma2_rn(yy, neg, __ffma2_rn(s, neg, t));  // (t - s) - yy
+        s = t;
+    }
+};
+
 // ------------------------------------------------------------------------------------------------------------
 // Pair-term arithmetic of the FP64 loop bodies.
 //
@@ -796,14 +815,13 @@ struct ForceF32 {
     struct Lhs {
         float x, y, z, vx, vy, vz, h, hinv, k4, A, c, rho, b2;
     };
+    // The four compensated sums as two pairs, (a_x, a_y) and (a_z, du/dt), for paired FP32 updates.
     struct Part {
-        Kahan ax, ay, az, du;
+        Kahan2 axy, azd;
         __device__ __forceinline__ void zero()
         {
-            ax.zero();
-            ay.zero();
-            az.zero();
-            du.zero();
+            axy.zero();
+            azd.zero();
         }
     };
     struct Acc {
@@ -855,56 +873,64 @@ struct ForceF32 {
         const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
         return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < fmaxf(L.b2, p.w);
     }
+    // Where two quantities go through the same operation (the x and y components, the i and j sides of the
+    // kernel gradient, ...) they share one paired FP32 instruction; every operation and its order is that of the
+    // scalar form, so the results are the same.
     static __device__ __forceinline__ void eval(const Args &A, const Lhs &L, const Tile &T, int k, Part &P)
     {
         const float4 p = T.p4[k];
         const float4 vm = T.v4[k];
         const float4 g = T.g4[k];
         const float2 cr = T.c2[k];
-        const float dx = L.x - p.x, dy = L.y - p.y, dz = L.z - p.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float2 neg = make_float2(-1.0f, -1.0f);
+        const float2 dxy = __ffma2_rn(make_float2(p.x, p.y), neg, make_float2(L.x, L.y));
+        const float dz = L.z - p.z;
+        const float r2 = fmaf(dxy.x, dxy.x, fmaf(dxy.y, dxy.y, dz * dz));
         const float rinv = rsqrt_ftz(r2 + 1e-30f);
         const float r = r2 * rinv;
-        const float qi = r * L.hinv, qj = r * g.y;
-        const float si = fma_sat(-0.5f, qi, 1.0f), ti = fma_sat(-1.0f, qi, 1.0f);
-        const float sj = fma_sat(-0.5f, qj, 1.0f), tj = fma_sat(-1.0f, qj, 1.0f);
-        const float Fi = (L.k4 * rinv) * ((ti - si) * (ti + si));
-        const float Fj = (g.z * rinv) * ((tj - sj) * (tj + sj));
-        const float dvx = L.vx - vm.x, dvy = L.vy - vm.y, dvz = L.vz - vm.z;
-        const float vdotr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
+        const float2 q = __fmul2_rn(make_float2(r, r), make_float2(L.hinv, g.y));  // q_i, q_j
+        const float2 sq = make_float2(fma_sat(-0.5f, q.x, 1.0f), fma_sat(-0.5f, q.y, 1.0f));
+        const float2 tq = make_float2(fma_sat(-1.0f, q.x, 1.0f), fma_sat(-1.0f, q.y, 1.0f));
+        // (F_i, F_j) = (k4 / r) ((t - s) (t + s)) for each side
+        const float2 F = __fmul2_rn(__fmul2_rn(make_float2(L.k4, g.z), make_float2(rinv, rinv)),
+                                    __fmul2_rn(__ffma2_rn(sq, neg, tq), __fadd2_rn(tq, sq)));
+        const float2 dvxy = __ffma2_rn(make_float2(vm.x, vm.y), neg, make_float2(L.vx, L.vy));
+        const float dvz = L.vz - vm.z;
+        const float vdotr = fmaf(dvxy.x, dxy.x, fmaf(dvxy.y, dxy.y, dvz * dz));
         const float vneg = 0.5f * (vdotr - fabsf(vdotr));  // min(v_ij . r_ij, 0)
-        const float hb = 0.5f * (L.h + g.x);
+        const float2 hc = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(make_float2(L.h, L.c), make_float2(g.x, cr.x)));
+        const float hb = hc.x, cb = hc.y;  // hbar, cbar
         const float D1 = fmaf(A.eps * hb, hb, r2);
         const float D2 = L.rho + cr.y;
         const float R = rcp_ftz(D1 * D2);
-        const float mu = (hb * vneg) * (D2 * R);
-        const float cb = 0.5f * (L.c + cr.x);
-        const float Ph = (mu * fmaf(A.beta, mu, -A.alpha * cb)) * (D1 * R);
-        const float Fs = Fi + Fj;
-        const float aF = L.A * Fi;
+        const float2 m1 = __fmul2_rn(make_float2(hb, D2), make_float2(vneg, R));
+        const float mu = m1.x * m1.y;  // (hbar v-) (D2 R)
+        const float2 m2 = __fmul2_rn(make_float2(mu, D1), make_float2(fmaf(A.beta, mu, -A.alpha * cb), R));
+        const float Ph = m2.x * m2.y;
+        const float Fs = F.x + F.y;
+        const float aF = L.A * F.x;
         const float mj = vm.w;
-        const float coef = mj * fmaf(Ph, Fs, fmaf(g.w, Fj, aF));
-        const float dcoef = (mj * vdotr) * fmaf(0.5f * Ph, Fs, aF);
-        P.ax.add(-coef * dx);
-        P.ay.add(-coef * dy);
-        P.az.add(-coef * dz);
-        P.du.add(dcoef);
+        const float ncoef = -mj * fmaf(Ph, Fs, fmaf(g.w, F.y, aF));  // -coef
+        const float2 m3 = __fmul2_rn(make_float2(mj, 0.5f), make_float2(vdotr, Ph));
+        const float dcoef = m3.x * fmaf(m3.y, Fs, aF);
+        P.axy.add(__fmul2_rn(make_float2(ncoef, ncoef), dxy));
+        P.azd.add(make_float2(ncoef * dz, dcoef));
     }
-    static __device__ __forceinline__ void merge2(float2 &a, const Kahan &p)
+    static __device__ __forceinline__ void merge2(float2 &a, float ps, float pc)
     {
         Kahan k;
         k.s = a.x;
         k.c = a.y;
-        k.merge(p.s, p.c);
+        k.merge(ps, pc);
         a.x = k.s;
         a.y = k.c;
     }
     static __device__ __forceinline__ void merge_part(Acc &a, const Part &P)
     {
-        merge2(a.ax, P.ax);
-        merge2(a.ay, P.ay);
-        merge2(a.az, P.az);
-        merge2(a.du, P.du);
+        merge2(a.ax, P.axy.s.x, P.axy.c.x);
+        merge2(a.ay, P.axy.s.y, P.axy.c.y);
+        merge2(a.az, P.azd.s.x, P.azd.c.x);
+        merge2(a.du, P.azd.s.y, P.azd.c.y);
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
