@@ -111,7 +111,8 @@ struct Scratch {
     float *xf, *yf, *zf;  // FP64 views: cell-relative float copies of the positions (input of the FP32 filter)
     float *hf;            // FP64 views: (float) h, rounded up (filter radius)
     // Per-particle values of the pair loops, in the view's precision.
-    //   FP64 density: d[0..4] the cubic-in-r spline coefficients -3/(2h^2), 3/(4h^3), -3/h, 3/(2h^2), -1/(4h^3)
+    //   FP64 density: d[0..4] the cubic-in-r spline coefficients -3/(2h^2), 3/(4h^3), -3/h, 3/(2h^2), -1/(4h^3),
+    //         d[5] 1/(pi h^3), d[6] c_s = sqrt(gamma (gamma - 1) u)
     //   FP64 force: d[0] h/2, d[1] -3/(pi h^4), d[2] 3/(pi h^5), d[3] 9/(4 pi h^6), d[4] -3/(4 pi h^6), d[5] P/rho^2,
     //         d[6] alpha c / 2
     //   FP32: d[0] 1/h, d[1] 1/(pi h^5), d[2] P/rho^2
@@ -151,7 +152,7 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
 // Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h) and coefficient
 // tables; FP32 force: 1/h, 1/(pi h^5), P/rho^2).
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &cs, cudaStream_t st, int *nl);
+                                const CellSpace &cs, double gamma, cudaStream_t st, int *nl);
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
                               const CellSpace &cs, double alpha, cudaStream_t st, int *nl);
 

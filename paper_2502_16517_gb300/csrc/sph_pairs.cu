@@ -255,6 +255,17 @@ __device__ __forceinline__ double rsqrt_seeded(double x)
     return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
+// sqrt(x), x >= 0, from the same FP32 seed y0 of 1/sqrt(x): g = x y0 and e = 1 - g y0 give
+// sqrt(x) = g (1 - e)^(-1/2) = g (1 + e/2 + 3e^2/8 + ...), truncated after e^2 (remainder ~(5/16) e0^3, below FP64
+// rounding): five FP64 operations, one fewer than x * rsqrt_seeded(x).  x = 0 gives 0 (g = 0).
+__device__ __forceinline__ double sqrt_seeded(double x)
+{
+    const double y = flt_to_dbl_bits(rsqrt_ftz(dbl_to_flt_bits(x)));
+    const double g = x * y;
+    const double e = fma(-g, y, 1.0);
+    return fma(g * e, fma(0.375, e, 0.5), g);
+}
+
 // 1/x, x > 0 within the float range: FP32 seed y0, then 1/x = y0 / (1 - e) = y0 (1 + e + e^2 ...) with
 // e = 1 - x y0, truncated after e^2 (remainder ~e0^3, below FP64 rounding): three FMAs.
 __device__ __forceinline__ double rcp_seeded(double x)
@@ -287,7 +298,7 @@ struct PairCommon {
 };
 
 // ---- density, FP64 ----
-// Per pair: r from one reciprocal square root, the piece of the spline chosen by integer compares of the bit
+// Per pair: r from one seeded square root, the piece of the spline chosen by integer compares of the bit
 // patterns of r against h_i and 2 h_i, and f evaluated as a cubic in r whose coefficients d_k h_i^-k come from
 // the per-particle set-up kernel.
 struct DensF64 {
@@ -298,6 +309,7 @@ struct DensF64 {
         PairCommon cm;
         const double *f[NF];                   // x, y, z, h and (k_density_prep_f64) e2 .. o3
         const double *m, *u;
+        const double *rk, *cs0;                // per particle (k_density_prep_f64): 1/(pi h^3), c_s
         const float *xf, *yf, *zf;             // cell-relative float positions (filter only)
         double *rho, *P, *cs;
         double gamma;
@@ -413,7 +425,7 @@ struct DensF64 {
         const double *s = L.s;
         const double dx = lds(s + X) - T.x[k], dy = lds(s + Y) - T.y[k], dz = lds(s + Z) - T.z[k];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const double r = r2 * rsqrt_seeded(r2);
+        const double r = sqrt_seeded(r2);
         const long long rb = __double_as_longlong(r);
         // bit patterns of h and 2 h: for r >= 0, r < h exactly when bits(r) < bits(h)
         const long long hb1 = __double_as_longlong(lds(s + H)), hb2 = hb1 + (1LL << 52);
@@ -429,10 +441,9 @@ struct DensF64 {
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
         const double h = A.f[H][i];
-        const double hinv = 1.0 / h;
-        const double rho = a * (kInvPi * hinv * hinv * hinv);
+        const double rho = a * A.rk[i];
         const double P = (A.gamma - 1.0) * rho * A.u[i];
-        const double cs = sqrt(A.gamma * P / rho);
+        const double cs = A.cs0[i];
         A.rho[i] = rho;
         A.P[i] = P;
         A.cs[i] = cs;
@@ -1387,7 +1398,8 @@ __global__ void k_density_prep_f64(const double *__restrict__ x, const double *_
                                    const int *__restrict__ cell_of_slot, int n, CellSpace cs, float *__restrict__ xf,
                                    float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2,
                                    double *__restrict__ e3, double *__restrict__ o1, double *__restrict__ o2,
-                                   double *__restrict__ o3)
+                                   double *__restrict__ o3, const double *__restrict__ u, double gamma,
+                                   double *__restrict__ rk, double *__restrict__ cs0)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -1398,6 +1410,11 @@ __global__ void k_density_prep_f64(const double *__restrict__ x, const double *_
     o1[s] = -3.0 * hi;
     o2[s] = 1.5 * h2;
     o3[s] = -0.25 * h3;
+    // the density's normalisation 1/(pi h^3), and the sound speed of the ideal-gas EOS: with P = (gamma - 1) rho u,
+    // c_s = sqrt(gamma P / rho) = sqrt(gamma (gamma - 1) u), which needs no density (so the pair kernel's per-particle
+    // epilogue, run by few lanes of a warp, has no division or square root left)
+    rk[s] = kInvPi * h3;
+    cs0[s] = sqrt(gamma * (gamma - 1.0) * u[s]);
 }
 
 // Per-particle quantities of the FP32 force loop: 1/h, 3/(pi h^4), P/rho^2.
@@ -1522,13 +1539,14 @@ int tile_or_default(int tj, int dflt)
 }  // namespace
 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &g, cudaStream_t st, int *nl)
+                                const CellSpace &g, double gamma, cudaStream_t st, int *nl)
 {
     if (n <= 0 || f32) return cudaSuccess;  // FP32 views are already cell-relative floats
     k_density_prep_f64<<<(n + 255) / 256, 256, 0, st>>>(
         (const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1], (const double *)soa.p[SPH_X][2],
         (const double *)soa.p[SPH_H][0], cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, (double *)scr.d[0],
-        (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3], (double *)scr.d[4]);
+        (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3], (double *)scr.d[4],
+        (const double *)soa.p[SPH_U][0], gamma, (double *)scr.d[5], (double *)scr.d[6]);
     ++*nl;
     return cudaGetLastError();
 }
@@ -1581,6 +1599,8 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
         A.f[D::O3] = (const double *)scr.d[4];
         A.m = (const double *)soa.p[SPH_MASS][0];
         A.u = (const double *)soa.p[SPH_U][0];
+        A.rk = (const double *)scr.d[5];
+        A.cs0 = (const double *)scr.d[6];
         A.xf = scr.xf;
         A.yf = scr.yf;
         A.zf = scr.zf;
