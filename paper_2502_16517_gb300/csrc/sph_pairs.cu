@@ -35,6 +35,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "sph_internal.cuh"
 
@@ -51,7 +52,7 @@ constexpr float kFar = 1e30f;  // sentinel coordinate: its squared distance over
 
 struct NbrTable {
     int start[27];
-    int pref[28];
+    int pref[32];  // prefix counts pref[0..27]; pref[28..31] = INT_MAX (sentinels of find_nbr's search)
     double shift[27][3];  // added to x_i - x_j for a j of neighbour q (0 or +-box)
     float offf[27][3];    // origin of neighbour cell q relative to the local cell origin: (float)(d * edge)
     int wrap;             // any shift != 0
@@ -112,6 +113,7 @@ __device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellS
             if (tid >= o) incl += up;
         }
         if (tid < 27) nb.pref[tid + 1] = incl;
+        else if (tid < 31) nb.pref[tid + 1] = INT_MAX;
         const bool any_wrap = __any_sync(kFull, wr && cnt > 0);
         if (tid == 0) {
             nb.pref[0] = 0;
@@ -127,15 +129,15 @@ __device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellS
     __syncthreads();
 }
 
-// Neighbour index q with pref[q] <= jj < pref[q+1] (empty neighbours have pref[q] == pref[q+1]).
+// Neighbour index q with pref[q] <= jj < pref[q+1] for 0 <= jj < pref[27] (empty neighbours have pref[q] ==
+// pref[q+1]): the largest q with pref[q] <= jj, found by five fixed, branch-free halving steps over pref[0..31].
 __device__ __forceinline__ int find_nbr(const NbrTable &nb, int jj)
 {
-    int lo = 0, hi = 27;  // invariant: pref[lo] <= jj < pref[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (nb.pref[mid] <= jj) lo = mid; else hi = mid;
-    }
-    return lo;
+    int q = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (nb.pref[q + step] <= jj) q += step;
+    return q;
 }
 
 template <typename T>
