@@ -71,6 +71,15 @@ def _load():
                 "or_kick": (None, [i64, dbl, _D, _D, _D, _D]),
                 "or_drift": (None, [i64, dbl, _D, _D, ctypes.c_int, _D]),
                 "or_h_iterate": (i64, [i64, _D, _D, _D, _D, ctypes.c_int, dbl, dbl, i32, _D, _I32]),
+                "or_kappa": (dbl, [ctypes.c_int]),
+                "or_kw": (dbl, [ctypes.c_int, dbl, dbl]),
+                "or_kdwdr": (dbl, [ctypes.c_int, dbl, dbl]),
+                "or_kdwdh": (dbl, [ctypes.c_int, dbl, dbl]),
+                "or_kernel_array": (None, [ctypes.c_int, ctypes.c_int, i64, _D, _D, _D]),
+                "or_density_ext": (None, [ctypes.c_int, i64, _D, _D, _D, _D, _D, ctypes.c_int, i64, _I64, _D, _D,
+                                          _D, _D, _D]),
+                "or_force_ext": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, _D, _D, _D, _D, _D, _D,
+                                        _D, _D, _D, _D, _D, ctypes.c_int, dbl, dbl, dbl, i64, _I64, _D, _D, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -146,6 +155,60 @@ def force(x, v, m, h, rho, P, cs, box, periodic=True, alpha=1.0, beta=2.0, eps=0
                      _p(box, _D), int(bool(periodic)), float(alpha), float(beta), float(eps), tg.size,
                      _p(tg, _I64), _p(a, _D), _p(du, _D))
     return a, du
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Kernel families (M4 cubic, M5 quartic: the paper's kernel, Section 2.1) and the fuller density / force views
+# (Section 2.1, Table 1).
+# ----------------------------------------------------------------------------------------------------------
+KERNEL_M4, KERNEL_M5 = 0, 1
+SCHEME_MINIMAL, SCHEME_EXTENDED = 0, 1
+
+
+def kappa(kern):
+    """Support radius in units of h: 2 (M4), 5/2 (M5)."""
+    return float(_load().or_kappa(int(kern)))
+
+
+def kernel(kern, which, r, h):
+    """W (which 0), dW/dr (1) or dW/dh (2) of kernel family `kern`, elementwise."""
+    r, h = np.broadcast_arrays(np.asarray(r, np.float64), np.asarray(h, np.float64))
+    r, h = _c(r, np.float64).ravel(), _c(h, np.float64).ravel()
+    out = np.empty_like(r)
+    _load().or_kernel_array(int(kern), int(which), r.size, _p(r, _D), _p(h, _D), _p(out, _D))
+    return out
+
+
+def density_ext(kern, x, v, m, h, box, periodic=True, targets=None):
+    """The fuller density view of the targets: dict rho, omega, nnb, divv, curlv ([nt, 3])."""
+    x, v, m, h = (_c(q, np.float64) for q in (x, v, m, h))
+    box = _c(box, np.float64)
+    n = m.size
+    tg = np.arange(n, dtype=np.int64) if targets is None else _c(targets, np.int64)
+    rho, om, nnb, dv = (np.empty(tg.size, np.float64) for _ in range(4))
+    curl = np.empty((tg.size, 3), np.float64)
+    _load().or_density_ext(int(kern), n, _p(x, _D), _p(v, _D), _p(m, _D), _p(h, _D), _p(box, _D),
+                           int(bool(periodic)), tg.size, _p(tg, _I64), _p(rho, _D), _p(om, _D), _p(nnb, _D),
+                           _p(dv, _D), _p(curl, _D))
+    return {"rho": rho, "omega": om, "nnb": nnb, "divv": dv, "curlv": curl}
+
+
+def force_ext(kern, use_gradh, use_balsara, x, v, m, h, rho, P, cs, omega, divv, curlv, box, periodic=True,
+              alpha=1.0, beta=2.0, eps=0.01, targets=None):
+    """(a_i, du_i/dt, vsig_i) of the fuller force view for the targets, brute force over all j."""
+    x, v, curlv = _c(x, np.float64), _c(v, np.float64), _c(curlv, np.float64)
+    m, h, rho, P, cs, omega, divv = (_c(q, np.float64) for q in (m, h, rho, P, cs, omega, divv))
+    box = _c(box, np.float64)
+    n = m.size
+    tg = np.arange(n, dtype=np.int64) if targets is None else _c(targets, np.int64)
+    a = np.empty((tg.size, 3), np.float64)
+    du = np.empty(tg.size, np.float64)
+    vs = np.empty(tg.size, np.float64)
+    _load().or_force_ext(int(kern), int(bool(use_gradh)), int(bool(use_balsara)), n, _p(x, _D), _p(v, _D),
+                         _p(m, _D), _p(h, _D), _p(rho, _D), _p(P, _D), _p(cs, _D), _p(omega, _D), _p(divv, _D),
+                         _p(curlv, _D), _p(box, _D), int(bool(periodic)), float(alpha), float(beta), float(eps),
+                         tg.size, _p(tg, _I64), _p(a, _D), _p(du, _D), _p(vs, _D))
+    return a, du, vs
 
 
 def neighbours(x, h, box, i, periodic=True, rad_factor=2.0):
@@ -331,6 +394,9 @@ def drift(dt, v, x, box, periodic=True):
 # ----------------------------------------------------------------------------------------------------------
 # Whole passes on AoS bytes (the composition f = W o C o f^ o C o N of Eq. 5, evaluated by the definition).
 # ----------------------------------------------------------------------------------------------------------
+VECTOR_FIELDS = ("x", "v", "a", "curlv")
+
+
 def unpack(aos, layout):
     """All physics fields of an AoS buffer in record order: dict name -> array ([n,3] for vectors)."""
     aos = _c(aos, np.uint8)
@@ -339,7 +405,7 @@ def unpack(aos, layout):
     ident = np.arange(n, dtype=np.int32)
     out = {}
     for name, off in layout["offsets"].items():
-        nc = 3 if name in ("x", "v", "a") else 1
+        nc = 3 if name in VECTOR_FIELDS else 1
         g = gather(aos, stride, ident, off, nc)
         out[name] = g.T.copy() if nc == 3 else g[0].copy()
     return out
@@ -393,3 +459,52 @@ def step_sampled(aos, layout, box, params, targets, periodic=True):
     a, du = force(x, f["v"], f["mass"], h, rho, P, cs, box, periodic, params["alpha"], params["beta"],
                   params["eps"], targets)
     return {"rho": rho[targets], "P": P[targets], "cs": cs[targets], "a": a, "dudt": du}
+
+
+def _scheme_of(params):
+    return int(params.get("kernel", KERNEL_M4)), int(params.get("scheme", SCHEME_MINIMAL))
+
+
+def step_all_ext(aos, layout, box, params, periodic=True):
+    """Expected results of one density + force pass with the kernel family and scheme of `params` ("kernel",
+    "scheme"): dict rho, P, cs, a, dudt, and for the extended scheme also nnb, divv, curlv, omega, vsig."""
+    kern, scheme = _scheme_of(params)
+    f = unpack(aos, layout)
+    d = density_ext(kern, f["x"], f["v"], f["mass"], f["h"], box, periodic)
+    P, cs = eos(d["rho"], f["u"], params["gamma"])
+    ext = scheme == SCHEME_EXTENDED
+    a, du, vs = force_ext(kern, ext, ext, f["x"], f["v"], f["mass"], f["h"], d["rho"], P, cs, d["omega"],
+                          d["divv"], d["curlv"], box, periodic, params["alpha"], params["beta"], params["eps"])
+    out = {"rho": d["rho"], "P": P, "cs": cs, "a": a, "dudt": du}
+    if ext:
+        out.update(nnb=d["nnb"], divv=d["divv"], curlv=d["curlv"], omega=d["omega"], vsig=vs)
+    return out
+
+
+def step_sampled_ext(aos, layout, box, params, targets, periodic=True):
+    """step_all_ext for sampled records of a large state, one by one: the force of i needs the density-view
+    outputs of every j within kappa max(h_i, h_j), computed here by brute force as well."""
+    kern, scheme = _scheme_of(params)
+    f = unpack(aos, layout)
+    x, h = f["x"], f["h"]
+    targets = np.asarray(targets, np.int64)
+    need = set(int(t) for t in targets)
+    for t in targets:
+        need.update(int(j) for j in neighbours(x, h, box, int(t), periodic, kappa(kern)))
+    need = np.array(sorted(need), np.int64)
+    n = h.size
+    d = density_ext(kern, x, f["v"], f["mass"], h, box, periodic, need)
+    full = {k: np.full((n, 3) if k == "curlv" else n, np.nan) for k in d}
+    for k, val in d.items():
+        full[k][need] = val
+    P = np.full(n, np.nan)
+    cs = np.full(n, np.nan)
+    P[need], cs[need] = eos(full["rho"][need], f["u"][need], params["gamma"])
+    ext = scheme == SCHEME_EXTENDED
+    a, du, vs = force_ext(kern, ext, ext, x, f["v"], f["mass"], h, full["rho"], P, cs, full["omega"], full["divv"],
+                          full["curlv"], box, periodic, params["alpha"], params["beta"], params["eps"], targets)
+    out = {"rho": full["rho"][targets], "P": P[targets], "cs": cs[targets], "a": a, "dudt": du}
+    if ext:
+        out.update(nnb=full["nnb"][targets], divv=full["divv"][targets], curlv=full["curlv"][targets],
+                   omega=full["omega"][targets], vsig=vs)
+    return out

@@ -20,6 +20,10 @@
  *   - the leapfrog kick-drift-kick of Section 2.1 (steps 3-5); or_kick / or_drift.
  *   - the smoothing-length iteration of Section 2.1 step 1 (density, grow or shrink h, repeat until every
  *     particle meets its termination test); or_h_iterate.
+ *   - the paper's own kernel, the quartic spline M5 (Section 2.1), next to the cubic spline; and the fuller
+ *     density and force views its Section 2.1 and Table 1 describe (neighbour count, velocity divergence and
+ *     rotation, the smoothing-length derivative terms): or_kw / or_kdwdr / or_kdwdh, or_density_ext,
+ *     or_force_ext.  The paper prints none of these formulas; the textbook forms used are named there.
  *
  * Compile with -ffp-contract=off: every product and sum below is rounded on its own, exactly as written.
  */
@@ -508,4 +512,200 @@ int64_t or_h_iterate(int64_t n, const double *x, const double *m, double *h, con
     free(rho_t);
     free(h_new);
     return undone;
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Kernel families (3D).  W(r, h) = sigma f(q) / h^3 with q = r / h and support q < kappa, written as sums of
+ * truncated powers (t)_+ = max(t, 0):
+ *   kern 0, cubic spline M4 (Monaghan & Lattanzio 1985): kappa = 2, sigma = 1/pi,
+ *     f(q) = 1/4 (2 - q)_+^3 - (1 - q)_+^3          (= 1 - 3/2 q^2 + 3/4 q^3 for q < 1, 1/4 (2 - q)^3 for q < 2);
+ *   kern 1, quartic spline M5 (Monaghan 1985; the paper's kernel, Section 2.1): kappa = 5/2, sigma = 1/(20 pi),
+ *     f(q) = (5/2 - q)_+^4 - 5 (3/2 - q)_+^4 + 10 (1/2 - q)_+^4.
+ * Derivatives: dW/dr = sigma f'(q) / h^4, and dW/dh = -sigma (3 f(q) + q f'(q)) / h^4 (d/dh of h^-3 f(r/h)).
+ * ------------------------------------------------------------------------------------------------------- */
+static double or_pos(double t) { return t > 0.0 ? t : 0.0; }
+
+double or_kappa(int kern) { return kern == 1 ? 2.5 : 2.0; }
+
+static double or_ksigma(int kern) { return kern == 1 ? 1.0 / (20.0 * OR_PI) : 1.0 / OR_PI; }
+
+static double or_kf(int kern, double q)
+{
+    if (kern == 1) {
+        double a = or_pos(2.5 - q), b = or_pos(1.5 - q), c = or_pos(0.5 - q);
+        return a * a * a * a - 5.0 * (b * b * b * b) + 10.0 * (c * c * c * c);
+    }
+    double a = or_pos(2.0 - q), b = or_pos(1.0 - q);
+    return 0.25 * (a * a * a) - b * b * b;
+}
+
+static double or_kfp(int kern, double q)
+{
+    if (kern == 1) {
+        double a = or_pos(2.5 - q), b = or_pos(1.5 - q), c = or_pos(0.5 - q);
+        return -4.0 * (a * a * a) + 20.0 * (b * b * b) - 40.0 * (c * c * c);
+    }
+    double a = or_pos(2.0 - q), b = or_pos(1.0 - q);
+    return -0.75 * (a * a) + 3.0 * (b * b);
+}
+
+double or_kw(int kern, double r, double h)
+{
+    double q = r / h;
+    return or_ksigma(kern) * or_kf(kern, q) / (h * h * h);
+}
+
+double or_kdwdr(int kern, double r, double h)
+{
+    double q = r / h;
+    return or_ksigma(kern) * or_kfp(kern, q) / (h * h * h * h);
+}
+
+double or_kdwdh(int kern, double r, double h)
+{
+    double q = r / h;
+    return -or_ksigma(kern) * (3.0 * or_kf(kern, q) + q * or_kfp(kern, q)) / (h * h * h * h);
+}
+
+/* which: 0 W, 1 dW/dr, 2 dW/dh, elementwise */
+void or_kernel_array(int kern, int which, int64_t n, const double *r, const double *h, double *out)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        if (which == 0) out[k] = or_kw(kern, r[k], h[k]);
+        else if (which == 1) out[k] = or_kdwdr(kern, r[k], h[k]);
+        else out[k] = or_kdwdh(kern, r[k], h[k]);
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * The fuller density view (Section 2.1 step 1 "the neighbour count, the rotational velocity vector, and
+ * various derivative properties"; Table 1's larger density sets).  For each target i, over every j with
+ * |r_ij| < kappa h_i (self included where it contributes):
+ *   rho_i         = sum_j m_j W(r_ij, h_i)
+ *   drho_i/dh_i   = sum_j m_j dW/dh(r_ij, h_i)
+ *   Omega_i       = 1 + h_i / (3 rho_i) drho_i/dh_i   (the grad-h term of Springel & Hernquist 2002 / Price 2012
+ *                                                       in 3D, where h ~ rho^(-1/3))
+ *   n_i           = number of j != i with |r_ij| < kappa h_i
+ *   (div v)_i     = -1/rho_i sum_j m_j v_ij . grad_i W(r_ij, h_i)
+ *   (curl v)_i    =  1/rho_i sum_j m_j v_ij x grad_i W(r_ij, h_i)
+ * with v_ij = v_i - v_j and grad_i W(r_ij, h) = dW/dr(r, h) r_ij / r (no contribution at r = 0).  On a uniform
+ * lattice the two velocity estimates return 3c for v = c x and 2 w for v = w x x.  curl_out is nt x 3.
+ * ------------------------------------------------------------------------------------------------------- */
+void or_density_ext(int kern, int64_t n, const double *x, const double *v, const double *m, const double *h,
+                    const double *box, int periodic, int64_t nt, const int64_t *targets, double *rho_out,
+                    double *omega_out, double *nnb_out, double *divv_out, double *curl_out)
+{
+    double kap = or_kappa(kern);
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets[t];
+        double rho = 0.0, drho = 0.0, cnt = 0.0, dv = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double dx = or_min_image(x[3 * i + 0] - x[3 * j + 0], box[0], periodic);
+            double dy = or_min_image(x[3 * i + 1] - x[3 * j + 1], box[1], periodic);
+            double dz = or_min_image(x[3 * i + 2] - x[3 * j + 2], box[2], periodic);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (!(r < kap * h[i])) continue;
+            rho += m[j] * or_kw(kern, r, h[i]);
+            drho += m[j] * or_kdwdh(kern, r, h[i]);
+            if (j != i) cnt += 1.0;
+            if (r > 0.0) {
+                double g = or_kdwdr(kern, r, h[i]) / r; /* grad_i W = g r_ij */
+                double vx = v[3 * i + 0] - v[3 * j + 0];
+                double vy = v[3 * i + 1] - v[3 * j + 1];
+                double vz = v[3 * i + 2] - v[3 * j + 2];
+                dv += m[j] * g * (vx * dx + vy * dy + vz * dz);
+                cx += m[j] * g * (vy * dz - vz * dy);
+                cy += m[j] * g * (vz * dx - vx * dz);
+                cz += m[j] * g * (vx * dy - vy * dx);
+            }
+        }
+        rho_out[t] = rho;
+        omega_out[t] = 1.0 + h[i] / (3.0 * rho) * drho;
+        nnb_out[t] = cnt;
+        divv_out[t] = -dv / rho;
+        curl_out[3 * t + 0] = cx / rho;
+        curl_out[3 * t + 1] = cy / rho;
+        curl_out[3 * t + 2] = cz / rho;
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * The fuller force view (Table 1's larger force sets: the density-loop outputs feed the force).  As or_force,
+ * with the kernel family `kern`, the support kappa max(h_i, h_j), and two switchable terms:
+ *   use_gradh:   P_k / rho_k^2 becomes P_k / (Omega_k rho_k^2) (the grad-h formulation, Price 2012);
+ *   use_balsara: Pi_ij is multiplied by (B_i + B_j) / 2 with the Balsara (1995) switch
+ *                B_k = |div v_k| / (|div v_k| + |curl v_k| + 1e-4 c_k / h_k), as in Gadget-2 (Springel 2005).
+ * Also the signal velocity vsig_i = max_j (c_i + c_j - 3 min(v_ij . r_ij / r, 0)) over the same pairs (a
+ * coincident pair counts c_i + c_j), 0 without neighbours.  With kern 0 and both switches off the sums are
+ * or_force's (up to the rounding of the kernel's truncated-power form).
+ * ------------------------------------------------------------------------------------------------------- */
+void or_force_ext(int kern, int use_gradh, int use_balsara, int64_t n, const double *x, const double *v,
+                  const double *m, const double *h, const double *rho, const double *P, const double *cs,
+                  const double *omega, const double *divv, const double *curl, const double *box, int periodic,
+                  double alpha, double beta, double eps, int64_t nt, const int64_t *targets, double *a_out,
+                  double *dudt_out, double *vsig_out)
+{
+    double kap = or_kappa(kern);
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets[t];
+        double ax = 0.0, ay = 0.0, az = 0.0, du = 0.0, vsig = 0.0;
+        double Bi = 1.0;
+        if (use_balsara) {
+            double ci = sqrt(curl[3 * i] * curl[3 * i] + curl[3 * i + 1] * curl[3 * i + 1] +
+                             curl[3 * i + 2] * curl[3 * i + 2]);
+            Bi = fabs(divv[i]) / (fabs(divv[i]) + ci + 1e-4 * cs[i] / h[i]);
+        }
+        double Oi = use_gradh ? omega[i] : 1.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = or_min_image(x[3 * i + 0] - x[3 * j + 0], box[0], periodic);
+            double dy = or_min_image(x[3 * i + 1] - x[3 * j + 1], box[1], periodic);
+            double dz = or_min_image(x[3 * i + 2] - x[3 * j + 2], box[2], periodic);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double hmax = h[i] > h[j] ? h[i] : h[j];
+            if (!(r < kap * hmax)) continue;
+            if (r == 0.0) {
+                double vs0 = cs[i] + cs[j];
+                if (vs0 > vsig) vsig = vs0;
+                continue;
+            }
+            double gi = or_kdwdr(kern, r, h[i]) / r;
+            double gj = or_kdwdr(kern, r, h[j]) / r;
+            double gbar = 0.5 * (gi + gj);
+            double vx = v[3 * i + 0] - v[3 * j + 0];
+            double vy = v[3 * i + 1] - v[3 * j + 1];
+            double vz = v[3 * i + 2] - v[3 * j + 2];
+            double vdotr = vx * dx + vy * dy + vz * dz;
+            double wij = vdotr / r;
+            double vs = cs[i] + cs[j] - 3.0 * (wij < 0.0 ? wij : 0.0);
+            if (vs > vsig) vsig = vs;
+            double visc = 0.0;
+            if (vdotr < 0.0) {
+                double hbar = 0.5 * (h[i] + h[j]);
+                double mu = hbar * vdotr / (r * r + eps * hbar * hbar);
+                double cbar = 0.5 * (cs[i] + cs[j]);
+                double rhobar = 0.5 * (rho[i] + rho[j]);
+                visc = (-alpha * cbar * mu + beta * mu * mu) / rhobar;
+                if (use_balsara) {
+                    double cj = sqrt(curl[3 * j] * curl[3 * j] + curl[3 * j + 1] * curl[3 * j + 1] +
+                                     curl[3 * j + 2] * curl[3 * j + 2]);
+                    double Bj = fabs(divv[j]) / (fabs(divv[j]) + cj + 1e-4 * cs[j] / h[j]);
+                    visc = visc * (0.5 * (Bi + Bj));
+                }
+            }
+            double Oj = use_gradh ? omega[j] : 1.0;
+            double Ai = P[i] / (Oi * rho[i] * rho[i]); /* Oi = 1: exactly P / (rho rho) */
+            double Aj = P[j] / (Oj * rho[j] * rho[j]);
+            double coef = m[j] * (Ai * gi + Aj * gj + visc * gbar);
+            ax -= coef * dx;
+            ay -= coef * dy;
+            az -= coef * dz;
+            du += m[j] * (Ai * gi * vdotr + 0.5 * visc * gbar * vdotr);
+        }
+        a_out[3 * t + 0] = ax;
+        a_out[3 * t + 1] = ay;
+        a_out[3 * t + 2] = az;
+        dudt_out[t] = du;
+        vsig_out[t] = vsig;
+    }
 }
