@@ -120,10 +120,12 @@ def _inputs():
     return f, lay, aos_h, ncell
 
 
-def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None, union=True):
+def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None, union=True,
+             params=None, tune_form="grid"):
     import torch
     from paper_2502_16517_gb300 import autotune, sph
     from paper_2502_16517_gb300 import workloads as wl
+    params = params or wl.SPH_PARAMS
     n = aos_h.shape[0]
     aos = torch.from_numpy(aos_h).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -134,11 +136,11 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
     tiles = None
     try:
         if tune_cache:
-            key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, "grid", n / float(np.prod(ncell)))
-            tiles = autotune.tuned_tiles(view, aos, n, wl.SPH_PARAMS, key, tune_cache)
+            key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, tune_form, n / float(np.prod(ncell)))
+            tiles = autotune.tuned_tiles(view, aos, n, params, key, tune_cache)
         for _ in range(max(warmup, 0)):
             flush.zero_()
-            sph.sph_step(view, aos, n, wl.SPH_PARAMS)
+            sph.sph_step(view, aos, n, params)
         sph.sph_view_sync(view)
         sph.sph_pair_counts(view, reset=True)
         sph.sph_view_timing(view, True)
@@ -155,7 +157,7 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
             for k in range(steps):
                 flush.zero_()
                 ev[k][0].record(stream)
-                sph.sph_step(view, aos, n, wl.SPH_PARAMS)
+                sph.sph_step(view, aos, n, params)
                 ev[k][1].record(stream)
             torch.cuda.synchronize(dev)
         finally:
@@ -175,6 +177,21 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
         "step_ms": step_ms, "wall_s": wall, "counts": counts, "phase_ms": phase_ms, "launches": launches,
         "clocks": sampler.summary() if sampler else None, "tiles": tiles, "union": union,
     }
+
+
+EXT_PARAMS_NOTE = ("quartic spline M5 (support 5h/2, the paper's kernel) with the fuller views: the density also "
+                   "writes the neighbour count, div v, curl v and Omega; the force uses grad-h terms and the Balsara "
+                   "switch and writes the signal velocity")
+
+
+def extended_inputs():
+    """The plain 262,144-particle input on the paper's 272-byte record with the fuller views' members, cells of
+    edge >= 5h/2 for the quartic spline."""
+    from paper_2502_16517_gb300 import workloads as wl
+    f = wl.plain()
+    lay = wl.extended_layout()
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled", canary=False)
+    return lay, aos_h, wl.ncell_for(f["box"], f["h"].max(), 2.5)
 
 
 def batched_inputs():
@@ -560,10 +577,18 @@ def main():
             runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
                                   tune_cache=tune_cache)
         per_loop = None
+        ext = None
         if args.only is None:
             # the paper's conversion pattern: one view per loop, converted forth and back around each
             per_loop = run_form(0, steps, warmup, dev, aos_h, lay, f["box"], ncell, tune_cache=tune_cache,
                                 union=False)
+            # the paper's kernel and fuller views on its 272-byte record
+            from paper_2502_16517_gb300 import workloads as wl
+            lay_e, aos_e, ncell_e = extended_inputs()
+            ext = run_form(0, steps, warmup, dev, aos_e, lay_e, f["box"], ncell_e, tune_cache=tune_cache,
+                           params=dict(wl.SPH_PARAMS, kernel=1, scheme=1), tune_form="grid_m5_extended")
+            ext["cells"] = int(np.prod(ncell_e))
+            del aos_e
         batched = {}
         if args.batched and args.only is None:
             fp, lay_b, aos_b = batched_inputs()
@@ -668,6 +693,16 @@ def main():
             "value": sp["value"], "ms_per_step": sp["ms_per_step"], "dtype": "f64",
             "phases_ms_per_step": sp["phases_ms_per_step"], "conversion": sp["conversion"],
             "gpu_launches": int(sum(sp["launches"].values()))}
+    if ext is not None:
+        ext["step_ms"] = list(ext["step_ms"])
+        se = summarize_form(0, ext, n, steps, world)
+        line["forms"]["extended_m5_f64"] = {
+            "workload": ("the plain 262,144-particle input on the paper's 272-byte record, " + EXT_PARAMS_NOTE +
+                         f"; {ext['cells']} periodic cells (edge >= 5h/2)"),
+            "value": se["value"], "ms_per_step": se["ms_per_step"], "dtype": "f64",
+            "pairs_per_step": (ext["counts"][1] + ext["counts"][2]) / steps,
+            "phases_ms_per_step": se["phases_ms_per_step"], "gpu_launches": int(sum(se["launches"].values())),
+            "tiles": ext["tiles"]}
     for form, b in large.items():
         b = dict(b)
         b["workload"] = ("large run: 2,097,152 particles, 8 Gaussian overdensities (sigma 0.05, 4x) on a uniform "

@@ -59,11 +59,18 @@ typedef enum sph_prec {
                     Kahan-compensated sums, FP64 global reductions                                          */
 } sph_prec;
 
-/* Particle members known to the library, in the order of sph_layout.off[].  x, v and a are three contiguous
- * doubles; every other member is one double.  All members are IEEE binary64 in the records. */
+/* Particle members known to the library, in the order of sph_layout.off[].  x, v, a and curl v are three
+ * contiguous doubles; every other member is one double.  All members are IEEE binary64 in the records.
+ * SPH_NNB .. SPH_VSIG are the members of the fuller views (SPH_SCHEME_EXTENDED; the neighbour count, the
+ * rotational velocity vector and the derivative properties of Section 2.1, Table 1's larger access sets):
+ *   SPH_NNB    neighbours within the support, the particle itself excluded (a count, stored as a double);
+ *   SPH_DIVV   velocity divergence  -1/rho_i sum_j m_j v_ij . grad_i W(r_ij, h_i);
+ *   SPH_CURLV  velocity curl         1/rho_i sum_j m_j v_ij x grad_i W(r_ij, h_i);
+ *   SPH_OMEGA  grad-h term           1 + h_i / (3 rho_i) sum_j m_j dW/dh(r_ij, h_i);
+ *   SPH_VSIG   signal velocity       max_j (c_i + c_j - 3 min(v_ij . r_ij / r_ij, 0)) over the force pairs. */
 enum {
     SPH_X = 0, SPH_V = 1, SPH_A = 2, SPH_MASS = 3, SPH_H = 4, SPH_RHO = 5, SPH_P = 6, SPH_U = 7, SPH_DUDT = 8,
-    SPH_CS = 9, SPH_NFIELDS = 10
+    SPH_CS = 9, SPH_NNB = 10, SPH_DIVV = 11, SPH_CURLV = 12, SPH_OMEGA = 13, SPH_VSIG = 14, SPH_NFIELDS = 15
 };
 #define SPH_BIT(f) (1u << (f))
 
@@ -74,6 +81,12 @@ enum {
     (SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_RHO) | SPH_BIT(SPH_P) | \
      SPH_BIT(SPH_CS))
 #define SPH_FORCE_OUT (SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT))
+/* The access sets of the fuller views (SPH_SCHEME_EXTENDED). */
+#define SPH_DENSITY_IN_EXT (SPH_DENSITY_IN | SPH_BIT(SPH_V))
+#define SPH_DENSITY_OUT_EXT \
+    (SPH_DENSITY_OUT | SPH_BIT(SPH_NNB) | SPH_BIT(SPH_DIVV) | SPH_BIT(SPH_CURLV) | SPH_BIT(SPH_OMEGA))
+#define SPH_FORCE_IN_EXT (SPH_FORCE_IN | SPH_BIT(SPH_OMEGA) | SPH_BIT(SPH_DIVV) | SPH_BIT(SPH_CURLV))
+#define SPH_FORCE_OUT_EXT (SPH_FORCE_OUT | SPH_BIT(SPH_VSIG))
 #define SPH_ALL_FIELDS ((1u << SPH_NFIELDS) - 1u)
 
 /* Device status bits (sph_view_status). */
@@ -103,12 +116,31 @@ typedef struct sph_domain {
     int32_t periodic;
 } sph_domain;
 
-/* Physics constants: ideal gas gamma; Monaghan viscosity alpha, beta, eps. */
+/* Smoothing kernels, W(r, h) = sigma f(r/h) / h^3 with support kappa h:
+ *   SPH_KERNEL_M4  cubic spline (Monaghan & Lattanzio 1985), kappa = 2;
+ *   SPH_KERNEL_M5  quartic spline (Monaghan 1985), kappa = 5/2: the paper's kernel (Section 2.1). */
+typedef enum sph_kernel { SPH_KERNEL_M4 = 0, SPH_KERNEL_M5 = 1 } sph_kernel;
+
+/* Equation sets of the two loops:
+ *   SPH_SCHEME_MINIMAL   density: rho, P, c_s; force: a, du/dt with the Monaghan viscosity;
+ *   SPH_SCHEME_EXTENDED  the fuller views of Section 2.1 / Table 1: the density also writes the neighbour count,
+ *                        div v, curl v and Omega (access sets SPH_DENSITY_*_EXT); the force uses
+ *                        P / (Omega rho^2) (grad-h terms), scales the viscosity by the pair mean of the Balsara
+ *                        switch |div v| / (|div v| + |curl v| + 1e-4 c / h), and writes the signal velocity
+ *                        (SPH_FORCE_*_EXT). */
+typedef enum sph_scheme { SPH_SCHEME_MINIMAL = 0, SPH_SCHEME_EXTENDED = 1 } sph_scheme;
+
+/* Physics constants: ideal gas gamma; Monaghan viscosity alpha, beta, eps; the kernel and the equation set
+ * (zero: the cubic spline and the minimal set).  Any kernel or scheme other than (M4, minimal) needs an FP64
+ * single-grid view (SPH_E_INVAL otherwise), cell edges of at least kappa h, and, for the extended scheme, the
+ * members of its access sets in the layout. */
 typedef struct sph_params {
     double gamma;
     double alpha;
     double beta;
     double eps;
+    int32_t kernel; /* sph_kernel */
+    int32_t scheme; /* sph_scheme */
 } sph_params;
 
 typedef struct sph_view_s *sph_view;

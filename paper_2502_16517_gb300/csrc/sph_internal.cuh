@@ -112,7 +112,10 @@ struct Scratch {
     float *hf;            // FP64 views: (float) h, rounded up (filter radius)
     // Per-particle values of the pair loops, in the view's precision.
     //   FP64 density: d[0..4] the cubic-in-r spline coefficients -3/(2h^2), 3/(4h^3), -3/h, 3/(2h^2), -1/(4h^3),
-    //         d[5] 1/(pi h^3), d[6] c_s = sqrt(gamma (gamma - 1) u)
+    //         d[5] 1/(pi h^3), d[6] c_s = sqrt(gamma (gamma - 1) u); other kernels / the extended scheme:
+    //         d[0] 1/h, d[1] sigma/h^3, d[2] sigma/h^4, d[6] c_s
+    //   FP64 force, other kernels / the extended scheme: d[0] h/2, d[1] 1/h, d[2] sigma/h^4, d[3] P/(Omega rho^2),
+    //         d[4] alpha c / 2, d[5] the Balsara switch
     //   FP64 force: d[0] h/2, d[1] -3/(pi h^4), d[2] 3/(pi h^5), d[3] 9/(4 pi h^6), d[4] -3/(4 pi h^6), d[5] P/rho^2,
     //         d[6] alpha c / 2
     //   FP32: d[0] 1/h, d[1] 1/(pi h^5), d[2] P/rho^2
@@ -152,9 +155,9 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
 // Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h) and coefficient
 // tables; FP32 force: 1/h, 1/(pi h^5), P/rho^2).
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &cs, double gamma, cudaStream_t st, int *nl);
+                                const CellSpace &cs, const sph_params &prm, cudaStream_t st, int *nl);
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const CellSpace &cs, double alpha, cudaStream_t st, int *nl);
+                              const CellSpace &cs, const sph_params &prm, cudaStream_t st, int *nl);
 
 // Pair-kernel launch shape: active particles staged per tile (0 = default of the path), and for patch views the
 // largest-first work list the persistent kernel pulls cells from.
@@ -175,7 +178,7 @@ cudaError_t launch_h_finish(const int *hstate, unsigned *status, cudaStream_t st
 
 // The pair kernels.
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                                 int ncells, int n, const CellSpace &cs, double gamma, const PairLaunch &pl,
+                                 int ncells, int n, const CellSpace &cs, const sph_params &prm, const PairLaunch &pl,
                                  unsigned *status, Counters *counters, cudaStream_t st, int *nl);
 cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
                                int ncells, int n, const CellSpace &cs, const sph_params &prm, const PairLaunch &pl,

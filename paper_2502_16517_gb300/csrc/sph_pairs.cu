@@ -803,6 +803,461 @@ struct ForceF64 {
     }
 };
 
+// ------------------------------------------------------------------------------------------------------------
+// Kernel families and the fuller views (FP64, single-grid views).  The two bodies below serve every
+// (kernel, scheme) pair except (cubic, minimal), which DensF64 / ForceF64 cover with the cubic's piece
+// coefficients.  Here the kernel is evaluated from q = r/h as a sum of truncated powers (t)_+ = max(t, 0):
+//   cubic M4 (support 2h, sigma 1/pi):         f = 1/4 (2 - q)_+^3 - (1 - q)_+^3
+//   quartic M5 (support 5h/2, sigma 1/(20 pi), the paper's kernel, Section 2.1):
+//                                              f = (5/2 - q)_+^4 - 5 (3/2 - q)_+^4 + 10 (1/2 - q)_+^4
+// W = sigma f / h^3, dW/dr = sigma f' / h^4 and dW/dh = -sigma (3 f + q f') / h^4: beyond the support every term
+// is zero, which is the masking of Section 5.6.
+// ------------------------------------------------------------------------------------------------------------
+struct KerM4 {
+    static constexpr double kappa = 2.0;
+    static constexpr float kappaf = 2.0f;
+    static constexpr double sigma = kInvPi;
+    static __device__ __forceinline__ void f_fp(double q, double &f, double &fp)
+    {
+        const double a = fmax(2.0 - q, 0.0), b = fmax(1.0 - q, 0.0);
+        const double a2 = a * a, b2 = b * b;
+        f = fma(0.25 * a2, a, -(b2 * b));
+        fp = fma(-0.75, a2, 3.0 * b2);
+    }
+    static __device__ __forceinline__ double fp_only(double q)
+    {
+        const double a = fmax(2.0 - q, 0.0), b = fmax(1.0 - q, 0.0);
+        return fma(-0.75, a * a, 3.0 * (b * b));
+    }
+};
+struct KerM5 {
+    static constexpr double kappa = 2.5;
+    static constexpr float kappaf = 2.5f;
+    static constexpr double sigma = kInvPi / 20.0;
+    static __device__ __forceinline__ void f_fp(double q, double &f, double &fp)
+    {
+        const double a = fmax(2.5 - q, 0.0), b = fmax(1.5 - q, 0.0), c = fmax(0.5 - q, 0.0);
+        const double a2 = a * a, b2 = b * b, c2 = c * c;
+        f = fma(10.0 * c2, c2, fma(-5.0 * b2, b2, a2 * a2));
+        fp = fma(-40.0 * c2, c, fma(20.0 * b2, b, -4.0 * (a2 * a)));
+    }
+    static __device__ __forceinline__ double fp_only(double q)
+    {
+        const double a = fmax(2.5 - q, 0.0), b = fmax(1.5 - q, 0.0), c = fmax(0.5 - q, 0.0);
+        return fma(-40.0 * (c * c), c, fma(20.0 * (b * b), b, -4.0 * ((a * a) * a)));
+    }
+};
+
+// Reduce-scatter of NV (a power of two <= 32) per-lane values over the warp: afterwards lane l holds the warp
+// sum of value l >> (5 - log2 NV).  Every value is summed over the butterfly tree xor 16, 8, 4, 2, 1.
+template <int NV>
+__device__ __forceinline__ double reduce_scatter(const double (&v)[NV], int lane)
+{
+    double cur[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) cur[k] = v[k];
+    int n = NV;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (n > 1) {
+            const bool up = (lane & o) != 0;
+            n >>= 1;
+#pragma unroll
+            for (int k = 0; k < NV / 2; ++k) {
+                if (k < n) {
+                    const double keep = up ? cur[k + n] : cur[k];
+                    const double send = up ? cur[k] : cur[k + n];
+                    cur[k] = keep + __shfl_xor_sync(kFull, send, o);
+                }
+            }
+        } else {
+            cur[0] += __shfl_xor_sync(kFull, cur[0], o);
+        }
+    }
+    return cur[0];
+}
+
+// Density of the kernel family Ker; with Ext also the fuller density view: drho/dh (for Omega), the neighbour
+// count, and the velocity divergence and curl estimates
+//   (div v)_i = -1/rho_i sum_j m_j v_ij . grad_i W(r_ij, h_i),  (curl v)_i = 1/rho_i sum_j m_j v_ij x grad_i W.
+template <class Ker, bool Ext>
+struct DensF64G {
+    enum { X, Y, Z, VX, VY, VZ, HINV, S0, S1, NF };  // slot members (VX..VZ read only with Ext)
+    struct Args {
+        PairCommon cm;
+        const double *f[NF];  // x, y, z, v, and (prep) 1/h, sigma/h^3, sigma/h^4
+        const double *m, *h, *u, *cs0;
+        const float *xf, *yf, *zf;
+        double *rho, *P, *cs;
+        double *nnb, *divv, *cx, *cy, *cz, *omega;  // Ext only
+        double gamma;
+    };
+    static constexpr int kRow = Ext ? 7 : 5;  // odd row length: x, y, z, m (, vx, vy, vz) and padding
+    struct Tile {
+        double *d;
+        float4 *f4;
+    };
+    struct Lhs {
+        const double *s;
+        float fx, fy, fz, b2;
+    };
+    struct Part {
+        double rho, drho, dv, cx, cy, cz;
+        int cnt;
+        __device__ __forceinline__ void zero()
+        {
+            rho = drho = dv = cx = cy = cz = 0.0;
+            cnt = 0;
+        }
+    };
+    struct Acc {
+        double rho, drho, dv, cx, cy, cz;
+        int cnt;
+    };
+    static constexpr int kStageBytes = kRow * 8 + 16;
+    static constexpr int kSlotDoubles = 17;
+    static constexpr int min_ctas(int nt) { return nt == 128 ? 6 : 3; }
+    // the two particles of a warp's queue: Ext reduces 12 sums with one 16-value reduce-scatter, the plain
+    // density its 2 sums; the neighbour counts are integer warp sums
+    static constexpr int kGroup = 2;
+    struct Group {
+        Part P0, P1;
+        int l0, l1;
+        __device__ __forceinline__ void zero() {}
+        __device__ __forceinline__ void put(int u, const Part &P, int li)
+        {
+            if (u == 0) { P0 = P; l0 = li; }
+            else { P1 = P; l1 = li; }
+        }
+        __device__ __forceinline__ void accumulate(Acc *acc, int nu, int lane)
+        {
+            if constexpr (Ext) {
+                const double v[16] = {P0.rho, P0.drho, P0.dv, P0.cx, P0.cy, P0.cz,
+                                      P1.rho, P1.drho, P1.dv, P1.cx, P1.cy, P1.cz, 0.0, 0.0, 0.0, 0.0};
+                const double t = reduce_scatter<16>(v, lane);
+                const int c0 = __reduce_add_sync(kFull, P0.cnt), c1 = __reduce_add_sync(kFull, P1.cnt);
+                const int g = lane >> 1;  // value index
+                if ((lane & 1) == 0 && g < 12) {
+                    const int u = g / 6, c = g - 6 * u;
+                    if (u < nu) {
+                        Acc &a = acc[u == 0 ? l0 : l1];
+                        if (c == 0) a.rho += t;
+                        else if (c == 1) a.drho += t;
+                        else if (c == 2) a.dv += t;
+                        else if (c == 3) a.cx += t;
+                        else if (c == 4) a.cy += t;
+                        else a.cz += t;
+                    }
+                }
+                if (lane == 0) acc[l0].cnt += c0;
+                if (lane == 0 && nu > 1) acc[l1].cnt += c1;
+            } else {
+                const double v[2] = {P0.rho, P1.rho};
+                const double t = reduce_scatter<2>(v, lane);
+                const int u = lane >> 4;
+                if ((lane & 15) == 0 && u < nu) acc[u == 0 ? l0 : l1].rho += t;
+                const int c0 = __reduce_add_sync(kFull, P0.cnt), c1 = __reduce_add_sync(kFull, P1.cnt);
+                if (lane == 0) acc[l0].cnt += c0;
+                if (lane == 0 && nu > 1) acc[l1].cnt += c1;
+            }
+        }
+    };
+
+    static __device__ Tile carve(unsigned char *s, int tj)
+    {
+        Tile t;
+        t.d = reinterpret_cast<double *>(s);
+        t.f4 = reinterpret_cast<float4 *>(t.d + kRow * tj);
+        return t;
+    }
+    static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
+                                                 int slot, int q)
+    {
+        double xs = A.f[X][slot], ys = A.f[Y][slot], zs = A.f[Z][slot];
+        if (nb.wrap) {  // the image of a neighbour across the periodic boundary
+            xs -= nb.shift[q][0];
+            ys -= nb.shift[q][1];
+            zs -= nb.shift[q][2];
+        }
+        double *row = T.d + t * kRow;
+        row[0] = xs;
+        row[1] = ys;
+        row[2] = zs;
+        row[3] = A.m[slot];
+        if constexpr (Ext) {
+            row[4] = A.f[VX][slot];
+            row[5] = A.f[VY][slot];
+            row[6] = A.f[VZ][slot];
+        }
+        T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
+                              0.0f);
+    }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *ws)
+    {
+        const int lane = threadIdx.x & 31;
+        if (lane < NF && (Ext || lane < VX || lane > VZ)) ws[lane] = A.f[lane][i];
+        __syncwarp();
+        Lhs L;
+        L.s = ws;
+        L.fx = A.xf[i];
+        L.fy = A.yf[i];
+        L.fz = A.zf[i];
+        const float rf = __fmaf_ru(Ker::kappaf * (1.0f + 4e-6f), __double2float_ru(A.h[i]), margin);
+        L.b2 = __fmul_ru(rf, rf);
+        return L;
+    }
+    static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
+    {
+        const float4 p = T.f4[k];
+        const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < L.b2;
+    }
+    static __device__ __forceinline__ bool eval(const Args &, const Lhs &L, const Tile &T, const NbrTable &,
+                                                bool, int, int k, Part &P)
+    {
+        const double *R_ = T.d + k * kRow;
+        const double *s = L.s;
+        const double dx = lds(s + X) - R_[0], dy = lds(s + Y) - R_[1], dz = lds(s + Z) - R_[2];
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double rinv = rsqrt_seeded(r2);
+        const double r = r2 * rinv;
+        const double q = r * lds(s + HINV);
+        double f, fp;
+        Ker::f_fp(q, f, fp);
+        const double mj = R_[3];
+        P.rho = fma(mj, lds(s + S0) * f, P.rho);
+        const bool supp = q < Ker::kappa;
+        P.cnt += supp ? 1 : 0;
+        if constexpr (Ext) {
+            const double s1 = lds(s + S1);
+            P.drho = fma(mj, -s1 * fma(q, fp, 3.0 * f), P.drho);
+            const double mG = mj * ((s1 * fp) * rinv);  // m_j dW/dr / r
+            const double vx = lds(s + VX) - R_[4], vy = lds(s + VY) - R_[5], vz = lds(s + VZ) - R_[6];
+            P.dv = fma(mG, fma(vx, dx, fma(vy, dy, vz * dz)), P.dv);
+            P.cx = fma(mG, fma(vy, dz, -(vz * dy)), P.cx);
+            P.cy = fma(mG, fma(vz, dx, -(vx * dz)), P.cy);
+            P.cz = fma(mG, fma(vx, dy, -(vy * dx)), P.cz);
+        }
+        return supp;
+    }
+    static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
+    {
+        const double h = A.h[i];
+        const double rho = a.rho;
+        const double P = (A.gamma - 1.0) * rho * A.u[i];
+        const double cs = A.cs0[i];
+        A.rho[i] = rho;
+        A.P[i] = P;
+        A.cs[i] = cs;
+        unsigned bits = 0;
+        if constexpr (Ext) {
+            const double ri = 1.0 / rho;
+            A.nnb[i] = (double)(a.cnt - 1);  // the local particle itself is in its own tile once
+            A.divv[i] = -a.dv * ri;
+            A.cx[i] = a.cx * ri;
+            A.cy[i] = a.cy * ri;
+            A.cz[i] = a.cz * ri;
+            const double om = 1.0 + h / (3.0 * rho) * a.drho;
+            A.omega[i] = om;
+            if (!isfinite(om) || !isfinite(a.dv) || !isfinite(a.cx) || !isfinite(a.cy) || !isfinite(a.cz))
+                bits |= SPH_DEV_NONFINITE;
+        }
+        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(P) || !isfinite(cs)) bits |= SPH_DEV_NONFINITE;
+        if (!(Ker::kappa * h <= A.cm.cs.g.min_edge)) bits |= SPH_DEV_H_TOO_BIG;
+        if (bits) atomicOr(A.cm.status, bits);
+    }
+    static __device__ __forceinline__ void count(const Args &A, unsigned long long cand,
+                                                 unsigned long long pairs)
+    {
+        atomicAdd(&A.cm.counters->dens_cand, cand);
+        atomicAdd(&A.cm.counters->dens_pairs, pairs);
+    }
+};
+
+// Force of the kernel family Ker; with Ext the fuller force view: P/rho^2 becomes P/(Omega rho^2) (grad-h
+// terms), the viscosity is scaled by the pair mean of the Balsara switch B, and the signal velocity
+// max_j (c_i + c_j - 3 min(v_ij . r_ij / r, 0)) is written too.  The per-particle A = P/(Omega rho^2) and B come
+// from the prep kernel (Omega = B = 1 without Ext).
+template <class Ker, bool Ext>
+struct ForceF64G {
+    enum { X, Y, Z, VX, VY, VZ, M, HH, HINV, S1, AP, ACH, RHO, CS, BAL, NF };
+    struct Args {
+        PairCommon cm;
+        const double *f[NF];
+        const float *xf, *yf, *zf, *hf;
+        double *ax, *ay, *az, *dudt, *vsig;
+        double beta, eps;
+    };
+    struct Tile {
+        double *d;
+        float4 *f4;
+        int *slot;
+    };
+    struct Lhs {
+        const double *s;
+        float fx, fy, fz, fh, margin;
+    };
+    struct Part {
+        double ax, ay, az, du, vs;
+        __device__ __forceinline__ void zero() { ax = ay = az = du = vs = 0.0; }
+    };
+    struct Acc {
+        double ax, ay, az, du, vs;
+    };
+    static constexpr int kStageBytes = NF * 8 + 16 + 4;
+    static constexpr int kSlotDoubles = 17;
+    // the fuller view's extra terms need more registers than three 256-thread CTAs per SM leave
+    static constexpr int min_ctas(int) { return Ext ? 2 : 3; }
+    static constexpr int kGroup = 2;
+    struct Group {
+        Part P0, P1;
+        int l0, l1;
+        __device__ __forceinline__ void zero() {}
+        __device__ __forceinline__ void put(int u, const Part &P, int li)
+        {
+            if (u == 0) { P0 = P; l0 = li; }
+            else { P1 = P; l1 = li; }
+        }
+        __device__ __forceinline__ void accumulate(Acc *acc, int nu, int lane)
+        {
+            const double v[8] = {P0.ax, P0.ay, P0.az, P0.du, P1.ax, P1.ay, P1.az, P1.du};
+            const double t = reduce_scatter<8>(v, lane);
+            const int g = lane >> 2, u = g >> 2, c = g & 3;
+            if ((lane & 3) == 0 && u < nu) {
+                Acc &a = acc[u == 0 ? l0 : l1];
+                if (c == 0) a.ax += t;
+                else if (c == 1) a.ay += t;
+                else if (c == 2) a.az += t;
+                else a.du += t;
+            }
+            if constexpr (Ext) {  // maxima are exact in any order
+                double m0 = P0.vs, m1 = P1.vs;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    m0 = fmax(m0, __shfl_xor_sync(kFull, m0, o));
+                    m1 = fmax(m1, __shfl_xor_sync(kFull, m1, o));
+                }
+                if (lane == 0) acc[l0].vs = fmax(acc[l0].vs, m0);
+                if (lane == 0 && nu > 1) acc[l1].vs = fmax(acc[l1].vs, m1);
+            }
+        }
+    };
+
+    static __device__ Tile carve(unsigned char *s, int tj)
+    {
+        Tile t;
+        t.d = reinterpret_cast<double *>(s);
+        t.f4 = reinterpret_cast<float4 *>(t.d + NF * tj);
+        t.slot = reinterpret_cast<int *>(t.f4 + tj);
+        return t;
+    }
+    static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
+                                                 int slot, int q)
+    {
+        double *row = T.d + t * NF;
+        double xs = A.f[X][slot], ys = A.f[Y][slot], zs = A.f[Z][slot];
+        if (nb.wrap) {
+            xs -= nb.shift[q][0];
+            ys -= nb.shift[q][1];
+            zs -= nb.shift[q][2];
+        }
+        row[X] = xs;
+        row[Y] = ys;
+        row[Z] = zs;
+#pragma unroll
+        for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
+        T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
+                              A.hf[slot]);
+        T.slot[t] = slot;
+    }
+    static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
+    static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *ws)
+    {
+        const int lane = threadIdx.x & 31;
+        if (lane < NF) ws[lane] = A.f[lane][i];
+        __syncwarp();
+        Lhs L;
+        L.s = ws;
+        L.fx = A.xf[i];
+        L.fy = A.yf[i];
+        L.fz = A.zf[i];
+        L.fh = A.hf[i];
+        L.margin = margin;
+        return L;
+    }
+    static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
+    {
+        const float4 p = T.f4[k];
+        const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
+        const float rf = __fmaf_ru(Ker::kappaf * (1.0f + 4e-6f), fmaxf(L.fh, p.w), L.margin);
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < __fmul_ru(rf, rf);
+    }
+    static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &,
+                                                bool, int i, int k, Part &P)
+    {
+        const double *R_ = T.d + k * NF;
+        const double *L_ = L.s;
+        const double dx = lds(L_ + X) - R_[X], dy = lds(L_ + Y) - R_[Y], dz = lds(L_ + Z) - R_[Z];
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double rinv = rsqrt_seeded(r2);
+        const double r = r2 * rinv;
+        const double qi = r * lds(L_ + HINV), qj = r * R_[HINV];
+        const double Fi = (lds(L_ + S1) * Ker::fp_only(qi)) * rinv;  // dW/dr(r, h_i) / r
+        const double Fj = (R_[S1] * Ker::fp_only(qj)) * rinv;
+        const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
+        const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
+        // Monaghan viscosity as in ForceF64: Ph = Pi / 2 = g (beta mu - alpha cbar), g = w R, mu = g D2
+        const double hb = lds(L_ + HH) + R_[HH];
+        const double D1 = fma(A.eps * hb, hb, r2);
+        const double D2 = lds(L_ + RHO) + R_[RHO];
+        const double R = rcp_seeded(D1 * D2);
+        const double g = (hb * vdotr) * R;
+        const double mu = g * D2;
+        const double t = fma(A.beta, mu, -(lds(L_ + ACH) + R_[ACH]));
+        double Ph = g * t;
+        if constexpr (Ext) Ph = Ph * (0.5 * (lds(L_ + BAL) + R_[BAL]));
+        if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
+        const double V = Ph * (Fi + Fj);
+        const double aF = lds(L_ + AP) * Fi;
+        const double mj = R_[M];
+        double coef = mj * fma(R_[AP], Fj, aF + V);
+        double dcoef = (mj * vdotr) * fma(0.5, V, aF);
+        const bool self = T.slot[k] == i;
+        const bool in = !self && (qi < Ker::kappa || qj < Ker::kappa);
+        if (self) {
+            coef = 0.0;
+            dcoef = 0.0;
+        }
+        P.ax = fma(-coef, dx, P.ax);
+        P.ay = fma(-coef, dy, P.ay);
+        P.az = fma(-coef, dz, P.az);
+        P.du += dcoef;
+        if constexpr (Ext) {
+            const double w = vdotr * rinv;
+            const double vs = (lds(L_ + CS) + R_[CS]) - 3.0 * fmin(w, 0.0);
+            if (in) P.vs = fmax(P.vs, vs);
+        }
+        return in;
+    }
+    static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
+    {
+        A.ax[i] = a.ax;
+        A.ay[i] = a.ay;
+        A.az[i] = a.az;
+        A.dudt[i] = a.du;
+        if constexpr (Ext) A.vsig[i] = a.vs;
+        if (!isfinite(a.ax) || !isfinite(a.ay) || !isfinite(a.az) || !isfinite(a.du))
+            atomicOr(A.cm.status, SPH_DEV_NONFINITE);
+    }
+    static __device__ __forceinline__ void count(const Args &A, unsigned long long cand,
+                                                 unsigned long long pairs)
+    {
+        atomicAdd(&A.cm.counters->force_cand, cand);
+        atomicAdd(&A.cm.counters->force_pairs, pairs);
+    }
+};
+
 // ---- force, FP32 (lane driver: candidates filtered into a per-lane hit mask, only hits evaluated) ----
 // grad_i W(r_ij, h) = F r_ij with F = 3 (t^2 - s^2) / (pi h^4 r), s = sat(1 - q/2), t = sat(1 - q) (the derivative
 // of f = 2 s^3 - t^3); 3/(pi h^4) comes per particle from k_force_prep_f32.  The viscosity uses
@@ -963,18 +1418,11 @@ struct ForceF32 {
     }
 };
 
+// Every accumulator starts at zero (value initialisation zeroes each member).
 template <class K>
-__device__ __forceinline__ void zero_acc(typename K::Acc &a);
-template <>
-__device__ __forceinline__ void zero_acc<DensF64>(double &a) { a = 0.0; }
-template <>
-__device__ __forceinline__ void zero_acc<DensF32>(float2 &a) { a = make_float2(0.f, 0.f); }
-template <>
-__device__ __forceinline__ void zero_acc<ForceF64>(ForceF64::Acc &a) { a.ax = a.ay = a.az = a.du = 0.0; }
-template <>
-__device__ __forceinline__ void zero_acc<ForceF32>(ForceF32::Acc &a)
+__device__ __forceinline__ void zero_acc(typename K::Acc &a)
 {
-    a.ax = a.ay = a.az = a.du = make_float2(0.f, 0.f);
+    a = typename K::Acc{};
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1456,6 +1904,57 @@ __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__r
     ach[s] = 0.5 * alpha * cs[s];
 }
 
+// Per-particle set-up of the kernel-family density (DensF64G): cell-relative float positions (filter), 1/h,
+// sigma/h^3, sigma/h^4 and the sound speed sqrt(gamma (gamma - 1) u) of the ideal-gas EOS.
+template <class Ker>
+__global__ void k_density_prep_g(const double *__restrict__ x, const double *__restrict__ y,
+                                 const double *__restrict__ z, const double *__restrict__ h,
+                                 const double *__restrict__ u, const int *__restrict__ cell_of_slot, int n,
+                                 CellSpace cs, double gamma, float *__restrict__ xf, float *__restrict__ yf,
+                                 float *__restrict__ zf, double *__restrict__ hinv, double *__restrict__ s0,
+                                 double *__restrict__ s1, double *__restrict__ cs0)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
+    const double hi = 1.0 / h[s], h3 = hi * hi * hi;
+    hinv[s] = hi;
+    s0[s] = Ker::sigma * h3;
+    s1[s] = Ker::sigma * (h3 * hi);
+    cs0[s] = sqrt(gamma * (gamma - 1.0) * u[s]);
+}
+
+// Per-particle set-up of the kernel-family force (ForceF64G): h/2, 1/h, sigma/h^4, A = P / (Omega rho^2),
+// alpha c / 2 and the Balsara switch B = |div v| / (|div v| + |curl v| + 1e-4 c / h); Omega = B = 1 without Ext.
+template <class Ker, bool Ext>
+__global__ void k_force_prep_g(const double *__restrict__ h, const double *__restrict__ P,
+                               const double *__restrict__ rho, const double *__restrict__ cs,
+                               const double *__restrict__ omega, const double *__restrict__ divv,
+                               const double *__restrict__ cx, const double *__restrict__ cy,
+                               const double *__restrict__ cz, double alpha, int n, double *__restrict__ hh,
+                               double *__restrict__ hinv, double *__restrict__ s1, double *__restrict__ A,
+                               double *__restrict__ ach, double *__restrict__ bal)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double hv = h[s];
+    const double hi = 1.0 / hv, h2 = hi * hi;
+    hh[s] = 0.5 * hv;
+    hinv[s] = hi;
+    s1[s] = Ker::sigma * (h2 * h2);
+    const double r = rho[s];
+    if constexpr (Ext) {
+        A[s] = P[s] / (omega[s] * r * r);
+        const double d = fabs(divv[s]);
+        const double c = sqrt(cx[s] * cx[s] + cy[s] * cy[s] + cz[s] * cz[s]);
+        bal[s] = d / (d + c + 1e-4 * cs[s] * hi);
+    } else {
+        A[s] = P[s] / (r * r);
+        bal[s] = 1.0;
+    }
+    ach[s] = 0.5 * alpha * cs[s];
+}
+
 template <class K>
 struct UsesLanes {
     static constexpr bool value = false;
@@ -1541,32 +2040,70 @@ int tile_or_default(int tj, int dflt)
 }  // namespace
 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &g, double gamma, cudaStream_t st, int *nl)
+                                const CellSpace &g, const sph_params &prm, cudaStream_t st, int *nl)
 {
     if (n <= 0 || f32) return cudaSuccess;  // FP32 views are already cell-relative floats
-    k_density_prep_f64<<<(n + 255) / 256, 256, 0, st>>>(
-        (const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1], (const double *)soa.p[SPH_X][2],
-        (const double *)soa.p[SPH_H][0], cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, (double *)scr.d[0],
-        (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3], (double *)scr.d[4],
-        (const double *)soa.p[SPH_U][0], gamma, (double *)scr.d[5], (double *)scr.d[6]);
+    const double gamma = prm.gamma;
+    const int nb = (n + 255) / 256;
+    const double *x = (const double *)soa.p[SPH_X][0], *y = (const double *)soa.p[SPH_X][1],
+                 *z = (const double *)soa.p[SPH_X][2], *h = (const double *)soa.p[SPH_H][0],
+                 *u = (const double *)soa.p[SPH_U][0];
+    double *const *d = reinterpret_cast<double *const *>(scr.d);
+    if (prm.kernel == SPH_KERNEL_M4 && prm.scheme == SPH_SCHEME_MINIMAL) {
+        k_density_prep_f64<<<nb, 256, 0, st>>>(x, y, z, h, cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, d[0], d[1],
+                                              d[2], d[3], d[4], u, gamma, d[5], d[6]);
+    } else if (prm.kernel == SPH_KERNEL_M5) {
+        k_density_prep_g<KerM5><<<nb, 256, 0, st>>>(x, y, z, h, u, cell_of_slot, n, g, gamma, scr.xf, scr.yf,
+                                                    scr.zf, d[0], d[1], d[2], d[6]);
+    } else {
+        k_density_prep_g<KerM4><<<nb, 256, 0, st>>>(x, y, z, h, u, cell_of_slot, n, g, gamma, scr.xf, scr.yf,
+                                                    scr.zf, d[0], d[1], d[2], d[6]);
+    }
     ++*nl;
     return cudaGetLastError();
 }
 
+namespace {
+
+template <class Ker, bool Ext>
+void force_prep_g(const SoaPtrs &soa, const Scratch &scr, int n, double alpha, cudaStream_t st)
+{
+    double *const *d = reinterpret_cast<double *const *>(scr.d);
+    const double *omega = Ext ? (const double *)soa.p[SPH_OMEGA][0] : nullptr;
+    const double *divv = Ext ? (const double *)soa.p[SPH_DIVV][0] : nullptr;
+    const double *cx = Ext ? (const double *)soa.p[SPH_CURLV][0] : nullptr;
+    const double *cy = Ext ? (const double *)soa.p[SPH_CURLV][1] : nullptr;
+    const double *cz = Ext ? (const double *)soa.p[SPH_CURLV][2] : nullptr;
+    k_force_prep_g<Ker, Ext><<<(n + 255) / 256, 256, 0, st>>>(
+        (const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0], (const double *)soa.p[SPH_RHO][0],
+        (const double *)soa.p[SPH_CS][0], omega, divv, cx, cy, cz, alpha, n, d[0], d[1], d[2], d[3], d[4], d[5]);
+}
+
+}  // namespace
+
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const CellSpace &g, double alpha, cudaStream_t st, int *nl)
+                              const CellSpace &g, const sph_params &prm, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     const int nb = (n + 255) / 256;
+    const double alpha = prm.alpha;
     if (!f32) {
         k_pos32<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
                                     (const double *)soa.p[SPH_X][2], (const double *)soa.p[SPH_H][0], cell_of_slot,
                                     n, g, scr.xf, scr.yf, scr.zf, scr.hf);
-        k_force_prep_f64<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
-                                             (const double *)soa.p[SPH_RHO][0], (const double *)soa.p[SPH_CS][0],
-                                             alpha, n, (double *)scr.d[0], (double *)scr.d[1], (double *)scr.d[2],
-                                             (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
-                                             (double *)scr.d[6]);
+        const bool ext = prm.scheme == SPH_SCHEME_EXTENDED;
+        if (prm.kernel == SPH_KERNEL_M4 && !ext) {
+            k_force_prep_f64<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
+                                                 (const double *)soa.p[SPH_RHO][0],
+                                                 (const double *)soa.p[SPH_CS][0], alpha, n, (double *)scr.d[0],
+                                                 (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3],
+                                                 (double *)scr.d[4], (double *)scr.d[5], (double *)scr.d[6]);
+        } else if (prm.kernel == SPH_KERNEL_M5) {
+            if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, st);
+            else force_prep_g<KerM5, false>(soa, scr, n, alpha, st);
+        } else {
+            force_prep_g<KerM4, true>(soa, scr, n, alpha, st);
+        }
         *nl += 2;
     } else {
         k_force_prep_f32<<<nb, 256, 0, st>>>((const float *)soa.p[SPH_H][0], (const float *)soa.p[SPH_P][0],
@@ -1577,14 +2114,98 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
     return cudaGetLastError();
 }
 
+namespace {
+
+template <class Ker, bool Ext>
+cudaError_t density_pairs_g(const SoaPtrs &soa, const Scratch &scr, PairCommon cm, int tj, double gamma,
+                            int ncells, const PairLaunch &pl, cudaStream_t st)
+{
+    using D = DensF64G<Ker, Ext>;
+    typename D::Args A;
+    cm.tj = tile_or_default(tj, 448);
+    A.cm = cm;
+    A.f[D::X] = (const double *)soa.p[SPH_X][0];
+    A.f[D::Y] = (const double *)soa.p[SPH_X][1];
+    A.f[D::Z] = (const double *)soa.p[SPH_X][2];
+    A.f[D::VX] = Ext ? (const double *)soa.p[SPH_V][0] : nullptr;
+    A.f[D::VY] = Ext ? (const double *)soa.p[SPH_V][1] : nullptr;
+    A.f[D::VZ] = Ext ? (const double *)soa.p[SPH_V][2] : nullptr;
+    A.f[D::HINV] = (const double *)scr.d[0];
+    A.f[D::S0] = (const double *)scr.d[1];
+    A.f[D::S1] = (const double *)scr.d[2];
+    A.m = (const double *)soa.p[SPH_MASS][0];
+    A.h = (const double *)soa.p[SPH_H][0];
+    A.u = (const double *)soa.p[SPH_U][0];
+    A.cs0 = (const double *)scr.d[6];
+    A.xf = scr.xf;
+    A.yf = scr.yf;
+    A.zf = scr.zf;
+    A.rho = (double *)soa.p[SPH_RHO][0];
+    A.P = (double *)soa.p[SPH_P][0];
+    A.cs = (double *)soa.p[SPH_CS][0];
+    A.nnb = Ext ? (double *)soa.p[SPH_NNB][0] : nullptr;
+    A.divv = Ext ? (double *)soa.p[SPH_DIVV][0] : nullptr;
+    A.cx = Ext ? (double *)soa.p[SPH_CURLV][0] : nullptr;
+    A.cy = Ext ? (double *)soa.p[SPH_CURLV][1] : nullptr;
+    A.cz = Ext ? (double *)soa.p[SPH_CURLV][2] : nullptr;
+    A.omega = Ext ? (double *)soa.p[SPH_OMEGA][0] : nullptr;
+    A.gamma = gamma;
+    return run_cells<D>(A, ncells, pl, st);
+}
+
+template <class Ker, bool Ext>
+cudaError_t force_pairs_g(const SoaPtrs &soa, const Scratch &scr, PairCommon cm, int tj, const sph_params &prm,
+                          int ncells, const PairLaunch &pl, cudaStream_t st)
+{
+    using F = ForceF64G<Ker, Ext>;
+    typename F::Args A;
+    cm.tj = tile_or_default(tj, 448);
+    A.cm = cm;
+    A.f[F::X] = (const double *)soa.p[SPH_X][0];
+    A.f[F::Y] = (const double *)soa.p[SPH_X][1];
+    A.f[F::Z] = (const double *)soa.p[SPH_X][2];
+    A.f[F::VX] = (const double *)soa.p[SPH_V][0];
+    A.f[F::VY] = (const double *)soa.p[SPH_V][1];
+    A.f[F::VZ] = (const double *)soa.p[SPH_V][2];
+    A.f[F::M] = (const double *)soa.p[SPH_MASS][0];
+    A.f[F::HH] = (const double *)scr.d[0];
+    A.f[F::HINV] = (const double *)scr.d[1];
+    A.f[F::S1] = (const double *)scr.d[2];
+    A.f[F::AP] = (const double *)scr.d[3];
+    A.f[F::ACH] = (const double *)scr.d[4];
+    A.f[F::BAL] = (const double *)scr.d[5];
+    A.f[F::RHO] = (const double *)soa.p[SPH_RHO][0];
+    A.f[F::CS] = (const double *)soa.p[SPH_CS][0];
+    A.xf = scr.xf;
+    A.yf = scr.yf;
+    A.zf = scr.zf;
+    A.hf = scr.hf;
+    A.ax = (double *)soa.p[SPH_A][0];
+    A.ay = (double *)soa.p[SPH_A][1];
+    A.az = (double *)soa.p[SPH_A][2];
+    A.dudt = (double *)soa.p[SPH_DUDT][0];
+    A.vsig = Ext ? (double *)soa.p[SPH_VSIG][0] : nullptr;
+    A.beta = prm.beta;
+    A.eps = prm.eps;
+    return run_cells<F>(A, ncells, pl, st);
+}
+
+}  // namespace
+
 cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
-                                 int ncells, int n, const CellSpace &g, double gamma, const PairLaunch &pl,
+                                 int ncells, int n, const CellSpace &g, const sph_params &prm, const PairLaunch &pl,
                                  unsigned *status, Counters *counters, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
     PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
     const int tj = pl.tj;
+    const double gamma = prm.gamma;
+    if (!f32 && prm.kernel == SPH_KERNEL_M5) {
+        return prm.scheme == SPH_SCHEME_EXTENDED ? density_pairs_g<KerM5, true>(soa, scr, cm, tj, gamma, ncells, pl, st)
+                                                 : density_pairs_g<KerM5, false>(soa, scr, cm, tj, gamma, ncells, pl, st);
+    }
+    if (!f32 && prm.scheme == SPH_SCHEME_EXTENDED) return density_pairs_g<KerM4, true>(soa, scr, cm, tj, gamma, ncells, pl, st);
     if (!f32) {
         DensF64::Args A;
         cm.tj = tile_or_default(tj, 512);
@@ -1636,6 +2257,11 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
     ++*nl;
     PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
     const int tj = pl.tj;
+    if (!f32 && prm.kernel == SPH_KERNEL_M5) {
+        return prm.scheme == SPH_SCHEME_EXTENDED ? force_pairs_g<KerM5, true>(soa, scr, cm, tj, prm, ncells, pl, st)
+                                                 : force_pairs_g<KerM5, false>(soa, scr, cm, tj, prm, ncells, pl, st);
+    }
+    if (!f32 && prm.scheme == SPH_SCHEME_EXTENDED) return force_pairs_g<KerM4, true>(soa, scr, cm, tj, prm, ncells, pl, st);
     if (!f32) {
         ForceF64::Args A;
         cm.tj = tile_or_default(tj, 448);  // 140 B per staged particle: three 256-thread CTAs per SM

@@ -21,7 +21,7 @@ using sphk::Grid;
 
 namespace {
 
-const int kNcomp[SPH_NFIELDS] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 1};
+const int kNcomp[SPH_NFIELDS] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 1, 1, 1, 3, 1, 1};
 
 }  // namespace
 
@@ -101,6 +101,15 @@ struct sph_view_s {
 namespace {
 
 sph_status cuda_fail(cudaError_t e) { return e == cudaSuccess ? SPH_OK : SPH_E_CUDA; }
+
+// The access sets of the two loops under the equation set of `p` (include/sph.h).
+bool extended(const sph_params *p) { return p->scheme == SPH_SCHEME_EXTENDED; }
+uint32_t dens_in(const sph_params *p) { return extended(p) ? SPH_DENSITY_IN_EXT : SPH_DENSITY_IN; }
+uint32_t dens_out(const sph_params *p) { return extended(p) ? SPH_DENSITY_OUT_EXT : SPH_DENSITY_OUT; }
+uint32_t force_in(const sph_params *p) { return extended(p) ? SPH_FORCE_IN_EXT : SPH_FORCE_IN; }
+uint32_t force_out(const sph_params *p) { return extended(p) ? SPH_FORCE_OUT_EXT : SPH_FORCE_OUT; }
+// Support radius of the kernel in units of h.
+double kappa_of(const sph_params *p) { return p->kernel == SPH_KERNEL_M5 ? 2.5 : 2.0; }
 
 bool layout_valid(const sph_layout *L, uint32_t *present)
 {
@@ -421,28 +430,39 @@ sph_status density_launch(sph_view_s *v, const sph_params *p, const int *skip)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_DENSITY_PREP);
-        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, p->gamma, v->st,
-                                      &ph.nl);
+        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_DENSITY);
         sphk::PairLaunch pl = pair_launch(v, v->tile_density, v->warps_density);
         pl.skip = skip;
-        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, p->gamma, pl,
+        e = sphk::launch_density_pairs(f32, v->soa, v->scr, v->cell_start, v->ncells, (int)v->n, v->cs, *p, pl,
                                        v->status, v->counters, v->st, &ph.nl);
     }
     return cuda_fail(e);
 }
 
-sph_status do_density(sph_view_s *v, const sph_params *p)
+// The kernel and equation set of `p`: anything but (cubic, minimal) needs an FP64 single-grid view.
+sph_status check_scheme(const sph_view_s *v, const sph_params *p)
 {
     if (!p) return SPH_E_INVAL;
-    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
-    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
-    sph_status s = density_launch(v, p, nullptr);
+    if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M5) return SPH_E_INVAL;
+    if (p->scheme != SPH_SCHEME_MINIMAL && p->scheme != SPH_SCHEME_EXTENDED) return SPH_E_INVAL;
+    if ((p->kernel != SPH_KERNEL_M4 || p->scheme != SPH_SCHEME_MINIMAL) && (v->prec != SPH_F64 || v->npatch_max > 0))
+        return SPH_E_INVAL;
+    return SPH_OK;
+}
+
+sph_status do_density(sph_view_s *v, const sph_params *p)
+{
+    sph_status s = check_scheme(v, p);
     if (s != SPH_OK) return s;
-    v->resident |= SPH_DENSITY_OUT;
+    if (!mask_present(v, dens_out(p))) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & dens_in(p)) != dens_in(p)) return SPH_E_STATE;
+    s = density_launch(v, p, nullptr);
+    if (s != SPH_OK) return s;
+    v->resident |= dens_out(p);
     return SPH_OK;
 }
 
@@ -455,8 +475,9 @@ sph_status do_density_h(sph_view_s *v, const sph_params *p, double eta, double t
     if (!p || !(eta > 0.0) || !(eta < 1e6) || !(tol > 0.0) || !(tol < 1.0) || max_iter < 1 || max_iter > 1000)
         return SPH_E_INVAL;
     if (v->npatch_max > 0) return SPH_E_INVAL;  // patch grids are sized once per bin from the patch's h
-    if (!mask_present(v, SPH_DENSITY_OUT)) return SPH_E_INVAL;
-    if (!v->binned || (v->resident & SPH_DENSITY_IN) != SPH_DENSITY_IN) return SPH_E_STATE;
+    if (check_scheme(v, p) != SPH_OK) return SPH_E_INVAL;
+    if (!mask_present(v, dens_out(p))) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & dens_in(p)) != dens_in(p)) return SPH_E_STATE;
     const int n = (int)v->n;
     cudaError_t e = cudaMemsetAsync(v->hdone, 0, (size_t)std::max(n, 1), v->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->hstate, 0, 4 * sizeof(int), v->st);
@@ -465,8 +486,8 @@ sph_status do_density_h(sph_view_s *v, const sph_params *p, double eta, double t
         sph_status s = density_launch(v, p, v->hstate + 1);
         if (s != SPH_OK) return s;
         Phase ph(v, SPH_PH_DENSITY);
-        e = sphk::launch_h_update(v->prec == SPH_F32, v->soa, n, eta, tol, 0.5 * v->g.min_edge, v->hdone, v->hstate,
-                                  v->status, v->st, &ph.nl);
+        e = sphk::launch_h_update(v->prec == SPH_F32, v->soa, n, eta, tol, v->g.min_edge / kappa_of(p), v->hdone,
+                                  v->hstate, v->status, v->st, &ph.nl);
         if (e != cudaSuccess) return SPH_E_CUDA;
     }
     sph_status s = density_launch(v, p, nullptr);
@@ -475,20 +496,20 @@ sph_status do_density_h(sph_view_s *v, const sph_params *p, double eta, double t
         Phase ph(v, SPH_PH_DENSITY);
         if (sphk::launch_h_finish(v->hstate, v->status, v->st, &ph.nl) != cudaSuccess) return SPH_E_CUDA;
     }
-    v->resident |= SPH_DENSITY_OUT;
+    v->resident |= dens_out(p);
     return SPH_OK;
 }
 
 sph_status do_force(sph_view_s *v, const sph_params *p)
 {
-    if (!p) return SPH_E_INVAL;
-    if (!mask_present(v, SPH_FORCE_OUT)) return SPH_E_INVAL;
-    if (!v->binned || (v->resident & SPH_FORCE_IN) != SPH_FORCE_IN) return SPH_E_STATE;
+    if (check_scheme(v, p) != SPH_OK) return SPH_E_INVAL;
+    if (!mask_present(v, force_out(p))) return SPH_E_INVAL;
+    if (!v->binned || (v->resident & force_in(p)) != force_in(p)) return SPH_E_STATE;
     const bool f32 = v->prec == SPH_F32;
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_FORCE_PREP);
-        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, p->alpha, v->st, &ph.nl);
+        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
@@ -498,13 +519,15 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
                                      &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
-    v->resident |= SPH_FORCE_OUT;
+    v->resident |= force_out(p);
     return SPH_OK;
 }
 
 sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
 {
-    sph_status s;
+    sph_status s = check_scheme(v, p);
+    if (s != SPH_OK) return s;
+    if (!mask_present(v, dens_out(p) | force_out(p))) return SPH_E_INVAL;
     if (v->npatch_max > 0) {
         if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch)) != SPH_OK) return s;
     } else if ((s = do_bin(v, aos, n)) != SPH_OK) {
@@ -512,28 +535,28 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     }
     // union view: one gather of every member either loop reads (each record is read once: its bytes arrive in
     // whole memory sectors, so a second pass for the force's extra member v would read the records again)
-    const uint32_t first = v->union_view ? ((SPH_DENSITY_IN | SPH_FORCE_IN) & ~SPH_DENSITY_OUT) : SPH_DENSITY_IN;
+    const uint32_t first = v->union_view ? ((dens_in(p) | force_in(p)) & ~dens_out(p)) : dens_in(p);
     if ((s = do_gather(v, aos, n, first)) != SPH_OK) return s;
-    uint32_t dens_out = SPH_DENSITY_OUT;
+    uint32_t d_out = dens_out(p);
     if (v->h_max_iter > 0) {
         if ((s = do_density_h(v, p, v->h_eta, v->h_tol, v->h_max_iter, true)) != SPH_OK) return s;
-        dens_out |= SPH_BIT(SPH_H);  // the iteration writes h as well
+        d_out |= SPH_BIT(SPH_H);  // the iteration writes h as well
     } else if ((s = do_density(v, p)) != SPH_OK) {
         return s;
     }
     if (!v->union_view) {
         // one view per loop, converted forth and back around each (the paper's prologue / epilogue per loop)
-        if ((s = do_scatter(v, aos, n, dens_out)) != SPH_OK) return s;
-        if ((s = do_gather(v, aos, n, SPH_FORCE_IN)) != SPH_OK) return s;
+        if ((s = do_scatter(v, aos, n, d_out)) != SPH_OK) return s;
+        if ((s = do_gather(v, aos, n, force_in(p))) != SPH_OK) return s;
         if ((s = do_force(v, p)) != SPH_OK) return s;
-        return do_scatter(v, aos, n, SPH_FORCE_OUT);
+        return do_scatter(v, aos, n, force_out(p));
     }
     // union view: the force reads its members and the density outputs where they are, in SoA, and every written
     // member is scattered once at the end
-    const uint32_t more = SPH_FORCE_IN & ~v->resident;
+    const uint32_t more = force_in(p) & ~v->resident;
     if (more && (s = do_gather(v, aos, n, more)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;
-    return do_scatter(v, aos, n, dens_out | SPH_FORCE_OUT);
+    return do_scatter(v, aos, n, d_out | force_out(p));
 }
 
 // Half kick on the view (v += a dt/2, u += du/dt dt/2), then write v and u back into the records.
@@ -843,7 +866,7 @@ sph_status sph_autotune(sph_view v, void *aos_dev, int64_t n, const sph_params *
     graph_drop(v);
     if (bd == 0 || bf == 0) return SPH_E_CUDA;
     // leave the records as one pass leaves them: the timed loops rewrote only SoA members, so scatter them again
-    if ((s = do_scatter(v, aos_dev, n, SPH_FORCE_OUT)) != SPH_OK) return s;
+    if ((s = do_scatter(v, aos_dev, n, dens_out(params) | force_out(params))) != SPH_OK) return s;
     if (chosen) {
         chosen[0] = bd;
         chosen[1] = bf;

@@ -18,10 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsph.so")
 # ---- constants (mirror include/sph.h) ----
 SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_DEVICE, SPH_E_TIMEOUT, SPH_E_NOTCONV, SPH_E_STATE = range(8)
 SPH_F64, SPH_F32 = 0, 1
-SPH_X, SPH_V, SPH_A, SPH_MASS, SPH_H, SPH_RHO, SPH_P, SPH_U, SPH_DUDT, SPH_CS = range(10)
-SPH_NFIELDS = 10
-FIELD_NAMES = ("x", "v", "a", "mass", "h", "rho", "P", "u", "dudt", "cs")
-NCOMP = (3, 3, 3, 1, 1, 1, 1, 1, 1, 1)
+(SPH_X, SPH_V, SPH_A, SPH_MASS, SPH_H, SPH_RHO, SPH_P, SPH_U, SPH_DUDT, SPH_CS, SPH_NNB, SPH_DIVV, SPH_CURLV,
+ SPH_OMEGA, SPH_VSIG) = range(15)
+SPH_NFIELDS = 15
+FIELD_NAMES = ("x", "v", "a", "mass", "h", "rho", "P", "u", "dudt", "cs", "nnb", "divv", "curlv", "omega", "vsig")
+NCOMP = (3, 3, 3, 1, 1, 1, 1, 1, 1, 1, 1, 1, 3, 1, 1)
+SPH_KERNEL_M4, SPH_KERNEL_M5 = 0, 1
+SPH_SCHEME_MINIMAL, SPH_SCHEME_EXTENDED = 0, 1
 
 
 def SPH_BIT(f):
@@ -33,6 +36,11 @@ SPH_DENSITY_OUT = SPH_BIT(SPH_RHO) | SPH_BIT(SPH_P) | SPH_BIT(SPH_CS)
 SPH_FORCE_IN = (SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_MASS) | SPH_BIT(SPH_H) | SPH_BIT(SPH_RHO)
                 | SPH_BIT(SPH_P) | SPH_BIT(SPH_CS))
 SPH_FORCE_OUT = SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT)
+SPH_DENSITY_IN_EXT = SPH_DENSITY_IN | SPH_BIT(SPH_V)
+SPH_DENSITY_OUT_EXT = (SPH_DENSITY_OUT | SPH_BIT(SPH_NNB) | SPH_BIT(SPH_DIVV) | SPH_BIT(SPH_CURLV)
+                       | SPH_BIT(SPH_OMEGA))
+SPH_FORCE_IN_EXT = SPH_FORCE_IN | SPH_BIT(SPH_OMEGA) | SPH_BIT(SPH_DIVV) | SPH_BIT(SPH_CURLV)
+SPH_FORCE_OUT_EXT = SPH_FORCE_OUT | SPH_BIT(SPH_VSIG)
 SPH_ALL_FIELDS = (1 << SPH_NFIELDS) - 1
 SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 0x2, 0x4, 0x8
 SPH_DEV_NOTCONV = 0x10
@@ -54,7 +62,7 @@ class sph_domain(ctypes.Structure):
 
 class sph_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("kernel", ctypes.c_int32), ("scheme", ctypes.c_int32)]
 
 
 class SphError(RuntimeError):
@@ -168,7 +176,9 @@ def make_domain(box, ncell, periodic=True) -> sph_domain:
 
 
 def make_params(p: dict) -> sph_params:
-    return sph_params(float(p["gamma"]), float(p["alpha"]), float(p["beta"]), float(p["eps"]))
+    """sph_params from a dict; "kernel" and "scheme" default to the cubic spline and the minimal set."""
+    return sph_params(float(p["gamma"]), float(p["alpha"]), float(p["beta"]), float(p["eps"]),
+                      int(p.get("kernel", SPH_KERNEL_M4)), int(p.get("scheme", SPH_SCHEME_MINIMAL)))
 
 
 # ---- the C ABI ----

@@ -25,7 +25,11 @@ SEED = 2502
 
 # Field order of the layout's offset table: the same order as the library's field bits.
 FIELDS = ("x", "v", "a", "mass", "h", "rho", "P", "u", "dudt", "cs")
-NCOMP = {"x": 3, "v": 3, "a": 3, "mass": 1, "h": 1, "rho": 1, "P": 1, "u": 1, "dudt": 1, "cs": 1}
+# the members of the fuller density / force views (neighbour count, div v, curl v, Omega, signal velocity)
+EXT_FIELDS = ("nnb", "divv", "curlv", "omega", "vsig")
+ALL_FIELDS = FIELDS + EXT_FIELDS
+NCOMP = {"x": 3, "v": 3, "a": 3, "mass": 1, "h": 1, "rho": 1, "P": 1, "u": 1, "dudt": 1, "cs": 1,
+         "nnb": 1, "divv": 1, "curlv": 3, "omega": 1, "vsig": 1}
 
 RECORD_STRIDE = 160
 RECORD_OFFSETS = {"x": 0, "v": 24, "a": 48, "mass": 72, "h": 80, "rho": 88, "P": 96, "u": 104, "dudt": 112,
@@ -35,6 +39,16 @@ ID_OFFSET, CELL_OFFSET, FLAGS_OFFSET = 128, 136, 140
 
 def default_layout():
     return {"stride": RECORD_STRIDE, "offsets": dict(RECORD_OFFSETS)}
+
+
+# The paper's default particle footprint, 272 bytes (Section 2.2): the 160-byte record above (members, id, cell,
+# flags, padding) followed by the fuller views' members and more administrative bytes.
+EXT_RECORD_STRIDE = 272
+EXT_RECORD_OFFSETS = dict(RECORD_OFFSETS, nnb=160, divv=168, curlv=176, omega=200, vsig=208)
+
+
+def extended_layout():
+    return {"stride": EXT_RECORD_STRIDE, "offsets": dict(EXT_RECORD_OFFSETS)}
 
 
 def shuffled_layout(seed=7, stride=None):
@@ -168,13 +182,13 @@ def pack_aos(fields, layout=None, order="shuffled", seed=SEED + 1, canary=True, 
             where[a:b] = a + rng.permutation(int(b - a))
     rec = np.empty_like(aos)
     rec[:] = aos
-    for name in FIELDS:
+    for name in ALL_FIELDS:
         if name not in fields or name not in offs:
             continue
         val = np.ascontiguousarray(np.asarray(fields[name], np.float64).reshape(n, NCOMP[name]))
         o = int(offs[name])
         rec[:, o:o + 8 * NCOMP[name]] = val.view(np.uint8).reshape(n, 8 * NCOMP[name])
-    if layout["offsets"] == RECORD_OFFSETS and stride >= ID_OFFSET + 8:
+    if all(layout["offsets"].get(k) == o for k, o in RECORD_OFFSETS.items()) and stride >= ID_OFFSET + 8:
         rec[:, ID_OFFSET:ID_OFFSET + 8] = np.arange(n, dtype=np.int64).view(np.uint8).reshape(n, 8)
     aos[where] = rec
     return aos, where
@@ -202,10 +216,11 @@ def large(n_side=128, seed=SEED):
     return clustered(n_side ** 3, nclusters=8, sigma=0.05, peak=4.0, hfac=1.2, n_side_equiv=n_side, seed=seed)
 
 
-def ncell_for(box, hmax):
-    """Largest cell count per axis with cell edge >= 2 h_max (and at least 3 for the periodic stencil)."""
+def ncell_for(box, hmax, kappa=2.0):
+    """Largest cell count per axis with cell edge >= kappa h_max, the kernel's support (2 for the cubic spline,
+    5/2 for the quartic), and at least 3 for the periodic stencil."""
     box = np.asarray(box, np.float64)
-    nc = np.floor(box / (2.0 * hmax)).astype(np.int64)
+    nc = np.floor(box / (kappa * hmax)).astype(np.int64)
     return np.maximum(nc, 3).astype(np.int32)
 
 
