@@ -22,7 +22,8 @@
  *     sph_view_create and frees it in sph_view_destroy.  No call other than sph_view_create and
  *     sph_step_host's first use allocates device memory.
  *   - Arguments are checked on the host first; a bad argument returns SPH_E_INVAL and enqueues nothing.
- *   - Problems found on the device (a position outside the box, 2h larger than a cell, a non-finite density)
+ *   - Problems found on the device (a position outside the box, the kernel support kappa h larger than a cell, a
+ *     non-finite density)
  *     set bits in the view's device status word; the next waiting call returns SPH_E_DEVICE and
  *     sph_view_status reports the bits.  Kernels never trap and never wait without a bound.
  *   - A view is used from one host thread at a time.
@@ -91,7 +92,7 @@ enum {
 
 /* Device status bits (sph_view_status). */
 #define SPH_DEV_POS_RANGE 0x1u  /* a position was outside [0, box] or not finite; it was clamped into a cell */
-#define SPH_DEV_H_TOO_BIG 0x2u  /* 2h exceeded the smallest cell edge: the 3^3 stencil may miss pairs      */
+#define SPH_DEV_H_TOO_BIG 0x2u  /* kappa h exceeded the smallest cell edge: the 3^3 stencil may miss pairs */
 #define SPH_DEV_NONFINITE 0x4u  /* a density, pressure or sound speed came out non-finite or <= 0           */
 #define SPH_DEV_TIMEOUT 0x8u    /* a bounded device-side wait gave up                                       */
 #define SPH_DEV_NOTCONV 0x10u   /* a smoothing-length iteration inside sph_step left particles unconverged   */
@@ -107,7 +108,8 @@ typedef struct sph_layout {
 } sph_layout;
 
 /* Domain [0, box[0]) x [0, box[1]) x [0, box[2]), cut into ncell[0] x ncell[1] x ncell[2] equal cells.  The
- * cell edge box[d]/ncell[d] must be at least 2 h of every particle (the interaction radius, Section 2.1); this is
+ * cell edge box[d]/ncell[d] must be at least kappa h of every particle (the interaction radius, Section 2.1:
+ * 2h for the cubic spline, 5h/2 for the quartic, see sph_params); this is
  * checked on the device (SPH_DEV_H_TOO_BIG).  periodic != 0 wraps every axis (minimum image) and then needs
  * ncell[d] >= 3; periodic == 0 is an open box.  At most 2^27 cells. */
 typedef struct sph_domain {
@@ -196,7 +198,7 @@ SPH_API sph_status sph_patches_step_graph(sph_view view, void *aos_dev, int64_t 
  * its final h.  The SoA members h, rho, P, c_s hold the result; scatter SPH_BIT(SPH_H) | SPH_DENSITY_OUT to
  * write it into the records.  Rounds after convergence cost one near-empty launch each; nothing inside waits,
  * then the call waits once and reports *rounds (rounds run) and *unconverged (particles not converged after the
- * last round).  The new h must keep 2h within the view's cell edge (else SPH_E_DEVICE, SPH_DEV_H_TOO_BIG): create
+ * last round).  The new h must keep kappa h within the view's cell edge (else SPH_E_DEVICE, SPH_DEV_H_TOO_BIG): create
  * the view with room for h to grow.  Grid views only.  Errors: SPH_E_INVAL (eta <= 0, tol not in (0, 1),
  * max_iter not in 1..1000, patch view), SPH_E_STATE (density view not resident), SPH_E_NOTCONV (particles left
  * unconverged; results are still written), SPH_E_DEVICE. */
@@ -262,17 +264,19 @@ SPH_API sph_status sph_bin(sph_view view, const void *aos_dev, int64_t n);
 SPH_API sph_status sph_aos_to_soa(sph_view view, const void *aos_dev, int64_t n, uint32_t in_mask);
 
 /* Density loop (Section 2.1 step 1; local-active order of Section 5.4): for every particle i,
- * rho_i = sum_j m_j W(|r_ij|, h_i) over the 3^3 neighbour cells of i's cell (self term included, cubic spline
- * with support 2h), then P_i = (gamma - 1) rho_i u_i and c_s,i = sqrt(gamma P_i / rho_i), written to the SoA
- * members rho, P, cs.  Needs SPH_DENSITY_IN resident (SPH_E_STATE otherwise) and SPH_DENSITY_OUT in the layout. */
+ * rho_i = sum_j m_j W(|r_ij|, h_i) over the 3^3 neighbour cells of i's cell (self term included; the kernel of
+ * params, support kappa h), then P_i = (gamma - 1) rho_i u_i and c_s,i = sqrt(gamma P_i / rho_i), written to the
+ * SoA members rho, P, cs; with the extended scheme also nnb, divv, curlv and omega (see the member list).  Needs
+ * the scheme's density input set resident (SPH_E_STATE otherwise) and its output set in the layout. */
 SPH_API sph_status sph_density(sph_view view, const sph_params *params);
 
 /* Force loop (Section 2.1 step 2): for every particle i and every j != i of the 3^3 neighbour cells with
- * |r_ij| < 2 max(h_i, h_j):
+ * |r_ij| < kappa max(h_i, h_j):
  *   a_i     = -sum_j m_j [P_i/rho_i^2 grad W(r_ij,h_i) + P_j/rho_j^2 grad W(r_ij,h_j) + Pi_ij gradbar]
  *   du_i/dt =  sum_j m_j [P_i/rho_i^2 v_ij . grad W(r_ij,h_i) + Pi_ij v_ij . gradbar / 2]
  * with the Monaghan viscosity Pi_ij (alpha, beta, eps of params) for approaching pairs, written to the SoA
- * members a, dudt.  Needs SPH_FORCE_IN resident (SPH_E_STATE otherwise). */
+ * members a, dudt.  The extended scheme divides each P_k / rho_k^2 by Omega_k, scales Pi_ij by the Balsara pair
+ * mean and writes vsig as well.  Needs the scheme's force input set resident (SPH_E_STATE otherwise). */
 SPH_API sph_status sph_force(sph_view view, const sph_params *params);
 
 /* Epilogue (Section 3.1, W o C_SoA^AoS of Eq. 5): for every member in out_mask, write SoA slot s back into record
