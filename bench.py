@@ -534,7 +534,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tiles (no autotuning)")
     ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the batched (patches) forms")
     ap.add_argument("--no-large", dest="large", action="store_false", help="skip the large ten-step run forms")
-    ap.add_argument("--only", choices=["f64", "f32", "batched_f32", "batched_f64"], default=None,
+    ap.add_argument("--only", choices=["f64", "f32", "batched_f32", "batched_f64", "extended_m5"], default=None,
                     help="run one form only (profiling runs); the JSON line then carries that form's numbers")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -567,6 +567,19 @@ def main():
             print(json.dumps({"metric": METRIC, "value": b["value"] * world, "unit": UNIT, "n_gpus": world,
                               "steps": steps, "warmup": warmup, "ms_per_step": b["ms_per_step"],
                               "higher_is_better": True, "form": args.only, "details": b}))
+        return 0
+    if args.only == "extended_m5":
+        # profiling runs of the quartic kernel with the fuller views: that form only
+        lay_e, aos_e, ncell_e = extended_inputs()
+        from paper_2502_16517_gb300 import workloads as wl
+        ext = run_form(0, steps, warmup, dev, aos_e, lay_e, f["box"], ncell_e, tune_cache=tune_cache,
+                       params=dict(wl.SPH_PARAMS, kernel=1, scheme=1), tune_form="grid_m5_extended")
+        se = summarize_form(0, ext, n, steps, world)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": se["value"], "unit": UNIT, "n_gpus": world,
+                              "steps": steps, "warmup": warmup, "ms_per_step": se["ms_per_step"],
+                              "higher_is_better": True, "form": args.only,
+                              "phases_ms_per_step": se["phases_ms_per_step"], "tiles": ext["tiles"]}))
         return 0
     forms = ["f64", "f32"] if args.only is None else [args.only]
     runs = {}

@@ -806,28 +806,41 @@ struct ForceF64 {
 // ------------------------------------------------------------------------------------------------------------
 // Kernel families and the fuller views (FP64, single-grid views).  The two bodies below serve every
 // (kernel, scheme) pair except (cubic, minimal), which DensF64 / ForceF64 cover with the cubic's piece
-// coefficients.  Here the kernel is evaluated from q = r/h as a sum of truncated powers (t)_+ = max(t, 0):
+// coefficients in r.  Here the kernel is evaluated from q = r/h; as sums of truncated powers (t)_+ = max(t, 0):
 //   cubic M4 (support 2h, sigma 1/pi):         f = 1/4 (2 - q)_+^3 - (1 - q)_+^3
 //   quartic M5 (support 5h/2, sigma 1/(20 pi), the paper's kernel, Section 2.1):
 //                                              f = (5/2 - q)_+^4 - 5 (3/2 - q)_+^4 + 10 (1/2 - q)_+^4
-// W = sigma f / h^3, dW/dr = sigma f' / h^4 and dW/dh = -sigma (3 f + q f') / h^4: beyond the support every term
-// is zero, which is the masking of Section 5.6.
+// W = sigma f / h^3, dW/dr = sigma f' / h^4 and dW/dh = -sigma (3 f + q f') / h^4: beyond the support every
+// coefficient is zero, which is the masking of Section 5.6.
 // ------------------------------------------------------------------------------------------------------------
+// f on each piece as a polynomial in q, f = sum_k a_k q^k, the piece chosen by integer compares of the bit
+// pattern of q (for doubles >= 0 the bit patterns order like the values) and every coefficient 0 beyond the
+// support: four FMAs for f, three for f', where the truncated powers cost about twice as many FP64 operations.
+// The expansions (of the truncated-power forms above, term by term):
+//   M4:  q < 1:  1 - 3/2 q^2 + 3/4 q^3            q < 2:  2 - 3q + 3/2 q^2 - 1/4 q^3
+//   M5:  q < 1/2: 115/8 - 15 q^2 + 6 q^4          q < 3/2: 55/4 + 5q - 30 q^2 + 20 q^3 - 4 q^4
+//        q < 5/2: 625/16 - 125/2 q + 75/2 q^2 - 10 q^3 + q^4
 struct KerM4 {
     static constexpr double kappa = 2.0;
     static constexpr float kappaf = 2.0f;
     static constexpr double sigma = kInvPi;
     static __device__ __forceinline__ void f_fp(double q, double &f, double &fp)
     {
-        const double a = fmax(2.0 - q, 0.0), b = fmax(1.0 - q, 0.0);
-        const double a2 = a * a, b2 = b * b;
-        f = fma(0.25 * a2, a, -(b2 * b));
-        fp = fma(-0.75, a2, 3.0 * b2);
+        const long long qb = __double_as_longlong(q);
+        const bool in = qb < 0x3FF0000000000000LL, out = qb < 0x4000000000000000LL;  // q < 1, q < 2
+        const double a3 = in ? 0.75 : (out ? -0.25 : 0.0), a2 = in ? -1.5 : (out ? 1.5 : 0.0);
+        const double a1 = in ? 0.0 : (out ? -3.0 : 0.0), a0 = in ? 1.0 : (out ? 2.0 : 0.0);
+        f = fma(fma(fma(a3, q, a2), q, a1), q, a0);
+        const double b2 = in ? 2.25 : (out ? -0.75 : 0.0), b1 = in ? -3.0 : (out ? 3.0 : 0.0);
+        fp = fma(fma(b2, q, b1), q, a1);
     }
     static __device__ __forceinline__ double fp_only(double q)
     {
-        const double a = fmax(2.0 - q, 0.0), b = fmax(1.0 - q, 0.0);
-        return fma(-0.75, a * a, 3.0 * (b * b));
+        const long long qb = __double_as_longlong(q);
+        const bool in = qb < 0x3FF0000000000000LL, out = qb < 0x4000000000000000LL;
+        const double b2 = in ? 2.25 : (out ? -0.75 : 0.0), b1 = in ? -3.0 : (out ? 3.0 : 0.0);
+        const double b0 = in ? 0.0 : (out ? -3.0 : 0.0);
+        return fma(fma(b2, q, b1), q, b0);
     }
 };
 struct KerM5 {
@@ -836,15 +849,29 @@ struct KerM5 {
     static constexpr double sigma = kInvPi / 20.0;
     static __device__ __forceinline__ void f_fp(double q, double &f, double &fp)
     {
-        const double a = fmax(2.5 - q, 0.0), b = fmax(1.5 - q, 0.0), c = fmax(0.5 - q, 0.0);
-        const double a2 = a * a, b2 = b * b, c2 = c * c;
-        f = fma(10.0 * c2, c2, fma(-5.0 * b2, b2, a2 * a2));
-        fp = fma(-40.0 * c2, c, fma(20.0 * b2, b, -4.0 * (a2 * a)));
+        const long long qb = __double_as_longlong(q);
+        // q < 1/2, q < 3/2, q < 5/2
+        const bool p0 = qb < 0x3FE0000000000000LL, p1 = qb < 0x3FF8000000000000LL, p2 = qb < 0x4004000000000000LL;
+        const double a4 = p0 ? 6.0 : (p1 ? -4.0 : (p2 ? 1.0 : 0.0));
+        const double a3 = p0 ? 0.0 : (p1 ? 20.0 : (p2 ? -10.0 : 0.0));
+        const double a2 = p0 ? -15.0 : (p1 ? -30.0 : (p2 ? 37.5 : 0.0));
+        const double a1 = p0 ? 0.0 : (p1 ? 5.0 : (p2 ? -62.5 : 0.0));
+        const double a0 = p0 ? 14.375 : (p1 ? 13.75 : (p2 ? 39.0625 : 0.0));
+        f = fma(fma(fma(fma(a4, q, a3), q, a2), q, a1), q, a0);
+        const double b3 = p0 ? 24.0 : (p1 ? -16.0 : (p2 ? 4.0 : 0.0));    // 4 a4
+        const double b2 = p0 ? 0.0 : (p1 ? 60.0 : (p2 ? -30.0 : 0.0));    // 3 a3
+        const double b1 = p0 ? -30.0 : (p1 ? -60.0 : (p2 ? 75.0 : 0.0));  // 2 a2
+        fp = fma(fma(fma(b3, q, b2), q, b1), q, a1);
     }
     static __device__ __forceinline__ double fp_only(double q)
     {
-        const double a = fmax(2.5 - q, 0.0), b = fmax(1.5 - q, 0.0), c = fmax(0.5 - q, 0.0);
-        return fma(-40.0 * (c * c), c, fma(20.0 * (b * b), b, -4.0 * ((a * a) * a)));
+        const long long qb = __double_as_longlong(q);
+        const bool p0 = qb < 0x3FE0000000000000LL, p1 = qb < 0x3FF8000000000000LL, p2 = qb < 0x4004000000000000LL;
+        const double b3 = p0 ? 24.0 : (p1 ? -16.0 : (p2 ? 4.0 : 0.0));
+        const double b2 = p0 ? 0.0 : (p1 ? 60.0 : (p2 ? -30.0 : 0.0));
+        const double b1 = p0 ? -30.0 : (p1 ? -60.0 : (p2 ? 75.0 : 0.0));
+        const double b0 = p0 ? 0.0 : (p1 ? 5.0 : (p2 ? -62.5 : 0.0));
+        return fma(fma(fma(b3, q, b2), q, b1), q, b0);
     }
 };
 
@@ -1107,8 +1134,8 @@ struct ForceF64G {
     };
     static constexpr int kStageBytes = NF * 8 + 16 + 4;
     static constexpr int kSlotDoubles = 17;
-    // the fuller view's extra terms need more registers than three 256-thread CTAs per SM leave
-    static constexpr int min_ctas(int) { return Ext ? 2 : 3; }
+    // three 256-thread CTAs per SM, as ForceF64 (the 448 tile's shared memory allows three)
+    static constexpr int min_ctas(int) { return 3; }
     static constexpr int kGroup = 2;
     struct Group {
         Part P0, P1;
