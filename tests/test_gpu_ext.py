@@ -209,3 +209,60 @@ def test_m5_cells_narrower_than_the_support_are_flagged(sph, oracle):
         assert sph.sph_view_status(v, clear=True) & sph.SPH_DEV_H_TOO_BIG
     finally:
         sph.sph_view_destroy(v)
+
+
+def test_extended_m5_kick_drift_kick_and_graph_replay(sph, oracle):
+    """Three leapfrog steps with the quartic kernel and the fuller views against the oracle's composition of the
+    same steps; then the same call through a captured graph, twice, gives the same bytes."""
+    f = wl.jittered_lattice(12, jitter=0.1, vel_sigma=0.2, seed=3)
+    lay = wl.extended_layout()
+    aos_h, _ = wl.pack_aos(f, lay)
+    n = aos_h.shape[0]
+    ncell = wl.ncell_for(f["box"], f["h"].max(), 2.5)
+    params = _params(1, 1)
+    dt, nsteps = 2e-3, 3
+    import torch
+    outs = []
+    side = torch.cuda.Stream(device=H.device())  # a graph is captured on a stream other than the legacy default
+    with torch.cuda.stream(side):
+        for graph in (False, True, True):
+            aos = H.to_dev(aos_h)
+            v = sph.sph_view_create(lay, sph.SPH_F64, n, (f["box"], ncell, True), side.cuda_stream)
+            try:
+                if graph:
+                    sph.sph_step_graph(v, aos, n, params, dt=dt, nsteps=nsteps)   # runs, then captures
+                    aos.copy_(H.to_dev(aos_h))
+                    sph.sph_step_graph(v, aos, n, params, dt=dt, nsteps=nsteps)   # replays
+                else:
+                    sph.sph_step(v, aos, n, params, dt=dt, nsteps=nsteps)
+                sph.sph_view_sync(v)
+                outs.append(aos.cpu().numpy())
+            finally:
+                sph.sph_view_destroy(v)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    st = oracle.unpack(aos_h, lay)
+    x, vel, u = st["x"], st["v"], st["u"]
+
+    def forces(x, vel, u):
+        d = oracle.density_ext(1, x, vel, st["mass"], st["h"], f["box"])
+        P, cs = oracle.eos(d["rho"], u, params["gamma"])
+        a, du, vs = oracle.force_ext(1, True, True, x, vel, st["mass"], st["h"], d["rho"], P, cs, d["omega"],
+                                     d["divv"], d["curlv"], f["box"], True, params["alpha"], params["beta"],
+                                     params["eps"])
+        return d, a, du, vs
+    d, a, du, vs = forces(x, vel, u)
+    for _ in range(nsteps):
+        vel, u = oracle.kick(0.5 * dt, a, du, vel, u)
+        x = oracle.drift(dt, vel, x, f["box"])
+        d, a, du, vs = forces(x, vel, u)
+        vel, u = oracle.kick(0.5 * dt, a, du, vel, u)
+    got = oracle.unpack(outs[0], lay)
+    tol = 1e-10
+    assert H.normwise(got["x"], x) <= tol
+    assert H.normwise(got["v"], vel) <= tol
+    assert H.rel_max(got["u"], u) <= tol
+    assert H.rel_max(got["rho"], d["rho"]) <= tol
+    assert H.rel_max(got["omega"], d["omega"]) <= tol
+    assert H.normwise(got["divv"], d["divv"]) <= tol and H.normwise(got["curlv"], d["curlv"]) <= tol
+    assert H.normwise(got["a"], a) <= tol
+    assert _rel_or_exact(got["vsig"], vs) <= tol
