@@ -10,20 +10,22 @@
 //   2. the active set is staged through shared memory in tiles of TJ particles holding only the SoA members the
 //      loop body reads, plus one float4 per particle for the distance filter; each tile is padded to a multiple
 //      of 64 with sentinel particles that no filter accepts;
-//   3. each warp takes one local particle i at a time: its 32 lanes sweep the tile 64 candidates per step with
-//      the FP32 distance filter, the survivors are compacted (ballot + popc) into a per-warp ring of 128 slots,
-//      and whenever 32 are queued the lanes evaluate the full pair term in the path's precision, one pair per
-//      lane.  Inside the term the support is applied as a mask (the neutral-element formulation of Section 5.6:
+//   3. each warp takes two local particles at a time (their FP64 members in two per-warp shared slots): its 32
+//      lanes sweep the tile 32 candidates per step with the FP32 distance filter for both, the survivors of both
+//      are compacted (ballot + popc) into one per-warp ring of 128 slots, tagged with their particle, and
+//      whenever 32 are queued the lanes evaluate the full pair term in the path's precision, one pair per lane.
+//      Inside the term the support is applied as a mask (the neutral-element formulation of Section 5.6:
 //      out-of-support coefficients are zero, no branch decides whether a term is summed);
-//   4. the per-lane partial sums are combined by shuffles and added to the particle's shared-memory
-//      accumulator; after the last tile each accumulator is finalised and written to the SoA arrays.
-// The compaction keeps the expensive evaluation at ~97 % lane occupancy although only ~15 % of the
+//   4. the per-lane partial sums are combined by reduce-scatters over the warp and added to the particles'
+//      shared-memory accumulators; after the last tile each accumulator is finalised and written to the SoA
+//      arrays.
+// The compaction keeps the expensive evaluation at ~95 % lane occupancy although only ~15 % of the
 // 3^3-stencil candidates lie inside the support (cell edge 2h).
 //
 // FP64 path: positions are the FP64 members; a neighbour across the periodic boundary is staged at its image
 // x_j -+ box, so x_i - x_j needs no wrap test in the pair term (the image differs from the minimum-image difference
-// by the rounding of one addition at the box scale).  The FP32 filter uses cell-relative float copies of the positions with a conservative
-// radius, so it never drops a pair the FP64 test keeps.  The FP64 pipe (1/64 of the FP32 rate on this part) is
+// by the rounding of one addition at the box scale).  The FP32 filter uses cell-relative float copies of the
+// positions with a conservative radius, so it never drops a pair the FP64 test keeps.  The FP64 pipe (1/64 of the FP32 rate on this part) is
 // the bound, so every per-pair FP64 instruction is counted: piece selection and masks run on the integer pipe,
 // reciprocals are FP32-seeded Newton iterations, per-particle factors are precomputed.
 // FP32 path: positions are cell-relative floats (the FP32 view), so x_i - x_j = r_i - (r_j + d * edge) with d the
@@ -1569,7 +1571,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
         for (int t = tid; t < nloc; t += NT) zero_acc<K>(S.acc[t]);
         for (int tb = 0; tb < NJ; tb += tj) {
             const int tn = min(tj, NJ - tb);
-            const int tnp = (tn + kStep - 1) / kStep * kStep;  // padded to whole filter steps (<= tj)
+            const int tnp = (tn + kStep - 1) / kStep * kStep;  // padded to a multiple of kStep (<= tj)
             __syncthreads();  // accumulators zeroed, previous tile consumed
             for (int t = tid; t < tnp; t += NT) {
                 if (t < tn) {
