@@ -471,6 +471,10 @@ struct DensF64 {
 // s >= 2^-24, so sat(2^24 s) counts the pairs in the support.
 struct DensF32 {
     static constexpr bool kMasked = true;
+    // CTAs per SM the register allocation must allow: 40 registers keep twelve 128-thread CTAs (the 1024 tile's
+    // shared memory allows twelve as well)
+    static constexpr int min_ctas(int nt) { return nt == 128 ? 12 : 6; }
+    static constexpr int min_ctas_persist(int nt) { return min_ctas(nt); }
     struct Args {
         PairCommon cm;
         const float *x, *y, *z, *m, *h, *u;
@@ -1295,6 +1299,11 @@ struct ForceF64G {
 // are the filter's hits, r^2 < 4 max(h_i, h_j)^2, minus the self pair of every local particle.
 struct ForceF32 {
     static constexpr bool kMasked = false;
+    // One CTA per cell: no register bound (0); the compiler's own choice (70 registers, seven 128-thread CTAs per
+    // SM) measured faster than a bound of seven CTAs (72 registers), and a bound of eight spills.  The
+    // persistent form (patch views) measured faster with the bound of seven.
+    static constexpr int min_ctas(int) { return 0; }
+    static constexpr int min_ctas_persist(int nt) { return nt == 128 ? 7 : 3; }
     struct Args {
         PairCommon cm;
         const float *x, *y, *z, *vx, *vy, *vz, *m, *h, *rho, *cs;
@@ -1713,7 +1722,7 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
 }
 
 template <class K, int NT>
-__global__ void __launch_bounds__(NT) k_cell_lanes(const typename K::Args A)
+__global__ void __launch_bounds__(NT, K::min_ctas(NT)) k_cell_lanes(const typename K::Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LaneShared<K> S;
@@ -1722,7 +1731,7 @@ __global__ void __launch_bounds__(NT) k_cell_lanes(const typename K::Args A)
 }
 
 template <class K, int NT>
-__global__ void __launch_bounds__(NT) k_cell_lanes_persist(const typename K::Args A,
+__global__ void __launch_bounds__(NT, K::min_ctas_persist(NT)) k_cell_lanes_persist(const typename K::Args A,
                                                                      const int *__restrict__ order,
                                                                      const int *__restrict__ count, int *next)
 {
