@@ -527,7 +527,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-block", type=int, default=10, help="oracle sample cube (lattice spacings) for cpu_baseline")
+    ap.add_argument("--cpu-block", type=int, default=12, help="oracle sample cube (lattice spacings) for cpu_baseline")
     ap.add_argument("--ref-block", type=int, default=4, help="oracle sample cube per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
