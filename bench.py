@@ -184,6 +184,24 @@ EXT_PARAMS_NOTE = ("quartic spline M5 (support 5h/2, the paper's kernel) with th
                    "switch and writes the signal velocity")
 
 
+def presorted_aos(aos_h, lay, box, ncell, dev):
+    """The plain records rearranged in cell order (the paper's continuous AoS, Section 6): the path's own binning of
+    the scattered records gives the slot -> record permutation, and record perm[s] moves to position s.  Host
+    preparation outside every timed region."""
+    import torch
+    from paper_2502_16517_gb300 import sph
+    n = aos_h.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    aos = torch.from_numpy(aos_h).to(dev)
+    view = sph.sph_view_create(lay, 0, n, (box, ncell, True), stream.cuda_stream)
+    try:
+        sph.sph_bin(view, aos, n)
+        perm = sph.sph_view_export_index(view, 0, n)
+    finally:
+        sph.sph_view_destroy(view)
+    return np.ascontiguousarray(aos_h[perm])
+
+
 def extended_inputs():
     """The plain 262,144-particle input on the paper's 272-byte record with the fuller views' members, cells of
     edge >= 5h/2 for the quartic spline."""
@@ -375,10 +393,13 @@ def summarize_form(prec, r, n, steps, world):
         "scatter_GBps": s_bytes / (ph["scatter"] * 1e-3) / 1e9 if ph["scatter"] > 0 else None,
         "gather_bytes_per_step": g_bytes, "scatter_bytes_per_step": s_bytes,
     }
+    # the paper's normalisation: cost per particle update of each loop, and of the whole step
+    upd = {"density_ns": ph["density"] * 1e6 / n, "force_ns": ph["force"] * 1e6 / n,
+           "step_ns": ms / steps * 1e6 / n, "particle_updates_per_s": world * 2.0 * n * steps / (ms / 1e3)}
     return {"value": value, "ms_per_step": ms / steps, "pairs_per_step": pairs_step,
             "density_pairs_per_step": r["counts"][1] / steps, "force_pairs_per_step": r["counts"][2] / steps,
             "candidates_per_step": (r["counts"][0] + r["counts"][3]) / steps, "phases_ms_per_step": ph,
-            "launches": nl, "conversion": conv}
+            "launches": nl, "conversion": conv, "per_particle_update": upd}
 
 
 def max_over_ranks(vals, device=None):
@@ -591,6 +612,7 @@ def main():
                                   tune_cache=tune_cache)
         per_loop = None
         ext = None
+        presorted = {}
         if args.only is None:
             # the paper's conversion pattern: one view per loop, converted forth and back around each
             per_loop = run_form(0, steps, warmup, dev, aos_h, lay, f["box"], ncell, tune_cache=tune_cache,
@@ -602,6 +624,12 @@ def main():
                            params=dict(wl.SPH_PARAMS, kernel=1, scheme=1), tune_form="grid_m5_extended")
             ext["cells"] = int(np.prod(ncell_e))
             del aos_e
+            # the paper's continuous AoS: the same records stored in cell order
+            aos_s = presorted_aos(aos_h, lay, f["box"], ncell, dev)
+            for fm in ("f64", "f32"):
+                presorted[fm] = run_form(0 if fm == "f64" else 1, steps, warmup, dev, aos_s, lay, f["box"], ncell,
+                                         tune_cache=tune_cache)
+            del aos_s
         batched = {}
         if args.batched and args.only is None:
             fp, lay_b, aos_b = batched_inputs()
@@ -634,6 +662,10 @@ def main():
     for k, fm in enumerate(forms):
         runs[fm]["step_ms"] = [tot[k] / steps] * steps
         summ[fm] = summarize_form(0 if fm == "f64" else 1, runs[fm], n, steps, world)
+    for r in [per_loop, ext] + list(presorted.values()):
+        if r is not None:
+            t = max_over_ranks([float(np.sum(r["step_ms"]))], dev)[0]
+            r["step_ms"] = [t / steps] * steps
     for b in batched.values():
         b["ms_per_step"] = max_over_ranks([b["ms_per_step"]], dev)[0]
         b["value"] = whole_job_rate(b["pairs_per_step"], world, b["ms_per_step"] * 1e-3)
@@ -685,6 +717,7 @@ def main():
         "phases_ms_per_step": s64["phases_ms_per_step"],
         "pairs_per_step": s64["pairs_per_step"],
         "candidates_per_step": s64["candidates_per_step"],
+        "per_particle_update": s64["per_particle_update"],
         "conversion": conv,
         "forms": {},
         "wall_s_timed_bracket": r64["wall_s"],
@@ -695,7 +728,8 @@ def main():
             "value": s32["value"], "ms_per_step": s32["ms_per_step"], "dtype": "f32",
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
             "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
-            "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"]}
+            "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"],
+            "per_particle_update": s32["per_particle_update"]}
     if per_loop is not None:
         per_loop["step_ms"] = list(per_loop["step_ms"])
         sp = summarize_form(0, per_loop, n, steps, world)
@@ -716,6 +750,17 @@ def main():
             "pairs_per_step": (ext["counts"][1] + ext["counts"][2]) / steps,
             "phases_ms_per_step": se["phases_ms_per_step"], "gpu_launches": int(sum(se["launches"].values())),
             "tiles": ext["tiles"]}
+    for fm, r in presorted.items():
+        r["step_ms"] = list(r["step_ms"])
+        sp = summarize_form(0 if fm == "f64" else 1, r, n, steps, world)
+        ref = summ.get(fm)
+        line["forms"][f"{fm}_presorted_aos"] = {
+            "workload": ("the plain input with its records stored in cell order (continuous AoS) instead of "
+                         "scattered; otherwise as the " + ("FP64" if fm == "f64" else "FP32") + " form"),
+            "value": sp["value"], "ms_per_step": sp["ms_per_step"], "dtype": fm,
+            "vs_scattered": sp["value"] / ref["value"] if ref else None,
+            "phases_ms_per_step": sp["phases_ms_per_step"], "conversion": sp["conversion"],
+            "gpu_launches": int(sum(sp["launches"].values()))}
     for form, b in large.items():
         b = dict(b)
         b["workload"] = ("large run: 2,097,152 particles, 8 Gaussian overdensities (sigma 0.05, 4x) on a uniform "

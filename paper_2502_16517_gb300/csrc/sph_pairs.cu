@@ -335,6 +335,7 @@ struct DensF64 {
     using Acc = double;
     static constexpr int kStageBytes = 4 * 8 + 16;
     static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
+    static constexpr bool kSkipSelf = false;  // rho_i includes m_i W(0, h_i)
     // CTAs per SM the register allocation must allow: shared memory allows seven of 128 threads at a 512 tile
     static constexpr int min_ctas(int nt) { return nt == 128 ? 7 : 3; }
     // The warp's lane partials of four local particles (u = 0..3) are reduced together: a reduce-scatter (xor 16
@@ -628,7 +629,6 @@ struct ForceF64 {
     struct Tile {
         double *d;
         float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
-        int *slot;
     };
     // The local particle: its FP64 members sit in the warp's shared slot (s[f], read again in every evaluation
     // round, which keeps them out of the registers); only the filter's FP32 copies stay in registers.
@@ -643,8 +643,10 @@ struct ForceF64 {
     struct Acc {
         double ax, ay, az, du;
     };
-    static constexpr int kStageBytes = NF * 8 + 16 + 4;
+    static constexpr int kStageBytes = NF * 8 + 16;
     static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
+    // The self pair contributes nothing (j != i in the sums), so the queue driver drops it at the filter.
+    static constexpr bool kSkipSelf = true;
     // CTAs per SM the register allocation must allow: shared memory allows three at a 448 tile (85 registers
     // at 256 threads)
     static constexpr int min_ctas(int) { return 3; }
@@ -694,7 +696,6 @@ struct ForceF64 {
         Tile t;
         t.d = reinterpret_cast<double *>(s);
         t.f4 = reinterpret_cast<float4 *>(t.d + NF * tj);
-        t.slot = reinterpret_cast<int *>(t.f4 + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
@@ -716,7 +717,6 @@ struct ForceF64 {
         for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               A.hf[slot]);
-        T.slot[t] = slot;
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     // Called by the whole warp; ws is the warp's slot (kSlotDoubles doubles of shared memory).
@@ -779,18 +779,12 @@ struct ForceF64 {
         const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
         const double aF = lds(L_ + AP) * Fi;
         const double mj = R_[M];
-        double coef = mj * fma(R_[AP], Fj, aF + V);
-        double dcoef = (mj * vdotr) * fma(0.5, V, aF);
-        const bool self = T.slot[k] == i;
-        if (self) {
-            coef = 0.0;
-            dcoef = 0.0;
-        }
+        const double coef = mj * fma(R_[AP], Fj, aF + V);
         P.ax = fma(-coef, dx, P.ax);
         P.ay = fma(-coef, dy, P.ay);
         P.az = fma(-coef, dz, P.az);
-        P.du += dcoef;
-        return !self && (io || jo);
+        P.du = fma(mj * vdotr, fma(0.5, V, aF), P.du);
+        return io || jo;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
@@ -949,6 +943,7 @@ struct DensF64G {
     };
     static constexpr int kStageBytes = kRow * 8 + 16;
     static constexpr int kSlotDoubles = 17;
+    static constexpr bool kSkipSelf = false;  // the sums include the self term
     static constexpr int min_ctas(int nt) { return nt == 128 ? 6 : 3; }
     // the two particles of a warp's queue: Ext reduces 12 sums with one 16-value reduce-scatter, the plain
     // density its 2 sums; the neighbour counts are integer warp sums
@@ -1125,7 +1120,6 @@ struct ForceF64G {
     struct Tile {
         double *d;
         float4 *f4;
-        int *slot;
     };
     struct Lhs {
         const double *s;
@@ -1138,8 +1132,9 @@ struct ForceF64G {
     struct Acc {
         double ax, ay, az, du, vs;
     };
-    static constexpr int kStageBytes = NF * 8 + 16 + 4;
+    static constexpr int kStageBytes = NF * 8 + 16;
     static constexpr int kSlotDoubles = 17;
+    static constexpr bool kSkipSelf = true;  // as ForceF64
     // three 256-thread CTAs per SM, as ForceF64 (the 448 tile's shared memory allows three)
     static constexpr int min_ctas(int) { return 3; }
     static constexpr int kGroup = 2;
@@ -1182,7 +1177,6 @@ struct ForceF64G {
         Tile t;
         t.d = reinterpret_cast<double *>(s);
         t.f4 = reinterpret_cast<float4 *>(t.d + NF * tj);
-        t.slot = reinterpret_cast<int *>(t.f4 + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
@@ -1202,7 +1196,6 @@ struct ForceF64G {
         for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               A.hf[slot]);
-        T.slot[t] = slot;
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     static __device__ __forceinline__ Lhs load(const Args &A, int i, float margin, double *ws)
@@ -1254,18 +1247,12 @@ struct ForceF64G {
         const double V = Ph * (Fi + Fj);
         const double aF = lds(L_ + AP) * Fi;
         const double mj = R_[M];
-        double coef = mj * fma(R_[AP], Fj, aF + V);
-        double dcoef = (mj * vdotr) * fma(0.5, V, aF);
-        const bool self = T.slot[k] == i;
-        const bool in = !self && (qi < Ker::kappa || qj < Ker::kappa);
-        if (self) {
-            coef = 0.0;
-            dcoef = 0.0;
-        }
+        const double coef = mj * fma(R_[AP], Fj, aF + V);
+        const bool in = qi < Ker::kappa || qj < Ker::kappa;
         P.ax = fma(-coef, dx, P.ax);
         P.ay = fma(-coef, dy, P.ay);
         P.az = fma(-coef, dz, P.az);
-        P.du += dcoef;
+        P.du = fma(mj * vdotr, fma(0.5, V, aF), P.du);
         if constexpr (Ext) {
             const double w = vdotr * rinv;
             const double vs = (lds(L_ + CS) + R_[CS]) - 3.0 * fmin(w, 0.0);
@@ -1483,10 +1470,13 @@ struct PairShared {
 // belong to: only the last round of the pair of particles runs part-full, where one particle per warp would leave
 // a part-full round per particle.  Each lane evaluates with the members of its entry's particle (shared slot 0 or
 // 1) into that particle's partial sums; the partials are reduced over the warp kGroup particles at a time.
+// With K::kSkipSelf the filter drops each particle's own entry: the local cell is neighbour 13 of the table (the
+// periodic domains have at least 3 cells per axis, so it appears once), which puts slot i at tile position
+// pref[13] + (i - start[13]) - tb.
 template <class K, int NT>
 __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const typename K::Tile &T,
-                                           PairShared<K, NT> &S, int ib, int nloc, int tnp, float margin, bool wrap,
-                                           unsigned long long &my_pairs)
+                                           PairShared<K, NT> &S, int ib, int nloc, int tb, int tnp, float margin,
+                                           bool wrap, unsigned long long &my_pairs)
 {
     constexpr int W = NT / 32;
     constexpr int kTag = 1 << 14;  // entry = candidate | kTag for the second particle (candidates < 4096)
@@ -1518,10 +1508,11 @@ __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const type
             const unsigned b = __ballot_sync(kFull, in);  // every lane votes
             if (lane == 0) my_pairs += __popc(b);
         };
+        const int self0 = nb.pref[13] + (i0 - nb.start[13]) - tb;  // tile position of i0 (i1 follows it)
         for (int jb = 0; jb < tnp; jb += 32) {
             const int k = jb + lane;
-            const bool p0 = K::filter(L0, T, k);
-            const bool p1 = two && K::filter(L1, T, k);
+            const bool p0 = K::filter(L0, T, k) && (!K::kSkipSelf || k != self0);
+            const bool p1 = two && K::filter(L1, T, k) && (!K::kSkipSelf || k != self0 + 1);
             const unsigned b0 = __ballot_sync(kFull, p0);
             const unsigned b1 = __ballot_sync(kFull, p1);
             const int c0 = __popc(b0);
@@ -1592,7 +1583,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            tile_pairs<K, NT>(A, T, S, ib, nloc, tnp, margin, wrap, my_pairs);
+            tile_pairs<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, my_pairs);
         }
         __syncthreads();
         for (int t = tid; t < nloc; t += NT) K::finish(A, ib + t, S.acc[t]);
