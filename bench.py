@@ -458,7 +458,8 @@ def roofline_of(prec, s, steps, peaks, measured=None):
     dur = ph[dom] * 1e-3  # one launch of the pair kernel per step
     achieved = flops / dur / 1e12
     peak = PEAK_FP64_TFLOPS if prec == 0 else PEAK_FP32_TFLOPS
-    kernel = (f"k_cell_pairs<{'Force' if dom == 'force' else 'Dens'}F64>" if prec == 0 else
+    # (the FP64 force body is instantiated per softening: eps > 0 here)
+    kernel = (("k_cell_pairs<ForceF64<true>>" if dom == "force" else "k_cell_pairs<DensF64>") if prec == 0 else
               f"k_cell_lanes<{'Force' if dom == 'force' else 'Dens'}F32>")
     traffic, traffic_src = profiled_traffic(kernel)
     return {"kernel": kernel,

@@ -116,12 +116,12 @@ struct Scratch {
     //         d[0] 1/h, d[1] sigma/h^3, d[2] sigma/h^4, d[6] c_s
     //   FP64 force, other kernels / the extended scheme: d[0] h/2, d[1] 1/h, d[2] sigma/h^4, d[3] P/(Omega rho^2),
     //         d[4] alpha c / 2, d[5] the Balsara switch
-    //   FP64 force: d[0] h/2, d[1] -3/(pi h^4), d[2] 3/(pi h^5), d[3] 9/(4 pi h^6), d[4] -3/(4 pi h^6), d[5] P/rho^2,
-    //         d[6] alpha c / 2
+    //   FP64 force: d[0] s h/2, d[1] -3/(pi h^4), d[2] 3/(pi h^5), d[3] 9/(4 pi h^6), d[4] -3/(4 pi h^6),
+    //         d[5] P/rho^2, d[6] alpha c / (2 s), d[7] (h/2)^2, with s = sqrt(eps) for eps > 0, else 1
     //   FP32: d[0] 1/h, d[1] 1/(pi h^5), d[2] P/rho^2
     void *d[8];
 };
-constexpr int kDerivedF64 = 7;
+constexpr int kDerivedF64 = 8;
 constexpr int kDerivedF32 = 3;
 
 struct Counters {

@@ -607,27 +607,38 @@ struct DensF32 {
 };
 
 // ---- force, FP64 ----
-// Per particle (k_force_prep_f64): hh = h/2, the gradient coefficients S0 = -3/(pi h^4), K1 = 3/(pi h^5),
-// K2i = 2.25/(pi h^6), K2o = -0.75/(pi h^6) so that grad_i W(r_ij, h) = F r_ij with
-//   F = K2i r - K1                  (r < h)
-//   F = S0 / r + K2o r + K1         (h <= r < 2h),   0 beyond,
-// A = P / rho^2 and ach = alpha c / 2.  Per pair the piece of each side is chosen by integer compares of
-// bits(r) - 2^52 (= bits(r/2)) and bits(r) - 2^53 (= bits(r/4)) against bits(hh); F then costs two FMAs.
+// Per particle (k_force_prep_f64): q2 = (h/2)^2 and the gradient coefficients S0 = -3/(pi h^4), K1 = 3/(pi h^5),
+// K2i = 2.25/(pi h^6), K2o = -0.75/(pi h^6), so that grad_i W(r_ij, h) = F r_ij with
+//   F = (K2i r^2) / r - K1            (r < h)
+//   F = (S0 + K2o r^2) / r + K1       (h <= r < 2h),   0 beyond,
+// i.e. F = fma(fma(a, r^2, b), 1/r, c) with (a, b, c) of the piece, which the pair picks for each side by integer
+// compares of bits(r^2) - 2^53 (= bits(r^2/4)) and bits(r^2) - 2^54 (= bits(r^2/16)) against bits(q2): r itself is
+// never formed.  A = P / rho^2.
+// The viscosity (Monaghan): mu = hbar w / D1 with w = v_ij . r_ij, D1 = r^2 + eps hbar^2, hbar = (h_i + h_j)/2,
+// D2 = rho_i + rho_j, and Pi / 2 = mu (beta mu - alpha cbar) / D2.  With soft (eps > 0) and s = sqrt(eps), each
+// particle carries hs = s h/2 and acs = alpha c / (2 s): then hbs = hs_i + hs_j = s hbar, D1 = hbs^2 + r^2, and
+// with R = 1 / (D1 D2), g = hbs w R (= s mu / D2) and mu' = g D2 (= s mu),
+//   Pi / 2 = g (beta/eps mu' - (acs_i + acs_j)),
+// the same value with no multiplication by eps per pair.  Without softening (eps = 0): s = 1 and D1 = r^2.
+template <bool kSoft>
 struct ForceF64 {
     // The 15 FP64 members a pair term reads from either particle, in this order (per-particle arrays in Args,
-    // one row per candidate in the tile).
-    enum { X, Y, Z, VX, VY, VZ, M, HH, S0, K1, K2I, K2O, AP, ACH, RHO, NF };
+    // one row per candidate in the tile); q2 is staged beside the rows.
+    enum { X, Y, Z, VX, VY, VZ, M, HS, S0, K1, K2I, K2O, AP, ACS, RHO, NF };
+    static constexpr int Q2 = NF;  // its place in the local particle's slot
     struct Args {
         PairCommon cm;
-        const double *f[NF];                // x, y, z, v, m, rho and (k_force_prep_f64) hh .. ach
+        const double *f[NF];                // x, y, z, v, m, rho and (k_force_prep_f64) hs .. acs
+        const double *q2;                   // (h/2)^2 (k_force_prep_f64)
         const float *xf, *yf, *zf, *hf;     // filter copies
         double *ax, *ay, *az, *dudt;
-        double beta, eps;
+        double beta_s;                      // beta / eps (soft), else beta
     };
     // Candidate k's members at d[k * NF + f]: one row address serves all fifteen loads (NF is odd, so 64-bit
-    // loads of 32 different rows hit distinct bank pairs).
+    // loads of 32 different rows hit distinct bank pairs); its q2 at q[k] (likewise).
     struct Tile {
         double *d;
+        double *q;
         float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
     };
     // The local particle: its FP64 members sit in the warp's shared slot (s[f], read again in every evaluation
@@ -643,7 +654,7 @@ struct ForceF64 {
     struct Acc {
         double ax, ay, az, du;
     };
-    static constexpr int kStageBytes = NF * 8 + 16;
+    static constexpr int kStageBytes = NF * 8 + 8 + 16;
     static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
     // The self pair contributes nothing (j != i in the sums), so the queue driver drops it at the filter.
     static constexpr bool kSkipSelf = true;
@@ -695,7 +706,8 @@ struct ForceF64 {
     {
         Tile t;
         t.d = reinterpret_cast<double *>(s);
-        t.f4 = reinterpret_cast<float4 *>(t.d + NF * tj);
+        t.q = t.d + NF * tj;
+        t.f4 = reinterpret_cast<float4 *>(t.q + tj);
         return t;
     }
     static __device__ __forceinline__ void stage(const Args &A, const Tile &T, const NbrTable &nb, int t,
@@ -715,6 +727,7 @@ struct ForceF64 {
         row[Z] = zs;
 #pragma unroll
         for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
+        T.q[t] = A.q2[slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
                               A.hf[slot]);
     }
@@ -724,6 +737,7 @@ struct ForceF64 {
     {
         const int lane = threadIdx.x & 31;
         if (lane < NF) ws[lane] = A.f[lane][i];
+        else if (lane == Q2) ws[Q2] = A.q2[i];
         __syncwarp();
         Lhs L;
         L.s = ws;
@@ -749,31 +763,26 @@ struct ForceF64 {
         const double dx = lds(L_ + X) - R_[X], dy = lds(L_ + Y) - R_[Y], dz = lds(L_ + Z) - R_[Z];
         const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double rinv = rsqrt_seeded(r2);
-        const double r = r2 * rinv;
-        const long long rb = __double_as_longlong(r);
-        const long long rh = rb - (1LL << 52), rq = rb - (2LL << 52);  // bits of r/2 and r/4
-        const double hhi = lds(L_ + HH), hhj = R_[HH];
-        const long long hbi = __double_as_longlong(hhi), hbj = __double_as_longlong(hhj);
-        const bool ii = rh < hbi, io = rq < hbi;  // r < h_i, r < 2 h_i
-        const bool ji = rh < hbj, jo = rq < hbj;  // r < h_j, r < 2 h_j
+        const long long rb = __double_as_longlong(r2);
+        const long long r4 = rb - (2LL << 52), r16 = rb - (4LL << 52);  // bits of r^2/4 and r^2/16
+        const long long qbi = __double_as_longlong(lds(L_ + Q2)), qbj = __double_as_longlong(T.q[k]);
+        const bool ii = r4 < qbi, io = r16 < qbi;  // r < h_i, r < 2 h_i
+        const bool ji = r4 < qbj, jo = r16 < qbj;  // r < h_j, r < 2 h_j
         const double K1i = lds(L_ + K1);
-        const double Fi = fma(ii ? 0.0 : (io ? lds(L_ + S0) : 0.0), rinv,
-                              fma(ii ? lds(L_ + K2I) : (io ? lds(L_ + K2O) : 0.0), r, ii ? -K1i : (io ? K1i : 0.0)));
+        const double Fi = fma(fma(ii ? lds(L_ + K2I) : (io ? lds(L_ + K2O) : 0.0), r2, ii ? 0.0 : (io ? lds(L_ + S0) : 0.0)),
+                              rinv, ii ? -K1i : (io ? K1i : 0.0));
         const double K1j = R_[K1];
-        const double Fj = fma(ji ? 0.0 : (jo ? R_[S0] : 0.0), rinv,
-                              fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r, ji ? -K1j : (jo ? K1j : 0.0)));
+        const double Fj = fma(fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r2, ji ? 0.0 : (jo ? R_[S0] : 0.0)),
+                              rinv, ji ? -K1j : (jo ? K1j : 0.0));
         const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
-        // Monaghan viscosity, Ph = Pi / 2 = mu (beta mu - alpha cbar) / D2 with mu = w / D1, w = hbar v.r,
-        // D1 = r^2 + eps hbar^2, D2 = rho_i + rho_j: one reciprocal R = 1 / (D1 D2) gives g = w R = mu / D2,
-        // mu = g D2 and Ph = g (beta mu - alpha cbar).
-        const double hb = hhi + hhj;
-        const double D1 = fma(A.eps * hb, hb, r2);
+        const double hbs = lds(L_ + HS) + R_[HS];
+        const double D1 = kSoft ? fma(hbs, hbs, r2) : r2;
         const double D2 = lds(L_ + RHO) + R_[RHO];
         const double R = rcp_seeded(D1 * D2);
-        const double g = (hb * vdotr) * R;
+        const double g = (hbs * vdotr) * R;
         const double mu = g * D2;
-        const double t = fma(A.beta, mu, -(lds(L_ + ACH) + R_[ACH]));
+        const double t = fma(A.beta_s, mu, -(lds(L_ + ACS) + R_[ACS]));
         double Ph = g * t;
         if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
         const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
@@ -1282,8 +1291,9 @@ struct ForceF64G {
 // grad_i W(r_ij, h) = F r_ij with F = 3 (t^2 - s^2) / (pi h^4 r), s = sat(1 - q/2), t = sat(1 - q) (the derivative
 // of f = 2 s^3 - t^3); 3/(pi h^4) comes per particle from k_force_prep_f32.  The viscosity uses
 // min(v_ij . r_ij, 0), which makes Pi_ij vanish for receding pairs without a branch.  A pair at r = 0 (the self
-// pair, or two coincident particles) contributes exactly 0: q = 0 gives F = 0, and r_ij = 0.  The pairs counted
-// are the filter's hits, r^2 < 4 max(h_i, h_j)^2, minus the self pair of every local particle.
+// pair, or two coincident particles) contributes exactly 0: q = 0 gives F = 0, r_ij = 0, and D1 >= 1e-30 keeps
+// the viscosity finite (0) there when eps = 0.  The pairs counted are the filter's hits,
+// r^2 < 4 max(h_i, h_j)^2, minus the self pair of every local particle.
 struct ForceF32 {
     static constexpr bool kMasked = false;
     // One CTA per cell: no register bound (0); the compiler's own choice (70 registers, seven 128-thread CTAs per
@@ -1379,7 +1389,8 @@ struct ForceF32 {
         const float2 dxy = __ffma2_rn(make_float2(p.x, p.y), neg, make_float2(L.x, L.y));
         const float dz = L.z - p.z;
         const float r2 = fmaf(dxy.x, dxy.x, fmaf(dxy.y, dxy.y, dz * dz));
-        const float rinv = rsqrt_ftz(r2 + 1e-30f);
+        const float r2e = r2 + 1e-30f;  // > 0 at r = 0; equal to r2 for r2 >= 2^-75
+        const float rinv = rsqrt_ftz(r2e);
         const float r = r2 * rinv;
         const float2 q = __fmul2_rn(make_float2(r, r), make_float2(L.hinv, g.y));  // q_i, q_j
         const float2 sq = make_float2(fma_sat(-0.5f, q.x, 1.0f), fma_sat(-0.5f, q.y, 1.0f));
@@ -1393,7 +1404,7 @@ struct ForceF32 {
         const float vneg = 0.5f * (vdotr - fabsf(vdotr));  // min(v_ij . r_ij, 0)
         const float2 hc = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(make_float2(L.h, L.c), make_float2(g.x, cr.x)));
         const float hb = hc.x, cb = hc.y;  // hbar, cbar
-        const float D1 = fmaf(A.eps * hb, hb, r2);
+        const float D1 = fmaf(A.eps * hb, hb, r2e);  // finite R at r = 0 even for eps = 0
         const float D2 = L.rho + cr.y;
         const float R = rcp_ftz(D1 * D2);
         const float2 m1 = __fmul2_rn(make_float2(hb, D2), make_float2(vneg, R));
@@ -1911,26 +1922,28 @@ __global__ void k_force_prep_f32(const float *__restrict__ h, const float *__res
     A[s] = P[s] / (r * r);
 }
 
-// Per-particle quantities of the FP64 force loop (see ForceF64).
+// Per-particle quantities of the FP64 force loop (see ForceF64); sc = sqrt(eps) with softening, else 1.
 __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__restrict__ P,
-                                 const double *__restrict__ rho, const double *__restrict__ cs, double alpha, int n,
-                                 double *__restrict__ hh, double *__restrict__ S0, double *__restrict__ K1,
-                                 double *__restrict__ K2i, double *__restrict__ K2o, double *__restrict__ A,
-                                 double *__restrict__ ach)
+                                 const double *__restrict__ rho, const double *__restrict__ cs, double alpha,
+                                 double sc, int n, double *__restrict__ hs, double *__restrict__ q2,
+                                 double *__restrict__ S0, double *__restrict__ K1, double *__restrict__ K2i,
+                                 double *__restrict__ K2o, double *__restrict__ A, double *__restrict__ acs)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double hv = h[s];
     const double hi = 1.0 / hv, h2 = hi * hi;
     const double s4 = kInvPi * h2 * h2;  // 1/(pi h^4)
-    hh[s] = 0.5 * hv;
+    const double hh = 0.5 * hv;
+    hs[s] = sc * hh;
+    q2[s] = hh * hh;
     S0[s] = -3.0 * s4;
     K1[s] = 3.0 * s4 * hi;
     K2i[s] = 2.25 * s4 * h2;
     K2o[s] = -0.75 * s4 * h2;
     const double r = rho[s];
     A[s] = P[s] / (r * r);
-    ach[s] = 0.5 * alpha * cs[s];
+    acs[s] = (0.5 * alpha) * cs[s] / sc;
 }
 
 // Per-particle set-up of the kernel-family density (DensF64G): cell-relative float positions (filter), 1/h,
@@ -2122,11 +2135,13 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
                                     n, g, scr.xf, scr.yf, scr.zf, scr.hf);
         const bool ext = prm.scheme == SPH_SCHEME_EXTENDED;
         if (prm.kernel == SPH_KERNEL_M4 && !ext) {
+            const double sc = prm.eps > 0.0 ? sqrt(prm.eps) : 1.0;
             k_force_prep_f64<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
                                                  (const double *)soa.p[SPH_RHO][0],
-                                                 (const double *)soa.p[SPH_CS][0], alpha, n, (double *)scr.d[0],
-                                                 (double *)scr.d[1], (double *)scr.d[2], (double *)scr.d[3],
-                                                 (double *)scr.d[4], (double *)scr.d[5], (double *)scr.d[6]);
+                                                 (const double *)soa.p[SPH_CS][0], alpha, sc, n, (double *)scr.d[0],
+                                                 (double *)scr.d[7], (double *)scr.d[1], (double *)scr.d[2],
+                                                 (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
+                                                 (double *)scr.d[6]);
         } else if (prm.kernel == SPH_KERNEL_M5) {
             if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, st);
             else force_prep_g<KerM5, false>(soa, scr, n, alpha, st);
@@ -2278,6 +2293,46 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
     return run_cells<DensF32>(A, ncells, pl, st);
 }
 
+namespace {
+
+template <bool kSoft>
+cudaError_t force_pairs_f64(const SoaPtrs &soa, const Scratch &scr, PairCommon cm, int tj, const sph_params &prm,
+                            int ncells, const PairLaunch &pl, cudaStream_t st)
+{
+    using F = ForceF64<kSoft>;
+    typename F::Args A;
+    cm.tj = tile_or_default(tj, 448);  // 144 B per staged particle: three 256-thread CTAs per SM
+    A.cm = cm;
+    A.f[F::X] = (const double *)soa.p[SPH_X][0];
+    A.f[F::Y] = (const double *)soa.p[SPH_X][1];
+    A.f[F::Z] = (const double *)soa.p[SPH_X][2];
+    A.f[F::VX] = (const double *)soa.p[SPH_V][0];
+    A.f[F::VY] = (const double *)soa.p[SPH_V][1];
+    A.f[F::VZ] = (const double *)soa.p[SPH_V][2];
+    A.f[F::M] = (const double *)soa.p[SPH_MASS][0];
+    A.f[F::RHO] = (const double *)soa.p[SPH_RHO][0];
+    A.f[F::HS] = (const double *)scr.d[0];
+    A.f[F::S0] = (const double *)scr.d[1];
+    A.f[F::K1] = (const double *)scr.d[2];
+    A.f[F::K2I] = (const double *)scr.d[3];
+    A.f[F::K2O] = (const double *)scr.d[4];
+    A.f[F::AP] = (const double *)scr.d[5];
+    A.f[F::ACS] = (const double *)scr.d[6];
+    A.q2 = (const double *)scr.d[7];
+    A.xf = scr.xf;
+    A.yf = scr.yf;
+    A.zf = scr.zf;
+    A.hf = scr.hf;
+    A.ax = (double *)soa.p[SPH_A][0];
+    A.ay = (double *)soa.p[SPH_A][1];
+    A.az = (double *)soa.p[SPH_A][2];
+    A.dudt = (double *)soa.p[SPH_DUDT][0];
+    A.beta_s = kSoft ? prm.beta / prm.eps : prm.beta;
+    return run_cells<F>(A, ncells, pl, st);
+}
+
+}  // namespace
+
 cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_start,
                                int ncells, int n, const CellSpace &g, const sph_params &prm, const PairLaunch &pl,
                                unsigned *status, Counters *counters, cudaStream_t st, int *nl)
@@ -2291,38 +2346,8 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
                                                  : force_pairs_g<KerM5, false>(soa, scr, cm, tj, prm, ncells, pl, st);
     }
     if (!f32 && prm.scheme == SPH_SCHEME_EXTENDED) return force_pairs_g<KerM4, true>(soa, scr, cm, tj, prm, ncells, pl, st);
-    if (!f32) {
-        ForceF64::Args A;
-        cm.tj = tile_or_default(tj, 448);  // 140 B per staged particle: three 256-thread CTAs per SM
-        A.cm = cm;
-        using F = ForceF64;
-        A.f[F::X] = (const double *)soa.p[SPH_X][0];
-        A.f[F::Y] = (const double *)soa.p[SPH_X][1];
-        A.f[F::Z] = (const double *)soa.p[SPH_X][2];
-        A.f[F::VX] = (const double *)soa.p[SPH_V][0];
-        A.f[F::VY] = (const double *)soa.p[SPH_V][1];
-        A.f[F::VZ] = (const double *)soa.p[SPH_V][2];
-        A.f[F::M] = (const double *)soa.p[SPH_MASS][0];
-        A.f[F::RHO] = (const double *)soa.p[SPH_RHO][0];
-        A.f[F::HH] = (const double *)scr.d[0];
-        A.f[F::S0] = (const double *)scr.d[1];
-        A.f[F::K1] = (const double *)scr.d[2];
-        A.f[F::K2I] = (const double *)scr.d[3];
-        A.f[F::K2O] = (const double *)scr.d[4];
-        A.f[F::AP] = (const double *)scr.d[5];
-        A.f[F::ACH] = (const double *)scr.d[6];
-        A.xf = scr.xf;
-        A.yf = scr.yf;
-        A.zf = scr.zf;
-        A.hf = scr.hf;
-        A.ax = (double *)soa.p[SPH_A][0];
-        A.ay = (double *)soa.p[SPH_A][1];
-        A.az = (double *)soa.p[SPH_A][2];
-        A.dudt = (double *)soa.p[SPH_DUDT][0];
-        A.beta = prm.beta;
-        A.eps = prm.eps;
-        return run_cells<ForceF64>(A, ncells, pl, st);
-    }
+    if (!f32) return prm.eps > 0.0 ? force_pairs_f64<true>(soa, scr, cm, tj, prm, ncells, pl, st)
+                                   : force_pairs_f64<false>(soa, scr, cm, tj, prm, ncells, pl, st);
     ForceF32::Args A;
     cm.tj = tile_or_default(tj, 512);
     A.cm = cm;

@@ -447,6 +447,7 @@ sph_status density_launch(sph_view_s *v, const sph_params *p, const int *skip)
 sph_status check_scheme(const sph_view_s *v, const sph_params *p)
 {
     if (!p) return SPH_E_INVAL;
+    if (!(p->eps >= 0.0) || !(p->eps < 1e300)) return SPH_E_INVAL;  // the softening must be finite and >= 0
     if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M5) return SPH_E_INVAL;
     if (p->scheme != SPH_SCHEME_MINIMAL && p->scheme != SPH_SCHEME_EXTENDED) return SPH_E_INVAL;
     if ((p->kernel != SPH_KERNEL_M4 || p->scheme != SPH_SCHEME_MINIMAL) && (v->prec != SPH_F64 || v->npatch_max > 0))

@@ -26,13 +26,15 @@ def sph():
 
 
 def _check(oracle, f, prec, periodic=True, ncell=None, order="shuffled", layout=None, label="",
-           separate_calls=True):
+           separate_calls=True, params=None):
     lay = layout or wl.default_layout()
+    params = params or wl.SPH_PARAMS
     aos_h, _ = wl.pack_aos(f, lay, order=order)
     ncell = wl.ncell_for(f["box"], f["h"].max()) if ncell is None else np.asarray(ncell, np.int32)
-    out, info = H.run_step(aos_h, lay, f["box"], ncell, prec, periodic, separate_calls=separate_calls)
+    out, info = H.run_step(aos_h, lay, f["box"], ncell, prec, periodic, params=params,
+                           separate_calls=separate_calls)
     got = oracle.unpack(out, lay)
-    ref = oracle.step_all(aos_h, lay, f["box"], wl.SPH_PARAMS, periodic)
+    ref = oracle.step_all(aos_h, lay, f["box"], params, periodic)
     errs = H.compare_fields(got, ref, prec, label)
     wm = H.written_mask(lay, ("rho", "P", "cs", "a", "dudt"))
     assert np.array_equal(out[:, ~wm], aos_h[:, ~wm]), "bytes outside the written members changed"
@@ -61,6 +63,20 @@ def test_random_ragged_unequal_h(sph, oracle, prec, seed):
          "mass": rng.uniform(0.5, 1.5, size=n) / n, "h": rng.uniform(0.04, 0.08, size=n),
          "u": rng.uniform(0.5, 1.5, size=n), "box": np.ones(3)}
     _check(oracle, f, prec, label=f"random{seed}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("visc", [{"eps": 0.0}, {"eps": 0.3, "alpha": 0.5, "beta": 1.0}], ids=["eps0", "eps0.3"])
+def test_viscosity_parameters(sph, oracle, prec, visc):
+    """No softening (eps = 0: D1 = r^2, the FP64 force's unsoftened variant) and a strong one with other alpha
+    and beta, on random particles with unequal h, approaching and receding pairs, and no coincident pair (with
+    eps = 0 the viscosity of a coincident pair is 0/0)."""
+    rng = np.random.default_rng(11)
+    n = 2100
+    f = {"x": rng.uniform(0, 1, size=(n, 3)), "v": rng.normal(0, 0.5, size=(n, 3)),
+         "mass": rng.uniform(0.5, 1.5, size=n) / n, "h": rng.uniform(0.04, 0.08, size=n),
+         "u": rng.uniform(0.5, 1.5, size=n), "box": np.ones(3)}
+    _check(oracle, f, prec, label=f"visc{visc['eps']}", params=dict(wl.SPH_PARAMS, **visc))
 
 
 @pytest.mark.parametrize("prec", [0, 1])

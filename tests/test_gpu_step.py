@@ -99,6 +99,10 @@ def test_call_order_and_argument_errors(sph):
         with pytest.raises(sph.SphError) as e:
             sph.sph_force(v, wl.SPH_PARAMS)
         assert e.value.status == sph.SPH_E_STATE
+        for eps in (-0.01, float("nan"), float("inf")):           # the softening must be finite and >= 0
+            with pytest.raises(sph.SphError) as e:
+                sph.sph_density(v, dict(wl.SPH_PARAMS, eps=eps))
+            assert e.value.status == sph.SPH_E_INVAL
         sph.sph_density(v, wl.SPH_PARAMS)
         sph.sph_soa_to_aos(v, aos, n, sph.SPH_DENSITY_OUT)
         sph.sph_bin(v, aos, n)                                     # re-binning invalidates the view
