@@ -132,8 +132,8 @@ typedef enum sph_kernel { SPH_KERNEL_M4 = 0, SPH_KERNEL_M5 = 1 } sph_kernel;
  *                        (SPH_FORCE_*_EXT). */
 typedef enum sph_scheme { SPH_SCHEME_MINIMAL = 0, SPH_SCHEME_EXTENDED = 1 } sph_scheme;
 
-/* Physics constants: ideal gas gamma; Monaghan viscosity alpha, beta, eps; the kernel and the equation set
- * (zero: the cubic spline and the minimal set).  Any kernel or scheme other than (M4, minimal) needs an FP64
+/* Physics constants: ideal gas gamma; Monaghan viscosity alpha, beta, eps (the softening of mu_ij: finite and
+ * >= 0, SPH_E_INVAL otherwise); the kernel and the equation set (zero: the cubic spline and the minimal set).  Any kernel or scheme other than (M4, minimal) needs an FP64
  * single-grid view (SPH_E_INVAL otherwise), cell edges of at least kappa h, and, for the extended scheme, the
  * members of its access sets in the layout. */
 typedef struct sph_params {
