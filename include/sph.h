@@ -20,7 +20,7 @@
  *   - Device pointers (suffix _dev) must be device memory of the view's GPU.  Host pointers are plain host
  *     memory.  The caller owns every buffer it passes; the view owns the memory it allocated in
  *     sph_view_create and frees it in sph_view_destroy.  No call other than sph_view_create and
- *     sph_step_host's first use allocates device memory.
+ *     sph_step_host's first staged use allocates device memory.
  *   - Arguments are checked on the host first; a bad argument returns SPH_E_INVAL and enqueues nothing.
  *   - Problems found on the device (a position outside the box, the kernel support kappa h larger than a cell, a
  *     non-finite density)
@@ -292,11 +292,19 @@ SPH_API sph_status sph_soa_to_aos(sph_view view, void *aos_dev, int64_t n, uint3
 SPH_API sph_status sph_step(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps,
                     double *stats_out);
 
-/* sph_step on records in HOST memory: copies the n records host->device into a staging buffer that the view
- * allocates on first use (n_max records), runs sph_step (dt, nsteps as there) and copies the records back,
- * then waits.  aos_host should be page-locked for full copy speed. */
+/* sph_step on records in HOST memory, then waits.  By default it copies the n records host->device into a
+ * staging buffer that the view allocates on first use (n_max records), runs sph_step (dt, nsteps as there) and
+ * copies the records back; aos_host should be page-locked for full copy speed.  With sph_view_set_host_direct
+ * on, nothing is copied in bulk: the kernels read the view members from the records and write the written
+ * members back across the host link, in place (the views of Section 4 applied to host-resident records).  That
+ * needs aos_host page-locked and mapped into the device's address space (cudaHostAlloc, cudaHostRegister);
+ * other memory returns SPH_E_INVAL before any launch.  In both modes aos_host must hold n records. */
 SPH_API sph_status sph_step_host(sph_view view, void *aos_host, int64_t n, const sph_params *params, double dt,
                          int32_t nsteps, double *stats_out);
+
+/* How sph_step_host reaches the host records: 0 = staged bulk copies (the default), 1 = in place (see
+ * sph_step_host).  Errors: SPH_E_INVAL (on not 0 or 1). */
+SPH_API sph_status sph_view_set_host_direct(sph_view view, int32_t on);
 
 /* FP64 global sums over the SoA members, in a fixed order (deterministic): out[0..2] = sum m v,
  * out[3..5] = sum m a, out[6] = sum m (|v|^2/2 + u), out[7] = sum m (v . a + du/dt).  Needs x, v, a, mass, u,

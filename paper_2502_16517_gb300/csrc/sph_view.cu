@@ -90,6 +90,7 @@ struct sph_view_s {
     int64_t g_launches[SPH_NPHASES];
     int persistent_ctas;           // CTAs of the persistent pair launches (patch views; 0 = as many as fit)
     bool union_view;               // one gather per member and one scatter per pass (sph_view_set_union)
+    bool host_direct;              // sph_step_host works on the page-locked records in place (sph_view_set_host_direct)
     // smoothing-length iteration
     unsigned char *hdone;          // per slot: converged
     int *hstate;                   // [left this round, all converged, rounds run, left after the last round]
@@ -800,6 +801,13 @@ sph_status sph_view_set_union(sph_view v, int32_t on)
     return SPH_OK;
 }
 
+sph_status sph_view_set_host_direct(sph_view v, int32_t on)
+{
+    if (!v || (on != 0 && on != 1)) return SPH_E_INVAL;
+    v->host_direct = on != 0;
+    return SPH_OK;
+}
+
 sph_status sph_view_set_tiles(sph_view v, int32_t tile_density, int32_t tile_force)
 {
     if (!v || tile_density < 0 || tile_force < 0 || tile_density > 4096 || tile_force > 4096) return SPH_E_INVAL;
@@ -903,6 +911,7 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     v->esz = prec == SPH_F64 ? 8 : 4;
     v->present = present;
     v->union_view = true;
+    v->host_direct = false;
     v->h_max_iter = 0;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
@@ -979,6 +988,7 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     v->present = present;
     v->persistent_ctas = 0;  // sized from the pair kernels' occupancy at launch
     v->union_view = true;
+    v->host_direct = false;
     v->h_max_iter = 0;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
@@ -1101,6 +1111,19 @@ sph_status sph_step_host(sph_view v, void *aos_host, int64_t n, const sph_params
                          int32_t nsteps, double *stats_out)
 {
     if (!v || !aos_host || !params || n < 0 || n > v->n_max) return SPH_E_INVAL;
+    if (v->host_direct) {
+        // the pass reads and writes the records where they are: only page-locked memory mapped into the device's
+        // address space qualifies (anything else is rejected before a launch)
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, aos_host) != cudaSuccess) {
+            cudaGetLastError();
+            return SPH_E_INVAL;
+        }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer) return SPH_E_INVAL;
+        sph_status s = do_step(v, at.devicePointer, n, params, dt, nsteps, stats_out);
+        if (s != SPH_OK) return s;
+        return sph_view_sync(v);
+    }
     if (!v->aos_stage) {
         const size_t bytes = (size_t)std::max<int64_t>(v->n_max, 1) * (size_t)v->layout.stride;
         if (cudaMalloc(&v->aos_stage, bytes) != cudaSuccess) {

@@ -107,6 +107,7 @@ _SIGS = {
     "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
     "sph_view_set_tiles": [_VP, _I32, _I32],
     "sph_view_set_union": [_VP, _I32],
+    "sph_view_set_host_direct": [_VP, _I32],
     "sph_view_set_warps": [_VP, _I32, _I32],
     "sph_view_get_tuning": [_VP, _VP],
     "sph_density_h": [_VP, _VP, ctypes.c_double, ctypes.c_double, _I32, _VP, _VP],
@@ -389,6 +390,10 @@ def sph_view_get_tuning(view):
 
 def sph_view_set_union(view, on=True):
     _check("sph_view_set_union", lib().sph_view_set_union(view, 1 if on else 0))
+
+
+def sph_view_set_host_direct(view, on=True):
+    _check("sph_view_set_host_direct", lib().sph_view_set_host_direct(view, int(on)))
 
 
 def sph_view_set_tiles(view, tile_density, tile_force):

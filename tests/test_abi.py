@@ -104,6 +104,7 @@ def test_create_null_out_and_null_view_calls(sph):
     assert lib.sph_view_sync(None) == sph.SPH_E_INVAL
     assert lib.sph_density(None, None) == sph.SPH_E_INVAL
     assert lib.sph_view_set_union(None, 1) == sph.SPH_E_INVAL
+    assert lib.sph_view_set_host_direct(None, 1) == sph.SPH_E_INVAL
     assert lib.sph_view_set_warps(None, 4, 4) == sph.SPH_E_INVAL
     assert lib.sph_view_get_tuning(None, None) == sph.SPH_E_INVAL
     assert lib.sph_view_destroy(None) == sph.SPH_OK

@@ -54,6 +54,42 @@ def test_step_host_equals_step(sph, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_step_host_in_place_equals_staged(sph, prec):
+    """sph_step_host with the records read and written in place across the host link gives the bytes of the
+    staged-copy mode, for one pass and for leapfrog steps; pageable memory is refused before any launch."""
+    import torch
+    f, lay, aos_h, ncell = _tiny_aos()
+    n = aos_h.shape[0]
+    out = {}
+    for direct in (False, True):
+        for nsteps in (0, 2):
+            host = torch.from_numpy(aos_h.copy()).pin_memory()
+            v = H.new_view(lay, prec, n, f["box"], ncell)
+            try:
+                sph.sph_view_set_host_direct(v, direct)
+                sph.sph_step_host(v, host, n, wl.SPH_PARAMS, dt=1e-3 if nsteps else 0.0, nsteps=nsteps)
+            finally:
+                sph.sph_view_destroy(v)
+            out[direct, nsteps] = host.numpy().copy()
+    assert np.array_equal(out[True, 0], out[False, 0])
+    assert np.array_equal(out[True, 2], out[False, 2])
+    assert not np.array_equal(out[True, 0], aos_h)
+    pageable = aos_h.copy()
+    v = H.new_view(lay, prec, n, f["box"], ncell)
+    try:
+        sph.sph_view_set_host_direct(v, True)
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_step_host(v, pageable, n, wl.SPH_PARAMS)
+        assert e.value.status == sph.SPH_E_INVAL
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_view_set_host_direct(v, 2)
+        assert e.value.status == sph.SPH_E_INVAL
+    finally:
+        sph.sph_view_destroy(v)
+    assert np.array_equal(pageable, aos_h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_reduce_matches_oracle_sums(sph, oracle, prec):
     """The FP64 sums run over the view's values: FP64 views hold the records' values, FP32 views their
     round-to-nearest casts (numpy's float32 cast), so the oracle sums those."""
