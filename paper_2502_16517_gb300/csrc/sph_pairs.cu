@@ -46,6 +46,7 @@ namespace sphk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kSignBit = (long long)0x8000000000000000ULL;  // sign bit of an FP64 bit pattern
 constexpr int kMaxLocal = 128;  // local particles per round of the FP64 driver (shared accumulators)
 // Threads per pair CTA ("warps per cell"): 128 or 256, chosen per loop by the view (autotuner).
 constexpr int kRing = 128;   // per-warp queue slots (at most 31 + 2 x 32 pending)
@@ -768,12 +769,13 @@ struct ForceF64 {
         const long long qbi = __double_as_longlong(lds(L_ + Q2)), qbj = __double_as_longlong(T.q[k]);
         const bool ii = r4 < qbi, io = r16 < qbi;  // r < h_i, r < 2 h_i
         const bool ji = r4 < qbj, jo = r16 < qbj;  // r < h_j, r < 2 h_j
-        const double K1i = lds(L_ + K1);
+        // c = -K1 (inner), K1 (outer), 0 (beyond): the sign bit is flipped on the integer pipe
+        const long long k1i = __double_as_longlong(lds(L_ + K1)), k1j = __double_as_longlong(R_[K1]);
+        const double Ci = __longlong_as_double(io ? (ii ? k1i ^ kSignBit : k1i) : 0LL);
+        const double Cj = __longlong_as_double(jo ? (ji ? k1j ^ kSignBit : k1j) : 0LL);
         const double Fi = fma(fma(ii ? lds(L_ + K2I) : (io ? lds(L_ + K2O) : 0.0), r2, ii ? 0.0 : (io ? lds(L_ + S0) : 0.0)),
-                              rinv, ii ? -K1i : (io ? K1i : 0.0));
-        const double K1j = R_[K1];
-        const double Fj = fma(fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r2, ji ? 0.0 : (jo ? R_[S0] : 0.0)),
-                              rinv, ji ? -K1j : (jo ? K1j : 0.0));
+                              rinv, Ci);
+        const double Fj = fma(fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r2, ji ? 0.0 : (jo ? R_[S0] : 0.0)), rinv, Cj);
         const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
         const double hbs = lds(L_ + HS) + R_[HS];
