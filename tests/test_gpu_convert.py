@@ -78,6 +78,36 @@ def test_bin_matches_oracle(sph, oracle, case, layout_kind):
     np.testing.assert_array_equal(g_cos, cos)
 
 
+@pytest.mark.parametrize("ncell", [(64, 64, 64), (256, 256, 256), (512, 512, 511)],
+                         ids=["64^3", "256^3", "near_2^27"])
+def test_bin_large_grids(sph, oracle, ncell):
+    """Sparse particles on large grids: the multi-CTA cell scan over 64 to 32,704 blocks, up to 133,955,584
+    cells (just under the 2^27 limit), bit-exact against the oracle's counting sort."""
+    rng = np.random.default_rng(7)
+    n = 20011
+    f = {"x": rng.uniform(0, 1, size=(n, 3)), "v": np.zeros((n, 3)), "mass": np.full(n, 1.0 / n),
+         "h": np.full(n, 1e-4), "u": np.ones(n), "box": np.ones(3)}
+    lay = wl.default_layout()
+    aos_h, _ = wl.pack_aos(f, lay, order="shuffled")
+    nc = np.asarray(ncell, np.int32)
+    x = oracle.unpack(aos_h, lay)["x"]
+    cell_of, start, perm, cos, bad = oracle.bin_cells(x, f["box"], nc)
+    assert bad == 0
+    aos = H.to_dev(aos_h)
+    v = H.new_view(lay, sph.SPH_F64, n, f["box"], nc)
+    try:
+        sph.sph_bin(v, aos, n)
+        sph.sph_view_sync(v)
+        g_perm = sph.sph_view_export_index(v, 0, n)
+        g_start = sph.sph_view_export_index(v, 1, int(np.prod(nc.astype(np.int64))) + 1)
+        g_cos = sph.sph_view_export_index(v, 2, n)
+    finally:
+        sph.sph_view_destroy(v)
+    np.testing.assert_array_equal(g_perm, perm)
+    np.testing.assert_array_equal(g_start, start)
+    np.testing.assert_array_equal(g_cos, cos)
+
+
 def test_bin_empty_input(sph):
     lay = wl.default_layout()
     aos = H.to_dev(np.zeros((4, lay["stride"]), np.uint8))
