@@ -1244,7 +1244,8 @@ struct ForceF64G {
         const double Fj = (R_[S1] * Ker::fp_only(qj)) * rinv;
         const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
-        // Monaghan viscosity as in ForceF64: Ph = Pi / 2 = g (beta mu - alpha cbar), g = w R, mu = g D2
+        // Monaghan viscosity, the unscaled form of ForceF64's: Ph = Pi / 2 = g (beta mu - alpha cbar), g = w R,
+        // mu = g D2, with D1 = r^2 + eps hbar^2 formed per pair
         const double hb = lds(L_ + HH) + R_[HH];
         const double D1 = fma(A.eps * hb, hb, r2);
         const double D2 = lds(L_ + RHO) + R_[RHO];
