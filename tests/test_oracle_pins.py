@@ -164,6 +164,21 @@ def test_two_particles_equal_h_approaching_viscosity(oracle):
     np.testing.assert_allclose(du, [-4.0, -4.0], rtol=1e-12)
 
 
+@pytest.mark.parametrize("alpha,beta,eps", [(1.0, 2.0, 0.0), (0.5, 1.0, 0.3), (0.0, 3.0, 0.05)])
+def test_two_particles_viscosity_parameters(oracle, alpha, beta, eps):
+    # The approaching pair above for other Monaghan constants: mu = -2w/(1 + eps) with 2w = 1 (eps softens
+    # hbar^2 against r^2 = h^2), Pi = (alpha c |mu| + beta mu^2)/rho, so K = alpha c/(1 + eps) + beta/(1 + eps)^2
+    # and again a_0x = -8 - 6 K, du_0/dt = 4 + 3 K.  Separates eps, alpha and beta (a swapped or misplaced
+    # constant changes K).
+    x = np.array([[0.5, 0.5, 0.5], [0.6, 0.5, 0.5]])
+    v = np.array([[0.5, 0, 0], [-0.5, 0, 0]], np.float64)
+    rho, P, cs, a, du = _two(oracle, x, v, np.full(2, 0.1), alpha=alpha, beta=beta, eps=eps)
+    c = math.sqrt(10.0 / 9.0)
+    K = alpha * c / (1.0 + eps) + beta / (1.0 + eps) ** 2
+    np.testing.assert_allclose(a[:, 0], [-8.0 - 6.0 * K, 8.0 + 6.0 * K], rtol=1e-12)
+    np.testing.assert_allclose(du, [4.0 + 3.0 * K] * 2, rtol=1e-12)
+
+
 def test_two_particles_unequal_h(oracle):
     # h_0 = 0.1, h_1 = 0.15, d = 0.12: q_0 = 1.2 (outer piece), q_1 = 0.8 (inner piece).
     # rho_0 = (1 + 0.128)/(pi h_0^3), rho_1 = (1 + 0.424)/(pi h_1^3);  A_k = (2/3)/rho_k;
