@@ -436,12 +436,13 @@ def whole_job_rate(units_per_rank, world, seconds):
     return world * float(units_per_rank) / float(seconds)
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, root=None):
     """DRAM bytes per launch of `kernel` from a committed ncu summary under profiles/ (its 'traffic:' line), if
-    the kernel's source file still has the hash the counters were taken on; else (None, reason)."""
+    the kernel's source file still has the hash the counters were taken on; else (None, reason).  root: the
+    directory holding profiles/ and the sources (default: this file's)."""
     import glob
     import hashlib
-    here = os.path.dirname(os.path.abspath(__file__))
+    here = root or os.path.dirname(os.path.abspath(__file__))
     for path in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
         with open(path) as fh:
             for line in fh:
