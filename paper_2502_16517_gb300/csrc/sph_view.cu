@@ -14,6 +14,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph_internal.cuh"
 
 using sphk::ConvPlan;
@@ -278,6 +280,13 @@ cudaEvent_t take_event(sph_view_s *v)
 }
 
 // Brackets the launches of one phase: counts them, and with timing on records two events around them.
+// One phase of the path (SPH_PH_*): its launches are counted, timed with CUDA events when the view's timing is
+// on, and enclosed in an NVTX range named after the phase, so that profilers can select a phase's kernels (the
+// ranges cost one function-pointer test when no tool is attached).
+const char *const kPhaseRange[SPH_NPHASES] = {"sph bin",   "sph gather",     "sph density prep",
+                                              "sph density", "sph scatter",  "sph force prep",
+                                              "sph force",   "sph reduce",   "sph kdk"};
+
 struct Phase {
     sph_view_s *v;
     int ph;
@@ -285,6 +294,7 @@ struct Phase {
     int nl = 0;
     Phase(sph_view_s *view, int phase) : v(view), ph(phase)
     {
+        nvtxRangePushA(kPhaseRange[phase]);
         if (v->timing) {
             e0 = take_event(v);
             if (e0) cudaEventRecord(e0, v->st);
@@ -292,6 +302,7 @@ struct Phase {
     }
     ~Phase()
     {
+        nvtxRangePop();
         v->launches[ph] += nl;
         if (e0) {
             cudaEvent_t e1 = take_event(v);
