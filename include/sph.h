@@ -49,7 +49,8 @@ typedef enum sph_status {
     SPH_E_NOMEM = 2,   /* a device or pinned allocation failed (sph_view_create, first sph_step_host)        */
     SPH_E_CUDA = 3,    /* a CUDA runtime call or a kernel launch failed                                      */
     SPH_E_DEVICE = 4,  /* the device status word has error bits set (see SPH_DEV_*)                          */
-    SPH_E_TIMEOUT = 5, /* a bounded device-side wait gave up                                                 */
+    SPH_E_TIMEOUT = 5, /* reserved for a bounded device-side wait; no kernel of this library waits, so no call
+                          returns it                                                                         */
     SPH_E_NOTCONV = 6, /* an iteration did not converge                                                      */
     SPH_E_STATE = 7    /* call order: e.g. sph_density before the density view was gathered                   */
 } sph_status;
@@ -94,7 +95,7 @@ enum {
 #define SPH_DEV_POS_RANGE 0x1u  /* a position was outside [0, box] or not finite; it was clamped into a cell */
 #define SPH_DEV_H_TOO_BIG 0x2u  /* kappa h exceeded the smallest cell edge: the 3^3 stencil may miss pairs */
 #define SPH_DEV_NONFINITE 0x4u  /* a density, pressure or sound speed came out non-finite or <= 0           */
-#define SPH_DEV_TIMEOUT 0x8u    /* a bounded device-side wait gave up                                       */
+#define SPH_DEV_TIMEOUT 0x8u    /* reserved (as SPH_E_TIMEOUT): no kernel of this library waits             */
 #define SPH_DEV_NOTCONV 0x10u   /* a smoothing-length iteration inside sph_step left particles unconverged   */
 
 /* Record layout: `stride` bytes per record (a multiple of 8, at most 65536); off[f] is the byte offset of
@@ -392,9 +393,10 @@ SPH_API sph_status sph_probe_fma_rate(int32_t prec, double *flops_per_s);
  * race on it and must be ordered by the caller.  Each call clears what must start at zero.
  * The first call on a device looks up the array's address with that device current; make that first call
  * before any stream capture.
+ * With n = 0 every cell_start entry becomes 0, and aos_dev, perm_dev and cell_of_slot_dev may be NULL.
  * Errors: SPH_E_INVAL for a null pointer, a bad layout or domain, or a size beyond the fixed capacity
- * (n > SPH_BIN_STATIC_MAX_PARTICLES or more than SPH_BIN_STATIC_MAX_CELLS cells); SPH_E_CUDA if the address
- * lookup or a launch fails. */
+ * (n > SPH_BIN_STATIC_MAX_PARTICLES, an axis or a product of axes above SPH_BIN_STATIC_MAX_CELLS cells);
+ * SPH_E_CUDA if the address lookup or a launch fails. */
 SPH_API sph_status sph_bin_static(const sph_layout *layout, const sph_domain *domain, const void *aos_dev, int64_t n,
                                   int32_t *perm_dev, int32_t *cell_start_dev, int32_t *cell_of_slot_dev,
                                   uint32_t *status_dev, void *cuda_stream);

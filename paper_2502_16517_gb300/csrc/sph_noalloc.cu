@@ -54,19 +54,24 @@ extern "C" sph_status sph_bin_static(const sph_layout *layout, const sph_domain 
                                      int64_t n, int32_t *perm_dev, int32_t *cell_start_dev,
                                      int32_t *cell_of_slot_dev, uint32_t *status_dev, void *cuda_stream)
 {
-    if (!layout || !domain || !aos_dev || !perm_dev || !cell_start_dev || !cell_of_slot_dev) return SPH_E_INVAL;
+    if (!layout || !domain || !cell_start_dev) return SPH_E_INVAL;
+    // the per-particle arrays may be NULL only when there are no particles
+    if (n != 0 && (!aos_dev || !perm_dev || !cell_of_slot_dev)) return SPH_E_INVAL;
     if (layout->stride <= 0 || layout->stride % 8 != 0 || layout->stride > 65536) return SPH_E_INVAL;
     const int32_t off_x = layout->off[SPH_X];
     if (off_x < 0 || off_x % 8 != 0 || (int64_t)off_x + 24 > layout->stride) return SPH_E_INVAL;
     if (reinterpret_cast<uintptr_t>(aos_dev) % 8 != 0) return SPH_E_INVAL;
+    // the fixed capacity of the static scratch, checked axis by axis so that the running product of the cell
+    // counts stays within kMaxC * kMaxC and cannot overflow
     int64_t ncells = 1;
     for (int a = 0; a < 3; ++a) {
         if (!(domain->box[a] > 0.0) || !(domain->box[a] < 1e300) || domain->ncell[a] < 1) return SPH_E_INVAL;
         if (domain->periodic && domain->ncell[a] < 3) return SPH_E_INVAL;
+        if (domain->ncell[a] > kMaxC) return SPH_E_INVAL;
         ncells *= domain->ncell[a];
+        if (ncells > kMaxC) return SPH_E_INVAL;
     }
-    // the fixed capacity of the static scratch
-    if (n < 0 || n > kMaxP || ncells > kMaxC) return SPH_E_INVAL;
+    if (n < 0 || n > kMaxP) return SPH_E_INVAL;
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return SPH_E_CUDA;

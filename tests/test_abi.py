@@ -128,3 +128,15 @@ def test_patches_create_rejects_bad_arguments(sph, kw):
     st = sph.lib().sph_patches_create(ctypes.byref(L), 0, 100, args["npatch_max"], box, args["ncell_cap"], None,
                                       ctypes.byref(out))
     assert st == sph.SPH_E_INVAL and not out.value
+
+
+@pytest.mark.parametrize("ncell", [(1 << 22, 1 << 21, 1 << 21),   # product wraps to 0 in 64-bit arithmetic
+                                   (65537, 1, 1),                   # one axis beyond the capacity
+                                   (300, 300, 1)])                  # 90,000 cells > SPH_BIN_STATIC_MAX_CELLS
+def test_static_bin_rejects_large_grids_on_the_host(sph, ncell):
+    # rejected before any device work, so the (never dereferenced) device pointers may be placeholders
+    fake = 1 << 20
+    st = sph.lib().sph_bin_static(ctypes.byref(sph.make_layout(_lay())),
+                                  ctypes.byref(sph.make_domain((1, 1, 1), ncell, False)), fake, 8, fake, fake, fake,
+                                  None, None)
+    assert st == sph.SPH_E_INVAL

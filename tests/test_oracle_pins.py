@@ -329,15 +329,43 @@ def test_fp32_positions_are_cell_relative(oracle):
     np.testing.assert_allclose(back.T, x[perm], atol=1e-7)
 
 
-def test_reduce_matches_numpy_sums(oracle):
-    rng = np.random.default_rng(1)
-    n = 1000
-    m, u, du = rng.uniform(size=n), rng.uniform(size=n), rng.normal(size=n)
-    v, a = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+def test_reduce_hand_computed_three_particles(oracle):
+    """All eight sums of a three-particle state worked out by hand (every product and sum exact in binary):
+      sum m v        = (2 - 2 + 1, -4 + 0 + 1, 6 + 1 + 0)                     = (1, -3, 7)
+      sum m a        = (1 + 1 - 2, 2 - 2 + 3, -2 + 0 + 0.5)                   = (0, 3, -1.5)
+      sum m (v^2/2 + u)   = 2 (7 + 1.5) + 0.5 (10 + 3) + 1 (1 + 0)           = 24.5
+      sum m (v.a + du/dt) = 2 (-4.5 + 0.25) + 0.5 (-8 - 1) + 1 (1 + 2)      = -10
+    The eight values differ from each other, so a slot written with another's quantity, a dropped 1/2, a missing
+    u or du/dt, or a wrong component pairing in v.a changes at least one of them."""
+    m = np.array([2.0, 0.5, 1.0])
+    v = np.array([[1.0, -2.0, 3.0], [-4.0, 0.0, 2.0], [1.0, 1.0, 0.0]])
+    a = np.array([[0.5, 1.0, -1.0], [2.0, -4.0, 0.0], [-2.0, 3.0, 0.5]])
+    u = np.array([1.5, 3.0, 0.0])
+    du = np.array([0.25, -1.0, 2.0])
     out = oracle.reduce_sums(m, v, a, u, du)
-    ref = np.concatenate([(m[:, None] * v).sum(0), (m[:, None] * a).sum(0),
-                          [np.sum(m * (0.5 * (v * v).sum(1) + u))], [np.sum(m * ((v * a).sum(1) + du))]])
-    np.testing.assert_allclose(out, ref, rtol=1e-12)
+    np.testing.assert_array_equal(out, [1.0, -3.0, 7.0, 0.0, 3.0, -1.5, 24.5, -10.0])
+    # the empty sum
+    np.testing.assert_array_equal(oracle.reduce_sums(np.zeros(0), np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0),
+                                                     np.zeros(0)), np.zeros(8))
+
+
+def test_reduce_of_oracle_forces_conserves_momentum_and_energy(oracle):
+    """On a random state whose a and du/dt come from the (separately pinned) force, the momentum change
+    sum m a (slots 3-5) and the energy change sum m (v.a + du/dt) (slot 7) vanish to round-off: the pair terms
+    are antisymmetric, and a pair's energy terms cancel.  The momentum slots 0-2 and the energy slot 6 are
+    non-zero on that state."""
+    f = wl.jittered_lattice(8, jitter=0.3, vel_sigma=0.3, seed=5)
+    p = wl.SPH_PARAMS
+    rho = oracle.density(f["x"], f["mass"], f["h"], f["box"])
+    P, cs = oracle.eos(rho, f["u"], p["gamma"])
+    a, du = oracle.force(f["x"], f["v"], f["mass"], f["h"], rho, P, cs, f["box"], True, p["alpha"], p["beta"],
+                         p["eps"])
+    out = oracle.reduce_sums(f["mass"], f["v"], a, f["u"], du)
+    scale_a = np.sum(f["mass"] * np.linalg.norm(a, axis=1))
+    scale_e = np.sum(f["mass"] * (np.abs(np.sum(f["v"] * a, axis=1)) + np.abs(du)))
+    assert np.all(np.abs(out[3:6]) <= 1e-13 * scale_a)
+    assert abs(out[7]) <= 1e-13 * scale_e
+    assert np.all(np.abs(out[0:3]) > 1e-6) and out[6] > 0.0
 
 
 def test_kick_drift_closed_form(oracle):
