@@ -70,6 +70,7 @@ def _load():
                 "or_reduce": (None, [i64, _D, _D, _D, _D, _D, _D]),
                 "or_kick": (None, [i64, dbl, _D, _D, _D, _D]),
                 "or_drift": (None, [i64, dbl, _D, _D, ctypes.c_int, _D]),
+                "or_drift_walls": (None, [i64, dbl, _D, _D, _D]),
                 "or_h_iterate": (i64, [i64, _D, _D, _D, _D, ctypes.c_int, dbl, dbl, i32, _D, _I32]),
                 "or_kappa": (dbl, [ctypes.c_int]),
                 "or_kw": (dbl, [ctypes.c_int, dbl, dbl]),
@@ -391,6 +392,15 @@ def drift(dt, v, x, box, periodic=True):
     return x
 
 
+def drift_walls(dt, v, x, box):
+    """x += v dt in the open box [0, box] with reflecting walls; returns the new (x, v)."""
+    box = _c(box, np.float64)
+    x = np.array(x, np.float64, copy=True, order="C")
+    v = np.array(v, np.float64, copy=True, order="C")
+    _load().or_drift_walls(x.shape[0], float(dt), _p(v, _D), _p(box, _D), _p(x, _D))
+    return x, v
+
+
 # ----------------------------------------------------------------------------------------------------------
 # Whole passes on AoS bytes (the composition f = W o C o f^ o C o N of Eq. 5, evaluated by the definition).
 # ----------------------------------------------------------------------------------------------------------
@@ -508,3 +518,66 @@ def step_sampled_ext(aos, layout, box, params, targets, periodic=True):
         out.update(nnb=full["nnb"][targets], divv=full["divv"][targets], curlv=full["curlv"][targets],
                    omega=full["omega"][targets], vsig=vs)
     return out
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Leapfrog kick-drift-kick runs (Section 2.1 steps 1-5), composed from the pieces above.
+# ----------------------------------------------------------------------------------------------------------
+def _forces(x, v, u, m, h, box, periodic, params):
+    """Density, EOS and force of every particle of one domain at (x, v, u)."""
+    rho = density(x, m, h, box, periodic)
+    P, cs = eos(rho, u, params["gamma"])
+    a, du = force(x, v, m, h, rho, P, cs, box, periodic, params["alpha"], params["beta"], params["eps"])
+    return rho, P, cs, a, du
+
+
+def kdk_run(fields, box, params, dt, nsteps, periodic=True, predict=True, from_records=False, patch_start=None):
+    """nsteps leapfrog steps from the state `fields` (dict x, v, u, mass, h and, with from_records, a and dudt).
+
+    Step order (Section 2.1): kick v, u by dt/2 with the current a, du/dt; drift x by dt (periodic wrap, or the
+    reflecting walls of an open box, which also turn the velocity); density, EOS and force at the new positions;
+    kick the half-step v, u by dt/2 with the new a, du/dt.  With predict, the density and force see predicted
+    values v_half + a dt/2 and u_half + du/dt dt/2 (the old a, du/dt), and the second kick, which starts again
+    from the half-step values, replaces them: the "predicted values" the paper's second kick resets (Section
+    2.2).  Without it they see the half-step values.  Unless from_records, one density + force pass first gives
+    the initial a, du/dt (from_records: the state's own a and dudt, as left by an earlier run).  patch_start:
+    independent open patches (records patch_start[p] .. patch_start[p+1]-1, no pair across patches, walls at
+    0 and box).  Returns dict x, v, u, rho, P, cs, a, dudt of the final state."""
+    x = np.array(fields["x"], np.float64)
+    v = np.array(fields["v"], np.float64)
+    u = np.array(fields["u"], np.float64)
+    m, h = np.asarray(fields["mass"], np.float64), np.asarray(fields["h"], np.float64)
+    n = u.size
+    segs = [(0, n)] if patch_start is None else [(int(patch_start[p]), int(patch_start[p + 1]))
+                                                 for p in range(len(patch_start) - 1)]
+    per = bool(periodic) and patch_start is None
+
+    def all_forces(x, v, u):
+        out = [np.zeros(n), np.zeros(n), np.zeros(n), np.zeros((n, 3)), np.zeros(n)]
+        for s, e in segs:
+            if e > s:
+                for dst, val in zip(out, _forces(x[s:e], v[s:e], u[s:e], m[s:e], h[s:e], box, per, params)):
+                    dst[s:e] = val
+        return out
+
+    if from_records:
+        a, du = np.array(fields["a"], np.float64), np.array(fields["dudt"], np.float64)
+        rho, P, cs = (np.array(fields[k], np.float64) for k in ("rho", "P", "cs"))
+    else:
+        rho, P, cs, a, du = all_forces(x, v, u)
+    for _ in range(nsteps):
+        vh, uh = kick(0.5 * dt, a, du, v, u)
+        if per:
+            x = drift(dt, vh, x, box, True)
+        else:
+            x, vh = drift_walls(dt, vh, x, box)
+        vp, up = kick(0.5 * dt, a, du, vh, uh) if predict else (vh, uh)
+        rho, P, cs, a, du = all_forces(x, vp, up)
+        v, u = kick(0.5 * dt, a, du, vh, uh)
+    return {"x": x, "v": v, "u": u, "rho": rho, "P": P, "cs": cs, "a": a, "dudt": du}
+
+
+def energy(m, v, u):
+    """Total energy sum m (|v|^2 / 2 + u) in FP64 (slot 6 of reduce_sums)."""
+    m, v, u = np.asarray(m, np.float64), np.asarray(v, np.float64), np.asarray(u, np.float64)
+    return float(reduce_sums(m, v, np.zeros_like(v), u, np.zeros_like(u))[6])

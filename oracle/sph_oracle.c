@@ -17,7 +17,8 @@
  *     (Monaghan & Lattanzio 1985), an ideal-gas EOS and the Monaghan (1992) artificial viscosity, with the
  *     symmetrised momentum / energy equations of Price (2012);  or_density / or_eos / or_force;
  *   - the FP64 global momentum and energy sums; or_reduce.
- *   - the leapfrog kick-drift-kick of Section 2.1 (steps 3-5); or_kick / or_drift.
+ *   - the leapfrog kick-drift-kick of Section 2.1 (steps 3-5); or_kick / or_drift, and or_drift_walls for
+ *     open boxes (reflecting walls).
  *   - the smoothing-length iteration of Section 2.1 step 1 (density, grow or shrink h, repeat until every
  *     particle meets its termination test); or_h_iterate.
  *   - the paper's own kernel, the quartic spline M5 (Section 2.1), next to the cubic spline; and the fuller
@@ -464,6 +465,32 @@ void or_drift(int64_t n, double dt, const double *v, const double *box, int peri
                 if (xn >= box[d]) xn = xn - box[d];
                 else if (xn < 0.0) xn = xn + box[d];
             }
+            x[3 * i + d] = xn;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Drift in an open box [0, box] with reflecting walls (the walls of an isolated patch; the paper's periodic
+ * and ghost-cell boundaries do not apply to a patch that shares no particles with any other).  Per axis:
+ * xn = x + v dt; a position past a wall is mirrored back through it and that velocity component changes sign
+ * (xn < 0: xn = -xn; xn > box: xn = 2 box - xn); a position still outside after one mirror (|v dt| > box) is
+ * clamped onto the wall.  x and v are updated in place.
+ * ------------------------------------------------------------------------------------------------------- */
+void or_drift_walls(int64_t n, double dt, double *v, const double *box, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            double xn = x[3 * i + d] + v[3 * i + d] * dt;
+            if (xn < 0.0) {
+                xn = -xn;
+                v[3 * i + d] = -v[3 * i + d];
+            } else if (xn > box[d]) {
+                xn = (box[d] + box[d]) - xn;
+                v[3 * i + d] = -v[3 * i + d];
+            }
+            if (xn < 0.0) xn = 0.0;
+            else if (xn > box[d]) xn = box[d];
             x[3 * i + d] = xn;
         }
     }
