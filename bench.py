@@ -218,10 +218,10 @@ def extended_inputs():
 
 
 def batched_inputs():
-    """The batched workload: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8, 256)) particles per cell
-    (records grouped by patch, scattered inside each patch)."""
+    """The batched workload: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8, 256)) particles per cell,
+    v ~ N(0, 0.1) as in the plain workload (records grouped by patch, scattered inside each patch)."""
     from paper_2502_16517_gb300 import workloads as wl
-    fp = wl.patches(4096, seed=wl.SEED)
+    fp = wl.patches(4096, seed=wl.SEED, vel_sigma=0.1)
     lay = wl.default_layout()
     aos_h, _ = wl.pack_aos(fp, lay, order="shuffled", segments=fp["patch_start"], canary=False)
     return fp, lay, aos_h
@@ -276,9 +276,14 @@ def run_large(prec, reps, dev, f, lay, aos_h, ncell, dt=None, nsteps=10, tune_ca
                 sph.sph_step_graph(view, aos, n, wl.SPH_PARAMS, dt=dt, nsteps=nsteps)
                 ev[k][1].record(stream)
             torch.cuda.synchronize(dev)
-            stats1 = sph.sph_reduce(view)
             counts = sph.sph_pair_counts(view, reset=True)
             out = aos.cpu().numpy()
+            stats1 = sph.sph_step(view, aos, n, wl.SPH_PARAMS, want_stats=True)   # sums of the final records
+            # the same run with the half-step values in the force (first-order energy error), for comparison
+            aos.copy_(aos0)
+            sph.sph_view_set_integrator(view, 0)
+            sph.sph_step(view, aos, n, wl.SPH_PARAMS, dt=dt, nsteps=nsteps)
+            stats_plain = sph.sph_step(view, aos, n, wl.SPH_PARAMS, want_stats=True)
         finally:
             sph.sph_view_destroy(view)
     ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
@@ -286,13 +291,26 @@ def run_large(prec, reps, dev, f, lay, aos_h, ncell, dt=None, nsteps=10, tune_ca
     return {"value": pairs_run * reps / (ms / 1e3), "ms_per_run": ms / reps, "pairs_per_run": pairs_run,
             "steps_per_run": nsteps, "passes_per_run": nsteps + 1, "dt": dt, "particles": int(n),
             "energy_rel_drift": float((stats1[6] - stats0[6]) / stats0[6]),
+            "energy_rel_drift_half_step_values": float((stats_plain[6] - stats0[6]) / stats0[6]),
+            "integrator": "leapfrog KDK, the force after each drift sees the predicted v, u (second kick resets them)",
             "momentum_abs": [float(x) for x in stats1[0:3]], "tiles": tiles, "dtype": "f64" if prec == 0 else "f32",
             "graph": "one CUDA graph launch per ten-step run"}, out
 
 
+def cfl_dt(rec, lay, courant=0.3):
+    """dt = courant * min h / max(c_s + |v|), in FP64 from records after a pass (host copy)."""
+    o = lay["offsets"]
+    hv = rec[:, o["h"]:o["h"] + 8].copy().view(np.float64)[:, 0]
+    cs = rec[:, o["cs"]:o["cs"] + 8].copy().view(np.float64)[:, 0]
+    vv = rec[:, o["v"]:o["v"] + 24].copy().view(np.float64)
+    return float(courant * hv.min() / np.max(cs + np.linalg.norm(vv, axis=1)))
+
+
 def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=8):
-    """Graph-captured steps over all patches (one graph launch per step); per-phase times from one extra
-    un-captured step with event timing."""
+    """One leapfrog step over all patches per graph launch: kick + drift (reflecting patch walls), bin, work list,
+    gather (with the predicted v, u), density, force, scatter, kick.  An initial pass (outside the timed region)
+    gives a, du/dt; then SPH_KDK_CONTINUE makes every launch exactly one step of one continuing run.  dt is the
+    CFL step of the initial state.  Per-phase times from one extra un-captured step with event timing."""
     import torch
     from paper_2502_16517_gb300 import autotune, sph
     from paper_2502_16517_gb300 import workloads as wl
@@ -309,8 +327,11 @@ def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=
             if tune_cache:
                 key = autotune.cache_key(torch.cuda.get_device_name(dev), prec, "patches", float(fp["lam"].mean()))
                 tiles = autotune.tuned_tiles(view, aos, n, wl.SPH_PARAMS, key, tune_cache)
+            e0 = sph.sph_patches_step(view, aos, n, ps, npatch, wl.SPH_PARAMS, want_stats=True)
+            dt = cfl_dt(aos.cpu().numpy(), lay)
+            sph.sph_view_set_integrator(view, sph.SPH_KDK_PREDICT | sph.SPH_KDK_CONTINUE)
             for _ in range(max(warmup, 1)):
-                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS, dt=dt, nsteps=1)
             sph.sph_view_sync(view)
             sph.sph_pair_counts(view, reset=True)
             sph.sph_view_phase_times(view, reset=True)
@@ -319,28 +340,33 @@ def run_batched(prec, steps, warmup, dev, fp, lay, aos_h, tune_cache=None, ncap=
             torch.cuda.synchronize(dev)
             for k in range(steps):
                 ev[k][0].record(stream)
-                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+                sph.sph_patches_step_graph(view, aos, n, ps, npatch, wl.SPH_PARAMS, dt=dt, nsteps=1)
                 ev[k][1].record(stream)
             torch.cuda.synchronize(dev)
             sph.sph_view_sync(view)
             step_ms = [a.elapsed_time(b) for a, b in ev]
             counts = sph.sph_pair_counts(view, reset=True)
             _, launches = sph.sph_view_phase_times(view, reset=True)
-            # phase breakdown (outside the timed region)
+            # phase breakdown (outside the timed region): one more step, un-captured, with event timing
             sph.sph_view_timing(view, True)
-            sph.sph_patches_step(view, aos, n, ps, npatch, wl.SPH_PARAMS)
+            e1 = sph.sph_patches_step(view, aos, n, ps, npatch, wl.SPH_PARAMS, dt=dt, nsteps=1, want_stats=True)
             phase_ms, _ = sph.sph_view_phase_times(view, reset=True)
             sph.sph_view_timing(view, False)
             sph.sph_view_sync(view)
+            x = aos.cpu().numpy()[:, lay["offsets"]["x"]:lay["offsets"]["x"] + 24].copy().view(np.float64)
         finally:
             sph.sph_view_destroy(view)
     ms = float(np.sum(step_ms))
     pairs_step = (counts[1] + counts[2]) / steps
+    nrun = max(warmup, 1) + steps + 1
     return {"value": pairs_step * steps / (ms / 1e3), "ms_per_step": ms / steps, "pairs_per_step": pairs_step,
-            "particles": int(n), "patches": int(npatch),
+            "particles": int(n), "patches": int(npatch), "dt": dt, "steps_run": nrun,
+            "energy_rel_change": float((e1[6] - e0[6]) / e0[6]),
+            "positions_inside_patch_boxes": bool(np.all((x >= 0.0) & (x <= 3.0))),
             "phases_ms": {nm: float(phase_ms[i]) for i, nm in enumerate(sph.PHASE_NAMES)},
             "gpu_launches": int(launches.sum()), "tiles": tiles, "dtype": "f64" if prec == 0 else "f32",
-            "graph": "one CUDA graph launch per step (bin, work list, gathers, density, force, scatters)"}
+            "graph": ("one CUDA graph launch per leapfrog step: kick + drift, bin, work list, gather, density, "
+                      "force, scatter, kick")}
 
 
 def run_e2e(prec, steps, warmup, dev, aos_h, lay, box, ncell, direct=False):
@@ -811,8 +837,9 @@ def main():
         line["forms"][f"large_{form}"] = b
     for form, b in batched.items():
         b = dict(b)
-        b["workload"] = ("batched form: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8,256)) per cell, "
-                         f"{b['particles']} particles, inputs larger than L2 (no flush)")
+        b["workload"] = ("batched form: 4096 independent 3x3x3-cell patches (reflecting walls), Poisson(lambda ~ "
+                         f"U(8,256)) per cell, v ~ N(0,0.1), {b['particles']} particles, one leapfrog step per "
+                         "graph launch, inputs larger than L2 (no flush)")
         b["speedup_vs_plain_f64"] = b["value"] / s64["value"]
         line["forms"][f"batched_{form}"] = b
     print(json.dumps(line))

@@ -174,21 +174,42 @@ SPH_API sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, i
 SPH_API sph_status sph_patches_bin(sph_view view, const void *aos_dev, int64_t n, const int64_t *patch_start_dev,
                                    int32_t npatch);
 
-/* One density + force pass over all patches, as sph_step with dt = 0: bin, gather, density, scatter, gather,
- * force, scatter.  stats_out as in sph_step. */
+/* sph_step over all patches: one density + force pass (bin, gather, density, force, scatter), and with dt > 0
+ * nsteps leapfrog steps after it, as in sph_step.  Every patch is a closed box [0, patch_box] with reflecting
+ * walls: a drift that carries a particle past a wall mirrors its position back through the wall and turns that
+ * velocity component (a particle that would still be outside, |v dt| > patch_box, is put on the wall).
+ * stats_out as in sph_step. */
 SPH_API sph_status sph_patches_step(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
-                                    int32_t npatch, const sph_params *params, double *stats_out);
+                                    int32_t npatch, const sph_params *params, double dt, int32_t nsteps,
+                                    double *stats_out);
 
 /* sph_step / sph_patches_step through a CUDA graph.  A call with a new argument set (aos_dev, n, params, dt,
- * nsteps, patch_start_dev, npatch) runs the step normally, then captures the same launch sequence into a graph;
- * a call repeating the previous argument set replays that graph (one launch for the whole step).  The records'
+ * nsteps, patch_start_dev, npatch, the integrator flags) runs the step normally, then captures the same launch
+ * sequence into a graph; a call repeating the previous argument set replays that graph (one launch for the whole
+ * step, kicks and drifts included).  The records'
  * contents may change between calls; the pointers and sizes may not without a new capture.  The view's stream
  * must not be the legacy default stream (SPH_E_INVAL).  Per-phase event timing is not recorded in replays.  Not
  * on patch views (sph_step_graph) / only on patch views (sph_patches_step_graph). */
 SPH_API sph_status sph_step_graph(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt,
                                   int32_t nsteps);
 SPH_API sph_status sph_patches_step_graph(sph_view view, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
-                                          int32_t npatch, const sph_params *params);
+                                          int32_t npatch, const sph_params *params, double dt, int32_t nsteps);
+
+/* Leapfrog options of sph_step, sph_patches_step and their graph forms (flags, OR-ed):
+ *   SPH_KDK_PREDICT   the density and force after a drift see predicted values, v_half + a dt/2 and
+ *                     u_half + du/dt dt/2 with the a, du/dt of the previous force pass; the second kick starts
+ *                     again from the half-step v, u in the records, which replaces the predicted values (the
+ *                     paper's second kick that resets the predicted values, Section 2.2).  The predicted values
+ *                     exist only in the view: the gather computes them, in FP64, from the record's members.  With
+ *                     them the energy error is second order in dt; without, the force sees the half-step v, u and
+ *                     the error is first order.  On by default.
+ *   SPH_KDK_CONTINUE  a call with dt > 0 skips its initial pass and starts the first kick from the a and du/dt
+ *                     already in the records (as a previous call left them), so that successive calls continue one
+ *                     run: each call is then exactly nsteps steps.  Off by default.
+ * Errors: SPH_E_INVAL (unknown flag bits). */
+#define SPH_KDK_PREDICT 0x1
+#define SPH_KDK_CONTINUE 0x2
+SPH_API sph_status sph_view_set_integrator(sph_view view, int32_t flags);
 
 /* Smoothing-length iteration (Section 2.1, step 1: compute the density, decide whether to grow or shrink the
  * interaction radius, recompute, until every particle meets its termination criterion) on the resident density
@@ -287,9 +308,12 @@ SPH_API sph_status sph_soa_to_aos(sph_view view, void *aos_dev, int64_t n, uint3
 
 /* One whole pass on device-resident records: bin, gather SPH_DENSITY_IN, density, scatter SPH_DENSITY_OUT, gather
  * SPH_FORCE_IN, force, scatter SPH_FORCE_OUT.  With dt > 0, nsteps leapfrog kick-drift-kick steps follow the
- * pass (Section 2.1 steps 3-5): kick v, u by dt/2; drift x by dt (periodic wrap); rebin; density; force;
- * kick by dt/2.  If stats_out is not NULL, waits and writes the eight FP64 sums of sph_reduce after the last
- * force pass. */
+ * pass (Section 2.1 steps 3-5): kick v, u by dt/2; drift x by dt (periodic wrap; an open box reflects at its
+ * walls as patches do, see sph_patches_step); rebin; density; force; kick by dt/2.  Kicks and drifts update the
+ * records in FP64, for both view precisions; sph_view_set_integrator selects predicted values (the default) and
+ * continuation.  Leapfrog steps need x, v, a, u and dudt in the layout; afterwards the view's v and u are no
+ * longer resident.  If stats_out is not NULL, waits and writes the eight FP64 sums of sph_reduce of the final
+ * state. */
 SPH_API sph_status sph_step(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps,
                     double *stats_out);
 

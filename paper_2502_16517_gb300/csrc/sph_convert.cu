@@ -18,7 +18,9 @@
 //   k_gather      CTA per tile of 256 slots.  Phase 1 reads, per record, only the 16-byte chunks that hold a
 //                 member of the mask (128-bit loads; consecutive threads take consecutive chunks of one record)
 //                 into shared memory; phase 2 transposes them out of shared memory into one SoA array per
-//                 member component, consecutive threads writing consecutive slots (coalesced).
+//                 member component, consecutive threads writing consecutive slots (coalesced).  After a drift,
+//                 v and u can arrive predicted (v + a dt/2, u + du/dt dt/2 from the same record, in FP64): the
+//                 view then carries the values the leapfrog's force needs, and the records keep theirs.
 //   k_scatter     the reverse: phase 1 reads the SoA arrays coalesced into shared memory, phase 2 writes each
 //                 member's 8 bytes back into its record; no other byte of a record is written.
 #include "sph_internal.cuh"
@@ -365,7 +367,9 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
     for (int idx = tid; idx < nout; idx += kTile) {
         const int k = idx / cnt;
         const int s = idx - k * cnt;
-        const double v = dbuf[(s * nch + plan.item_chunk[k]) * cw + plan.item_sub[k]];
+        double v = dbuf[(s * nch + plan.item_chunk[k]) * cw + plan.item_sub[k]];
+        const int pc = plan.item_pred_chunk[k];
+        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[(s * nch + pc) * cw + plan.item_pred_sub[k]], plan.pred_dt));
         if (!F32) {
             static_cast<double *>(plan.soa[k])[base + s] = v;
         } else {

@@ -98,6 +98,9 @@ struct ConvPlan {
     int item_chunk[kMaxItems];  // which loaded chunk holds the item
     int item_sub[kMaxItems];    // which 8-byte half of that chunk
     int item_pos[kMaxItems];    // -1, or the axis of a position component (FP32 views store it cell-relative)
+    int item_pred_chunk[kMaxItems];  // gather only: -1, or the chunk holding the rate the item is predicted with
+    int item_pred_sub[kMaxItems];    // ... and its 8-byte half
+    double pred_dt;                  // predicted value = item + rate * pred_dt, each operation rounded in FP64
     void *soa[kMaxItems];       // SoA array of the item (n_max elements)
 };
 
@@ -191,9 +194,9 @@ cudaError_t launch_work_list(const CellSpace &cs, const int *cell_start, int nce
 cudaError_t launch_reduce(bool f32, const SoaPtrs &soa, int n, double *partials, double *out, cudaStream_t st,
                           int *nl);
 
-cudaError_t launch_kick(bool f32, const SoaPtrs &soa, int n, double dtk, cudaStream_t st, int *nl);
-
-cudaError_t launch_drift_aos(uint8_t *aos, int64_t stride, int off_x, int off_v, int n, const Grid &g,
-                             double dt, cudaStream_t st, int *nl);
+// Leapfrog on the records: nkick half kicks of v, u by dtk with the records' a, du/dt, then (drift) x += v dt with
+// the periodic wrap of g, or the reflecting walls of an open box [0, g.box].  off = {x, v, a, u, dudt} offsets.
+cudaError_t launch_kick_drift_aos(uint8_t *aos, int64_t stride, const int off[5], int n, const Grid &g, double dtk,
+                                  int nkick, double dt, bool drift, cudaStream_t st, int *nl);
 
 }  // namespace sphk

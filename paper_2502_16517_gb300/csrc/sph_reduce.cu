@@ -5,8 +5,8 @@
 // Deterministic: a fixed grid (from n only), each CTA sums a fixed contiguous slot range with a fixed
 // thread-stride order and a fixed shared-memory tree, then one CTA adds the CTA partials in order.
 //
-// Leapfrog (paper Section 2.1 steps 3-5): kicks update v and u of the SoA view, the drift updates x in place in
-// the AoS records (positions change cells, so the next pass re-bins from the records).
+// Leapfrog (paper Section 2.1 steps 3-5): kicks and drifts update v, u and x in place in the AoS records, in FP64
+// (positions change cells, so the next pass re-bins from the records).
 #include "sph_internal.cuh"
 
 namespace sphk {
@@ -78,40 +78,57 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__re
 
 // v + a dt, each operation rounded on its own (no contraction), as the leapfrog is written.
 __device__ __forceinline__ double kick1(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }
-__device__ __forceinline__ float kick1(float v, float a, float d) { return __fadd_rn(v, __fmul_rn(a, d)); }
 
-template <typename T>
-__global__ void k_kick(SoaPtrs s, int n, double dtk)
+// Kicks and drift on the records, in FP64 for both view precisions (the records are the state; the SoA views are
+// temporary, Section 4).  Per record: nkick half kicks v += a dtk, u += du/dt dtk (two when the second kick of one
+// step and the first kick of the next meet), then, with drift, x += v dt, wrapped into [0, box) on a periodic
+// grid, or mirrored at the walls of an open box (the velocity component turns; a position still outside after
+// one mirror is put on the wall).  One thread per record.
+__global__ void k_kick_drift_aos(uint8_t *__restrict__ aos, int64_t stride, int off_x, int off_v, int off_a,
+                                 int off_u, int off_du, int n, Grid g, double dtk, int nkick, double dt, int drift)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T *vx = (T *)s.p[SPH_V][0], *vy = (T *)s.p[SPH_V][1], *vz = (T *)s.p[SPH_V][2];
-    const T *ax = (const T *)s.p[SPH_A][0], *ay = (const T *)s.p[SPH_A][1], *az = (const T *)s.p[SPH_A][2];
-    T *u = (T *)s.p[SPH_U][0];
-    const T *du = (const T *)s.p[SPH_DUDT][0];
-    const T d = (T)dtk;
-    vx[i] = kick1(vx[i], ax[i], d);
-    vy[i] = kick1(vy[i], ay[i], d);
-    vz[i] = kick1(vz[i], az[i], d);
-    u[i] = kick1(u[i], du[i], d);
-}
-
-// Drift in the records: x += v dt, wrapped into [0, box) on periodic axes.  One thread per record.
-__global__ void k_drift_aos(uint8_t *__restrict__ aos, int64_t stride, int off_x, int off_v, int n, Grid g, double dt)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double *x = reinterpret_cast<double *>(aos + (int64_t)i * stride + off_x);
-    const double *v = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_v);
+    uint8_t *rec = aos + (int64_t)i * stride;
+    double *xp = reinterpret_cast<double *>(rec + off_x);
+    double *vp = reinterpret_cast<double *>(rec + off_v);
+    double v[3] = {vp[0], vp[1], vp[2]};
+    if (nkick > 0) {
+        const double *ap = reinterpret_cast<const double *>(rec + off_a);
+        double *up = reinterpret_cast<double *>(rec + off_u);
+        const double a[3] = {ap[0], ap[1], ap[2]};
+        const double du = *reinterpret_cast<const double *>(rec + off_du);
+        double u = *up;
+        for (int k = 0; k < nkick; ++k) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double xn = __dadd_rn(x[d], __dmul_rn(v[d], dt));
-        if (g.periodic) {
-            if (xn >= g.box[d]) xn = __dsub_rn(xn, g.box[d]);
-            else if (xn < 0.0) xn = __dadd_rn(xn, g.box[d]);
+            for (int d = 0; d < 3; ++d) v[d] = kick1(v[d], a[d], dtk);
+            u = kick1(u, du, dtk);
         }
-        x[d] = xn;
+        *up = u;
     }
+    if (drift) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double xn = __dadd_rn(xp[d], __dmul_rn(v[d], dt));
+            if (g.periodic) {
+                if (xn >= g.box[d]) xn = __dsub_rn(xn, g.box[d]);
+                else if (xn < 0.0) xn = __dadd_rn(xn, g.box[d]);
+            } else {
+                if (xn < 0.0) {
+                    xn = -xn;
+                    v[d] = -v[d];
+                } else if (xn > g.box[d]) {
+                    xn = __dsub_rn(__dadd_rn(g.box[d], g.box[d]), xn);
+                    v[d] = -v[d];
+                }
+                if (xn < 0.0) xn = 0.0;
+                else if (xn > g.box[d]) xn = g.box[d];
+            }
+            xp[d] = xn;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) vp[d] = v[d];
 }
 
 }  // namespace
@@ -133,24 +150,13 @@ cudaError_t launch_reduce(bool f32, const SoaPtrs &soa, int n, double *partials,
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(bool f32, const SoaPtrs &soa, int n, double dtk, cudaStream_t st, int *nl)
+cudaError_t launch_kick_drift_aos(uint8_t *aos, int64_t stride, const int off[5], int n, const Grid &g, double dtk,
+                                  int nkick, double dt, bool drift, cudaStream_t st, int *nl)
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
-    if (f32) {
-        k_kick<float><<<(n + 255) / 256, 256, 0, st>>>(soa, n, dtk);
-    } else {
-        k_kick<double><<<(n + 255) / 256, 256, 0, st>>>(soa, n, dtk);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_drift_aos(uint8_t *aos, int64_t stride, int off_x, int off_v, int n, const Grid &g, double dt,
-                             cudaStream_t st, int *nl)
-{
-    if (n <= 0) return cudaSuccess;
-    ++*nl;
-    k_drift_aos<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, off_v, n, g, dt);
+    k_kick_drift_aos<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off[0], off[1], off[2], off[3], off[4], n, g, dtk,
+                                                      nkick, dt, drift ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,8 @@ struct sph_view_s {
     int *h_hstate;                 // pinned host copy of hstate
     double h_eta, h_tol;
     int h_max_iter;                // 0: sph_step runs one density pass
+    int32_t integrator;            // SPH_KDK_* flags of sph_view_set_integrator
+    int32_t g_integrator;          // the flags the captured graph was captured with
 };
 
 namespace {
@@ -170,16 +172,25 @@ Grid make_grid(const sph_domain &D)
     return g;
 }
 
-// Build the conversion plan for the members in `mask`.  vec16: items are served from 16-byte chunks.
-void build_plan(const sph_view_s *v, uint32_t mask, bool vec16, ConvPlan *p)
+// The member whose rate predicts member f after a drift (v from a, u from du/dt), or -1.
+int pred_source(int f) { return f == SPH_V ? SPH_A : (f == SPH_U ? SPH_DUDT : -1); }
+
+// Build the conversion plan for the members in `mask`.  vec16: items are served from 16-byte chunks.  pred_dt != 0
+// (gathers only): v and u are gathered predicted, v + a pred_dt and u + du/dt pred_dt.
+void build_plan(const sph_view_s *v, uint32_t mask, bool vec16, ConvPlan *p, double pred_dt = 0.0)
 {
     memset(p, 0, sizeof(*p));
     std::vector<int> chunks;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         if (!(mask & SPH_BIT(f))) continue;
+        const int src = pred_dt != 0.0 ? pred_source(f) : -1;
         for (int c = 0; c < kNcomp[f]; ++c) {
             const int off = v->layout.off[f] + 8 * c;
             chunks.push_back(vec16 ? (off / 16) * 16 : off);
+            if (src >= 0) {
+                const int so = v->layout.off[src] + 8 * c;
+                chunks.push_back(vec16 ? (so / 16) * 16 : so);
+            }
         }
     }
     std::sort(chunks.begin(), chunks.end());
@@ -196,10 +207,19 @@ void build_plan(const sph_view_s *v, uint32_t mask, bool vec16, ConvPlan *p)
             p->item_chunk[k] = (int)(std::lower_bound(chunks.begin(), chunks.end(), ch) - chunks.begin());
             p->item_sub[k] = vec16 ? (off - ch) / 8 : 0;
             p->item_pos[k] = (f == SPH_X && v->prec == SPH_F32) ? c : -1;
+            p->item_pred_chunk[k] = -1;
+            const int src = pred_dt != 0.0 ? pred_source(f) : -1;
+            if (src >= 0) {
+                const int so = v->layout.off[src] + 8 * c;
+                const int sch = vec16 ? (so / 16) * 16 : so;
+                p->item_pred_chunk[k] = (int)(std::lower_bound(chunks.begin(), chunks.end(), sch) - chunks.begin());
+                p->item_pred_sub[k] = vec16 ? (so - sch) / 8 : 0;
+            }
             p->soa[k] = v->soa.p[f][c];
         }
     }
     p->nitems = k;
+    p->pred_dt = pred_dt;
 }
 
 // Bump allocator over one device allocation, 256-byte aligned pieces.
@@ -399,14 +419,15 @@ sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64
     return SPH_OK;
 }
 
-sph_status do_gather(sph_view_s *v, const void *aos, int64_t n, uint32_t mask)
+// Gather the members of `mask`; pred_dt != 0 gathers v and u predicted by pred_dt (see build_plan).
+sph_status do_gather(sph_view_s *v, const void *aos, int64_t n, uint32_t mask, double pred_dt = 0.0)
 {
     if (!aos || !aos_aligned(aos, 8) || !mask_present(v, mask)) return SPH_E_INVAL;
     if (!v->binned) return SPH_E_STATE;
     if (n != v->n) return SPH_E_INVAL;
     const bool vec16 = (v->layout.stride % 16) == 0 && aos_aligned(aos, 16) && v->layout.stride <= 16 * sphk::kMaxChunks;
     ConvPlan plan;
-    build_plan(v, mask, vec16, &plan);
+    build_plan(v, mask, vec16, &plan, pred_dt);
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_GATHER);
@@ -536,7 +557,9 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     return SPH_OK;
 }
 
-sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
+// One density + force pass on the records.  pred_dt != 0: the pass follows a drift, and v and u enter the view
+// predicted by pred_dt with the records' a and du/dt (the leapfrog's predicted values; the records keep theirs).
+sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double pred_dt = 0.0)
 {
     sph_status s = check_scheme(v, p);
     if (s != SPH_OK) return s;
@@ -549,7 +572,7 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     // union view: one gather of every member either loop reads (each record is read once: its bytes arrive in
     // whole memory sectors, so a second pass for the force's extra member v would read the records again)
     const uint32_t first = v->union_view ? ((dens_in(p) | force_in(p)) & ~dens_out(p)) : dens_in(p);
-    if ((s = do_gather(v, aos, n, first)) != SPH_OK) return s;
+    if ((s = do_gather(v, aos, n, first, pred_dt)) != SPH_OK) return s;
     uint32_t d_out = dens_out(p);
     if (v->h_max_iter > 0) {
         if ((s = do_density_h(v, p, v->h_eta, v->h_tol, v->h_max_iter, true)) != SPH_OK) return s;
@@ -560,30 +583,16 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p)
     if (!v->union_view) {
         // one view per loop, converted forth and back around each (the paper's prologue / epilogue per loop)
         if ((s = do_scatter(v, aos, n, d_out)) != SPH_OK) return s;
-        if ((s = do_gather(v, aos, n, force_in(p))) != SPH_OK) return s;
+        if ((s = do_gather(v, aos, n, force_in(p), pred_dt)) != SPH_OK) return s;
         if ((s = do_force(v, p)) != SPH_OK) return s;
         return do_scatter(v, aos, n, force_out(p));
     }
     // union view: the force reads its members and the density outputs where they are, in SoA, and every written
     // member is scattered once at the end
     const uint32_t more = force_in(p) & ~v->resident;
-    if (more && (s = do_gather(v, aos, n, more)) != SPH_OK) return s;
+    if (more && (s = do_gather(v, aos, n, more, pred_dt)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;
     return do_scatter(v, aos, n, d_out | force_out(p));
-}
-
-// Half kick on the view (v += a dt/2, u += du/dt dt/2), then write v and u back into the records.
-sph_status do_kick(sph_view_s *v, void *aos, int64_t n, double dtk)
-{
-    const uint32_t need = SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
-    if ((v->resident & need) != need) return SPH_E_STATE;
-    cudaError_t e;
-    {
-        Phase ph(v, SPH_PH_KDK);
-        e = sphk::launch_kick(v->prec == SPH_F32, v->soa, (int)n, dtk, v->st, &ph.nl);
-    }
-    if (e != cudaSuccess) return SPH_E_CUDA;
-    return do_scatter(v, aos, n, SPH_BIT(SPH_V) | SPH_BIT(SPH_U));
 }
 
 sph_status do_reduce(sph_view_s *v, double *out)
@@ -619,26 +628,46 @@ sph_status read_status(sph_view_s *v, uint32_t *bits, bool clear)
     return SPH_OK;
 }
 
+// Kicks (nkick half kicks by dt/2) and, with drift, the drift by dt, on the records (sphk::launch_kick_drift_aos):
+// periodic grids wrap, open boxes and patches reflect at their walls.
+sph_status do_kick_drift(sph_view_s *v, void *aos, int64_t n, double dt, int nkick, bool drift)
+{
+    const int off[5] = {v->layout.off[SPH_X], v->layout.off[SPH_V], v->layout.off[SPH_A], v->layout.off[SPH_U],
+                        v->layout.off[SPH_DUDT]};
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_KDK);
+        e = sphk::launch_kick_drift_aos(static_cast<uint8_t *>(aos), v->layout.stride, off, (int)n, v->g, 0.5 * dt,
+                                        nkick, dt, drift, v->st, &ph.nl);
+    }
+    return cuda_fail(e);
+}
+
+// sph_step: a pass (unless SPH_KDK_CONTINUE), then nsteps leapfrog steps (Section 2.1 steps 3-5): kick by dt/2,
+// drift by dt, re-bin + pass (with the predicted v, u under SPH_KDK_PREDICT), kick by dt/2.  Both kicks and the
+// drift act on the records in FP64; a step's second kick and the next step's first kick run in one launch, in
+// that order (the same operations as two launches).
 sph_status do_step(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double dt, int32_t nsteps,
                    double *stats_out)
 {
     if (!p || !aos || nsteps < 0 || !(dt >= 0.0) || !(dt < 1e300)) return SPH_E_INVAL;
     const bool kdk = dt > 0.0 && nsteps > 0;
-    if (kdk && !mask_present(v, SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT)))
-        return SPH_E_INVAL;
-    sph_status s = do_pass(v, aos, n, p);
-    if (s != SPH_OK) return s;
+    const uint32_t need = SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
+    if (kdk && !mask_present(v, need)) return SPH_E_INVAL;
+    if (kdk && (n < 0 || n > v->n_max || !aos_aligned(aos, 8))) return SPH_E_INVAL;
+    const bool cont = kdk && (v->integrator & SPH_KDK_CONTINUE);
+    const double pred_dt = (v->integrator & SPH_KDK_PREDICT) ? 0.5 * dt : 0.0;
+    sph_status s;
+    if (!cont && (s = do_pass(v, aos, n, p)) != SPH_OK) return s;
     for (int32_t k = 0; kdk && k < nsteps; ++k) {
-        if ((s = do_kick(v, aos, n, 0.5 * dt)) != SPH_OK) return s;
-        cudaError_t e;
-        {
-            Phase ph(v, SPH_PH_KDK);
-            e = sphk::launch_drift_aos(static_cast<uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X],
-                                       v->layout.off[SPH_V], (int)n, v->g, dt, v->st, &ph.nl);
-        }
-        if (e != cudaSuccess) return SPH_E_CUDA;
-        if ((s = do_pass(v, aos, n, p)) != SPH_OK) return s;
-        if ((s = do_kick(v, aos, n, 0.5 * dt)) != SPH_OK) return s;
+        if ((s = do_kick_drift(v, aos, n, dt, k == 0 ? 1 : 2, true)) != SPH_OK) return s;
+        if ((s = do_pass(v, aos, n, p, pred_dt)) != SPH_OK) return s;
+    }
+    if (kdk) {
+        if ((s = do_kick_drift(v, aos, n, dt, 1, false)) != SPH_OK) return s;
+        // the view's v and u are the predicted (or half-step) values: stale against the kicked records
+        v->resident &= ~(SPH_BIT(SPH_V) | SPH_BIT(SPH_U));
+        if (stats_out && (s = do_gather(v, aos, n, SPH_BIT(SPH_V) | SPH_BIT(SPH_U))) != SPH_OK) return s;
     }
     if (stats_out) return do_reduce(v, stats_out);
     return SPH_OK;
@@ -660,7 +689,7 @@ sph_status do_step_graph(sph_view_s *v, void *aos, int64_t n, const sph_params *
     if (v->st == nullptr) return SPH_E_INVAL;  // the legacy default stream cannot be captured
     const bool same = v->graph_valid && v->g_aos == aos && v->g_n == n && memcmp(&v->g_p, p, sizeof(*p)) == 0 &&
                       v->g_dt == dt && v->g_nsteps == nsteps && v->g_ps == v->patch_start &&
-                      v->g_npatch == v->npatch;
+                      v->g_npatch == v->npatch && v->g_integrator == v->integrator;
     if (same) {
         if (cudaGraphLaunch(v->g_exec, v->st) != cudaSuccess) return SPH_E_CUDA;
         for (int k = 0; k < SPH_NPHASES; ++k) v->launches[k] += v->g_launches[k];
@@ -703,6 +732,7 @@ sph_status do_step_graph(sph_view_s *v, void *aos, int64_t n, const sph_params *
     v->g_nsteps = nsteps;
     v->g_ps = v->patch_start;
     v->g_npatch = v->npatch;
+    v->g_integrator = v->integrator;
     return SPH_OK;
 }
 
@@ -741,12 +771,19 @@ sph_status sph_step_graph(sph_view v, void *aos_dev, int64_t n, const sph_params
 }
 
 sph_status sph_patches_step_graph(sph_view v, void *aos_dev, int64_t n, const int64_t *patch_start_dev,
-                                  int32_t npatch, const sph_params *params)
+                                  int32_t npatch, const sph_params *params, double dt, int32_t nsteps)
 {
     if (!v || v->npatch_max <= 0 || !patch_start_dev || npatch < 1 || npatch > v->npatch_max) return SPH_E_INVAL;
     v->patch_start = patch_start_dev;
     v->npatch = npatch;
-    return do_step_graph(v, aos_dev, n, params, 0.0, 0);
+    return do_step_graph(v, aos_dev, n, params, dt, nsteps);
+}
+
+sph_status sph_view_set_integrator(sph_view v, int32_t flags)
+{
+    if (!v || (flags & ~(SPH_KDK_PREDICT | SPH_KDK_CONTINUE)) != 0) return SPH_E_INVAL;
+    v->integrator = flags;
+    return SPH_OK;
 }
 
 sph_status sph_density_h(sph_view v, const sph_params *params, double eta, double tol, int32_t max_iter,
@@ -924,6 +961,7 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     v->union_view = true;
     v->host_direct = false;
     v->h_max_iter = 0;
+    v->integrator = SPH_KDK_PREDICT;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
@@ -1001,6 +1039,7 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     v->union_view = true;
     v->host_direct = false;
     v->h_max_iter = 0;
+    v->integrator = SPH_KDK_PREDICT;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
@@ -1046,13 +1085,13 @@ sph_status sph_patches_bin(sph_view v, const void *aos_dev, int64_t n, const int
 }
 
 sph_status sph_patches_step(sph_view v, void *aos_dev, int64_t n, const int64_t *patch_start_dev, int32_t npatch,
-                            const sph_params *params, double *stats_out)
+                            const sph_params *params, double dt, int32_t nsteps, double *stats_out)
 {
     if (!v) return SPH_E_INVAL;
     if (v->npatch_max <= 0 || !patch_start_dev || npatch < 1 || npatch > v->npatch_max) return SPH_E_INVAL;
     v->patch_start = patch_start_dev;
     v->npatch = npatch;
-    return do_step(v, aos_dev, n, params, 0.0, 0, stats_out);
+    return do_step(v, aos_dev, n, params, dt, nsteps, stats_out);
 }
 
 sph_status sph_view_destroy(sph_view v)

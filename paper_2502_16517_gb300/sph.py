@@ -47,6 +47,7 @@ SPH_DEV_NOTCONV = 0x10
 (SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
  SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
 SPH_NPHASES = 9
+SPH_KDK_PREDICT, SPH_KDK_CONTINUE = 0x1, 0x2
 SPH_BIN_STATIC_MAX_PARTICLES = 262144
 SPH_BIN_STATIC_MAX_CELLS = 65536
 PHASE_NAMES = ("bin", "gather", "density_prep", "density", "scatter", "force_prep", "force", "reduce", "kdk")
@@ -102,9 +103,11 @@ _SIGS = {
     "sph_patches_create": [ctypes.POINTER(sph_layout), ctypes.c_int, _I64, _I32, ctypes.POINTER(ctypes.c_double), _I32,
                            _VP, ctypes.POINTER(_VP)],
     "sph_patches_bin": [_VP, _VP, _I64, _VP, _I32],
-    "sph_patches_step": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params), ctypes.POINTER(ctypes.c_double)],
+    "sph_patches_step": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params), ctypes.c_double, _I32,
+                         ctypes.POINTER(ctypes.c_double)],
     "sph_step_graph": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.c_double, _I32],
-    "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params)],
+    "sph_patches_step_graph": [_VP, _VP, _I64, _VP, _I32, ctypes.POINTER(sph_params), ctypes.c_double, _I32],
+    "sph_view_set_integrator": [_VP, _I32],
     "sph_view_set_tiles": [_VP, _I32, _I32],
     "sph_view_set_union": [_VP, _I32],
     "sph_view_set_host_direct": [_VP, _I32],
@@ -334,11 +337,11 @@ def sph_patches_bin(view, aos_dev, n, patch_start_dev, npatch):
     _check("sph_patches_bin", lib().sph_patches_bin(view, _addr(aos_dev), int(n), _addr(patch_start_dev), int(npatch)))
 
 
-def sph_patches_step(view, aos_dev, n, patch_start_dev, npatch, params, want_stats=False):
+def sph_patches_step(view, aos_dev, n, patch_start_dev, npatch, params, dt=0.0, nsteps=0, want_stats=False):
     P = params if isinstance(params, sph_params) else make_params(params)
     stats = (ctypes.c_double * 8)() if want_stats else None
     _check("sph_patches_step", lib().sph_patches_step(view, _addr(aos_dev), int(n), _addr(patch_start_dev), int(npatch),
-                                                      ctypes.byref(P), stats))
+                                                      ctypes.byref(P), float(dt), int(nsteps), stats))
     return np.array(stats[:]) if want_stats else None
 
 
@@ -347,10 +350,16 @@ def sph_step_graph(view, aos_dev, n, params, dt=0.0, nsteps=0):
     _check("sph_step_graph", lib().sph_step_graph(view, _addr(aos_dev), int(n), ctypes.byref(P), float(dt), int(nsteps)))
 
 
-def sph_patches_step_graph(view, aos_dev, n, patch_start_dev, npatch, params):
+def sph_patches_step_graph(view, aos_dev, n, patch_start_dev, npatch, params, dt=0.0, nsteps=0):
     P = params if isinstance(params, sph_params) else make_params(params)
     _check("sph_patches_step_graph", lib().sph_patches_step_graph(view, _addr(aos_dev), int(n), _addr(patch_start_dev),
-                                                                  int(npatch), ctypes.byref(P)))
+                                                                  int(npatch), ctypes.byref(P), float(dt),
+                                                                  int(nsteps)))
+
+
+def sph_view_set_integrator(view, flags=SPH_KDK_PREDICT):
+    """Leapfrog options: SPH_KDK_PREDICT (default) and/or SPH_KDK_CONTINUE."""
+    _check("sph_view_set_integrator", lib().sph_view_set_integrator(view, int(flags)))
 
 
 def sph_density_h(view, params, eta=1.2, tol=1e-6, max_iter=30, allow_unconverged=False):

@@ -41,25 +41,8 @@ def cfl_dt(out, lay, courant=0.3):
     return courant * st["h"].min() / np.max(st["cs"] + np.linalg.norm(st["v"], axis=1))
 
 
-def _oracle_kdk(oracle, st, box, dt, nsteps, p):
-    x, v, u = st["x"], st["v"], st["u"]
-
-    def forces(x, v, u):
-        rho = oracle.density(x, st["mass"], st["h"], box)
-        P, cs = oracle.eos(rho, u, p["gamma"])
-        a, du = oracle.force(x, v, st["mass"], st["h"], rho, P, cs, box, True, p["alpha"], p["beta"], p["eps"])
-        return rho, a, du
-    rho, a, du = forces(x, v, u)
-    for _ in range(nsteps):
-        v, u = oracle.kick(0.5 * dt, a, du, v, u)
-        x = oracle.drift(dt, v, x, box)
-        rho, a, du = forces(x, v, u)
-        v, u = oracle.kick(0.5 * dt, a, du, v, u)
-    return {"x": x, "v": v, "u": u, "rho": rho, "a": a}
-
-
-@pytest.mark.parametrize("prec", [0, 1])
-def test_ten_kdk_steps_small_clustered_parity(sph, oracle, side_stream, prec):
+@pytest.mark.parametrize("prec,predict", [(0, True), (1, True), (0, False), (1, False)])
+def test_ten_kdk_steps_small_clustered_parity(sph, oracle, side_stream, prec, predict):
     f = wl.clustered(4096, sigma=0.05, peak=4.0, n_side_equiv=16, seed=8)
     lay = wl.default_layout()
     aos_h, _ = wl.pack_aos(f, lay)
@@ -71,12 +54,13 @@ def test_ten_kdk_steps_small_clustered_parity(sph, oracle, side_stream, prec):
     aos = H.to_dev(aos_h)
     v = sph.sph_view_create(lay, prec, n, (f["box"], ncell, True), side_stream.cuda_stream)
     try:
+        sph.sph_view_set_integrator(v, sph.SPH_KDK_PREDICT if predict else 0)
         sph.sph_step_graph(v, aos, n, p, dt=dt, nsteps=10)
         sph.sph_view_sync(v)
         out = aos.cpu().numpy()
     finally:
         sph.sph_view_destroy(v)
-    ref = _oracle_kdk(oracle, oracle.unpack(aos_h, lay), f["box"], dt, 10, p)
+    ref = oracle.kdk_run(oracle.unpack(aos_h, lay), f["box"], p, dt, 10, predict=predict)
     got = oracle.unpack(out, lay)
     tol = 1e-10 if prec == 0 else 1e-3
     d = got["x"] - ref["x"]
@@ -88,7 +72,7 @@ def test_ten_kdk_steps_small_clustered_parity(sph, oracle, side_stream, prec):
     assert H.normwise(got["a"], ref["a"]) <= tol
 
 
-def _large_run(sph, aos_h, lay, box, ncell, prec, stream, dt=None, nsteps=10):
+def _large_run(sph, aos_h, lay, box, ncell, prec, stream, dt=None, nsteps=10, predict=True):
     """Initial pass, then nsteps KDK steps as one graph launch, then one more pass so that the force sees the
     final velocities.  Returns (stats after the initial pass, stats after the final pass, final records, dt)."""
     n = aos_h.shape[0]
@@ -96,6 +80,7 @@ def _large_run(sph, aos_h, lay, box, ncell, prec, stream, dt=None, nsteps=10):
     aos = H.to_dev(aos_h)
     v = sph.sph_view_create(lay, prec, n, (box, ncell, True), stream.cuda_stream)
     try:
+        sph.sph_view_set_integrator(v, sph.SPH_KDK_PREDICT if predict else 0)
         s0 = sph.sph_step(v, aos, n, p, want_stats=True)          # initial pass: rho, P, c_s, a, du/dt
         if dt is None:
             dt = cfl_dt(aos.cpu().numpy(), lay)
@@ -113,8 +98,10 @@ def test_large_run_full_size_properties(sph, oracle, side_stream):
     - Momentum: zero initially (v = 0) and conserved exactly by the pairwise-antisymmetric force (FP64).
     - Energy rate: the semi-discrete equations conserve sum m (|v|^2/2 + u) exactly, so sum m (v.a + du/dt)
       vanishes up to round-off when a and du/dt are evaluated with the same v (the final pass).
-    - Energy drift of the leapfrog as read here is first order in dt: the force at t_{n+1} sees the half-step
-      velocity, so the ten-step drift halves when dt halves (twenty steps of dt/2).
+    - Energy drift: with the half-step values in the force (SPH_KDK_PREDICT off) the leapfrog's energy error is
+      first order in dt, so the ten-step drift halves when dt halves (twenty steps of dt/2).  With the predicted
+      values (the default) it is second order; at this dt the ten-step drift is not yet in its asymptotic regime
+      (the oracle's small clustered runs show it), so only its size is checked: far below the first-order drift.
     - The FP32 path follows the FP64 path over the ten steps."""
     f = wl.large()
     lay = wl.default_layout()
@@ -128,10 +115,14 @@ def test_large_run_full_size_properties(sph, oracle, side_stream):
     assert np.all(np.abs(s1[0:3]) <= 1e-12 * np.sum(m[:, None] * np.abs(st64["v"])))
     scale = np.sum(m * (np.abs(np.sum(st64["v"] * st64["a"], axis=1)) + np.abs(st64["dudt"])))
     assert scale > 0 and abs(s1[7]) <= 1e-10 * scale
-    drift1 = (s1[6] - s0[6]) / s0[6]
-    h0, h1, _, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 0, side_stream, dt=0.5 * dt, nsteps=20)
+    drift_pred = (s1[6] - s0[6]) / s0[6]
+    p0, p1, _, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 0, side_stream, dt=dt, predict=False)
+    drift1 = (p1[6] - p0[6]) / p0[6]
+    h0, h1, _, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 0, side_stream, dt=0.5 * dt, nsteps=20,
+                              predict=False)
     drift2 = (h1[6] - h0[6]) / h0[6]
     assert 0 < drift1 < 0.1 and 1.6 < drift1 / drift2 < 2.5
+    assert abs(drift_pred) < 0.1 * drift1
     t0, t1, out32, _ = _large_run(sph, aos_h, lay, f["box"], ncell, 1, side_stream, dt=dt)
     st32 = oracle.unpack(out32, lay)
     assert abs(t1[7]) <= 1e-4 * scale
@@ -139,7 +130,7 @@ def test_large_run_full_size_properties(sph, oracle, side_stream):
     d -= np.round(d)
     assert np.max(np.abs(d)) / f["h"][0] < 1e-3
     assert H.rel_max(st32["rho"], st64["rho"]) < 1e-3
-    assert abs((t1[6] - t0[6]) / t0[6] - drift1) < 1e-3 * abs(drift1)
+    assert abs((t1[6] - t0[6]) / t0[6] - drift_pred) < 1e-3 * drift1
     assert np.all(np.isfinite(st64["a"])) and np.all(np.isfinite(st32["a"]))
 
 

@@ -224,22 +224,10 @@ def test_kick_drift_kick_steps(sph, oracle, prec):
         out = aos.cpu().numpy()
     finally:
         sph.sph_view_destroy(v)
-    # oracle: initial pass, then per step kick / drift / pass / kick
-    st = oracle.unpack(aos_h, lay)
+    # oracle: initial pass, then per step kick / drift / pass with the predicted values / kick
     p = wl.SPH_PARAMS
-    x, vel, u = st["x"], st["v"], st["u"]
-
-    def forces(x, vel, u):
-        rho = oracle.density(x, st["mass"], st["h"], f["box"])
-        P, cs = oracle.eos(rho, u, p["gamma"])
-        a, du = oracle.force(x, vel, st["mass"], st["h"], rho, P, cs, f["box"], True, p["alpha"], p["beta"], p["eps"])
-        return rho, a, du
-    rho, a, du = forces(x, vel, u)
-    for _ in range(nsteps):
-        vel, u = oracle.kick(0.5 * dt, a, du, vel, u)
-        x = oracle.drift(dt, vel, x, f["box"])
-        rho, a, du = forces(x, vel, u)
-        vel, u = oracle.kick(0.5 * dt, a, du, vel, u)
+    ref = oracle.kdk_run(oracle.unpack(aos_h, lay), f["box"], p, dt, nsteps)
+    x, vel, u, rho, a = ref["x"], ref["v"], ref["u"], ref["rho"], ref["a"]
     got = oracle.unpack(out, lay)
     tol = 1e-10 if prec == 0 else 1e-4
     assert H.normwise(got["x"], x) <= tol
