@@ -124,7 +124,7 @@ def _inputs():
 
 
 def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, tune_cache=None, union=True,
-             params=None, tune_form="grid", flush_l2=True):
+             params=None, tune_form="grid", flush_l2=True, keep_out=False):
     import torch
     from paper_2502_16517_gb300 import autotune, sph
     from paper_2502_16517_gb300 import workloads as wl
@@ -176,11 +176,12 @@ def run_form(prec, steps, warmup, dev, aos_h, lay, box, ncell, clocks_gpu=None, 
         counts = sph.sph_pair_counts(view)
         phase_ms, launches = sph.sph_view_phase_times(view)
         sph.sph_view_timing(view, False)
+        out = aos.cpu().numpy() if keep_out else None      # the records after the last timed step
     finally:
         sph.sph_view_destroy(view)
     return {
         "step_ms": step_ms, "wall_s": wall, "counts": counts, "phase_ms": phase_ms, "launches": launches,
-        "clocks": sampler.summary() if sampler else None, "tiles": tiles, "union": union,
+        "clocks": sampler.summary() if sampler else None, "tiles": tiles, "union": union, "out": out,
     }
 
 
@@ -518,10 +519,20 @@ def roofline_of(prec, s, steps, peaks, measured=None):
 # ----------------------------------------------------------------------------------------------------------
 # the oracle on a bounded sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------------------------------------
-def oracle_sample(aos_h, lay, f, block_cells, seed=0):
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(aos_h, lay, f, block_cells, seed=0, threads=1):
     """Time the FP64 oracle on a compact sample: the force of every particle in a cube of block_cells^3 lattice
-    spacings, and the density of every particle within 2 h_max of that cube (all the force needs).  Work and
-    pairs are those of the same pass restricted to the sample.  Returns (pairs, seconds, description)."""
+    spacings, and the density of every particle within 2 h_max of that cube (all the force needs), with the
+    targets split over `threads` host threads.  Work and pairs are those of the same pass restricted to the sample.
+    Returns (pairs, seconds, description, values) with values = the oracle's rho, P, c_s of the halo and
+    a, du/dt of the cube, by record."""
     import oracle
     p = {"gamma": 5.0 / 3.0, "alpha": 1.0, "beta": 2.0, "eps": 0.01}
     n = aos_h.shape[0]
@@ -532,32 +543,37 @@ def oracle_sample(aos_h, lay, f, block_cells, seed=0):
     c = rng.uniform(0.2, 0.8, size=3)
     t0 = time.perf_counter()
     st = oracle.unpack(aos_h, lay)
-    x = st["x"]
-    d = x - c
-    d -= box * np.round(d / box)
-    half = 0.5 * block_cells * s
-    blk = np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
-    halo = np.nonzero(np.all(np.abs(d) <= half + 2.0 * hmax * (1 + 1e-9), axis=1))[0]
-    rho = np.full(n, np.nan)
-    rho[halo] = oracle.density(x, st["mass"], st["h"], box, True, halo)
-    P = np.full(n, np.nan)
-    cs = np.full(n, np.nan)
-    P[halo], cs[halo] = oracle.eos(rho[halo], st["u"][halo], p["gamma"])
-    a, du = oracle.force(x, st["v"], st["mass"], st["h"], rho, P, cs, box, True, p["alpha"], p["beta"], p["eps"],
-                         blk)
+    values = oracle.cube_sample(st, box, p, c, 0.5 * block_cells * s, 2.0 * hmax * (1 + 1e-9), threads)
     secs = time.perf_counter() - t0
     # in-support pairs of the sample (counted outside the timed region)
+    x, halo, blk = st["x"], values["halo"], values["block"]
     dens_pairs = sum(oracle.neighbours(x, st["h"], box, int(i)).size for i in halo)
     force_pairs = sum(oracle.neighbours(x, st["h"], box, int(i)).size - 1 for i in blk)
-    desc = (f"brute-force FP64 oracle, single thread: density of {halo.size} and force of {blk.size} particles "
-            f"(a {block_cells}^3-spacing cube plus its 2h halo) of the 262,144-particle workload, each against "
-            f"all {n} particles")
-    return dens_pairs + force_pairs, secs, desc
+    desc = (f"brute-force FP64 oracle on {threads} host thread(s): density of {halo.size} and force of {blk.size} "
+            f"particles (a {block_cells}^3-spacing cube plus its 2h halo) of the 262,144-particle workload, each "
+            f"against all {n} particles")
+    return dens_pairs + force_pairs, secs, desc, values
 
 
 def cpu_baseline(aos_h, lay, f, block_cells):
-    pairs, secs, desc = oracle_sample(aos_h, lay, f, block_cells)
-    return {"value": pairs / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": secs}
+    cores = host_cores()
+    pairs, secs, desc, values = oracle_sample(aos_h, lay, f, block_cells, threads=cores)
+    return {"value": pairs / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "seconds": secs}, values
+
+
+def error_vs_oracle(out_records, lay, values):
+    """Per-field error of the GPU's records against the oracle's sample values: rho, P, c_s as the largest
+    relative error over the halo, a and du/dt normwise (max |err| / max |ref|) over the cube."""
+    import oracle
+    got = oracle.unpack(out_records, lay)
+    h, b = values["halo"], values["block"]
+    err = {k: float(np.max(np.abs(got[k][h] - values[k]) / np.abs(values[k]))) for k in ("rho", "P", "cs")}
+    for k in ("a", "dudt"):
+        ref = values[k]
+        err[k] = float(np.max(np.abs(got[k][b] - ref)) / np.max(np.abs(ref)))
+    err["particles"] = {"rho_P_cs": int(h.size), "a_dudt": int(b.size)}
+    return err
 
 
 def reference_arm(args):
@@ -566,11 +582,12 @@ def reference_arm(args):
         return 0
     f, lay, aos_h, ncell = _inputs()
     block = args.ref_block
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(aos_h, lay, f, block, seed=1)
+        oracle_sample(aos_h, lay, f, block, seed=1, threads=cores)
     tot_pairs, tot_s = 0, 0.0
     for k in range(args.steps):
-        pairs, secs, desc = oracle_sample(aos_h, lay, f, block, seed=2 + k)
+        pairs, secs, desc, _ = oracle_sample(aos_h, lay, f, block, seed=2 + k, threads=cores)
         tot_pairs += pairs
         tot_s += secs
     value = tot_pairs / tot_s
@@ -579,7 +596,7 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles": int(aos_h.shape[0]),
                        "step": "one bounded sample of the pass (see cpu_baseline.sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -592,7 +609,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-block", type=int, default=12, help="oracle sample cube (lattice spacings) for cpu_baseline")
-    ap.add_argument("--ref-block", type=int, default=4, help="oracle sample cube per step of --impl reference")
+    ap.add_argument("--ref-block", type=int, default=8, help="oracle sample cube per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tiles (no autotuning)")
@@ -652,7 +669,7 @@ def main():
     try:
         for k, form in enumerate(forms):
             runs[form] = run_form(0 if form == "f64" else 1, steps, warmup, dev, aos_h, lay, f["box"], ncell,
-                                  tune_cache=tune_cache)
+                                  tune_cache=tune_cache, keep_out=True)
         per_loop = None
         ext = None
         warm = None
@@ -747,8 +764,13 @@ def main():
         torch.distributed.destroy_process_group()
         return 0
     cpu = None
+    errors = {}
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(aos_h, lay, f, args.cpu_block)
+        cpu, oracle_values = cpu_baseline(aos_h, lay, f, args.cpu_block)
+        # the same oracle values, compared with the records of each timed form's last step
+        for fm in forms:
+            errors[fm] = error_vs_oracle(runs[fm]["out"], lay, oracle_values)
+            errors[fm]["bar"] = 1e-12 if fm == "f64" else 2e-5
     hbm = peaks.get("hbm_gbs")
     conv = dict(s64["conversion"])
     if hbm:
@@ -769,6 +791,7 @@ def main():
                    "pairs": "density pairs incl. self + ordered force pairs, counted on the device",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": roofline_of(prec_main, s64, steps, peaks, fma_peak[main_form]),
+        "error_vs_oracle": errors.get(main_form),
         "measured_fma_peak_tflops": fma_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -790,7 +813,7 @@ def main():
             "speedup_vs_f64": s32["value"] / s64["value"], "phases_ms_per_step": s32["phases_ms_per_step"],
             "roofline": roofline_of(1, s32, steps, peaks, fma_peak["f32"]), "conversion": s32["conversion"],
             "gpu_launches": int(sum(s32["launches"].values())), "tiles": runs["f32"]["tiles"],
-            "per_particle_update": s32["per_particle_update"]}
+            "per_particle_update": s32["per_particle_update"], "error_vs_oracle": errors.get("f32")}
     if per_loop is not None:
         per_loop["step_ms"] = list(per_loop["step_ms"])
         sp = summarize_form(0, per_loop, n, steps, world)

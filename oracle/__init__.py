@@ -581,3 +581,39 @@ def energy(m, v, u):
     """Total energy sum m (|v|^2 / 2 + u) in FP64 (slot 6 of reduce_sums)."""
     m, v, u = np.asarray(m, np.float64), np.asarray(v, np.float64), np.asarray(u, np.float64)
     return float(reduce_sums(m, v, np.zeros_like(v), u, np.zeros_like(u))[6])
+
+
+def _split_targets(fn, targets, threads):
+    """fn(chunk) over contiguous chunks of `targets` on `threads` host threads (the C loops release the GIL);
+    results concatenated in target order, each value the one a single call gives."""
+    import concurrent.futures as cf
+    targets = np.asarray(targets, np.int64)
+    chunks = [c for c in np.array_split(targets, max(1, min(4 * threads, targets.size))) if c.size]
+    if threads <= 1 or len(chunks) <= 1:
+        return fn(targets)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(fn, chunks))
+    if isinstance(parts[0], tuple):
+        return tuple(np.concatenate([p[k] for p in parts]) for k in range(len(parts[0])))
+    return np.concatenate(parts)
+
+
+def cube_sample(fields, box, params, centre, half, halo, threads=1):
+    """The pass restricted to a cube of a periodic state: the force (a, du/dt) of every particle within `half` of
+    `centre` (per axis, minimum image) and the density, P and c_s of every particle within half + halo (all that
+    force needs when halo >= 2 h_max), brute force against all particles, on `threads` host threads.
+    Returns dict block, halo (particle indices), rho, P, cs (of the halo), a, dudt (of the block)."""
+    x, m, h = fields["x"], fields["mass"], fields["h"]
+    n = m.size
+    d = x - np.asarray(centre, np.float64)
+    d -= box * np.round(d / box)
+    blk = np.nonzero(np.all(np.abs(d) <= half, axis=1))[0]
+    hal = np.nonzero(np.all(np.abs(d) <= half + halo, axis=1))[0]
+    rho = np.full(n, np.nan)
+    rho[hal] = _split_targets(lambda t: density(x, m, h, box, True, t), hal, threads)
+    P = np.full(n, np.nan)
+    cs = np.full(n, np.nan)
+    P[hal], cs[hal] = eos(rho[hal], fields["u"][hal], params["gamma"])
+    a, du = _split_targets(lambda t: force(x, fields["v"], m, h, rho, P, cs, box, True, params["alpha"],
+                                           params["beta"], params["eps"], t), blk, threads)
+    return {"block": blk, "halo": hal, "rho": rho[hal], "P": P[hal], "cs": cs[hal], "a": a, "dudt": du}
