@@ -310,8 +310,8 @@ SPH_API sph_status sph_soa_to_aos(sph_view view, void *aos_dev, int64_t n, uint3
  * SPH_FORCE_IN, force, scatter SPH_FORCE_OUT.  With dt > 0, nsteps leapfrog kick-drift-kick steps follow the
  * pass (Section 2.1 steps 3-5): kick v, u by dt/2; drift x by dt (periodic wrap; an open box reflects at its
  * walls as patches do, see sph_patches_step); rebin; density; force; kick by dt/2.  Kicks and drifts update the
- * records in FP64, for both view precisions; sph_view_set_integrator selects predicted values (the default) and
- * continuation.  Leapfrog steps need x, v, a, u and dudt in the layout; afterwards the view's v and u are no
+ * records in FP64, for both view precisions, inside the step's bin kernel (first kick, drift) and its last scatter
+ * (second kick); sph_view_set_integrator selects predicted values (the default) and continuation.  Leapfrog steps need x, v, a, u and dudt in the layout; afterwards the view's v and u are no
  * longer resident.  If stats_out is not NULL, waits and writes the eight FP64 sums of sph_reduce of the final
  * state. */
 SPH_API sph_status sph_step(sph_view view, void *aos_dev, int64_t n, const sph_params *params, double dt, int32_t nsteps,
@@ -376,7 +376,7 @@ enum {
     SPH_PH_FORCE_PREP = 5,   /* force loop's per-particle preparation                                      */
     SPH_PH_FORCE = 6,        /* force pair kernel                                                          */
     SPH_PH_REDUCE = 7,       /* FP64 global sums                                                           */
-    SPH_PH_KDK = 8,          /* kicks and drifts                                                           */
+    SPH_PH_KDK = 8,          /* reserved: the kicks and the drift run inside a step's bin and scatter kernels */
     SPH_NPHASES = 9
 };
 

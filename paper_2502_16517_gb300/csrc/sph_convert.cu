@@ -22,7 +22,10 @@
 //                 v and u can arrive predicted (v + a dt/2, u + du/dt dt/2 from the same record, in FP64): the
 //                 view then carries the values the leapfrog's force needs, and the records keep theirs.
 //   k_scatter     the reverse: phase 1 reads the SoA arrays coalesced into shared memory, phase 2 writes each
-//                 member's 8 bytes back into its record; no other byte of a record is written.
+//                 member's 8 bytes back into its record; no other byte of a record is written (the leapfrog's
+//                 second kick, when fused in, also rewrites v and u of the record).
+// The leapfrog's first kick and drift run inside k_bin_count / k_bin_count_patches of the pass that follows them,
+// which read the records anyway.
 #include "sph_internal.cuh"
 
 namespace sphk {
@@ -47,16 +50,66 @@ __device__ __forceinline__ int cell_coord(double x, double inv, int n, double bo
     return k;
 }
 
+// v + a d, each operation rounded on its own (no contraction), as the leapfrog is written.
+__device__ __forceinline__ double kick1(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }
+
+// The leapfrog's first kick and its drift on one record (in place): v += a dtk, u += du/dt dtk, then x += v dt,
+// wrapped into [0, box) on a periodic grid, or mirrored at the walls of an open box (that velocity component turns;
+// a position still outside after one mirror, |v dt| > box, is put on the wall).  Returns the new position in x.
+__device__ __forceinline__ void kick_drift_record(uint8_t *rec, int off_x, const KickDrift &kd, const Grid &g,
+                                                  double x[3])
+{
+    double *xp = reinterpret_cast<double *>(rec + off_x);
+    double *vp = reinterpret_cast<double *>(rec + kd.off_v);
+    double *up = reinterpret_cast<double *>(rec + kd.off_u);
+    const double *ap = reinterpret_cast<const double *>(rec + kd.off_a);
+    const double du = *reinterpret_cast<const double *>(rec + kd.off_du);
+    double v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        v[d] = kick1(vp[d], ap[d], kd.dtk);
+        double xn = __dadd_rn(xp[d], __dmul_rn(v[d], kd.dt));
+        if (g.periodic) {
+            if (xn >= g.box[d]) xn = __dsub_rn(xn, g.box[d]);
+            else if (xn < 0.0) xn = __dadd_rn(xn, g.box[d]);
+        } else {
+            if (xn < 0.0) {
+                xn = -xn;
+                v[d] = -v[d];
+            } else if (xn > g.box[d]) {
+                xn = __dsub_rn(__dadd_rn(g.box[d], g.box[d]), xn);
+                v[d] = -v[d];
+            }
+            if (xn < 0.0) xn = 0.0;
+            else if (xn > g.box[d]) xn = g.box[d];
+        }
+        x[d] = xn;
+        xp[d] = xn;
+        vp[d] = v[d];
+    }
+    *up = kick1(*up, du, kd.dtk);
+}
+
+// KD: the records are kicked and drifted first (the leapfrog fused into the bin); their new positions are binned.
+template <bool KD>
 __global__ void k_bin_count(const uint8_t *__restrict__ aos, int64_t stride, int off_x, int n, Grid g,
-                            int *__restrict__ cell_of, int *__restrict__ count, unsigned *status)
+                            int *__restrict__ cell_of, int *__restrict__ count, unsigned *status, KickDrift kd)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double *xp = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_x);
+    double x[3];
+    if (KD) {
+        kick_drift_record(kd.aos + (int64_t)i * stride, off_x, kd, g, x);
+    } else {
+        const double *xp = reinterpret_cast<const double *>(aos + (int64_t)i * stride + off_x);
+        x[0] = __ldg(xp + 0);
+        x[1] = __ldg(xp + 1);
+        x[2] = __ldg(xp + 2);
+    }
     bool bad = false;
-    const int kx = cell_coord(__ldg(xp + 0), g.inv[0], g.n[0], g.box[0], bad);
-    const int ky = cell_coord(__ldg(xp + 1), g.inv[1], g.n[1], g.box[1], bad);
-    const int kz = cell_coord(__ldg(xp + 2), g.inv[2], g.n[2], g.box[2], bad);
+    const int kx = cell_coord(x[0], g.inv[0], g.n[0], g.box[0], bad);
+    const int ky = cell_coord(x[1], g.inv[1], g.n[1], g.box[1], bad);
+    const int kz = cell_coord(x[2], g.inv[2], g.n[2], g.box[2], bad);
     const int c = kx + g.n[0] * (ky + g.n[1] * kz);
     cell_of[i] = c;
     atomicAdd(&count[c], 1);
@@ -269,14 +322,16 @@ __global__ void __launch_bounds__(256) k_patch_grid(const uint8_t *__restrict__ 
 }
 
 // Global cell of every record of a patch view, one CTA per patch: floor(x * (n / box)) per axis in the patch's
-// grid, clamped (positions outside [0, box] set SPH_DEV_POS_RANGE).
+// grid, clamped (positions outside [0, box] set SPH_DEV_POS_RANGE).  KD: each record is kicked and drifted (walls
+// of the patch box) first.
+template <bool KD>
 __global__ void __launch_bounds__(256) k_bin_count_patches(const uint8_t *__restrict__ aos, int64_t stride, int off_x,
                                                            const int64_t *__restrict__ patch_start, Grid g,
                                                            const int *__restrict__ patch_n,
                                                            const double *__restrict__ patch_inv,
                                                            const int *__restrict__ patch_cell_base,
                                                            int *__restrict__ cell_of, int *__restrict__ count,
-                                                           unsigned *status)
+                                                           unsigned *status, KickDrift kd)
 {
     const int p = blockIdx.x;
     const int64_t s = patch_start[p], e = patch_start[p + 1];
@@ -285,10 +340,18 @@ __global__ void __launch_bounds__(256) k_bin_count_patches(const uint8_t *__rest
     const int cb = patch_cell_base[p];
     bool bad = false;
     for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const double *xp = reinterpret_cast<const double *>(aos + i * stride + off_x);
-        const int kx = cell_coord(__ldg(xp + 0), ix, nx, g.box[0], bad);
-        const int ky = cell_coord(__ldg(xp + 1), iy, ny, g.box[1], bad);
-        const int kz = cell_coord(__ldg(xp + 2), iz, nz, g.box[2], bad);
+        double x[3];
+        if (KD) {
+            kick_drift_record(kd.aos + i * stride, off_x, kd, g, x);
+        } else {
+            const double *xp = reinterpret_cast<const double *>(aos + i * stride + off_x);
+            x[0] = __ldg(xp + 0);
+            x[1] = __ldg(xp + 1);
+            x[2] = __ldg(xp + 2);
+        }
+        const int kx = cell_coord(x[0], ix, nx, g.box[0], bad);
+        const int ky = cell_coord(x[1], iy, ny, g.box[1], bad);
+        const int kz = cell_coord(x[2], iz, nz, g.box[2], bad);
         const int c = cb + kx + nx * (ky + ny * kz);
         cell_of[i] = c;
         atomicAdd(&count[c], 1);
@@ -420,6 +483,15 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.item_off[k]);
         *p = sval[idx];
     }
+    if (plan.kick_dt != 0.0) {
+        // the leapfrog's second kick fused into the epilogue: v += a dt/2, u += du/dt dt/2 with the values just
+        // written (the same doubles the record now holds)
+        for (int idx = tid; idx < 4 * cnt; idx += kTile) {
+            const int s = idx >> 2, c = idx & 3;
+            double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
+            *p = kick1(*p, sval[s * ni + plan.kick_item[c]], plan.kick_dt);
+        }
+    }
 }
 
 }  // namespace
@@ -450,12 +522,18 @@ void launch_scan(const int *count, int ncells_host, const int *ncells_dev, int n
 
 cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
                        int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl)
+                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl,
+                       const KickDrift *kd)
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells, st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status);
+        if (kd) {
+            k_bin_count<true><<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status, *kd);
+        } else {
+            k_bin_count<false><<<(n + 255) / 256, 256, 0, st>>>(aos, stride, off_x, n, g, cell_of, count, status,
+                                                                KickDrift{});
+        }
         ++*nl;
     }
     launch_scan(count, ncells, nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
@@ -475,7 +553,7 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
                                int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
                                int *ncells_dev, int *cell_of, int *count, int *cell_start, int *fill,
                                int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp, unsigned *status,
-                               cudaStream_t st, int *nl)
+                               cudaStream_t st, int *nl, const KickDrift *kd)
 {
     // patch_edge holds 3 * npatch edges followed by 3 * npatch inverses
     double *patch_inv = patch_edge + 3 * (size_t)npatch;
@@ -486,8 +564,14 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
     if (e != cudaSuccess) return e;
     *nl += 2;
     if (n > 0) {
-        k_bin_count_patches<<<npatch, 256, 0, st>>>(aos, stride, off_x, patch_start, box, patch_n, patch_inv,
-                                                    patch_cell_base, cell_of, count, status);
+        if (kd) {
+            k_bin_count_patches<true><<<npatch, 256, 0, st>>>(aos, stride, off_x, patch_start, box, patch_n,
+                                                              patch_inv, patch_cell_base, cell_of, count, status, *kd);
+        } else {
+            k_bin_count_patches<false><<<npatch, 256, 0, st>>>(aos, stride, off_x, patch_start, box, patch_n,
+                                                               patch_inv, patch_cell_base, cell_of, count, status,
+                                                               KickDrift{});
+        }
         ++*nl;
     }
     launch_scan(count, ncells_cap, ncells_dev, ncells_cap, cell_start, fill, scan_tmp, st, nl);

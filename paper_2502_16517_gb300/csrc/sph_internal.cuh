@@ -101,6 +101,11 @@ struct ConvPlan {
     int item_pred_chunk[kMaxItems];  // gather only: -1, or the chunk holding the rate the item is predicted with
     int item_pred_sub[kMaxItems];    // ... and its 8-byte half
     double pred_dt;                  // predicted value = item + rate * pred_dt, each operation rounded in FP64
+    // scatter only: with kick_dt != 0, the record's v (3 components) and u are kicked by kick_dt times the
+    // scattered items kick_item[0..3] (a_x, a_y, a_z, du/dt), after those are written
+    double kick_dt;
+    int kick_item[4];
+    int kick_off[4];
     void *soa[kMaxItems];       // SoA array of the item (n_max elements)
 };
 
@@ -131,13 +136,26 @@ struct Counters {
     unsigned long long dens_cand, dens_pairs, force_pairs, force_cand;
 };
 
+// Leapfrog work fused into a pass (Section 2.1 steps 3-5; on the records, in FP64 for both view precisions): the
+// bin kernel first kicks v, u by a dtk, du/dt dtk and drifts x by v dt (the periodic wrap of the grid, or the
+// reflecting walls of an open box or patch), then bins the new position; the last scatter of the pass kicks v, u by
+// the new a, du/dt it writes.  aos is the records the bin reads, writable.
+struct KickDrift {
+    uint8_t *aos;
+    int off_v, off_a, off_u, off_du;
+    double dtk;  // half kick
+    double dt;   // drift
+};
+
 // ---- launchers: each enqueues on `st`, adds the number of kernels it launched to *nl and returns the first
 // CUDA error (cudaGetLastError after the launches). ----
 // scan_tmp: scan_tmp_ints(cells) ints of scratch for the multi-CTA scan of large grids (nullptr: one-CTA scan).
 int scan_tmp_ints(int ncells_cap);
+// kd (may be null): kick and drift every record before binning it (see KickDrift).
 cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, const Grid &g, int ncells,
                        int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
+                       int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl,
+                       const KickDrift *kd = nullptr);
 
 // Patch binning: per-patch grids from the patches' largest h (cells per axis capped at ncap), global cell ids,
 // then the same counting sort as launch_bin over at most ncells_cap cells.
@@ -146,7 +164,8 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
                                int *patch_n, double *patch_edge, int *patch_cells, int *patch_cell_base,
                                int *ncells_dev, int *cell_of,
                                int *count, int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot,
-                               int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
+                               int *scan_tmp, unsigned *status, cudaStream_t st, int *nl,
+                               const KickDrift *kd = nullptr);
 
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
                           const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &cs, bool f32,
@@ -194,9 +213,6 @@ cudaError_t launch_work_list(const CellSpace &cs, const int *cell_start, int nce
 cudaError_t launch_reduce(bool f32, const SoaPtrs &soa, int n, double *partials, double *out, cudaStream_t st,
                           int *nl);
 
-// Leapfrog on the records: nkick half kicks of v, u by dtk with the records' a, du/dt, then (drift) x += v dt with
-// the periodic wrap of g, or the reflecting walls of an open box [0, g.box].  off = {x, v, a, u, dudt} offsets.
-cudaError_t launch_kick_drift_aos(uint8_t *aos, int64_t stride, const int off[5], int n, const Grid &g, double dtk,
-                                  int nkick, double dt, bool drift, cudaStream_t st, int *nl);
+
 
 }  // namespace sphk

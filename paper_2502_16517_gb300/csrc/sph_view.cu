@@ -350,7 +350,8 @@ sph_status drain_timings(sph_view_s *v)
     return SPH_OK;
 }
 
-sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
+// kd (may be null): the leapfrog's first kick and drift, fused into the bin kernel.
+sph_status do_bin(sph_view_s *v, const void *aos, int64_t n, const sphk::KickDrift *kd = nullptr)
 {
     if (v->npatch_max > 0) return SPH_E_INVAL;  // patch views bin with sph_patches_bin
     if (!aos || n < 0 || n > v->n_max || !aos_aligned(aos, 8)) return SPH_E_INVAL;
@@ -360,7 +361,7 @@ sph_status do_bin(sph_view_s *v, const void *aos, int64_t n)
         Phase ph(v, SPH_PH_BIN);
         e = sphk::launch_bin(static_cast<const uint8_t *>(aos), v->layout.stride, v->layout.off[SPH_X], (int)n, v->g,
                              v->ncells, v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
-                             v->cell_of_slot, v->scan_tmp, v->status, v->st, &ph.nl);
+                             v->cell_of_slot, v->scan_tmp, v->status, v->st, &ph.nl, kd);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->n = n;
@@ -386,7 +387,8 @@ sphk::PairLaunch pair_launch(const sph_view_s *v, int tj, int warps)
     return pl;
 }
 
-sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64_t *patch_start, int npatch)
+sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64_t *patch_start, int npatch,
+                          const sphk::KickDrift *kd = nullptr)
 {
     if (v->npatch_max <= 0) return SPH_E_INVAL;  // not a patch view
     if (!aos || !patch_start || n < 0 || n > v->n_max || !aos_aligned(aos, 8)) return SPH_E_INVAL;
@@ -407,7 +409,7 @@ sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64
                                      v->patch_n, v->patch_edge, v->patch_cells, v->patch_cell_base,
                                      v->patch_cell_base + npatch, v->cell_of, v->count, v->cell_start, v->fill,
                                      v->perm_tmp, v->perm, v->cell_of_slot, v->scan_tmp, v->status, v->st,
-                                     &ph.nl);
+                                     &ph.nl, kd);
         if (e == cudaSuccess)
             e = sphk::launch_work_list(v->cs, v->cell_start, v->ncells, v->cell_bucket, v->bucket_count,
                                        v->work_order, v->work_count, v->st, &ph.nl);
@@ -439,7 +441,9 @@ sph_status do_gather(sph_view_s *v, const void *aos, int64_t n, uint32_t mask, d
     return SPH_OK;
 }
 
-sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask)
+// Scatter the members of `mask`; kick_dt != 0 (the mask holds a and du/dt) also kicks the records' v and u by
+// kick_dt times the a, du/dt written (the leapfrog's second kick, fused into the epilogue).
+sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask, double kick_dt = 0.0)
 {
     if (!aos || !aos_aligned(aos, 8) || !mask_present(v, mask)) return SPH_E_INVAL;
     if (!v->binned) return SPH_E_STATE;
@@ -447,6 +451,25 @@ sph_status do_scatter(sph_view_s *v, void *aos, int64_t n, uint32_t mask)
     if ((mask & ~v->resident) != 0) return SPH_E_STATE;
     ConvPlan plan;
     build_plan(v, mask, false, &plan);
+    if (kick_dt != 0.0) {
+        const uint32_t need = SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT);
+        if ((mask & need) != need || !mask_present(v, SPH_BIT(SPH_V) | SPH_BIT(SPH_U))) return SPH_E_INVAL;
+        // items are listed member by member in member order: find a's three components and du/dt
+        int k = 0, ka = -1, kdu = -1;
+        for (int f = 0; f < SPH_NFIELDS; ++f) {
+            if (!(mask & SPH_BIT(f))) continue;
+            if (f == SPH_A) ka = k;
+            if (f == SPH_DUDT) kdu = k;
+            k += kNcomp[f];
+        }
+        plan.kick_dt = kick_dt;
+        for (int c = 0; c < 3; ++c) {
+            plan.kick_item[c] = ka + c;
+            plan.kick_off[c] = v->layout.off[SPH_V] + 8 * c;
+        }
+        plan.kick_item[3] = kdu;
+        plan.kick_off[3] = v->layout.off[SPH_U];
+    }
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_SCATTER);
@@ -557,16 +580,31 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     return SPH_OK;
 }
 
-// One density + force pass on the records.  pred_dt != 0: the pass follows a drift, and v and u enter the view
-// predicted by pred_dt with the records' a and du/dt (the leapfrog's predicted values; the records keep theirs).
-sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double pred_dt = 0.0)
+// One density + force pass on the records.  With dt > 0 the pass is one leapfrog step (Section 2.1 steps 3-5):
+// the bin kernel first kicks v, u by dt/2 and drifts x by dt, the view gathers v and u predicted by pred_dt with
+// the records' a and du/dt (the leapfrog's predicted values, when pred_dt != 0; the records keep theirs), and the
+// last scatter kicks the records' v, u by dt/2 with the new a, du/dt.
+sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double dt = 0.0, double pred_dt = 0.0)
 {
     sph_status s = check_scheme(v, p);
     if (s != SPH_OK) return s;
     if (!mask_present(v, dens_out(p) | force_out(p))) return SPH_E_INVAL;
+    sphk::KickDrift kd;
+    const sphk::KickDrift *kdp = nullptr;
+    if (dt > 0.0) {
+        kd.aos = static_cast<uint8_t *>(aos);
+        kd.off_v = v->layout.off[SPH_V];
+        kd.off_a = v->layout.off[SPH_A];
+        kd.off_u = v->layout.off[SPH_U];
+        kd.off_du = v->layout.off[SPH_DUDT];
+        kd.dtk = 0.5 * dt;
+        kd.dt = dt;
+        kdp = &kd;
+    }
+    const double kick_dt = 0.5 * dt;
     if (v->npatch_max > 0) {
-        if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch)) != SPH_OK) return s;
-    } else if ((s = do_bin(v, aos, n)) != SPH_OK) {
+        if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch, kdp)) != SPH_OK) return s;
+    } else if ((s = do_bin(v, aos, n, kdp)) != SPH_OK) {
         return s;
     }
     // union view: one gather of every member either loop reads (each record is read once: its bytes arrive in
@@ -585,14 +623,14 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p, dou
         if ((s = do_scatter(v, aos, n, d_out)) != SPH_OK) return s;
         if ((s = do_gather(v, aos, n, force_in(p), pred_dt)) != SPH_OK) return s;
         if ((s = do_force(v, p)) != SPH_OK) return s;
-        return do_scatter(v, aos, n, force_out(p));
+        return do_scatter(v, aos, n, force_out(p), kick_dt);
     }
     // union view: the force reads its members and the density outputs where they are, in SoA, and every written
     // member is scattered once at the end
     const uint32_t more = force_in(p) & ~v->resident;
     if (more && (s = do_gather(v, aos, n, more, pred_dt)) != SPH_OK) return s;
     if ((s = do_force(v, p)) != SPH_OK) return s;
-    return do_scatter(v, aos, n, d_out | force_out(p));
+    return do_scatter(v, aos, n, d_out | force_out(p), kick_dt);
 }
 
 sph_status do_reduce(sph_view_s *v, double *out)
@@ -628,25 +666,10 @@ sph_status read_status(sph_view_s *v, uint32_t *bits, bool clear)
     return SPH_OK;
 }
 
-// Kicks (nkick half kicks by dt/2) and, with drift, the drift by dt, on the records (sphk::launch_kick_drift_aos):
-// periodic grids wrap, open boxes and patches reflect at their walls.
-sph_status do_kick_drift(sph_view_s *v, void *aos, int64_t n, double dt, int nkick, bool drift)
-{
-    const int off[5] = {v->layout.off[SPH_X], v->layout.off[SPH_V], v->layout.off[SPH_A], v->layout.off[SPH_U],
-                        v->layout.off[SPH_DUDT]};
-    cudaError_t e;
-    {
-        Phase ph(v, SPH_PH_KDK);
-        e = sphk::launch_kick_drift_aos(static_cast<uint8_t *>(aos), v->layout.stride, off, (int)n, v->g, 0.5 * dt,
-                                        nkick, dt, drift, v->st, &ph.nl);
-    }
-    return cuda_fail(e);
-}
-
-// sph_step: a pass (unless SPH_KDK_CONTINUE), then nsteps leapfrog steps (Section 2.1 steps 3-5): kick by dt/2,
-// drift by dt, re-bin + pass (with the predicted v, u under SPH_KDK_PREDICT), kick by dt/2.  Both kicks and the
-// drift act on the records in FP64; a step's second kick and the next step's first kick run in one launch, in
-// that order (the same operations as two launches).
+// sph_step: a pass (unless SPH_KDK_CONTINUE), then nsteps leapfrog steps (Section 2.1 steps 3-5), each one pass
+// that kicks by dt/2, drifts by dt, re-bins, gathers (with the predicted v, u under SPH_KDK_PREDICT), computes the
+// density and the force, scatters and kicks by dt/2.  Kicks and drift act on the records in FP64, inside the
+// pass's bin and last scatter kernels.
 sph_status do_step(sph_view_s *v, void *aos, int64_t n, const sph_params *p, double dt, int32_t nsteps,
                    double *stats_out)
 {
@@ -654,17 +677,14 @@ sph_status do_step(sph_view_s *v, void *aos, int64_t n, const sph_params *p, dou
     const bool kdk = dt > 0.0 && nsteps > 0;
     const uint32_t need = SPH_BIT(SPH_X) | SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
     if (kdk && !mask_present(v, need)) return SPH_E_INVAL;
-    if (kdk && (n < 0 || n > v->n_max || !aos_aligned(aos, 8))) return SPH_E_INVAL;
     const bool cont = kdk && (v->integrator & SPH_KDK_CONTINUE);
     const double pred_dt = (v->integrator & SPH_KDK_PREDICT) ? 0.5 * dt : 0.0;
     sph_status s;
     if (!cont && (s = do_pass(v, aos, n, p)) != SPH_OK) return s;
     for (int32_t k = 0; kdk && k < nsteps; ++k) {
-        if ((s = do_kick_drift(v, aos, n, dt, k == 0 ? 1 : 2, true)) != SPH_OK) return s;
-        if ((s = do_pass(v, aos, n, p, pred_dt)) != SPH_OK) return s;
+        if ((s = do_pass(v, aos, n, p, dt, pred_dt)) != SPH_OK) return s;
     }
     if (kdk) {
-        if ((s = do_kick_drift(v, aos, n, dt, 1, false)) != SPH_OK) return s;
         // the view's v and u are the predicted (or half-step) values: stale against the kicked records
         v->resident &= ~(SPH_BIT(SPH_V) | SPH_BIT(SPH_U));
         if (stats_out && (s = do_gather(v, aos, n, SPH_BIT(SPH_V) | SPH_BIT(SPH_U))) != SPH_OK) return s;

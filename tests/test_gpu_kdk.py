@@ -96,7 +96,8 @@ def test_patches_kdk_steps_in_one_graph(sph, oracle, side_stream, prec, predict)
     _compare(got, ref, prec, f["box"])
     assert got["x"].min() >= 0.0 and got["x"].max() <= 3.0
     assert np.sum(np.sign(got["v"]) != np.sign(f["v"])) > 0        # some particle met a wall
-    assert launches[sph.SPH_PH_KDK] > 0
+    # the kicks and drifts run inside the bin and scatter kernels of each step's pass: one bin per pass
+    assert launches[sph.SPH_PH_BIN] > 0 and np.max(np.abs(got["x"] - f["x"])) > 0.0
     # members outside the leapfrog's and the loops' sets are untouched
     wm = H.written_mask(lay, ("x", "v", "u", "rho", "P", "cs", "a", "dudt"))
     assert np.array_equal(out[:, ~wm], aos_h[:, ~wm])
