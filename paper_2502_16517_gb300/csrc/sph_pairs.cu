@@ -1490,16 +1490,11 @@ struct PairShared {
 template <class K, int NT>
 __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const typename K::Tile &T,
                                            PairShared<K, NT> &S, int ib, int nloc, int tb, int tnp, float margin,
-                                           bool wrap, int rot, unsigned long long &my_pairs)
+                                           bool wrap, unsigned long long &my_pairs)
 {
     constexpr int W = NT / 32;
     constexpr int kTag = 1 << 14;  // entry = candidate | kTag for the second particle (candidates < 4096)
-    const int lane = threadIdx.x & 31;
-    // The pairs of particles go to the warps round-robin starting at warp `rot` (which varies from cell to cell):
-    // a cell's leftover pairs then fall on different warps, and so on different SM sub-partitions (warp w of a CTA
-    // issues on sub-partition w mod 4), whose FP64 pipes would otherwise see unequal work.  Which warp evaluates a
-    // pair does not change its results.
-    const int warp = ((threadIdx.x >> 5) - rot) & (W - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     int *q = S.ring[warp];
     const NbrTable &nb = S.nb;
@@ -1602,7 +1597,7 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            tile_pairs<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, c & (NT / 32 - 1), my_pairs);
+            tile_pairs<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, my_pairs);
         }
         __syncthreads();
         for (int t = tid; t < nloc; t += NT) K::finish(A, ib + t, S.acc[t]);
