@@ -218,11 +218,12 @@ def extended_inputs():
     return lay, aos_h, wl.ncell_for(f["box"], f["h"].max(), 2.5)
 
 
-def batched_inputs():
+def batched_inputs(npatch=4096):
     """The batched workload: 4096 independent 3x3x3-cell patches, Poisson(lambda ~ U(8, 256)) particles per cell,
-    v ~ N(0, 0.1) as in the plain workload (records grouped by patch, scattered inside each patch)."""
+    v ~ N(0, 0.1) as in the plain workload (records grouped by patch, scattered inside each patch).  Profiling
+    runs may take fewer patches of the same distribution."""
     from paper_2502_16517_gb300 import workloads as wl
-    fp = wl.patches(4096, seed=wl.SEED, vel_sigma=0.1)
+    fp = wl.patches(npatch, seed=wl.SEED, vel_sigma=0.1)
     lay = wl.default_layout()
     aos_h, _ = wl.pack_aos(fp, lay, order="shuffled", segments=fp["patch_start"], canary=False)
     return fp, lay, aos_h
@@ -618,6 +619,8 @@ def main():
     ap.add_argument("--no-large", dest="large", action="store_false", help="skip the large ten-step run forms")
     ap.add_argument("--only", choices=["f64", "f32", "batched_f32", "batched_f64", "extended_m5"], default=None,
                     help="run one form only (profiling runs); the JSON line then carries that form's numbers")
+    ap.add_argument("--patches", type=int, default=4096,
+                    help="patches of the batched form with --only batched_* (profiling runs on a smaller case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -642,7 +645,7 @@ def main():
     tune_cache = os.path.join(tempfile.mkdtemp(prefix="sph_tiles_"), "tiles.json") if not args.no_tune else None
     if args.only in ("batched_f32", "batched_f64"):
         # profiling runs of one batched form: its graph-captured steps only
-        fp, lay_b, aos_b = batched_inputs()
+        fp, lay_b, aos_b = batched_inputs(args.patches)
         b = run_batched(0 if args.only == "batched_f64" else 1, steps, warmup, dev, fp, lay_b, aos_b,
                         tune_cache=tune_cache)
         if rank == 0:
