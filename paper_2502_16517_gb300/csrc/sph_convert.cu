@@ -56,19 +56,13 @@ __device__ __forceinline__ double kick1(double v, double a, double d) { return _
 // The leapfrog's first kick and its drift on one record (in place): v += a dtk, u += du/dt dtk, then x += v dt,
 // wrapped into [0, box) on a periodic grid, or mirrored at the walls of an open box (that velocity component turns;
 // a position still outside after one mirror, |v dt| > box, is put on the wall).  Returns the new position in x.
-__device__ __forceinline__ void kick_drift_record(uint8_t *rec, int off_x, const KickDrift &kd, const Grid &g,
-                                                  double x[3])
+__device__ __forceinline__ void kick_drift(double x[3], double v[3], double &u, const double a[3], double du,
+                                           double dtk, double dt, const Grid &g)
 {
-    double *xp = reinterpret_cast<double *>(rec + off_x);
-    double *vp = reinterpret_cast<double *>(rec + kd.off_v);
-    double *up = reinterpret_cast<double *>(rec + kd.off_u);
-    const double *ap = reinterpret_cast<const double *>(rec + kd.off_a);
-    const double du = *reinterpret_cast<const double *>(rec + kd.off_du);
-    double v[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        v[d] = kick1(vp[d], ap[d], kd.dtk);
-        double xn = __dadd_rn(xp[d], __dmul_rn(v[d], kd.dt));
+        v[d] = kick1(v[d], a[d], dtk);
+        double xn = __dadd_rn(x[d], __dmul_rn(v[d], dt));
         if (g.periodic) {
             if (xn >= g.box[d]) xn = __dsub_rn(xn, g.box[d]);
             else if (xn < 0.0) xn = __dadd_rn(xn, g.box[d]);
@@ -84,10 +78,30 @@ __device__ __forceinline__ void kick_drift_record(uint8_t *rec, int off_x, const
             else if (xn > g.box[d]) xn = g.box[d];
         }
         x[d] = xn;
-        xp[d] = xn;
+    }
+    u = kick1(u, du, dtk);
+}
+
+__device__ __forceinline__ void kick_drift_record(uint8_t *rec, int off_x, const KickDrift &kd, const Grid &g,
+                                                  double x[3])
+{
+    double *xp = reinterpret_cast<double *>(rec + off_x);
+    double *vp = reinterpret_cast<double *>(rec + kd.off_v);
+    double *up = reinterpret_cast<double *>(rec + kd.off_u);
+    const double *ap = reinterpret_cast<const double *>(rec + kd.off_a);
+    const double a[3] = {ap[0], ap[1], ap[2]};
+    double v[3] = {vp[0], vp[1], vp[2]};
+    double u = *up;
+    x[0] = xp[0];
+    x[1] = xp[1];
+    x[2] = xp[2];
+    kick_drift(x, v, u, a, *reinterpret_cast<const double *>(rec + kd.off_du), kd.dtk, kd.dt, g);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xp[d] = x[d];
         vp[d] = v[d];
     }
-    *up = kick1(*up, du, kd.dtk);
+    *up = u;
 }
 
 // KD: the records are kicked and drifted first (the leapfrog fused into the bin); their new positions are binned.
@@ -494,6 +508,162 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
     }
 }
 
+// Record pass (RecordPlan): CTA per tile of kTile consecutive records.  Phase 1 loads the plan's 16-byte chunks of
+// the tile's records into shared memory, consecutive threads on consecutive chunks (coalesced).  Phase 2, one
+// thread per record: with KD the kick and drift on the shared copies (written back to the record: x, v, u), then
+// the cell of the position in the grid or in its patch's grid, the histogram and the range check.  Phase 3 writes
+// the staged items in record order (coalesced), v and u predicted where the plan asks.
+template <bool KD, bool PATCH, bool F32>
+__global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos, int64_t stride, int n,
+                                                       const RecordPlan rp, Grid g,
+                                                       const int64_t *__restrict__ patch_start, int npatch,
+                                                       const int *__restrict__ patch_n,
+                                                       const double *__restrict__ patch_inv,
+                                                       const int *__restrict__ patch_cell_base,
+                                                       int *__restrict__ cell_of, int *__restrict__ count,
+                                                       unsigned *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int prange[2];
+    const int base = blockIdx.x * kTile;
+    const int cnt = min(kTile, n - base);
+    const int tid = threadIdx.x;
+    const int nch = rp.conv.nchunks;
+    uint4 *buf = reinterpret_cast<uint4 *>(smem);
+    const uint8_t *tile = aos + (int64_t)base * stride;
+    for (int idx = tid; idx < cnt * nch; idx += kTile) {
+        const int s = idx / nch;
+        const int c = idx - s * nch;
+        buf[idx] = *reinterpret_cast<const uint4 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[c]);
+    }
+    if (PATCH && tid < 2) {
+        // patch of the tile's first / last record: the largest p with patch_start[p] <= i
+        const int64_t i = base + (tid == 0 ? 0 : cnt - 1);
+        int lo = 0, hi = npatch;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (patch_start[mid] <= i) lo = mid; else hi = mid;
+        }
+        prange[tid] = lo;
+    }
+    __syncthreads();
+    double *dbuf = reinterpret_cast<double *>(smem);
+    if (tid < cnt) {
+        double *r = dbuf + (size_t)tid * nch * 2;
+        double x[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[d] = r[rp.x_ch[d] * 2 + rp.x_sub[d]];
+        if (KD) {
+            double v[3], a[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                v[d] = r[rp.kd_ch[3 + d] * 2 + rp.kd_sub[3 + d]];
+                a[d] = r[rp.kd_ch[6 + d] * 2 + rp.kd_sub[6 + d]];
+            }
+            double u = r[rp.kd_ch[9] * 2 + rp.kd_sub[9]];
+            const double du = r[rp.kd_ch[10] * 2 + rp.kd_sub[10]];
+            kick_drift(x, v, u, a, du, rp.dtk, rp.dt, g);
+            const double nv[7] = {x[0], x[1], x[2], v[0], v[1], v[2], u};
+            uint8_t *rec = aos + (int64_t)(base + tid) * stride;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                r[rp.kd_ch[k < 6 ? k : 9] * 2 + rp.kd_sub[k < 6 ? k : 9]] = nv[k];
+                *reinterpret_cast<double *>(rec + rp.kd_off[k]) = nv[k];
+            }
+        }
+        bool bad = false;
+        int c;
+        if (PATCH) {
+            int lo = prange[0], hi = prange[1] + 1;
+            const int64_t i = base + tid;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (patch_start[mid] <= i) lo = mid; else hi = mid;
+            }
+            const int nx = patch_n[3 * lo], ny = patch_n[3 * lo + 1], nz = patch_n[3 * lo + 2];
+            const int kx = cell_coord(x[0], patch_inv[3 * lo], nx, g.box[0], bad);
+            const int ky = cell_coord(x[1], patch_inv[3 * lo + 1], ny, g.box[1], bad);
+            const int kz = cell_coord(x[2], patch_inv[3 * lo + 2], nz, g.box[2], bad);
+            c = patch_cell_base[lo] + kx + nx * (ky + ny * kz);
+        } else {
+            const int kx = cell_coord(x[0], g.inv[0], g.n[0], g.box[0], bad);
+            const int ky = cell_coord(x[1], g.inv[1], g.n[1], g.box[1], bad);
+            const int kz = cell_coord(x[2], g.inv[2], g.n[2], g.box[2], bad);
+            c = kx + g.n[0] * (ky + g.n[1] * kz);
+        }
+        cell_of[base + tid] = c;
+        atomicAdd(&count[c], 1);
+        if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
+    }
+    __syncthreads();
+    const ConvPlan &plan = rp.conv;
+    const int ni = plan.nitems;
+    for (int idx = tid; idx < cnt * ni; idx += kTile) {
+        const int k = idx / cnt;
+        const int s = idx - k * cnt;
+        double v = dbuf[(s * nch + plan.item_chunk[k]) * 2 + plan.item_sub[k]];
+        const int pc = plan.item_pred_chunk[k];
+        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[(s * nch + pc) * 2 + plan.item_pred_sub[k]], plan.pred_dt));
+        if (!F32 || plan.item_pos[k] >= 0) {
+            static_cast<double *>(plan.soa[k])[base + s] = v;
+        } else {
+            static_cast<float *>(plan.soa[k])[base + s] = __double2float_rn(v);
+        }
+    }
+}
+
+// Permutation of staged items into slot order (PermutePlan), CTA per tile of kTile slots; FP32 positions become
+// (float)(x - origin of the slot's cell), with the origin as the gather computes it.
+template <bool F32>
+__global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm, const int *__restrict__ cell_of_slot,
+                                                   int n, const PermutePlan pp, const CellSpace cs)
+{
+    __shared__ int srec[kTile];
+    __shared__ double sorg[F32 ? 3 * kTile : 1];
+    __shared__ int prange[2];
+    const int base = blockIdx.x * kTile;
+    const int cnt = min(kTile, n - base);
+    const int tid = threadIdx.x;
+    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    bool haspos = false;
+    if (F32) {
+        for (int k = 0; k < pp.nitems; ++k) haspos = haspos || pp.item_pos[k] >= 0;
+        if (haspos && cs.npatch > 0 && tid < 2) {
+            CellLoc L;
+            locate_cell(cs, cell_of_slot[base + (tid == 0 ? 0 : cnt - 1)], L);
+            prange[tid] = L.patch;
+        }
+    }
+    __syncthreads();
+    if (F32 && haspos) {
+        const int lo = cs.npatch > 0 ? prange[0] : 0, hi = cs.npatch > 0 ? prange[1] + 1 : 0;
+        for (int s = tid; s < cnt; s += kTile) {
+            CellLoc L;
+            locate_cell_in(cs, cell_of_slot[base + s], lo, hi, L);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sorg[3 * s + a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < cnt * pp.nitems; idx += kTile) {
+        const int k = idx / cnt;
+        const int s = idx - k * cnt;
+        const int i = srec[s];
+        if (!F32) {
+            static_cast<double *>(pp.dst[k])[base + s] = static_cast<const double *>(pp.src[k])[i];
+        } else {
+            const int axis = pp.item_pos[k];
+            float o;
+            if (axis >= 0) {
+                o = __double2float_rn(__dsub_rn(static_cast<const double *>(pp.src[k])[i], sorg[3 * s + axis]));
+            } else {
+                o = static_cast<const float *>(pp.src[k])[i];
+            }
+            static_cast<float *>(pp.dst[k])[base + s] = o;
+        }
+    }
+}
+
 }  // namespace
 
 int scan_tmp_ints(int ncells_cap) { return 3 * ((ncells_cap + kScanChunk - 1) / kScanChunk) + 4; }
@@ -624,6 +794,101 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
     } else {
         cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_scatter<false><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+
+template <bool KD, bool PATCH, bool F32>
+void record_pass(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, const Grid &g, const int64_t *patch_start,
+                 int npatch, const int *patch_n, const double *patch_inv, const int *patch_cell_base, int *cell_of,
+                 int *count, unsigned *status, cudaStream_t st)
+{
+    const size_t smem = (size_t)kTile * rp.conv.nchunks * 16;
+    cudaFuncSetAttribute(k_record_pass<KD, PATCH, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_record_pass<KD, PATCH, F32><<<(n + kTile - 1) / kTile, kTile, smem, st>>>(
+        aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base, cell_of, count, status);
+}
+
+template <bool KD, bool PATCH>
+void record_pass_p(bool f32, uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, const Grid &g,
+                   const int64_t *patch_start, int npatch, const int *patch_n, const double *patch_inv,
+                   const int *patch_cell_base, int *cell_of, int *count, unsigned *status, cudaStream_t st)
+{
+    if (f32) {
+        record_pass<KD, PATCH, true>(aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base,
+                                     cell_of, count, status, st);
+    } else {
+        record_pass<KD, PATCH, false>(aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base,
+                                      cell_of, count, status, st);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
+                              int ncells, const int64_t *patch_start, int npatch, int ncap, int off_h, int *patch_n,
+                              double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
+                              int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
+                              int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl)
+{
+    const bool patches = npatch > 0;
+    double *patch_inv = patches ? patch_edge + 3 * (size_t)npatch : nullptr;
+    if (patches) {
+        k_patch_grid<<<npatch, 256, 0, st>>>(aos, stride, off_h, patch_start, g, ncap, patch_n, patch_edge,
+                                             patch_inv, patch_cells);
+        k_scan_cells<<<1, kScanThreads, 0, st>>>(patch_cells, npatch, nullptr, patch_cell_base, fill);
+        *nl += 2;
+    }
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        ++*nl;
+        if (rp.kd) {
+            if (patches) {
+                record_pass_p<true, true>(f32, aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv,
+                                          patch_cell_base, cell_of, count, status, st);
+            } else {
+                record_pass_p<true, false>(f32, aos, stride, n, rp, g, nullptr, 0, nullptr, nullptr, nullptr,
+                                           cell_of, count, status, st);
+            }
+        } else {
+            if (patches) {
+                record_pass_p<false, true>(f32, aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv,
+                                           patch_cell_base, cell_of, count, status, st);
+            } else {
+                record_pass_p<false, false>(f32, aos, stride, n, rp, g, nullptr, 0, nullptr, nullptr, nullptr,
+                                            cell_of, count, status, st);
+            }
+        }
+    }
+    launch_scan(count, ncells, patches ? ncells_dev : nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
+    if (n > 0) {
+        *nl += 2;
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        if (patches) {
+            k_cell_sort<<<2048, 256, 0, st>>>(cell_start, ncells, ncells_dev, perm_tmp, perm, cell_of_slot);
+        } else {
+            const long long threads = (long long)ncells * 32;
+            const long long blocks = (threads + 255) / 256;
+            k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,
+                                                                                    perm_tmp, perm, cell_of_slot);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
+                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl)
+{
+    if (n <= 0 || pp.nitems == 0) return cudaSuccess;
+    ++*nl;
+    const int blocks = (n + kTile - 1) / kTile;
+    if (f32) {
+        k_permute<true><<<blocks, kTile, 0, st>>>(perm, cell_of_slot, n, pp, cs);
+    } else {
+        k_permute<false><<<blocks, kTile, 0, st>>>(perm, cell_of_slot, n, pp, cs);
     }
     return cudaGetLastError();
 }

@@ -147,6 +147,31 @@ struct KickDrift {
     double dt;   // drift
 };
 
+// Record-order pass of a pass's bin and first gather, fused (and, with kd, the leapfrog's first kick and drift):
+// every record is read once, in record order, with coalesced 16-byte chunk loads; its cell is binned from the
+// (drifted) position, and the members of the view are written, in record order, to scratch arrays (predicted
+// where asked).  A permutation then moves them to the slot order of the SoA view.
+struct RecordPlan {
+    // chunks loaded per record; items: the staged view members, conv.soa[k] = their record-order scratch array
+    // (FP64 for FP64 views and for FP32 views' positions, which get their cell-relative cast in the permutation;
+    // float otherwise); item_pos marks the position items; item_pred_* / pred_dt as for the gather
+    ConvPlan conv;
+    int x_ch[3], x_sub[3];  // the position components in the loaded chunks
+    int kd;                 // kick and drift first
+    int kd_ch[11], kd_sub[11];  // x0..2, v0..2, a0..2, u, du/dt in the loaded chunks
+    int kd_off[7];              // record offsets of x0..2, v0..2, u (written back)
+    double dtk, dt;
+};
+
+// The permutation of a staged gather: dst[k][s] = src[k][perm[s]], positions of FP32 views cast relative to the
+// slot's cell origin as the gather does.
+struct PermutePlan {
+    int nitems;
+    int item_pos[kMaxItems];
+    const void *src[kMaxItems];
+    void *dst[kMaxItems];
+};
+
 // ---- launchers: each enqueues on `st`, adds the number of kernels it launched to *nl and returns the first
 // CUDA error (cudaGetLastError after the launches). ----
 // scan_tmp: scan_tmp_ints(cells) ints of scratch for the multi-CTA scan of large grids (nullptr: one-CTA scan).
@@ -166,6 +191,16 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
                                int *count, int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot,
                                int *scan_tmp, unsigned *status, cudaStream_t st, int *nl,
                                const KickDrift *kd = nullptr);
+
+// Bin with a record pass (see RecordPlan; records 16-byte aligned, stride a multiple of 16): single grids
+// (npatch == 0) or patch views (the per-patch grids of launch_bin_patches first).  f32: the view's precision.
+cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
+                              int ncells, const int64_t *patch_start, int npatch, int ncap, int off_h, int *patch_n,
+                              double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
+                              int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
+                              int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
+cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
+                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl);
 
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
                           const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &cs, bool f32,

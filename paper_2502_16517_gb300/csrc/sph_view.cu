@@ -57,6 +57,7 @@ struct sph_view_s {
 
     void *arena;
     sphk::SoaPtrs soa;
+    sphk::SoaPtrs stage;  // record-order scratch of the staged gather (8 bytes per element, n_max elements)
     sphk::Scratch scr;
     int *cell_of, *count, *cell_start, *fill, *perm_tmp, *perm, *cell_of_slot;
     int *scan_tmp;  // multi-CTA scan scratch
@@ -100,6 +101,7 @@ struct sph_view_s {
     double h_eta, h_tol;
     int h_max_iter;                // 0: sph_step runs one density pass
     int32_t integrator;            // SPH_KDK_* flags of sph_view_set_integrator
+    bool staged_bin;               // a pass bins and gathers in one record pass (do_bin_gather) where it can
     int32_t g_integrator;          // the flags the captured graph was captured with
 };
 
@@ -241,6 +243,11 @@ void carve(sph_view_s *v, Bump &b)
         for (int c = 0; c < 3; ++c) v->soa.p[f][c] = nullptr;
         if (!(v->present & SPH_BIT(f))) continue;
         for (int c = 0; c < kNcomp[f]; ++c) v->soa.p[f][c] = b.take(nm * v->esz);
+    }
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        for (int c = 0; c < 3; ++c) v->stage.p[f][c] = nullptr;
+        if (!(v->present & SPH_BIT(f))) continue;
+        for (int c = 0; c < kNcomp[f]; ++c) v->stage.p[f][c] = b.take(nm * 8);
     }
     memset(&v->scr, 0, sizeof(v->scr));
     if (v->prec == SPH_F64) {
@@ -418,6 +425,114 @@ sph_status do_bin_patches(sph_view_s *v, const void *aos, int64_t n, const int64
     v->n = n;
     v->binned = true;
     v->resident = 0;
+    return SPH_OK;
+}
+
+// The bin of a pass fused with its first gather (sphk::launch_bin_staged + launch_permute): one coalesced pass over
+// the records in record order bins them (after the leapfrog's first kick and drift when kd is given) and stages
+// the members of `mask` (v and u predicted by pred_dt when it is not 0); a permutation moves them to slot order.
+// Returns SPH_E_INVAL when the layout does not suit the record pass (16-byte aligned records with at most 12 loaded
+// chunks): the caller then bins and gathers separately.
+sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, const sphk::KickDrift *kd,
+                         double pred_dt)
+{
+    if (!aos || n < 0 || n > v->n_max || !mask_present(v, mask | SPH_BIT(SPH_X))) return SPH_E_INVAL;
+    if ((v->layout.stride % 16) != 0 || !aos_aligned(aos, 16) || v->layout.stride > 16 * sphk::kMaxChunks)
+        return SPH_E_INVAL;
+    if (v->npatch_max > 0 && (!v->patch_start || !(v->present & SPH_BIT(SPH_H)))) return SPH_E_INVAL;
+    sphk::RecordPlan rp;
+    memset(&rp, 0, sizeof(rp));
+    // chunks: the staged items (with their prediction sources), the position, the leapfrog's members
+    std::vector<int> chunks;
+    auto chunk_of = [&](int off) { return (off / 16) * 16; };
+    uint32_t need = mask | SPH_BIT(SPH_X);
+    if (kd) need |= SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
+    if (pred_dt != 0.0 && (mask & (SPH_BIT(SPH_V) | SPH_BIT(SPH_U)))) need |= SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT);
+    if (!mask_present(v, need)) return SPH_E_INVAL;
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(need & SPH_BIT(f))) continue;
+        for (int c = 0; c < kNcomp[f]; ++c) chunks.push_back(chunk_of(v->layout.off[f] + 8 * c));
+    }
+    std::sort(chunks.begin(), chunks.end());
+    chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
+    if (chunks.size() > 12) return SPH_E_INVAL;  // shared memory of the record pass: kTile x 12 x 16 B
+    auto locate = [&](int off, int *ch, int *sub) {
+        const int c0 = chunk_of(off);
+        *ch = (int)(std::lower_bound(chunks.begin(), chunks.end(), c0) - chunks.begin());
+        *sub = (off - c0) / 8;
+    };
+    ConvPlan &p = rp.conv;
+    p.nchunks = (int)chunks.size();
+    for (size_t k = 0; k < chunks.size(); ++k) p.chunk_off[k] = chunks[k];
+    const bool f32 = v->prec == SPH_F32;
+    int k = 0;
+    sphk::PermutePlan pp;
+    memset(&pp, 0, sizeof(pp));
+    for (int f = 0; f < SPH_NFIELDS; ++f) {
+        if (!(mask & SPH_BIT(f))) continue;
+        const int src = pred_dt != 0.0 ? pred_source(f) : -1;
+        for (int c = 0; c < kNcomp[f]; ++c, ++k) {
+            const int off = v->layout.off[f] + 8 * c;
+            p.item_off[k] = off;
+            locate(off, &p.item_chunk[k], &p.item_sub[k]);
+            p.item_pos[k] = (f == SPH_X && f32) ? c : -1;
+            p.item_pred_chunk[k] = -1;
+            if (src >= 0) locate(v->layout.off[src] + 8 * c, &p.item_pred_chunk[k], &p.item_pred_sub[k]);
+            p.soa[k] = v->stage.p[f][c];
+            pp.item_pos[k] = p.item_pos[k];
+            pp.src[k] = v->stage.p[f][c];
+            pp.dst[k] = v->soa.p[f][c];
+        }
+    }
+    p.nitems = k;
+    p.pred_dt = pred_dt;
+    pp.nitems = k;
+    for (int d = 0; d < 3; ++d) locate(v->layout.off[SPH_X] + 8 * d, &rp.x_ch[d], &rp.x_sub[d]);
+    if (kd) {
+        rp.kd = 1;
+        for (int d = 0; d < 3; ++d) {
+            locate(v->layout.off[SPH_X] + 8 * d, &rp.kd_ch[d], &rp.kd_sub[d]);
+            locate(v->layout.off[SPH_V] + 8 * d, &rp.kd_ch[3 + d], &rp.kd_sub[3 + d]);
+            locate(v->layout.off[SPH_A] + 8 * d, &rp.kd_ch[6 + d], &rp.kd_sub[6 + d]);
+            rp.kd_off[d] = v->layout.off[SPH_X] + 8 * d;
+            rp.kd_off[3 + d] = v->layout.off[SPH_V] + 8 * d;
+        }
+        locate(v->layout.off[SPH_U], &rp.kd_ch[9], &rp.kd_sub[9]);
+        locate(v->layout.off[SPH_DUDT], &rp.kd_ch[10], &rp.kd_sub[10]);
+        rp.kd_off[6] = v->layout.off[SPH_U];
+        rp.dtk = kd->dtk;
+        rp.dt = kd->dt;
+    }
+    const bool patches = v->npatch_max > 0;
+    if (patches) {
+        v->cs.npatch = v->npatch;
+        v->cs.patch_cell_base = v->patch_cell_base;
+        v->cs.patch_n = v->patch_n;
+        v->cs.patch_edge = v->patch_edge;
+        v->cs.ncells_dev = v->patch_cell_base + v->npatch;
+    }
+    cudaError_t e;
+    {
+        Phase ph(v, SPH_PH_BIN);
+        e = sphk::launch_bin_staged(static_cast<uint8_t *>(aos), v->layout.stride, (int)n, rp, f32, v->g, v->ncells,
+                                    patches ? v->patch_start : nullptr, patches ? v->npatch : 0, v->ncap,
+                                    patches ? v->layout.off[SPH_H] : 0, v->patch_n, v->patch_edge, v->patch_cells,
+                                    v->patch_cell_base, patches ? v->patch_cell_base + v->npatch : nullptr,
+                                    v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
+                                    v->cell_of_slot, v->scan_tmp, v->status, v->st, &ph.nl);
+        if (e == cudaSuccess && patches)
+            e = sphk::launch_work_list(v->cs, v->cell_start, v->ncells, v->cell_bucket, v->bucket_count,
+                                       v->work_order, v->work_count, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    {
+        Phase ph(v, SPH_PH_GATHER);
+        e = sphk::launch_permute(v->perm, v->cell_of_slot, (int)n, pp, v->cs, f32, v->st, &ph.nl);
+    }
+    if (e != cudaSuccess) return SPH_E_CUDA;
+    v->n = n;
+    v->binned = true;
+    v->resident = mask;
     return SPH_OK;
 }
 
@@ -602,15 +717,20 @@ sph_status do_pass(sph_view_s *v, void *aos, int64_t n, const sph_params *p, dou
         kdp = &kd;
     }
     const double kick_dt = 0.5 * dt;
-    if (v->npatch_max > 0) {
-        if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch, kdp)) != SPH_OK) return s;
-    } else if ((s = do_bin(v, aos, n, kdp)) != SPH_OK) {
-        return s;
-    }
     // union view: one gather of every member either loop reads (each record is read once: its bytes arrive in
     // whole memory sectors, so a second pass for the force's extra member v would read the records again)
     const uint32_t first = v->union_view ? ((dens_in(p) | force_in(p)) & ~dens_out(p)) : dens_in(p);
-    if ((s = do_gather(v, aos, n, first, pred_dt)) != SPH_OK) return s;
+    // the bin and the first gather in one record pass where the layout allows, else one after the other
+    if (v->staged_bin && do_bin_gather(v, aos, n, first, kdp, pred_dt) == SPH_OK) {
+        // staged
+    } else {
+        if (v->npatch_max > 0) {
+            if ((s = do_bin_patches(v, aos, n, v->patch_start, v->npatch, kdp)) != SPH_OK) return s;
+        } else if ((s = do_bin(v, aos, n, kdp)) != SPH_OK) {
+            return s;
+        }
+        if ((s = do_gather(v, aos, n, first, pred_dt)) != SPH_OK) return s;
+    }
     uint32_t d_out = dens_out(p);
     if (v->h_max_iter > 0) {
         if ((s = do_density_h(v, p, v->h_eta, v->h_tol, v->h_max_iter, true)) != SPH_OK) return s;
@@ -982,6 +1102,7 @@ sph_status sph_view_create(const sph_layout *layout, sph_prec prec, int64_t n_ma
     v->host_direct = false;
     v->h_max_iter = 0;
     v->integrator = SPH_KDK_PREDICT;
+    v->staged_bin = true;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
@@ -1060,6 +1181,7 @@ sph_status sph_patches_create(const sph_layout *layout, sph_prec prec, int64_t n
     v->host_direct = false;
     v->h_max_iter = 0;
     v->integrator = SPH_KDK_PREDICT;
+    v->staged_bin = true;
     v->h_eta = 1.2;
     v->h_tol = 1e-6;
     v->ev_free = new (std::nothrow) std::vector<cudaEvent_t>();
