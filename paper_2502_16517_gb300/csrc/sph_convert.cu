@@ -419,34 +419,34 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
     }
     const int nch = plan.nchunks;
     const int nload = cnt * nch;
+    const int cw = VEC16 ? 2 : 1;  // doubles per chunk
+    // a slot's chunks occupy rs doubles of shared memory, rs odd: the same member of 32 consecutive slots then
+    // falls on distinct bank pairs when phase 2 reads across slots
+    const int rs = (cw * nch) | 1;
+    double *dbuf = reinterpret_cast<double *>(smem);
     if (VEC16) {
-        uint4 *buf = reinterpret_cast<uint4 *>(smem);
         for (int idx = tid; idx < nload; idx += kTile) {
             const int s = idx / nch;
             const int c = idx - s * nch;
-            const uint4 *p = reinterpret_cast<const uint4 *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]);
-            buf[idx] = __ldg(p);
+            const double2 w = __ldg(reinterpret_cast<const double2 *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]));
+            dbuf[s * rs + 2 * c] = w.x;
+            dbuf[s * rs + 2 * c + 1] = w.y;
         }
     } else {
-        unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem);
         for (int idx = tid; idx < nload; idx += kTile) {
             const int s = idx / nch;
             const int c = idx - s * nch;
-            const unsigned long long *p =
-                reinterpret_cast<const unsigned long long *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]);
-            buf[idx] = __ldg(p);
+            dbuf[s * rs + c] = __ldg(reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]));
         }
     }
     __syncthreads();
-    const double *dbuf = reinterpret_cast<const double *>(smem);
-    const int cw = VEC16 ? 2 : 1;  // doubles per chunk
     const int nout = cnt * plan.nitems;
     for (int idx = tid; idx < nout; idx += kTile) {
         const int k = idx / cnt;
         const int s = idx - k * cnt;
-        double v = dbuf[(s * nch + plan.item_chunk[k]) * cw + plan.item_sub[k]];
+        double v = dbuf[s * rs + plan.item_chunk[k] * cw + plan.item_sub[k]];
         const int pc = plan.item_pred_chunk[k];
-        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[(s * nch + pc) * cw + plan.item_pred_sub[k]], plan.pred_dt));
+        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[s * rs + pc * cw + plan.item_pred_sub[k]], plan.pred_dt));
         if (!F32) {
             static_cast<double *>(plan.soa[k])[base + s] = v;
         } else {
@@ -475,7 +475,17 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
     const int ni = plan.nitems;
+    const bool kick = plan.kick_dt != 0.0;
+    double *skick = sval + (size_t)kTile * ni;  // with the kick: the records' v (3) and u, 4 per slot
     for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    if (kick) {
+        __syncthreads();
+        // the records' current v and u, read before any write of this CTA (their loads overlap the SoA reads)
+        for (int idx = tid; idx < 4 * cnt; idx += kTile) {
+            const int s = idx >> 2, c = idx & 3;
+            skick[idx] = *reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
+        }
+    }
     const int nin = cnt * ni;
     for (int idx = tid; idx < nin; idx += kTile) {
         const int k = idx / cnt;
@@ -497,13 +507,13 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.item_off[k]);
         *p = sval[idx];
     }
-    if (plan.kick_dt != 0.0) {
+    if (kick) {
         // the leapfrog's second kick fused into the epilogue: v += a dt/2, u += du/dt dt/2 with the values just
         // written (the same doubles the record now holds)
         for (int idx = tid; idx < 4 * cnt; idx += kTile) {
             const int s = idx >> 2, c = idx & 3;
             double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
-            *p = kick1(*p, sval[s * ni + plan.kick_item[c]], plan.kick_dt);
+            *p = kick1(skick[idx], sval[s * ni + plan.kick_item[c]], plan.kick_dt);
         }
     }
 }
@@ -529,12 +539,17 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
     const int nch = rp.conv.nchunks;
-    uint4 *buf = reinterpret_cast<uint4 *>(smem);
+    // a record's chunks occupy rs = 2 nch + 1 doubles of shared memory: the odd stride puts the same member of 32
+    // consecutive records on distinct bank pairs (phases 2 and 3 read across records)
+    const int rs = 2 * nch + 1;
+    double *dbuf = reinterpret_cast<double *>(smem);
     const uint8_t *tile = aos + (int64_t)base * stride;
     for (int idx = tid; idx < cnt * nch; idx += kTile) {
         const int s = idx / nch;
         const int c = idx - s * nch;
-        buf[idx] = *reinterpret_cast<const uint4 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[c]);
+        const double2 w = *reinterpret_cast<const double2 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[c]);
+        dbuf[s * rs + 2 * c] = w.x;
+        dbuf[s * rs + 2 * c + 1] = w.y;
     }
     if (PATCH && tid < 2) {
         // patch of the tile's first / last record: the largest p with patch_start[p] <= i
@@ -547,9 +562,8 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
         prange[tid] = lo;
     }
     __syncthreads();
-    double *dbuf = reinterpret_cast<double *>(smem);
     if (tid < cnt) {
-        double *r = dbuf + (size_t)tid * nch * 2;
+        double *r = dbuf + (size_t)tid * rs;
         double x[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) x[d] = r[rp.x_ch[d] * 2 + rp.x_sub[d]];
@@ -601,9 +615,9 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     for (int idx = tid; idx < cnt * ni; idx += kTile) {
         const int k = idx / cnt;
         const int s = idx - k * cnt;
-        double v = dbuf[(s * nch + plan.item_chunk[k]) * 2 + plan.item_sub[k]];
+        double v = dbuf[s * rs + plan.item_chunk[k] * 2 + plan.item_sub[k]];
         const int pc = plan.item_pred_chunk[k];
-        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[(s * nch + pc) * 2 + plan.item_pred_sub[k]], plan.pred_dt));
+        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[s * rs + pc * 2 + plan.item_pred_sub[k]], plan.pred_dt));
         if (!F32 || plan.item_pos[k] >= 0) {
             static_cast<double *>(plan.soa[k])[base + s] = v;
         } else {
@@ -760,7 +774,7 @@ cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const 
     if (n <= 0 || plan.nitems == 0) return cudaSuccess;
     ++*nl;
     const int blocks = (n + kTile - 1) / kTile;
-    const size_t smem = (size_t)kTile * plan.nchunks * (vec16 ? 16 : 8);
+    const size_t smem = (size_t)kTile * (((vec16 ? 2 : 1) * plan.nchunks) | 1) * 8;
     if (vec16) {
         if (f32) {
             cudaFuncSetAttribute(k_gather<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -787,7 +801,7 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
     if (n <= 0 || plan.nitems == 0) return cudaSuccess;
     ++*nl;
     const int blocks = (n + kTile - 1) / kTile;
-    const size_t smem = (size_t)kTile * plan.nitems * 8;
+    const size_t smem = (size_t)kTile * (plan.nitems + (plan.kick_dt != 0.0 ? 4 : 0)) * 8;
     if (f32) {
         cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_scatter<true><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
@@ -805,7 +819,7 @@ void record_pass(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, cons
                  int npatch, const int *patch_n, const double *patch_inv, const int *patch_cell_base, int *cell_of,
                  int *count, unsigned *status, cudaStream_t st)
 {
-    const size_t smem = (size_t)kTile * rp.conv.nchunks * 16;
+    const size_t smem = (size_t)kTile * (2 * rp.conv.nchunks + 1) * 8;
     cudaFuncSetAttribute(k_record_pass<KD, PATCH, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_record_pass<KD, PATCH, F32><<<(n + kTile - 1) / kTile, kTile, smem, st>>>(
         aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base, cell_of, count, status);
