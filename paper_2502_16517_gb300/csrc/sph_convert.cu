@@ -33,6 +33,7 @@ namespace sphk {
 namespace {
 
 constexpr int kTile = 256;
+constexpr int kUnroll = 8;  // independent global loads a conversion thread issues before it stores any of them
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int cell_coord(double x, double inv, int n, double box, bool &bad)
@@ -424,19 +425,50 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
     // falls on distinct bank pairs when phase 2 reads across slots
     const int rs = (cw * nch) | 1;
     double *dbuf = reinterpret_cast<double *>(smem);
+    // several independent loads in flight per thread before the first store (see k_record_pass)
     if (VEC16) {
-        for (int idx = tid; idx < nload; idx += kTile) {
-            const int s = idx / nch;
-            const int c = idx - s * nch;
-            const double2 w = __ldg(reinterpret_cast<const double2 *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]));
-            dbuf[s * rs + 2 * c] = w.x;
-            dbuf[s * rs + 2 * c + 1] = w.y;
+        for (int i0 = tid; i0 < nload; i0 += kUnroll * kTile) {
+            double2 w[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < nload) {
+                    const int s = idx / nch;
+                    w[u] = __ldg(reinterpret_cast<const double2 *>(aos + (int64_t)srec[s] * stride +
+                                                                   plan.chunk_off[idx - s * nch]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < nload) {
+                    const int s = idx / nch;
+                    const int c = idx - s * nch;
+                    dbuf[s * rs + 2 * c] = w[u].x;
+                    dbuf[s * rs + 2 * c + 1] = w[u].y;
+                }
+            }
         }
     } else {
-        for (int idx = tid; idx < nload; idx += kTile) {
-            const int s = idx / nch;
-            const int c = idx - s * nch;
-            dbuf[s * rs + c] = __ldg(reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride + plan.chunk_off[c]));
+        for (int i0 = tid; i0 < nload; i0 += kUnroll * kTile) {
+            double w[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < nload) {
+                    const int s = idx / nch;
+                    w[u] = __ldg(reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride +
+                                                                  plan.chunk_off[idx - s * nch]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < nload) {
+                    const int s = idx / nch;
+                    dbuf[s * rs + idx - s * nch] = w[u];
+                }
+            }
         }
     }
     __syncthreads();
@@ -481,24 +513,49 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
     if (kick) {
         __syncthreads();
         // the records' current v and u, read before any write of this CTA (their loads overlap the SoA reads)
-        for (int idx = tid; idx < 4 * cnt; idx += kTile) {
-            const int s = idx >> 2, c = idx & 3;
-            skick[idx] = *reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
+        for (int i0 = tid; i0 < 4 * cnt; i0 += 4 * kTile) {
+            double w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < 4 * cnt)
+                    w[u] = *reinterpret_cast<const double *>(aos + (int64_t)srec[idx >> 2] * stride +
+                                                             plan.kick_off[idx & 3]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = i0 + u * kTile;
+                if (idx < 4 * cnt) skick[idx] = w[u];
+            }
         }
     }
     const int nin = cnt * ni;
-    for (int idx = tid; idx < nin; idx += kTile) {
-        const int k = idx / cnt;
-        const int s = idx - k * cnt;
-        double v;
-        if (!F32) {
-            v = static_cast<const double *>(plan.soa[k])[base + s];
-        } else {
-            v = (double)static_cast<const float *>(plan.soa[k])[base + s];
-            const int axis = plan.item_pos[k];
-            if (axis >= 0) v = __dadd_rn(cell_origin(cs, cell_of_slot[base + s], axis), v);
+    for (int i0 = tid; i0 < nin; i0 += kUnroll * kTile) {
+        double w[kUnroll];  // kUnroll independent loads in flight before the first store
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < nin) {
+                const int k = idx / cnt;
+                const int s = idx - k * cnt;
+                w[u] = F32 ? (double)static_cast<const float *>(plan.soa[k])[base + s]
+                           : static_cast<const double *>(plan.soa[k])[base + s];
+            }
         }
-        sval[s * ni + k] = v;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < nin) {
+                const int k = idx / cnt;
+                const int s = idx - k * cnt;
+                double v = w[u];
+                if (F32) {
+                    const int axis = plan.item_pos[k];
+                    if (axis >= 0) v = __dadd_rn(cell_origin(cs, cell_of_slot[base + s], axis), v);
+                }
+                sval[s * ni + k] = v;
+            }
+        }
     }
     __syncthreads();
     for (int idx = tid; idx < nin; idx += kTile) {
@@ -544,12 +601,28 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     const int rs = 2 * nch + 1;
     double *dbuf = reinterpret_cast<double *>(smem);
     const uint8_t *tile = aos + (int64_t)base * stride;
-    for (int idx = tid; idx < cnt * nch; idx += kTile) {
-        const int s = idx / nch;
-        const int c = idx - s * nch;
-        const double2 w = *reinterpret_cast<const double2 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[c]);
-        dbuf[s * rs + 2 * c] = w.x;
-        dbuf[s * rs + 2 * c + 1] = w.y;
+    // kUnroll independent 16-byte loads per thread are issued before the first of them is stored, so that each
+    // thread keeps several loads in flight (one at a time bounds the pass by memory latency, not bandwidth)
+    for (int i0 = tid; i0 < cnt * nch; i0 += kUnroll * kTile) {
+        double2 w[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < cnt * nch) {
+                const int s = idx / nch;
+                w[u] = *reinterpret_cast<const double2 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[idx - s * nch]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < cnt * nch) {
+                const int s = idx / nch;
+                const int c = idx - s * nch;
+                dbuf[s * rs + 2 * c] = w[u].x;
+                dbuf[s * rs + 2 * c + 1] = w[u].y;
+            }
+        }
     }
     if (PATCH && tid < 2) {
         // patch of the tile's first / last record: the largest p with patch_start[p] <= i
@@ -659,21 +732,34 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < cnt * pp.nitems; idx += kTile) {
-        const int k = idx / cnt;
-        const int s = idx - k * cnt;
-        const int i = srec[s];
-        if (!F32) {
-            static_cast<double *>(pp.dst[k])[base + s] = static_cast<const double *>(pp.src[k])[i];
-        } else {
-            const int axis = pp.item_pos[k];
-            float o;
-            if (axis >= 0) {
-                o = __double2float_rn(__dsub_rn(static_cast<const double *>(pp.src[k])[i], sorg[3 * s + axis]));
-            } else {
-                o = static_cast<const float *>(pp.src[k])[i];
+    const int total = cnt * pp.nitems;
+    for (int i0 = tid; i0 < total; i0 += kUnroll * kTile) {
+        double w[kUnroll];  // kUnroll independent loads in flight before the first store
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < total) {
+                const int k = idx / cnt;
+                const int i = srec[idx - k * cnt];
+                w[u] = (!F32 || pp.item_pos[k] >= 0) ? static_cast<const double *>(pp.src[k])[i]
+                                                     : (double)static_cast<const float *>(pp.src[k])[i];
             }
-            static_cast<float *>(pp.dst[k])[base + s] = o;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = i0 + u * kTile;
+            if (idx < total) {
+                const int k = idx / cnt;
+                const int s = idx - k * cnt;
+                if (!F32) {
+                    static_cast<double *>(pp.dst[k])[base + s] = w[u];
+                } else {
+                    const int axis = pp.item_pos[k];
+                    // positions: (float)(x - origin); other members: the float the record pass stored (exact)
+                    const float o = axis >= 0 ? __double2float_rn(__dsub_rn(w[u], sorg[3 * s + axis])) : (float)w[u];
+                    static_cast<float *>(pp.dst[k])[base + s] = o;
+                }
+            }
         }
     }
 }
