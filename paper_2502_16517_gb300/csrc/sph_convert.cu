@@ -36,6 +36,12 @@ constexpr int kTile = 256;
 constexpr int kUnroll = 8;  // independent global loads a conversion thread issues before it stores any of them
 constexpr unsigned kFull = 0xffffffffu;
 
+// q / d for 0 <= q < 256 d and 1 <= d <= 40 by multiplication with inv = ceil(2^20 / d) and a shift (exact in that
+// range, checked exhaustively; the product stays below 2^29): the conversion kernels' index arithmetic without
+// integer division.
+__host__ __device__ __forceinline__ unsigned div_inv(unsigned d) { return ((1u << 20) + d - 1) / d; }
+__device__ __forceinline__ int div_small(int q, unsigned inv) { return (int)(((unsigned)q * inv) >> 20); }
+
 __device__ __forceinline__ int cell_coord(double x, double inv, int n, double box, bool &bad)
 {
     if (!(x >= 0.0 && x <= box)) bad = true;
@@ -426,6 +432,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
     const int rs = (cw * nch) | 1;
     double *dbuf = reinterpret_cast<double *>(smem);
     // several independent loads in flight per thread before the first store (see k_record_pass)
+    const unsigned inv_nch = div_inv(nch);
     if (VEC16) {
         for (int i0 = tid; i0 < nload; i0 += kUnroll * kTile) {
             double2 w[kUnroll];
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             for (int u = 0; u < kUnroll; ++u) {
                 const int idx = i0 + u * kTile;
                 if (idx < nload) {
-                    const int s = idx / nch;
+                    const int s = div_small(idx, inv_nch);
                     w[u] = __ldg(reinterpret_cast<const double2 *>(aos + (int64_t)srec[s] * stride +
                                                                    plan.chunk_off[idx - s * nch]));
                 }
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             for (int u = 0; u < kUnroll; ++u) {
                 const int idx = i0 + u * kTile;
                 if (idx < nload) {
-                    const int s = idx / nch;
+                    const int s = div_small(idx, inv_nch);
                     const int c = idx - s * nch;
                     dbuf[s * rs + 2 * c] = w[u].x;
                     dbuf[s * rs + 2 * c + 1] = w[u].y;
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             for (int u = 0; u < kUnroll; ++u) {
                 const int idx = i0 + u * kTile;
                 if (idx < nload) {
-                    const int s = idx / nch;
+                    const int s = div_small(idx, inv_nch);
                     w[u] = __ldg(reinterpret_cast<const double *>(aos + (int64_t)srec[s] * stride +
                                                                   plan.chunk_off[idx - s * nch]));
                 }
@@ -465,17 +472,15 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
             for (int u = 0; u < kUnroll; ++u) {
                 const int idx = i0 + u * kTile;
                 if (idx < nload) {
-                    const int s = idx / nch;
+                    const int s = div_small(idx, inv_nch);
                     dbuf[s * rs + idx - s * nch] = w[u];
                 }
             }
         }
     }
     __syncthreads();
-    const int nout = cnt * plan.nitems;
-    for (int idx = tid; idx < nout; idx += kTile) {
-        const int k = idx / cnt;
-        const int s = idx - k * cnt;
+    for (int kk = 0; kk < plan.nitems * (tid < cnt ? 1 : 0); ++kk) {  // one slot per thread, item by item
+        const int k = kk, s = tid;
         double v = dbuf[s * rs + plan.item_chunk[k] * cw + plan.item_sub[k]];
         const int pc = plan.item_pred_chunk[k];
         if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[s * rs + pc * cw + plan.item_pred_sub[k]], plan.pred_dt));
@@ -507,62 +512,52 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
     const int ni = plan.nitems;
+    const int sst = ni | 1;  // odd stride of a slot's values in shared memory (no bank conflicts across slots)
     const bool kick = plan.kick_dt != 0.0;
-    double *skick = sval + (size_t)kTile * ni;  // with the kick: the records' v (3) and u, 4 per slot
-    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
-    if (kick) {
-        __syncthreads();
-        // the records' current v and u, read before any write of this CTA (their loads overlap the SoA reads)
-        for (int i0 = tid; i0 < 4 * cnt; i0 += 4 * kTile) {
-            double w[4];
+    double *skick = sval + (size_t)kTile * sst;  // with the kick: the records' v (3) and u, 4 per slot
+    if (tid < cnt) {
+        // phase 1, one slot per thread: its record, its SoA values and (kick) the record's v and u, all loads
+        // independent, so they are in flight together
+        const int s = tid;
+        const int rec = perm[base + s];
+        srec[s] = rec;
+        double w[kMaxItems];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = i0 + u * kTile;
-                if (idx < 4 * cnt)
-                    w[u] = *reinterpret_cast<const double *>(aos + (int64_t)srec[idx >> 2] * stride +
-                                                             plan.kick_off[idx & 3]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = i0 + u * kTile;
-                if (idx < 4 * cnt) skick[idx] = w[u];
-            }
-        }
-    }
-    const int nin = cnt * ni;
-    for (int i0 = tid; i0 < nin; i0 += kUnroll * kTile) {
-        double w[kUnroll];  // kUnroll independent loads in flight before the first store
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int idx = i0 + u * kTile;
-            if (idx < nin) {
-                const int k = idx / cnt;
-                const int s = idx - k * cnt;
-                w[u] = F32 ? (double)static_cast<const float *>(plan.soa[k])[base + s]
+        for (int k = 0; k < kMaxItems; ++k) {
+            if (k < ni)
+                w[k] = F32 ? (double)static_cast<const float *>(plan.soa[k])[base + s]
                            : static_cast<const double *>(plan.soa[k])[base + s];
-            }
+        }
+        double kv[4];
+        if (kick) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                kv[c] = *reinterpret_cast<const double *>(aos + (int64_t)rec * stride + plan.kick_off[c]);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int idx = i0 + u * kTile;
-            if (idx < nin) {
-                const int k = idx / cnt;
-                const int s = idx - k * cnt;
-                double v = w[u];
-                if (F32) {
-                    const int axis = plan.item_pos[k];
-                    if (axis >= 0) v = __dadd_rn(cell_origin(cs, cell_of_slot[base + s], axis), v);
-                }
-                sval[s * ni + k] = v;
+        for (int k = 0; k < kMaxItems; ++k) {
+            if (k >= ni) break;
+            double v = w[k];
+            if (F32) {
+                const int axis = plan.item_pos[k];
+                if (axis >= 0) v = __dadd_rn(cell_origin(cs, cell_of_slot[base + s], axis), v);
             }
+            sval[s * sst + k] = v;
+        }
+        if (kick) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) skick[4 * s + c] = kv[c];
         }
     }
     __syncthreads();
+    // phase 2: consecutive threads write consecutive members of a record (a warp's stores cover few records)
+    const int nin = cnt * ni;
+    const unsigned inv_ni = div_inv(ni);
     for (int idx = tid; idx < nin; idx += kTile) {
-        const int s = idx / ni;
+        const int s = div_small(idx, inv_ni);
         const int k = idx - s * ni;
         double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.item_off[k]);
-        *p = sval[idx];
+        *p = sval[s * sst + k];
     }
     if (kick) {
         // the leapfrog's second kick fused into the epilogue: v += a dt/2, u += du/dt dt/2 with the values just
@@ -570,7 +565,7 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         for (int idx = tid; idx < 4 * cnt; idx += kTile) {
             const int s = idx >> 2, c = idx & 3;
             double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
-            *p = kick1(skick[idx], sval[s * ni + plan.kick_item[c]], plan.kick_dt);
+            *p = kick1(skick[idx], sval[s * sst + plan.kick_item[c]], plan.kick_dt);
         }
     }
 }
@@ -603,13 +598,14 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     const uint8_t *tile = aos + (int64_t)base * stride;
     // kUnroll independent 16-byte loads per thread are issued before the first of them is stored, so that each
     // thread keeps several loads in flight (one at a time bounds the pass by memory latency, not bandwidth)
+    const unsigned inv_nch = div_inv(nch);
     for (int i0 = tid; i0 < cnt * nch; i0 += kUnroll * kTile) {
         double2 w[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int idx = i0 + u * kTile;
             if (idx < cnt * nch) {
-                const int s = idx / nch;
+                const int s = div_small(idx, inv_nch);
                 w[u] = *reinterpret_cast<const double2 *>(tile + (int64_t)s * stride + rp.conv.chunk_off[idx - s * nch]);
             }
         }
@@ -617,7 +613,7 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
         for (int u = 0; u < kUnroll; ++u) {
             const int idx = i0 + u * kTile;
             if (idx < cnt * nch) {
-                const int s = idx / nch;
+                const int s = div_small(idx, inv_nch);
                 const int c = idx - s * nch;
                 dbuf[s * rs + 2 * c] = w[u].x;
                 dbuf[s * rs + 2 * c + 1] = w[u].y;
@@ -684,17 +680,17 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     }
     __syncthreads();
     const ConvPlan &plan = rp.conv;
-    const int ni = plan.nitems;
-    for (int idx = tid; idx < cnt * ni; idx += kTile) {
-        const int k = idx / cnt;
-        const int s = idx - k * cnt;
-        double v = dbuf[s * rs + plan.item_chunk[k] * 2 + plan.item_sub[k]];
-        const int pc = plan.item_pred_chunk[k];
-        if (pc >= 0) v = __dadd_rn(v, __dmul_rn(dbuf[s * rs + pc * 2 + plan.item_pred_sub[k]], plan.pred_dt));
-        if (!F32 || plan.item_pos[k] >= 0) {
-            static_cast<double *>(plan.soa[k])[base + s] = v;
-        } else {
-            static_cast<float *>(plan.soa[k])[base + s] = __double2float_rn(v);
+    if (tid < cnt) {  // one record per thread (kTile records per tile): item by item, coalesced across threads
+        const double *r = dbuf + (size_t)tid * rs;
+        for (int k = 0; k < plan.nitems; ++k) {
+            double v = r[plan.item_chunk[k] * 2 + plan.item_sub[k]];
+            const int pc = plan.item_pred_chunk[k];
+            if (pc >= 0) v = __dadd_rn(v, __dmul_rn(r[pc * 2 + plan.item_pred_sub[k]], plan.pred_dt));
+            if (!F32 || plan.item_pos[k] >= 0) {
+                static_cast<double *>(plan.soa[k])[base + tid] = v;
+            } else {
+                static_cast<float *>(plan.soa[k])[base + tid] = __double2float_rn(v);
+            }
         }
     }
 }
@@ -732,33 +728,25 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
         }
         __syncthreads();
     }
-    const int total = cnt * pp.nitems;
-    for (int i0 = tid; i0 < total; i0 += kUnroll * kTile) {
-        double w[kUnroll];  // kUnroll independent loads in flight before the first store
+    if (tid < cnt) {  // one slot per thread: all of its items' loads in flight before the stores
+        const int s = tid, i = srec[s];
+        double w[kMaxItems];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int idx = i0 + u * kTile;
-            if (idx < total) {
-                const int k = idx / cnt;
-                const int i = srec[idx - k * cnt];
-                w[u] = (!F32 || pp.item_pos[k] >= 0) ? static_cast<const double *>(pp.src[k])[i]
+        for (int k = 0; k < kMaxItems; ++k) {
+            if (k < pp.nitems)
+                w[k] = (!F32 || pp.item_pos[k] >= 0) ? static_cast<const double *>(pp.src[k])[i]
                                                      : (double)static_cast<const float *>(pp.src[k])[i];
-            }
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int idx = i0 + u * kTile;
-            if (idx < total) {
-                const int k = idx / cnt;
-                const int s = idx - k * cnt;
-                if (!F32) {
-                    static_cast<double *>(pp.dst[k])[base + s] = w[u];
-                } else {
-                    const int axis = pp.item_pos[k];
-                    // positions: (float)(x - origin); other members: the float the record pass stored (exact)
-                    const float o = axis >= 0 ? __double2float_rn(__dsub_rn(w[u], sorg[3 * s + axis])) : (float)w[u];
-                    static_cast<float *>(pp.dst[k])[base + s] = o;
-                }
+        for (int k = 0; k < kMaxItems; ++k) {
+            if (k >= pp.nitems) break;
+            if (!F32) {
+                static_cast<double *>(pp.dst[k])[base + s] = w[k];
+            } else {
+                const int axis = pp.item_pos[k];
+                // positions: (float)(x - origin); other members: the float the record pass stored (exact)
+                const float o = axis >= 0 ? __double2float_rn(__dsub_rn(w[k], sorg[3 * s + axis])) : (float)w[k];
+                static_cast<float *>(pp.dst[k])[base + s] = o;
             }
         }
     }
@@ -887,7 +875,7 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
     if (n <= 0 || plan.nitems == 0) return cudaSuccess;
     ++*nl;
     const int blocks = (n + kTile - 1) / kTile;
-    const size_t smem = (size_t)kTile * (plan.nitems + (plan.kick_dt != 0.0 ? 4 : 0)) * 8;
+    const size_t smem = (size_t)kTile * ((plan.nitems | 1) + (plan.kick_dt != 0.0 ? 4 : 0)) * 8;
     if (f32) {
         cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_scatter<true><<<blocks, kTile, smem, st>>>(aos, stride, perm, cell_of_slot, n, plan, g);
