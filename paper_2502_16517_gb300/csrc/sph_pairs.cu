@@ -1616,12 +1616,10 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
 //                whose term is barely dearer than the distance test;
 //   otherwise:   the lane tests 32 of its candidates into a bit mask, then evaluates its hits -- the force,
 //                whose term costs several times the test and covers ~15 % of the candidates.
-template <class K, int NT>
+template <class K>
 struct LaneShared {
     NbrTable nb;
     unsigned long long pairs;
-    // the filtered sweep's per-warp hit queues: 32 entries per lane (one window), tile positions
-    unsigned short q[K::kMasked ? 1 : NT / 32][K::kMasked ? 1 : 1024];
 };
 
 template <class K>
@@ -1660,62 +1658,9 @@ __device__ __forceinline__ unsigned hit_sweep(const typename K::Args &A, const t
     return nhit;
 }
 
-// The filtered sweep with the hits of a window shared out among the lanes of the particle.  Windows of 32 candidates
-// per lane, as in hit_sweep; the lanes of one particle within a warp (a contiguous lane range, from
-// __match_any_sync) write their hits to their part of the warp's queue in lane order and then evaluate them
-// round-robin, so a lane with many hits no longer holds up the others (the evaluation is several times dearer
-// than the test).  Every lane of the warp runs every window (inactive lanes have no candidates); the pairing of
-// hits to lanes is fixed by the data, so results are deterministic.
-template <class K>
-__device__ __forceinline__ unsigned hit_sweep_shared(const typename K::Args &A, const typename K::Lhs &L,
-                                                     const typename K::Tile &T, int li, int s, int ns, int tn,
-                                                     bool active, unsigned short *wq, typename K::Part &P)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned gmask = __match_any_sync(kFull, li);
-    const int lo = __ffs(gmask) - 1, g = __popc(gmask), j = lane - lo;
-    unsigned short *q = wq + lo * 32;
-    const int stride = 32 * ns;
-    const int nwin = active ? (tn + stride - 1) / stride : 0;
-    // the windows: every lane of a warp runs the warp's largest count (particles of a warp share tn and ns)
-    const int nwin_w = __reduce_max_sync(kFull, (unsigned)nwin);
-    unsigned nhit = 0;
-    for (int w = 0; w < nwin_w; ++w) {
-        const int k0 = w * stride + s;
-        unsigned hits = 0;
-        if (w < nwin) {
-#pragma unroll
-            for (int b = 0; b < 32; ++b) {
-                const int k = k0 + b * ns;
-                if (k < tn && K::filter(L, T, k)) hits |= 1u << b;
-            }
-        }
-        const int c = __popc(hits);
-        nhit += c;
-        // exclusive prefix of the hit counts over my particle's lanes (they are contiguous from lo)
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (j >= o) incl += t;
-        }
-        const int total = __shfl_sync(kFull, incl, lo + g - 1);
-        int pos = incl - c;
-        while (hits) {
-            const int b = __ffs(hits) - 1;
-            hits &= hits - 1u;
-            q[pos++] = (unsigned short)(k0 + b * ns);
-        }
-        __syncwarp();
-        for (int e = j; e < total; e += g) K::eval(A, L, T, q[e], P);
-        __syncwarp();  // the queue is rewritten by the next window
-    }
-    return nhit;
-}
-
 template <class K, int NT>
 __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, int c, const typename K::Tile &T,
-                                                   LaneShared<K, NT> &S, unsigned char *smem)
+                                                   LaneShared<K> &S, unsigned char *smem)
 {
     if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
@@ -1750,10 +1695,12 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
                 if (tid == 0 && (tn & 1)) K::pad(T, tn);  // tn < tj here: tiles are multiples of 64
             }
             __syncthreads();
-            if constexpr (K::kMasked) {
-                if (active) K::sweep(L, T, s, ns, tn, P);
-            } else {
-                my_pairs += hit_sweep_shared<K>(A, L, T, active ? li : -1, s, ns, tn, active, S.q[tid >> 5], P);
+            if (active) {
+                if constexpr (K::kMasked) {
+                    K::sweep(L, T, s, ns, tn, P);
+                } else {
+                    my_pairs += hit_sweep<K>(A, L, T, s, ns, tn, P);
+                }
             }
         }
         if constexpr (K::kMasked) {
@@ -1783,7 +1730,7 @@ template <class K, int NT>
 __global__ void __launch_bounds__(NT, K::min_ctas(NT)) k_cell_lanes(const typename K::Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LaneShared<K, NT> S;
+    __shared__ LaneShared<K> S;
     const typename K::Tile T = K::carve(smem, A.cm.tj);
     process_cell_lanes<K, NT>(A, blockIdx.x, T, S, smem);
 }
@@ -1794,7 +1741,7 @@ __global__ void __launch_bounds__(NT, K::min_ctas_persist(NT)) k_cell_lanes_pers
                                                                      const int *__restrict__ count, int *next)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ LaneShared<K, NT> S;
+    __shared__ LaneShared<K> S;
     __shared__ int w;
     const typename K::Tile T = K::carve(smem, A.cm.tj);
     const int total = *count;
