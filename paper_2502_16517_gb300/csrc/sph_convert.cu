@@ -42,6 +42,28 @@ constexpr unsigned kFull = 0xffffffffu;
 __host__ __device__ __forceinline__ unsigned div_inv(unsigned d) { return ((1u << 20) + d - 1) / d; }
 __device__ __forceinline__ int div_small(int q, unsigned inv) { return (int)(((unsigned)q * inv) >> 20); }
 
+// cell_coord on the integer pipe: the same value and the same range flag as cell_coord below, with one FP64
+// multiply; the compares and the floor work on the bit patterns (for doubles >= 0 they order like the values; a
+// set sign bit is a negative value, -0.0 or a negative NaN; an all-ones exponent is an infinity or a NaN).
+__device__ __forceinline__ int cell_coord_bits(double x, double inv, int n, double box, bool &bad)
+{
+    const long long kNeg0 = (long long)0x8000000000000000ULL;
+    const long long xb = __double_as_longlong(x);
+    const long long bb = __double_as_longlong(box);  // box > 0, finite
+    // x >= 0 && x <= box, false for NaN: -0.0 counts as 0; a positive NaN or +inf has bits above any finite box
+    if (!((xb >= 0 && xb <= bb) || xb == kNeg0)) bad = true;
+    const long long yb = __double_as_longlong(__dmul_rn(x, inv));
+    if (yb < 0) return 0;                                   // negative, -0.0 or negative NaN: floor < 0 or NaN
+    const int ex = (int)(yb >> 52);                          // biased exponent (sign clear)
+    if (ex == 2047) return (yb & 0xFFFFFFFFFFFFFLL) ? 0 : n - 1;  // NaN: 0; +inf: clamped
+    const int e = ex - 1023;
+    if (e < 0) return 0;                                     // 0 <= y < 1
+    if (e >= 31) return n - 1;                               // y >= 2^31 > n - 1
+    const long long m = (yb & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int f = (int)(m >> (52 - e));                      // floor(y)
+    return f > n - 1 ? n - 1 : f;
+}
+
 __device__ __forceinline__ int cell_coord(double x, double inv, int n, double box, bool &bad)
 {
     if (!(x >= 0.0 && x <= box)) bad = true;
@@ -87,6 +109,48 @@ __device__ __forceinline__ void kick_drift(double x[3], double v[3], double &u, 
         x[d] = xn;
     }
     u = kick1(u, du, dtk);
+}
+
+// kick_drift with the reuse of the product a dtk for the predicted velocity (v_pred = v_half + a dtk, the oracle's
+// second application of the same kick: the same product, so the same bits), and the position compares on the
+// integer pipe (bit patterns as in cell_coord_bits).  vp, up receive the predicted v, u.
+__device__ __forceinline__ void kick_drift_predict(double x[3], double v[3], double &u, const double a[3], double du,
+                                                   double dtk, double dt, const Grid &g, double vp[3], double &up)
+{
+    const long long kNeg0 = (long long)0x8000000000000000ULL;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double ad = __dmul_rn(a[d], dtk);
+        v[d] = __dadd_rn(v[d], ad);
+        double xn = __dadd_rn(x[d], __dmul_rn(v[d], dt));
+        const long long xb = __double_as_longlong(xn), bb = __double_as_longlong(g.box[d]);
+        const bool nan = ((xb >> 52) & 0x7FF) == 0x7FF && (xb & 0xFFFFFFFFFFFFFLL) != 0;
+        const bool neg = xb < 0 && xb != kNeg0 && !nan;      // xn < 0
+        const bool ge = xb >= 0 && xb >= bb && !nan;         // xn >= box (positive, not NaN)
+        const bool gt = ge && xb != bb;                      // xn > box
+        if (g.periodic) {
+            if (ge) xn = __dsub_rn(xn, g.box[d]);
+            else if (neg) xn = __dadd_rn(xn, g.box[d]);
+        } else {
+            if (neg) {
+                xn = -xn;
+                v[d] = -v[d];
+            } else if (gt) {
+                xn = __dsub_rn(__dadd_rn(g.box[d], g.box[d]), xn);
+                v[d] = -v[d];
+            }
+            // still outside after one mirror: onto the wall
+            const long long yb = __double_as_longlong(xn);
+            const bool ynan = ((yb >> 52) & 0x7FF) == 0x7FF && (yb & 0xFFFFFFFFFFFFFLL) != 0;
+            if (yb < 0 && yb != kNeg0 && !ynan) xn = 0.0;
+            else if (yb >= 0 && yb > bb && !ynan) xn = g.box[d];
+        }
+        x[d] = xn;
+        vp[d] = __dadd_rn(v[d], ad);
+    }
+    const double ud = __dmul_rn(du, dtk);
+    u = __dadd_rn(u, ud);
+    up = __dadd_rn(u, ud);
 }
 
 __device__ __forceinline__ void kick_drift_record(uint8_t *rec, int off_x, const KickDrift &kd, const Grid &g,
@@ -645,12 +709,16 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
             }
             double u = r[rp.kd_ch[9] * 2 + rp.kd_sub[9]];
             const double du = r[rp.kd_ch[10] * 2 + rp.kd_sub[10]];
-            kick_drift(x, v, u, a, du, rp.dtk, rp.dt, g);
+            double vp[3], up;
+            kick_drift_predict(x, v, u, a, du, rp.dtk, rp.dt, g, vp, up);
+            // the records get the half-step v, u; the staged view gets the predicted ones (kd_pred) or those
             const double nv[7] = {x[0], x[1], x[2], v[0], v[1], v[2], u};
+            const double sv[7] = {x[0], x[1], x[2], rp.kd_pred ? vp[0] : v[0], rp.kd_pred ? vp[1] : v[1],
+                                  rp.kd_pred ? vp[2] : v[2], rp.kd_pred ? up : u};
             uint8_t *rec = aos + (int64_t)(base + tid) * stride;
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
-                r[rp.kd_ch[k < 6 ? k : 9] * 2 + rp.kd_sub[k < 6 ? k : 9]] = nv[k];
+                r[rp.kd_ch[k < 6 ? k : 9] * 2 + rp.kd_sub[k < 6 ? k : 9]] = sv[k];
                 *reinterpret_cast<double *>(rec + rp.kd_off[k]) = nv[k];
             }
         }
@@ -664,14 +732,14 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
                 if (patch_start[mid] <= i) lo = mid; else hi = mid;
             }
             const int nx = patch_n[3 * lo], ny = patch_n[3 * lo + 1], nz = patch_n[3 * lo + 2];
-            const int kx = cell_coord(x[0], patch_inv[3 * lo], nx, g.box[0], bad);
-            const int ky = cell_coord(x[1], patch_inv[3 * lo + 1], ny, g.box[1], bad);
-            const int kz = cell_coord(x[2], patch_inv[3 * lo + 2], nz, g.box[2], bad);
+            const int kx = cell_coord_bits(x[0], patch_inv[3 * lo], nx, g.box[0], bad);
+            const int ky = cell_coord_bits(x[1], patch_inv[3 * lo + 1], ny, g.box[1], bad);
+            const int kz = cell_coord_bits(x[2], patch_inv[3 * lo + 2], nz, g.box[2], bad);
             c = patch_cell_base[lo] + kx + nx * (ky + ny * kz);
         } else {
-            const int kx = cell_coord(x[0], g.inv[0], g.n[0], g.box[0], bad);
-            const int ky = cell_coord(x[1], g.inv[1], g.n[1], g.box[1], bad);
-            const int kz = cell_coord(x[2], g.inv[2], g.n[2], g.box[2], bad);
+            const int kx = cell_coord_bits(x[0], g.inv[0], g.n[0], g.box[0], bad);
+            const int ky = cell_coord_bits(x[1], g.inv[1], g.n[1], g.box[1], bad);
+            const int kz = cell_coord_bits(x[2], g.inv[2], g.n[2], g.box[2], bad);
             c = kx + g.n[0] * (ky + g.n[1] * kz);
         }
         cell_of[base + tid] = c;

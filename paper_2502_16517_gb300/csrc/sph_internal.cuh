@@ -160,6 +160,7 @@ struct RecordPlan {
     int kd;                 // kick and drift first
     int kd_ch[11], kd_sub[11];  // x0..2, v0..2, a0..2, u, du/dt in the loaded chunks
     int kd_off[7];              // record offsets of x0..2, v0..2, u (written back)
+    int kd_pred;                // the staged v, u are predicted by dtk (the items then carry no prediction)
     double dtk, dt;
 };
 

@@ -502,6 +502,12 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
         rp.kd_off[6] = v->layout.off[SPH_U];
         rp.dtk = kd->dtk;
         rp.dt = kd->dt;
+        // the pass's prediction is the step's half kick (pred_dt = dt/2 = dtk): the record pass applies it with
+        // the kick's own products, and the staged items carry none
+        if (pred_dt != 0.0 && pred_dt == kd->dtk) {
+            rp.kd_pred = 1;
+            for (int k = 0; k < p.nitems; ++k) p.item_pred_chunk[k] = -1;
+        }
     }
     const bool patches = v->npatch_max > 0;
     if (patches) {
