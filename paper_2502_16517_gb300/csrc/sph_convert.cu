@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
 // the cell of the position in the grid or in its patch's grid, the histogram and the range check.  Phase 3 writes
 // the staged items in record order (coalesced), v and u predicted where the plan asks.
 template <bool KD, bool PATCH, bool F32>
-__global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos, int64_t stride, int n,
+__global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ aos, int64_t stride, int n,
                                                        const RecordPlan rp, Grid g,
                                                        const int64_t *__restrict__ patch_start, int npatch,
                                                        const int *__restrict__ patch_n,
@@ -663,10 +663,11 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
     // kUnroll independent 16-byte loads per thread are issued before the first of them is stored, so that each
     // thread keeps several loads in flight (one at a time bounds the pass by memory latency, not bandwidth)
     const unsigned inv_nch = div_inv(nch);
-    for (int i0 = tid; i0 < cnt * nch; i0 += kUnroll * kTile) {
-        double2 w[kUnroll];
+    constexpr int kU = 4;  // loads in flight per thread (six CTAs per SM keep 48 warps issuing them)
+    for (int i0 = tid; i0 < cnt * nch; i0 += kU * kTile) {
+        double2 w[kU];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
             const int idx = i0 + u * kTile;
             if (idx < cnt * nch) {
                 const int s = div_small(idx, inv_nch);
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(kTile) k_record_pass(uint8_t *__restrict__ aos
             }
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
             const int idx = i0 + u * kTile;
             if (idx < cnt * nch) {
                 const int s = div_small(idx, inv_nch);
@@ -815,6 +816,70 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
                 // positions: (float)(x - origin); other members: the float the record pass stored (exact)
                 const float o = axis >= 0 ? __double2float_rn(__dsub_rn(w[k], sorg[3 * s + axis])) : (float)w[k];
                 static_cast<float *>(pp.dst[k])[base + s] = o;
+            }
+        }
+    }
+}
+
+// Permutation of staged items for patch views, CTA per patch.  A patch's records and its slots are the same
+// index range [patch_start[p], patch_start[p+1]) (cells are patch-major), so each item's values for the patch are
+// read once, coalesced, into shared memory, and the permuted reads hit shared memory; the slot writes are
+// coalesced as well.  FP32 positions take the origin of the slot's cell from the patch's own grid.  A patch of more
+// than kPatchCap records reads its items straight from global memory instead.
+constexpr int kPatchThreads = 512;
+constexpr int kPatchCap = 8192;  // records of a patch staged in shared memory (64 KB of doubles)
+
+template <bool F32>
+__global__ void __launch_bounds__(kPatchThreads) k_permute_patches(const int *__restrict__ perm,
+                                                                   const int *__restrict__ cell_of_slot,
+                                                                   const int64_t *__restrict__ patch_start,
+                                                                   const PermutePlan pp, const CellSpace cs)
+{
+    extern __shared__ __align__(16) double sh[];
+    const int p = blockIdx.x;
+    const int ps = (int)patch_start[p], np = (int)(patch_start[p + 1] - ps);
+    if (np <= 0) return;  // CTA-uniform
+    const bool staged = np <= kPatchCap;
+    const int tid = threadIdx.x;
+    const int nx = cs.patch_n[3 * p], ny = cs.patch_n[3 * p + 1];
+    const int cb = cs.patch_cell_base[p];
+    for (int k = 0; k < pp.nitems; ++k) {
+        const bool wide = !F32 || pp.item_pos[k] >= 0;
+        if (staged) {
+            __syncthreads();  // the previous item's reads of sh are done
+            for (int i0 = tid; i0 < np; i0 += 4 * kPatchThreads) {
+                double w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * kPatchThreads;
+                    if (i < np)
+                        w[u] = wide ? static_cast<const double *>(pp.src[k])[ps + i]
+                                    : (double)static_cast<const float *>(pp.src[k])[ps + i];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * kPatchThreads;
+                    if (i < np) sh[i] = w[u];
+                }
+            }
+            __syncthreads();
+        }
+        const int axis = F32 ? pp.item_pos[k] : -1;
+        const double edge = axis >= 0 ? cs.patch_edge[3 * p + axis] : 0.0;
+        for (int t = tid; t < np; t += kPatchThreads) {
+            const int slot = ps + t;
+            const int r = perm[slot];
+            const double v = staged ? sh[r - ps]
+                                    : (wide ? static_cast<const double *>(pp.src[k])[r]
+                                            : (double)static_cast<const float *>(pp.src[k])[r]);
+            if (!F32) {
+                static_cast<double *>(pp.dst[k])[slot] = v;
+            } else if (axis >= 0) {
+                const int local = cell_of_slot[slot] - cb;
+                const int kc = axis == 0 ? local % nx : (axis == 1 ? (local / nx) % ny : local / (nx * ny));
+                static_cast<float *>(pp.dst[k])[slot] = __double2float_rn(__dsub_rn(v, __dmul_rn((double)kc, edge)));
+            } else {
+                static_cast<float *>(pp.dst[k])[slot] = (float)v;
             }
         }
     }
@@ -1036,10 +1101,21 @@ cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordP
 }
 
 cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
-                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl)
+                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl, const int64_t *patch_start)
 {
     if (n <= 0 || pp.nitems == 0) return cudaSuccess;
     ++*nl;
+    if (cs.npatch > 0 && patch_start) {
+        const size_t smem = (size_t)kPatchCap * 8;
+        if (f32) {
+            cudaFuncSetAttribute(k_permute_patches<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_permute_patches<true><<<cs.npatch, kPatchThreads, smem, st>>>(perm, cell_of_slot, patch_start, pp, cs);
+        } else {
+            cudaFuncSetAttribute(k_permute_patches<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_permute_patches<false><<<cs.npatch, kPatchThreads, smem, st>>>(perm, cell_of_slot, patch_start, pp, cs);
+        }
+        return cudaGetLastError();
+    }
     const int blocks = (n + kTile - 1) / kTile;
     if (f32) {
         k_permute<true><<<blocks, kTile, 0, st>>>(perm, cell_of_slot, n, pp, cs);
