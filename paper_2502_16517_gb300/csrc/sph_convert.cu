@@ -34,6 +34,7 @@ namespace {
 
 constexpr int kTile = 256;
 constexpr int kUnroll = 8;  // independent global loads a conversion thread issues before it stores any of them
+constexpr int kHmaxSlots = 8;  // patches of a record-pass tile whose h maximum is gathered in shared memory
 constexpr unsigned kFull = 0xffffffffu;
 
 // q / d for 0 <= q < 256 d and 1 <= d <= 40 by multiplication with inv = ceil(2^20 / d) and a shift (exact in that
@@ -370,6 +371,28 @@ __global__ void k_cell_sort(const int *__restrict__ cell_start, int ncells_host,
     }
 }
 
+// Grid of patch p from its largest h: per axis n = floor(box / (2 h_max)) cells (at least 1, at most ncap,
+// lowered while box / n < 2 h_max after rounding), the cell edge box / n and the inverse n / box, each rounded once
+// in FP64, and the patch's cell count.
+__device__ __forceinline__ void patch_grid_one(int p, double hm, const Grid &g, int ncap, int *patch_n,
+                                               double *patch_edge, double *patch_inv, int *patch_cells)
+{
+    int cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        int nn = ncap;
+        if (hm > 0.0) {
+            const double f = floor(g.box[a] / (2.0 * hm));
+            nn = f >= (double)ncap ? ncap : (f >= 1.0 ? (int)f : 1);
+            while (nn > 1 && __ddiv_rn(g.box[a], (double)nn) < 2.0 * hm) --nn;
+        }
+        patch_n[3 * p + a] = nn;
+        patch_edge[3 * p + a] = __ddiv_rn(g.box[a], (double)nn);
+        patch_inv[3 * p + a] = __ddiv_rn((double)nn, g.box[a]);
+        cells *= nn;
+    }
+    patch_cells[p] = cells;
+}
+
 // Patch grids: per patch (one CTA) the largest h of its records, then per axis n = floor(box / (2 h_max)) cells
 // (at least 1, at most ncap, lowered while box / n < 2 h_max after rounding), the cell edge box / n and the inverse
 // n / box, each rounded once in FP64, and the patch's cell count.
@@ -389,21 +412,20 @@ __global__ void __launch_bounds__(256) k_patch_grid(const uint8_t *__restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) hm = fmax(hm, red[w]);
-        int cells = 1;
-        for (int a = 0; a < 3; ++a) {
-            int nn = ncap;
-            if (hm > 0.0) {
-                const double f = floor(g.box[a] / (2.0 * hm));
-                nn = f >= (double)ncap ? ncap : (f >= 1.0 ? (int)f : 1);
-                while (nn > 1 && __ddiv_rn(g.box[a], (double)nn) < 2.0 * hm) --nn;
-            }
-            patch_n[3 * p + a] = nn;
-            patch_edge[3 * p + a] = __ddiv_rn(g.box[a], (double)nn);
-            patch_inv[3 * p + a] = __ddiv_rn((double)nn, g.box[a]);
-            cells *= nn;
-        }
-        patch_cells[p] = cells;
+        patch_grid_one(p, hm, g, ncap, patch_n, patch_edge, patch_inv, patch_cells);
     }
+}
+
+// The same grids from the per-patch h_max the record pass gathered (bit patterns of positive doubles, which
+// order like the values), one thread per patch.
+__global__ void k_patch_grid_hmax(const unsigned long long *__restrict__ hmax_bits, int npatch, Grid g, int ncap,
+                                  int *__restrict__ patch_n, double *__restrict__ patch_edge,
+                                  double *__restrict__ patch_inv, int *__restrict__ patch_cells)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npatch) return;
+    patch_grid_one(p, __longlong_as_double((long long)hmax_bits[p]), g, ncap, patch_n, patch_edge, patch_inv,
+                   patch_cells);
 }
 
 // Global cell of every record of a patch view, one CTA per patch: floor(x * (n / box)) per axis in the patch's
@@ -647,10 +669,11 @@ __global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ 
                                                        const double *__restrict__ patch_inv,
                                                        const int *__restrict__ patch_cell_base,
                                                        int *__restrict__ cell_of, int *__restrict__ count,
-                                                       unsigned *status)
+                                                       unsigned *status, unsigned long long *__restrict__ hmax_bits)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int prange[2];
+    __shared__ unsigned long long hmx[kHmaxSlots];  // patch views: the tile's largest h per patch (bit patterns)
     const int base = blockIdx.x * kTile;
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
@@ -685,6 +708,7 @@ __global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ 
             }
         }
     }
+    if (PATCH && tid < kHmaxSlots) hmx[tid] = 0ull;
     if (PATCH && tid < 2) {
         // patch of the tile's first / last record: the largest p with patch_start[p] <= i
         const int64_t i = base + (tid == 0 ? 0 : cnt - 1);
@@ -723,31 +747,35 @@ __global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ 
                 *reinterpret_cast<double *>(rec + rp.kd_off[k]) = nv[k];
             }
         }
-        bool bad = false;
-        int c;
         if (PATCH) {
+            // patch views bin later, per patch (k_patch_bin), once the patch grids are known; here the largest h
+            // of each patch is gathered for them (h > 0, infinities included, NaN left out, as fmax would)
             int lo = prange[0], hi = prange[1] + 1;
             const int64_t i = base + tid;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
                 if (patch_start[mid] <= i) lo = mid; else hi = mid;
             }
-            const int nx = patch_n[3 * lo], ny = patch_n[3 * lo + 1], nz = patch_n[3 * lo + 2];
-            const int kx = cell_coord_bits(x[0], patch_inv[3 * lo], nx, g.box[0], bad);
-            const int ky = cell_coord_bits(x[1], patch_inv[3 * lo + 1], ny, g.box[1], bad);
-            const int kz = cell_coord_bits(x[2], patch_inv[3 * lo + 2], nz, g.box[2], bad);
-            c = patch_cell_base[lo] + kx + nx * (ky + ny * kz);
+            const long long hb = __double_as_longlong(r[rp.h_ch * 2 + rp.h_sub]);
+            if (hb > 0 && hb <= 0x7FF0000000000000LL) {
+                const int slot = lo - prange[0];
+                if (slot < kHmaxSlots) atomicMax(&hmx[slot], (unsigned long long)hb);
+                else atomicMax(&hmax_bits[lo], (unsigned long long)hb);
+            }
         } else {
+            bool bad = false;
             const int kx = cell_coord_bits(x[0], g.inv[0], g.n[0], g.box[0], bad);
             const int ky = cell_coord_bits(x[1], g.inv[1], g.n[1], g.box[1], bad);
             const int kz = cell_coord_bits(x[2], g.inv[2], g.n[2], g.box[2], bad);
-            c = kx + g.n[0] * (ky + g.n[1] * kz);
+            const int c = kx + g.n[0] * (ky + g.n[1] * kz);
+            cell_of[base + tid] = c;
+            atomicAdd(&count[c], 1);
+            if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
         }
-        cell_of[base + tid] = c;
-        atomicAdd(&count[c], 1);
-        if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
     }
     __syncthreads();
+    if (PATCH && tid < kHmaxSlots && tid <= prange[1] - prange[0] && hmx[tid] != 0ull)
+        atomicMax(&hmax_bits[prange[0] + tid], hmx[tid]);
     const ConvPlan &plan = rp.conv;
     if (tid < cnt) {  // one record per thread (kTile records per tile): item by item, coalesced across threads
         const double *r = dbuf + (size_t)tid * rs;
@@ -828,6 +856,129 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
 // than kPatchCap records reads its items straight from global memory instead.
 constexpr int kPatchThreads = 512;
 constexpr int kPatchCap = 8192;  // records of a patch staged in shared memory (64 KB of doubles)
+
+// Bin of one patch, CTA per patch (patch views, after the record pass and the patch grids): the cell of every
+// record from its staged (drifted) position, the patch's cell counts, cell_start of its cells (global slot
+// offsets: the patch's slots are its record range), and the stable slot order -- ascending record index inside a
+// cell.  Each warp owns a contiguous range of the patch's records: it counts per cell (lanes with the same cell
+// found by __match_any_sync), the counts are turned into per-warp bases (cell-major, warp order), and each warp
+// places its records in order, ranked among equal cells by lane.  Cells of a key (up to kPatchCap records) are
+// kept in shared memory between the passes.
+constexpr int kBinWarps = kPatchThreads / 32;
+constexpr int kBinCellCap = 512;  // cells of a patch grid: ncap^3 <= 512 (ncap <= 8)
+
+__device__ __forceinline__ int patch_cell_of(const double *x0, const double *x1, const double *x2, int i,
+                                             const Grid &g, int nx, int ny, int nz, const double *inv, bool &bad)
+{
+    const int kx = cell_coord_bits(x0[i], inv[0], nx, g.box[0], bad);
+    const int ky = cell_coord_bits(x1[i], inv[1], ny, g.box[1], bad);
+    const int kz = cell_coord_bits(x2[i], inv[2], nz, g.box[2], bad);
+    return kx + nx * (ky + ny * kz);
+}
+
+__global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const double *__restrict__ x0,
+                                                             const double *__restrict__ x1,
+                                                             const double *__restrict__ x2,
+                                                             const int64_t *__restrict__ patch_start, Grid g,
+                                                             const int *__restrict__ patch_n,
+                                                             const double *__restrict__ patch_inv,
+                                                             const int *__restrict__ patch_cell_base,
+                                                             const int *__restrict__ ncells_dev, int n,
+                                                             int *__restrict__ cell_start, int *__restrict__ perm,
+                                                             int *__restrict__ cell_of_slot, unsigned *status)
+{
+    extern __shared__ __align__(16) int bsm[];
+    int *cnt = bsm;                              // [kBinWarps][kBinCellCap]
+    int *off = cnt + kBinWarps * kBinCellCap;    // [kBinCellCap]
+    unsigned short *key = reinterpret_cast<unsigned short *>(off + kBinCellCap);  // [kPatchCap]
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (p == 0 && tid == 0) cell_start[*ncells_dev] = n;
+    const int ps = (int)patch_start[p], np = (int)(patch_start[p + 1] - ps);
+    const int nx = patch_n[3 * p], ny = patch_n[3 * p + 1], nz = patch_n[3 * p + 2];
+    const int ncp = nx * ny * nz, cb = patch_cell_base[p];
+    const double inv[3] = {patch_inv[3 * p], patch_inv[3 * p + 1], patch_inv[3 * p + 2]};
+    if (np <= 0) {  // CTA-uniform: an empty patch's cells all start at its offset
+        for (int c = tid; c < ncp; c += kPatchThreads) cell_start[cb + c] = ps;
+        return;
+    }
+    for (int i = tid; i < kBinWarps * kBinCellCap; i += kPatchThreads) cnt[i] = 0;
+    __syncthreads();
+    const bool keyed = np <= kPatchCap;
+    const int R = (np + kBinWarps - 1) / kBinWarps;
+    const int r0 = min(np, w * R), r1 = min(np, r0 + R);
+    int *mine = cnt + w * kBinCellCap;
+    bool bad = false;
+    for (int b = r0; b < r1; b += 32) {
+        const int i = b + lane;
+        int c = -1;
+        if (i < r1) {
+            c = patch_cell_of(x0, x1, x2, ps + i, g, nx, ny, nz, inv, bad);
+            if (keyed) key[i] = (unsigned short)c;
+        }
+        const unsigned grp = __match_any_sync(kFull, c);
+        if (c >= 0 && lane == __ffs(grp) - 1) mine[c] += __popc(grp);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per cell: warp bases in warp order, then the exclusive scan over cells
+    for (int c = tid; c < ncp; c += kPatchThreads) {
+        int run = 0;
+        for (int ww = 0; ww < kBinWarps; ++ww) {
+            const int t = cnt[ww * kBinCellCap + c];
+            cnt[ww * kBinCellCap + c] = run;
+            run += t;
+        }
+        off[c] = run;
+    }
+    __syncthreads();
+    if (w == 0) {  // one warp scans the (at most 512) cell totals: 16 consecutive cells per lane
+        constexpr int per = kBinCellCap / 32;
+        int v[per], sum = 0;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int c = lane * per + k;
+            v[k] = c < ncp ? off[c] : 0;
+            sum += v[k];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            const int c = lane * per + k;
+            if (c < ncp) off[c] = run;
+            run += v[k];
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < ncp; c += kPatchThreads) {
+        const int o = off[c];
+        cell_start[cb + c] = ps + o;
+        for (int ww = 0; ww < kBinWarps; ++ww) cnt[ww * kBinCellCap + c] += o;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = r0; b < r1; b += 32) {
+        const int i = b + lane;
+        int c = -1;
+        if (i < r1) c = keyed ? (int)key[i] : patch_cell_of(x0, x1, x2, ps + i, g, nx, ny, nz, inv, bad);
+        const unsigned grp = __match_any_sync(kFull, c);
+        if (c >= 0) {
+            const int slot = ps + mine[c] + __popc(grp & lt);
+            perm[slot] = ps + i;
+            cell_of_slot[slot] = cb + c;
+        }
+        __syncwarp();
+        if (c >= 0 && lane == __ffs(grp) - 1) mine[c] += __popc(grp);
+        __syncwarp();
+    }
+    if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
+}
 
 template <bool F32>
 __global__ void __launch_bounds__(kPatchThreads) k_permute_patches(const int *__restrict__ perm,
@@ -1024,78 +1175,81 @@ namespace {
 template <bool KD, bool PATCH, bool F32>
 void record_pass(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, const Grid &g, const int64_t *patch_start,
                  int npatch, const int *patch_n, const double *patch_inv, const int *patch_cell_base, int *cell_of,
-                 int *count, unsigned *status, cudaStream_t st)
+                 int *count, unsigned *status, unsigned long long *hmax, cudaStream_t st)
 {
     const size_t smem = (size_t)kTile * (2 * rp.conv.nchunks + 1) * 8;
     cudaFuncSetAttribute(k_record_pass<KD, PATCH, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_record_pass<KD, PATCH, F32><<<(n + kTile - 1) / kTile, kTile, smem, st>>>(
-        aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base, cell_of, count, status);
+        aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base, cell_of, count, status, hmax);
 }
 
 template <bool KD, bool PATCH>
 void record_pass_p(bool f32, uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, const Grid &g,
-                   const int64_t *patch_start, int npatch, const int *patch_n, const double *patch_inv,
-                   const int *patch_cell_base, int *cell_of, int *count, unsigned *status, cudaStream_t st)
+                   const int64_t *patch_start, int npatch, int *cell_of, int *count, unsigned *status,
+                   unsigned long long *hmax, cudaStream_t st)
 {
     if (f32) {
-        record_pass<KD, PATCH, true>(aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base,
-                                     cell_of, count, status, st);
+        record_pass<KD, PATCH, true>(aos, stride, n, rp, g, patch_start, npatch, nullptr, nullptr, nullptr, cell_of,
+                                     count, status, hmax, st);
     } else {
-        record_pass<KD, PATCH, false>(aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv, patch_cell_base,
-                                      cell_of, count, status, st);
+        record_pass<KD, PATCH, false>(aos, stride, n, rp, g, patch_start, npatch, nullptr, nullptr, nullptr, cell_of,
+                                      count, status, hmax, st);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
-                              int ncells, const int64_t *patch_start, int npatch, int ncap, int off_h, int *patch_n,
+                              int ncells, const int64_t *patch_start, int npatch, int ncap, int *patch_n,
                               double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
-                              int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                              int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl)
+                              unsigned long long *hmax, const double *const xs[3], int *cell_of, int *count,
+                              int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp,
+                              unsigned *status, cudaStream_t st, int *nl)
 {
-    const bool patches = npatch > 0;
-    double *patch_inv = patches ? patch_edge + 3 * (size_t)npatch : nullptr;
-    if (patches) {
-        k_patch_grid<<<npatch, 256, 0, st>>>(aos, stride, off_h, patch_start, g, ncap, patch_n, patch_edge,
-                                             patch_inv, patch_cells);
+    if (npatch > 0) {
+        // patch views: record pass (leapfrog, staging, h maxima), patch grids, then one bin per patch
+        double *patch_inv = patch_edge + 3 * (size_t)npatch;
+        cudaError_t e = cudaMemsetAsync(hmax, 0, sizeof(unsigned long long) * (size_t)npatch, st);
+        if (e != cudaSuccess) return e;
+        if (n > 0) {
+            ++*nl;
+            if (rp.kd) {
+                record_pass_p<true, true>(f32, aos, stride, n, rp, g, patch_start, npatch, nullptr, nullptr, status,
+                                          hmax, st);
+            } else {
+                record_pass_p<false, true>(f32, aos, stride, n, rp, g, patch_start, npatch, nullptr, nullptr, status,
+                                           hmax, st);
+            }
+        }
+        k_patch_grid_hmax<<<(npatch + 255) / 256, 256, 0, st>>>(hmax, npatch, g, ncap, patch_n, patch_edge,
+                                                                 patch_inv, patch_cells);
         k_scan_cells<<<1, kScanThreads, 0, st>>>(patch_cells, npatch, nullptr, patch_cell_base, fill);
-        *nl += 2;
+        const size_t smem = (size_t)(kBinWarps * kBinCellCap + kBinCellCap) * 4 + (size_t)kPatchCap * 2;
+        cudaFuncSetAttribute(k_patch_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_patch_bin<<<npatch, kPatchThreads, smem, st>>>(xs[0], xs[1], xs[2], patch_start, g, patch_n, patch_inv,
+                                                          patch_cell_base, ncells_dev, n, cell_start, perm,
+                                                          cell_of_slot, status);
+        *nl += 3;
+        return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncells, st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
         ++*nl;
         if (rp.kd) {
-            if (patches) {
-                record_pass_p<true, true>(f32, aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv,
-                                          patch_cell_base, cell_of, count, status, st);
-            } else {
-                record_pass_p<true, false>(f32, aos, stride, n, rp, g, nullptr, 0, nullptr, nullptr, nullptr,
-                                           cell_of, count, status, st);
-            }
+            record_pass_p<true, false>(f32, aos, stride, n, rp, g, nullptr, 0, cell_of, count, status, nullptr, st);
         } else {
-            if (patches) {
-                record_pass_p<false, true>(f32, aos, stride, n, rp, g, patch_start, npatch, patch_n, patch_inv,
-                                           patch_cell_base, cell_of, count, status, st);
-            } else {
-                record_pass_p<false, false>(f32, aos, stride, n, rp, g, nullptr, 0, nullptr, nullptr, nullptr,
-                                            cell_of, count, status, st);
-            }
+            record_pass_p<false, false>(f32, aos, stride, n, rp, g, nullptr, 0, cell_of, count, status, nullptr, st);
         }
     }
-    launch_scan(count, ncells, patches ? ncells_dev : nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
+    launch_scan(count, ncells, nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
         *nl += 2;
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
-        if (patches) {
-            k_cell_sort<<<2048, 256, 0, st>>>(cell_start, ncells, ncells_dev, perm_tmp, perm, cell_of_slot);
-        } else {
-            const long long threads = (long long)ncells * 32;
-            const long long blocks = (threads + 255) / 256;
-            k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,
-                                                                                    perm_tmp, perm, cell_of_slot);
-        }
+        const long long threads = (long long)ncells * 32;
+        const long long blocks = (threads + 255) / 256;
+        k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,
+                                                                                perm_tmp, perm, cell_of_slot);
     }
     return cudaGetLastError();
 }

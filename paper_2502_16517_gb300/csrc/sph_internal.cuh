@@ -161,6 +161,7 @@ struct RecordPlan {
     int kd_ch[11], kd_sub[11];  // x0..2, v0..2, a0..2, u, du/dt in the loaded chunks
     int kd_off[7];              // record offsets of x0..2, v0..2, u (written back)
     int kd_pred;                // the staged v, u are predicted by dtk (the items then carry no prediction)
+    int h_ch, h_sub;            // patch views: h in the loaded chunks (the record pass gathers each patch's max)
     double dtk, dt;
 };
 
@@ -195,11 +196,14 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
 
 // Bin with a record pass (see RecordPlan; records 16-byte aligned, stride a multiple of 16): single grids
 // (npatch == 0) or patch views (the per-patch grids of launch_bin_patches first).  f32: the view's precision.
+// Patch views gather each patch's largest h in the record pass (hmax: npatch words of scratch), build the patch
+// grids from them and bin every patch in one CTA from the staged positions xs (the record-order scratch of x).
 cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
-                              int ncells, const int64_t *patch_start, int npatch, int ncap, int off_h, int *patch_n,
+                              int ncells, const int64_t *patch_start, int npatch, int ncap, int *patch_n,
                               double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
-                              int *cell_of, int *count, int *cell_start, int *fill, int *perm_tmp, int *perm,
-                              int *cell_of_slot, int *scan_tmp, unsigned *status, cudaStream_t st, int *nl);
+                              unsigned long long *hmax, const double *const xs[3], int *cell_of, int *count,
+                              int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp,
+                              unsigned *status, cudaStream_t st, int *nl);
 // patch_start (patch views): the per-patch form, items staged per patch in shared memory.
 cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
                            const CellSpace &cs, bool f32, cudaStream_t st, int *nl,

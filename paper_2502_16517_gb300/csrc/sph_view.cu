@@ -49,6 +49,7 @@ struct sph_view_s {
     int *patch_n, *patch_cells, *patch_cell_base;
     double *patch_edge;  // 3 npatch_max edges, then 3 npatch_max inverses
     int *cell_bucket, *bucket_count, *work_order, *work_count, *work_next;
+    unsigned long long *hmax;  // per patch: the largest h (bit pattern) of the record pass
 
     int64_t n;
     bool binned;
@@ -278,6 +279,7 @@ void carve(sph_view_s *v, Bump &b)
         v->work_order = (int *)b.take(nc * 4);
         v->work_count = (int *)b.take(4);
         v->work_next = (int *)b.take(4);
+        v->hmax = (unsigned long long *)b.take(np * 8);
     }
     v->hdone = (unsigned char *)b.take(nm);
     v->hstate = (int *)b.take(4 * sizeof(int));
@@ -447,6 +449,9 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
     auto chunk_of = [&](int off) { return (off / 16) * 16; };
     uint32_t need = mask | SPH_BIT(SPH_X);
     if (kd) need |= SPH_BIT(SPH_V) | SPH_BIT(SPH_A) | SPH_BIT(SPH_U) | SPH_BIT(SPH_DUDT);
+    if (v->npatch_max > 0) need |= SPH_BIT(SPH_H);
+    // the patch bin reads the staged positions: x is staged whatever the mask
+    if (v->npatch_max > 0 && !(mask & SPH_BIT(SPH_X))) return SPH_E_INVAL;
     if (pred_dt != 0.0 && (mask & (SPH_BIT(SPH_V) | SPH_BIT(SPH_U)))) need |= SPH_BIT(SPH_A) | SPH_BIT(SPH_DUDT);
     if (!mask_present(v, need)) return SPH_E_INVAL;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
@@ -488,6 +493,7 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
     p.pred_dt = pred_dt;
     pp.nitems = k;
     for (int d = 0; d < 3; ++d) locate(v->layout.off[SPH_X] + 8 * d, &rp.x_ch[d], &rp.x_sub[d]);
+    if (v->npatch_max > 0) locate(v->layout.off[SPH_H], &rp.h_ch, &rp.h_sub);
     if (kd) {
         rp.kd = 1;
         for (int d = 0; d < 3; ++d) {
@@ -520,12 +526,14 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_BIN);
+        const double *xs[3] = {(const double *)v->stage.p[SPH_X][0], (const double *)v->stage.p[SPH_X][1],
+                               (const double *)v->stage.p[SPH_X][2]};
         e = sphk::launch_bin_staged(static_cast<uint8_t *>(aos), v->layout.stride, (int)n, rp, f32, v->g, v->ncells,
                                     patches ? v->patch_start : nullptr, patches ? v->npatch : 0, v->ncap,
-                                    patches ? v->layout.off[SPH_H] : 0, v->patch_n, v->patch_edge, v->patch_cells,
-                                    v->patch_cell_base, patches ? v->patch_cell_base + v->npatch : nullptr,
-                                    v->cell_of, v->count, v->cell_start, v->fill, v->perm_tmp, v->perm,
-                                    v->cell_of_slot, v->scan_tmp, v->status, v->st, &ph.nl);
+                                    v->patch_n, v->patch_edge, v->patch_cells, v->patch_cell_base,
+                                    patches ? v->patch_cell_base + v->npatch : nullptr, v->hmax, xs, v->cell_of,
+                                    v->count, v->cell_start, v->fill, v->perm_tmp, v->perm, v->cell_of_slot,
+                                    v->scan_tmp, v->status, v->st, &ph.nl);
         if (e == cudaSuccess && patches)
             e = sphk::launch_work_list(v->cs, v->cell_start, v->ncells, v->cell_bucket, v->bucket_count,
                                        v->work_order, v->work_count, v->st, &ph.nl);
