@@ -849,14 +849,8 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
     }
 }
 
-// Permutation of staged items for patch views, CTA per (patch, item).  A patch's records and its slots are the same
-// index range [patch_start[p], patch_start[p+1]) (cells are patch-major), so the item's values for the patch are
-// read once, coalesced, into shared memory, and the permuted reads hit shared memory; the slot writes are
-// coalesced as well.  FP32 positions take the origin of the slot's cell from the patch's own grid.  A patch of more
-// than kPatchCap records reads its items straight from global memory instead.
 constexpr int kPatchThreads = 512;
-constexpr int kPermThreads = 256;
-constexpr int kPatchCap = 8192;  // records of a patch staged in shared memory (64 KB of doubles)
+constexpr int kPatchCap = 8192;  // records of a patch whose cells k_patch_bin keeps in shared memory
 
 // Bin of one patch, CTA per patch (patch views, after the record pass and the patch grids): the cell of every
 // record from its staged (drifted) position, the patch's cell counts, cell_start of its cells (global slot
@@ -979,59 +973,6 @@ __global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const double *__res
         __syncwarp();
     }
     if (bad) atomicOr(status, SPH_DEV_POS_RANGE);
-}
-
-template <bool F32>
-__global__ void __launch_bounds__(kPermThreads) k_permute_patches(const int *__restrict__ perm,
-                                                                  const int *__restrict__ cell_of_slot,
-                                                                  const int64_t *__restrict__ patch_start,
-                                                                  const PermutePlan pp, const CellSpace cs)
-{
-    extern __shared__ __align__(16) double sh[];
-    const int p = blockIdx.x, k = blockIdx.y;  // one item of one patch per CTA
-    const int ps = (int)patch_start[p], np = (int)(patch_start[p + 1] - ps);
-    if (np <= 0) return;  // CTA-uniform
-    const bool staged = np <= kPatchCap;
-    const int tid = threadIdx.x;
-    const bool wide = !F32 || pp.item_pos[k] >= 0;
-    if (staged) {
-        for (int i0 = tid; i0 < np; i0 += 4 * kPermThreads) {
-            double w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * kPermThreads;
-                if (i < np)
-                    w[u] = wide ? static_cast<const double *>(pp.src[k])[ps + i]
-                                : (double)static_cast<const float *>(pp.src[k])[ps + i];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * kPermThreads;
-                if (i < np) sh[i] = w[u];
-            }
-        }
-        __syncthreads();
-    }
-    const int axis = F32 ? pp.item_pos[k] : -1;
-    const double edge = axis >= 0 ? cs.patch_edge[3 * p + axis] : 0.0;
-    const int nx = cs.patch_n[3 * p], ny = cs.patch_n[3 * p + 1];
-    const int cb = cs.patch_cell_base[p];
-    for (int t = tid; t < np; t += kPermThreads) {
-        const int slot = ps + t;
-        const int r = perm[slot];
-        const double v = staged ? sh[r - ps]
-                                : (wide ? static_cast<const double *>(pp.src[k])[r]
-                                        : (double)static_cast<const float *>(pp.src[k])[r]);
-        if (!F32) {
-            static_cast<double *>(pp.dst[k])[slot] = v;
-        } else if (axis >= 0) {
-            const int local = cell_of_slot[slot] - cb;
-            const int kc = axis == 0 ? local % nx : (axis == 1 ? (local / nx) % ny : local / (nx * ny));
-            static_cast<float *>(pp.dst[k])[slot] = __double2float_rn(__dsub_rn(v, __dmul_rn((double)kc, edge)));
-        } else {
-            static_cast<float *>(pp.dst[k])[slot] = (float)v;
-        }
-    }
 }
 
 }  // namespace
@@ -1253,23 +1194,10 @@ cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordP
 }
 
 cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
-                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl, const int64_t *patch_start)
+                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl)
 {
     if (n <= 0 || pp.nitems == 0) return cudaSuccess;
     ++*nl;
-    if (cs.npatch > 0 && patch_start) {
-        const size_t smem = (size_t)kPatchCap * 8;
-        if (f32) {
-            cudaFuncSetAttribute(k_permute_patches<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_permute_patches<true><<<dim3(cs.npatch, pp.nitems), kPermThreads, smem, st>>>(perm, cell_of_slot,
-                                                                                             patch_start, pp, cs);
-        } else {
-            cudaFuncSetAttribute(k_permute_patches<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_permute_patches<false><<<dim3(cs.npatch, pp.nitems), kPermThreads, smem, st>>>(perm, cell_of_slot,
-                                                                                              patch_start, pp, cs);
-        }
-        return cudaGetLastError();
-    }
     const int blocks = (n + kTile - 1) / kTile;
     if (f32) {
         k_permute<true><<<blocks, kTile, 0, st>>>(perm, cell_of_slot, n, pp, cs);

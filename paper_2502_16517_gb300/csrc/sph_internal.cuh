@@ -204,10 +204,8 @@ cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordP
                               unsigned long long *hmax, const double *const xs[3], int *cell_of, int *count,
                               int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp,
                               unsigned *status, cudaStream_t st, int *nl);
-// patch_start (patch views): the per-patch form, items staged per patch in shared memory.
 cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,
-                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl,
-                           const int64_t *patch_start = nullptr);
+                           const CellSpace &cs, bool f32, cudaStream_t st, int *nl);
 
 cudaError_t launch_gather(const uint8_t *aos, int64_t stride, bool vec16, const int *perm,
                           const int *cell_of_slot, int n, const ConvPlan &plan, const CellSpace &cs, bool f32,

@@ -541,8 +541,7 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
         Phase ph(v, SPH_PH_GATHER);
-        e = sphk::launch_permute(v->perm, v->cell_of_slot, (int)n, pp, v->cs, f32, v->st, &ph.nl,
-                                 patches ? v->patch_start : nullptr);
+        e = sphk::launch_permute(v->perm, v->cell_of_slot, (int)n, pp, v->cs, f32, v->st, &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     v->n = n;
