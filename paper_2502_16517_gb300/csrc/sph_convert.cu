@@ -777,16 +777,17 @@ __global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ 
     if (PATCH && tid < kHmaxSlots && tid <= prange[1] - prange[0] && hmx[tid] != 0ull)
         atomicMax(&hmax_bits[prange[0] + tid], hmx[tid]);
     const ConvPlan &plan = rp.conv;
-    if (tid < cnt) {  // one record per thread (kTile records per tile): item by item, coalesced across threads
+    if (tid < cnt) {  // one record per thread (kTile records per tile): its packed row
         const double *r = dbuf + (size_t)tid * rs;
+        uint8_t *row = rp.rows + (int64_t)(base + tid) * rp.row_bytes;
         for (int k = 0; k < plan.nitems; ++k) {
             double v = r[plan.item_chunk[k] * 2 + plan.item_sub[k]];
             const int pc = plan.item_pred_chunk[k];
             if (pc >= 0) v = __dadd_rn(v, __dmul_rn(r[pc * 2 + plan.item_pred_sub[k]], plan.pred_dt));
             if (!F32 || plan.item_pos[k] >= 0) {
-                static_cast<double *>(plan.soa[k])[base + tid] = v;
+                *reinterpret_cast<double *>(row + rp.row_off[k]) = v;
             } else {
-                static_cast<float *>(plan.soa[k])[base + tid] = __double2float_rn(v);
+                *reinterpret_cast<float *>(row + rp.row_off[k]) = __double2float_rn(v);
             }
         }
     }
@@ -825,14 +826,15 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
         }
         __syncthreads();
     }
-    if (tid < cnt) {  // one slot per thread: all of its items' loads in flight before the stores
-        const int s = tid, i = srec[s];
+    if (tid < cnt) {  // one slot per thread: its record's packed row, all loads in flight before the stores
+        const int s = tid;
+        const uint8_t *row = pp.rows + (int64_t)srec[s] * pp.row_bytes;
         double w[kMaxItems];
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) {
             if (k < pp.nitems)
-                w[k] = (!F32 || pp.item_pos[k] >= 0) ? static_cast<const double *>(pp.src[k])[i]
-                                                     : (double)static_cast<const float *>(pp.src[k])[i];
+                w[k] = (!F32 || pp.item_pos[k] >= 0) ? *reinterpret_cast<const double *>(row + pp.row_off[k])
+                                                     : (double)*reinterpret_cast<const float *>(row + pp.row_off[k]);
         }
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) {
@@ -862,18 +864,18 @@ constexpr int kPatchCap = 8192;  // records of a patch whose cells k_patch_bin k
 constexpr int kBinWarps = kPatchThreads / 32;
 constexpr int kBinCellCap = 512;  // cells of a patch grid: ncap^3 <= 512 (ncap <= 8)
 
-__device__ __forceinline__ int patch_cell_of(const double *x0, const double *x1, const double *x2, int i,
-                                             const Grid &g, int nx, int ny, int nz, const double *inv, bool &bad)
+__device__ __forceinline__ int patch_cell_of(const uint8_t *rows, int row_bytes, int x_off, int i, const Grid &g,
+                                             int nx, int ny, int nz, const double *inv, bool &bad)
 {
-    const int kx = cell_coord_bits(x0[i], inv[0], nx, g.box[0], bad);
-    const int ky = cell_coord_bits(x1[i], inv[1], ny, g.box[1], bad);
-    const int kz = cell_coord_bits(x2[i], inv[2], nz, g.box[2], bad);
+    const double *x = reinterpret_cast<const double *>(rows + (int64_t)i * row_bytes + x_off);
+    const int kx = cell_coord_bits(x[0], inv[0], nx, g.box[0], bad);
+    const int ky = cell_coord_bits(x[1], inv[1], ny, g.box[1], bad);
+    const int kz = cell_coord_bits(x[2], inv[2], nz, g.box[2], bad);
     return kx + nx * (ky + ny * kz);
 }
 
-__global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const double *__restrict__ x0,
-                                                             const double *__restrict__ x1,
-                                                             const double *__restrict__ x2,
+__global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const uint8_t *__restrict__ rows, int row_bytes,
+                                                             int x_off,
                                                              const int64_t *__restrict__ patch_start, Grid g,
                                                              const int *__restrict__ patch_n,
                                                              const double *__restrict__ patch_inv,
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const double *__res
         const int i = b + lane;
         int c = -1;
         if (i < r1) {
-            c = patch_cell_of(x0, x1, x2, ps + i, g, nx, ny, nz, inv, bad);
+            c = patch_cell_of(rows, row_bytes, x_off, ps + i, g, nx, ny, nz, inv, bad);
             if (keyed) key[i] = (unsigned short)c;
         }
         const unsigned grp = __match_any_sync(kFull, c);
@@ -961,7 +963,7 @@ __global__ void __launch_bounds__(kPatchThreads) k_patch_bin(const double *__res
     for (int b = r0; b < r1; b += 32) {
         const int i = b + lane;
         int c = -1;
-        if (i < r1) c = keyed ? (int)key[i] : patch_cell_of(x0, x1, x2, ps + i, g, nx, ny, nz, inv, bad);
+        if (i < r1) c = keyed ? (int)key[i] : patch_cell_of(rows, row_bytes, x_off, ps + i, g, nx, ny, nz, inv, bad);
         const unsigned grp = __match_any_sync(kFull, c);
         if (c >= 0) {
             const int slot = ps + mine[c] + __popc(grp & lt);
@@ -1141,7 +1143,7 @@ void record_pass_p(bool f32, uint8_t *aos, int64_t stride, int n, const RecordPl
 cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
                               int ncells, const int64_t *patch_start, int npatch, int ncap, int *patch_n,
                               double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
-                              unsigned long long *hmax, const double *const xs[3], int *cell_of, int *count,
+                              unsigned long long *hmax, int x_off, int *cell_of, int *count,
                               int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp,
                               unsigned *status, cudaStream_t st, int *nl)
 {
@@ -1165,7 +1167,7 @@ cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordP
         k_scan_cells<<<1, kScanThreads, 0, st>>>(patch_cells, npatch, nullptr, patch_cell_base, fill);
         const size_t smem = (size_t)(kBinWarps * kBinCellCap + kBinCellCap) * 4 + (size_t)kPatchCap * 2;
         cudaFuncSetAttribute(k_patch_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_patch_bin<<<npatch, kPatchThreads, smem, st>>>(xs[0], xs[1], xs[2], patch_start, g, patch_n, patch_inv,
+        k_patch_bin<<<npatch, kPatchThreads, smem, st>>>(rp.rows, rp.row_bytes, x_off, patch_start, g, patch_n, patch_inv,
                                                           patch_cell_base, ncells_dev, n, cell_start, perm,
                                                           cell_of_slot, status);
         *nl += 3;

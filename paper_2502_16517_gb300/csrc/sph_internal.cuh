@@ -152,10 +152,14 @@ struct KickDrift {
 // (drifted) position, and the members of the view are written, in record order, to scratch arrays (predicted
 // where asked).  A permutation then moves them to the slot order of the SoA view.
 struct RecordPlan {
-    // chunks loaded per record; items: the staged view members, conv.soa[k] = their record-order scratch array
-    // (FP64 for FP64 views and for FP32 views' positions, which get their cell-relative cast in the permutation;
-    // float otherwise); item_pos marks the position items; item_pred_* / pred_dt as for the gather
+    // chunks loaded per record; items: the staged view members, written to one packed row per record (record
+    // order): item k at byte row_off[k] of the row, as a double for FP64 views and for FP32 views' positions (which
+    // get their cell-relative cast in the permutation), as a float otherwise; item_pos marks the position items;
+    // item_pred_* / pred_dt as for the gather
     ConvPlan conv;
+    uint8_t *rows;
+    int row_bytes;
+    int row_off[kMaxItems];
     int x_ch[3], x_sub[3];  // the position components in the loaded chunks
     int kd;                 // kick and drift first
     int kd_ch[11], kd_sub[11];  // x0..2, v0..2, a0..2, u, du/dt in the loaded chunks
@@ -170,7 +174,9 @@ struct RecordPlan {
 struct PermutePlan {
     int nitems;
     int item_pos[kMaxItems];
-    const void *src[kMaxItems];
+    const uint8_t *rows;  // the record pass's packed rows (RecordPlan)
+    int row_bytes;
+    int row_off[kMaxItems];
     void *dst[kMaxItems];
 };
 
@@ -197,11 +203,11 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
 // Bin with a record pass (see RecordPlan; records 16-byte aligned, stride a multiple of 16): single grids
 // (npatch == 0) or patch views (the per-patch grids of launch_bin_patches first).  f32: the view's precision.
 // Patch views gather each patch's largest h in the record pass (hmax: npatch words of scratch), build the patch
-// grids from them and bin every patch in one CTA from the staged positions xs (the record-order scratch of x).
+// grids from them and bin every patch in one CTA from the staged positions (x_off: byte offset of x in a row).
 cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordPlan &rp, bool f32, const Grid &g,
                               int ncells, const int64_t *patch_start, int npatch, int ncap, int *patch_n,
                               double *patch_edge, int *patch_cells, int *patch_cell_base, int *ncells_dev,
-                              unsigned long long *hmax, const double *const xs[3], int *cell_of, int *count,
+                              unsigned long long *hmax, int x_off, int *cell_of, int *count,
                               int *cell_start, int *fill, int *perm_tmp, int *perm, int *cell_of_slot, int *scan_tmp,
                               unsigned *status, cudaStream_t st, int *nl);
 cudaError_t launch_permute(const int *perm, const int *cell_of_slot, int n, const PermutePlan &pp,

@@ -58,7 +58,8 @@ struct sph_view_s {
 
     void *arena;
     sphk::SoaPtrs soa;
-    sphk::SoaPtrs stage;  // record-order scratch of the staged gather (8 bytes per element, n_max elements)
+    uint8_t *stage_rows;  // record-order packed rows of the staged gather (n_max rows of at most stage_row_max B)
+    int stage_row_max;
     sphk::Scratch scr;
     int *cell_of, *count, *cell_start, *fill, *perm_tmp, *perm, *cell_of_slot;
     int *scan_tmp;  // multi-CTA scan scratch
@@ -245,11 +246,11 @@ void carve(sph_view_s *v, Bump &b)
         if (!(v->present & SPH_BIT(f))) continue;
         for (int c = 0; c < kNcomp[f]; ++c) v->soa.p[f][c] = b.take(nm * v->esz);
     }
-    for (int f = 0; f < SPH_NFIELDS; ++f) {
-        for (int c = 0; c < 3; ++c) v->stage.p[f][c] = nullptr;
-        if (!(v->present & SPH_BIT(f))) continue;
-        for (int c = 0; c < kNcomp[f]; ++c) v->stage.p[f][c] = b.take(nm * 8);
-    }
+    int comps = 0;
+    for (int f = 0; f < SPH_NFIELDS; ++f)
+        if (v->present & SPH_BIT(f)) comps += kNcomp[f];
+    v->stage_row_max = 8 * comps;
+    v->stage_rows = (uint8_t *)b.take(nm * (size_t)v->stage_row_max);
     memset(&v->scr, 0, sizeof(v->scr));
     if (v->prec == SPH_F64) {
         v->scr.xf = (float *)b.take(nm * 4);
@@ -483,15 +484,35 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
             p.item_pos[k] = (f == SPH_X && f32) ? c : -1;
             p.item_pred_chunk[k] = -1;
             if (src >= 0) locate(v->layout.off[src] + 8 * c, &p.item_pred_chunk[k], &p.item_pred_sub[k]);
-            p.soa[k] = v->stage.p[f][c];
             pp.item_pos[k] = p.item_pos[k];
-            pp.src[k] = v->stage.p[f][c];
             pp.dst[k] = v->soa.p[f][c];
         }
     }
     p.nitems = k;
     p.pred_dt = pred_dt;
     pp.nitems = k;
+    // the packed row: doubles first (FP64 views: every item; FP32 views: the positions), then floats
+    int rb = 0, x_off = -1;
+    for (int q = 0; q < k; ++q) {
+        if (!f32 || p.item_pos[q] >= 0) {
+            rp.row_off[q] = rb;
+            if (p.item_off[q] == v->layout.off[SPH_X]) x_off = rb;
+            rb += 8;
+        }
+    }
+    for (int q = 0; q < k; ++q) {
+        if (f32 && p.item_pos[q] < 0) {
+            rp.row_off[q] = rb;
+            rb += 4;
+        }
+    }
+    rb = (rb + 7) & ~7;
+    if (rb > v->stage_row_max || x_off < 0) return SPH_E_INVAL;
+    rp.rows = v->stage_rows;
+    rp.row_bytes = rb;
+    pp.rows = v->stage_rows;
+    pp.row_bytes = rb;
+    for (int q = 0; q < k; ++q) pp.row_off[q] = rp.row_off[q];
     for (int d = 0; d < 3; ++d) locate(v->layout.off[SPH_X] + 8 * d, &rp.x_ch[d], &rp.x_sub[d]);
     if (v->npatch_max > 0) locate(v->layout.off[SPH_H], &rp.h_ch, &rp.h_sub);
     if (kd) {
@@ -526,12 +547,10 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_BIN);
-        const double *xs[3] = {(const double *)v->stage.p[SPH_X][0], (const double *)v->stage.p[SPH_X][1],
-                               (const double *)v->stage.p[SPH_X][2]};
         e = sphk::launch_bin_staged(static_cast<uint8_t *>(aos), v->layout.stride, (int)n, rp, f32, v->g, v->ncells,
                                     patches ? v->patch_start : nullptr, patches ? v->npatch : 0, v->ncap,
                                     v->patch_n, v->patch_edge, v->patch_cells, v->patch_cell_base,
-                                    patches ? v->patch_cell_base + v->npatch : nullptr, v->hmax, xs, v->cell_of,
+                                    patches ? v->patch_cell_base + v->npatch : nullptr, v->hmax, x_off, v->cell_of,
                                     v->count, v->cell_start, v->fill, v->perm_tmp, v->perm, v->cell_of_slot,
                                     v->scan_tmp, v->status, v->st, &ph.nl);
         if (e == cudaSuccess && patches)
