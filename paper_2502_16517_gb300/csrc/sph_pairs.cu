@@ -280,12 +280,18 @@ __device__ __forceinline__ double rcp_seeded(double x)
     return fma(y, fma(e, e, e), y);
 }
 
-// Shared-memory load the compiler may not hoist or merge (asm volatile): for values read again on purpose in
+// Shared-memory loads the compiler may not hoist or merge (asm volatile): for values read again on purpose in
 // every round of a loop, so that they do not occupy registers across it.
 __device__ __forceinline__ double lds(const double *p)
 {
     double v;
     asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+__device__ __forceinline__ float ldsf(const float *p)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
     return v;
 }
 
@@ -337,6 +343,7 @@ struct DensF64 {
     static constexpr int kStageBytes = 4 * 8 + 16;
     static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
     static constexpr bool kSkipSelf = false;  // rho_i includes m_i W(0, h_i)
+    static constexpr bool kSplit = false;     // one queue (see tile_pairs_split)
     // CTAs per SM the register allocation must allow: shared memory allows seven of 128 threads at a 512 tile
     static constexpr int min_ctas(int nt) { return nt == 128 ? 7 : 3; }
     // The warp's lane partials of four local particles (u = 0..3) are reduced together: a reduce-scatter (xor 16
@@ -640,13 +647,14 @@ struct ForceF64 {
     struct Tile {
         double *d;
         double *q;
-        float4 *f4;  // filter: cell-relative position seen from the local cell, (float) h rounded up
+        float4 *f4;  // filter: cell-relative position seen from the local cell, its filter radius
     };
     // The local particle: its FP64 members sit in the warp's shared slot (s[f], read again in every evaluation
-    // round, which keeps them out of the registers); only the filter's FP32 copies stay in registers.
+    // round, which keeps them out of the registers), and so does its FP32 velocity (read by the receding
+    // estimate); only the filter's FP32 copies stay in registers.
     struct Lhs {
         const double *s;
-        float fx, fy, fz, fh, margin;
+        float fx, fy, fz, rf;
     };
     struct Part {
         double ax, ay, az, du;
@@ -656,9 +664,14 @@ struct ForceF64 {
         double ax, ay, az, du;
     };
     static constexpr int kStageBytes = NF * 8 + 8 + 16;
-    static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
+    // slot of a local particle: its members, q2, then its FP32 velocity (two doubles' room); odd: see PairShared
+    static constexpr int kSlotDoubles = 19;
+    static constexpr int kVelF = 16;  // the FP32 velocity's place in the slot (in doubles)
     // The self pair contributes nothing (j != i in the sums), so the queue driver drops it at the filter.
     static constexpr bool kSkipSelf = true;
+    // Receding pairs (v_ij . r_ij >= 0) have no viscosity: the queued hits are sorted by an FP32 estimate of
+    // v_ij . r_ij, and rounds of estimated receding pairs skip the viscosity terms (tile_pairs_split).
+    static constexpr bool kSplit = true;
     // CTAs per SM the register allocation must allow: shared memory allows three at a 448 tile (85 registers
     // at 256 threads)
     static constexpr int min_ctas(int) { return 3; }
@@ -730,7 +743,7 @@ struct ForceF64 {
         for (int f = VX; f < NF; ++f) row[f] = A.f[f][slot];
         T.q[t] = A.q2[slot];
         T.f4[t] = make_float4(A.xf[slot] + nb.offf[q][0], A.yf[slot] + nb.offf[q][1], A.zf[slot] + nb.offf[q][2],
-                              A.hf[slot]);
+                              radius(A.hf[slot], nb.margin));
     }
     static __device__ __forceinline__ void sentinel(const Tile &T, int t) { T.f4[t] = make_float4(kFar, kFar, kFar, 0.f); }
     // Called by the whole warp; ws is the warp's slot (kSlotDoubles doubles of shared memory).
@@ -739,25 +752,60 @@ struct ForceF64 {
         const int lane = threadIdx.x & 31;
         if (lane < NF) ws[lane] = A.f[lane][i];
         else if (lane == Q2) ws[Q2] = A.q2[i];
+        else if (lane < Q2 + 4)
+            reinterpret_cast<float *>(ws + kVelF)[lane - Q2 - 1] = __double2float_rn(A.f[VX + lane - Q2 - 1][i]);
         __syncwarp();
         Lhs L;
         L.s = ws;
         L.fx = A.xf[i];
         L.fy = A.yf[i];
         L.fz = A.zf[i];
-        L.fh = A.hf[i];
-        L.margin = margin;
+        L.rf = radius(A.hf[i], margin);
         return L;
     }
+    // The filter radius of a particle: 2 h (1 + 4e-6) + margin, rounded up, from the float h rounded up (the slack
+    // covers the rounding of the cell-relative FP32 positions).  Rounding up is monotone, so the larger of two
+    // particles' radii is the radius of the larger h.
+    static __device__ __forceinline__ float radius(float hf, float margin)
+    {
+        return __fmaf_ru(2.0f * (1.0f + 4e-6f), hf, margin);
+    }
+    // r < 2 max(h_i, h_j) with a conservative FP32 radius, so that it never drops a pair the FP64 test keeps.
     static __device__ __forceinline__ bool filter(const Lhs &L, const Tile &T, int k)
     {
         const float4 p = T.f4[k];
         const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
-        const float rf = __fmaf_ru(2.0f * (1.0f + 4e-6f), fmaxf(L.fh, p.w), L.margin);
+        const float rf = fmaxf(L.rf, p.w);
         return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < __fmul_ru(rf, rf);
     }
+    // Candidate k's velocity, approximately: the FP32 pattern of each member's sign, exponent and top 20 mantissa
+    // bits (the high word of the double, re-biased; exact truncation in the FP32 normal range, meaningless
+    // outside it).  It serves only the queue choice below, which costs time when wrong, never accuracy.
+    static __device__ __forceinline__ float3 vel_estimate(const Tile &T, int k)
+    {
+        const int *w = reinterpret_cast<const int *>(T.d + k * NF);
+        const auto f = [](int h) {
+            const unsigned m = ((unsigned)h & 0x7fffffffu) - 0x38000000u;  // exponent bias 1023 -> 127
+            return __uint_as_float((m << 3) | ((unsigned)h & 0x80000000u));
+        };
+        return make_float3(f(w[2 * VX + 1]), f(w[2 * VY + 1]), f(w[2 * VZ + 1]));
+    }
+    // Whether the FP32 estimate of v_ij . r_ij is positive (the pair of the local particle L and candidate k
+    // probably recedes): cell-relative FP32 positions, the local particle's FP32 velocity from its slot.
+    static __device__ __forceinline__ bool receding(const Lhs &L, const Tile &T, int k)
+    {
+        const float4 p = T.f4[k];
+        const float3 vj = vel_estimate(T, k);
+        const float *v = reinterpret_cast<const float *>(L.s + kVelF);
+        const float dx = L.fx - p.x, dy = L.fy - p.y, dz = L.fz - p.z;
+        return fmaf(ldsf(v) - vj.x, dx, fmaf(ldsf(v + 1) - vj.y, dy, (ldsf(v + 2) - vj.z) * dz)) > 0.0f;
+    }
+    // visc (warp-uniform): the whole term.  !visc (a round of pairs estimated receding): the viscosity terms only
+    // where the FP64 v_ij . r_ij is negative after all (bits of -0 included), exactly as the whole term takes them;
+    // elsewhere they are zero and skipped (the acceleration and du/dt then differ from the whole term's at most in
+    // the sign of an exact zero).
     static __device__ __forceinline__ bool eval(const Args &A, const Lhs &L, const Tile &T, const NbrTable &nb,
-                                                bool wrap, int i, int k, Part &P)
+                                                bool wrap, int i, int k, Part &P, bool visc)
     {
         const double *R_ = T.d + k * NF;
         const double *L_ = L.s;
@@ -778,23 +826,28 @@ struct ForceF64 {
         const double Fj = fma(fma(ji ? R_[K2I] : (jo ? R_[K2O] : 0.0), r2, ji ? 0.0 : (jo ? R_[S0] : 0.0)), rinv, Cj);
         const double dvx = lds(L_ + VX) - R_[VX], dvy = lds(L_ + VY) - R_[VY], dvz = lds(L_ + VZ) - R_[VZ];
         const double vdotr = fma(dvx, dx, fma(dvy, dy, dvz * dz));
-        const double hbs = lds(L_ + HS) + R_[HS];
-        const double D1 = kSoft ? fma(hbs, hbs, r2) : r2;
-        const double D2 = lds(L_ + RHO) + R_[RHO];
-        const double R = rcp_seeded(D1 * D2);
-        const double g = (hbs * vdotr) * R;
-        const double mu = g * D2;
-        const double t = fma(A.beta_s, mu, -(lds(L_ + ACS) + R_[ACS]));
-        double Ph = g * t;
-        if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
-        const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
         const double aF = lds(L_ + AP) * Fi;
+        double cpart = aF, dpart = aF;  // aF + V and aF + V/2
+        if (visc || __double2hiint(vdotr) < 0) {
+            const double hbs = lds(L_ + HS) + R_[HS];
+            const double D1 = kSoft ? fma(hbs, hbs, r2) : r2;
+            const double D2 = lds(L_ + RHO) + R_[RHO];
+            const double R = rcp_seeded(D1 * D2);
+            const double g = (hbs * vdotr) * R;
+            const double mu = g * D2;
+            const double t = fma(A.beta_s, mu, -(lds(L_ + ACS) + R_[ACS]));
+            double Ph = g * t;
+            if (__double2hiint(vdotr) >= 0) Ph = 0.0;  // receding (or v.r = +0): no viscosity
+            const double V = Ph * (Fi + Fj);             // Pi * gradbar / r_ij
+            cpart = aF + V;
+            dpart = fma(0.5, V, aF);
+        }
         const double mj = R_[M];
-        const double coef = mj * fma(R_[AP], Fj, aF + V);
+        const double coef = mj * fma(R_[AP], Fj, cpart);
         P.ax = fma(-coef, dx, P.ax);
         P.ay = fma(-coef, dy, P.ay);
         P.az = fma(-coef, dz, P.az);
-        P.du = fma(mj * vdotr, fma(0.5, V, aF), P.du);
+        P.du = fma(mj * vdotr, dpart, P.du);
         return io || jo;
     }
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
@@ -955,6 +1008,7 @@ struct DensF64G {
     static constexpr int kStageBytes = kRow * 8 + 16;
     static constexpr int kSlotDoubles = 17;
     static constexpr bool kSkipSelf = false;  // the sums include the self term
+    static constexpr bool kSplit = false;
     static constexpr int min_ctas(int nt) { return nt == 128 ? 6 : 3; }
     // the two particles of a warp's queue: Ext reduces 12 sums with one 16-value reduce-scatter, the plain
     // density its 2 sums; the neighbour counts are integer warp sums
@@ -1146,6 +1200,7 @@ struct ForceF64G {
     static constexpr int kStageBytes = NF * 8 + 16;
     static constexpr int kSlotDoubles = 17;
     static constexpr bool kSkipSelf = true;  // as ForceF64
+    static constexpr bool kSplit = false;
     // three 256-thread CTAs per SM, as ForceF64 (the 448 tile's shared memory allows three)
     static constexpr int min_ctas(int) { return 3; }
     static constexpr int kGroup = 2;
@@ -1471,7 +1526,10 @@ template <class K, int NT>
 struct PairShared {
     NbrTable nb;
     typename K::Acc acc[kMaxLocal];
-    int ring[NT / 32][kRing];
+    union {
+        int ring[NT / 32][kRing];                 // tile_pairs: one queue per warp
+        unsigned short ring2[NT / 32][2][kRing];  // tile_pairs_split: Q, then A and B (half a ring each)
+    };
     // per warp: its two local particles (K::load); an odd slot length puts member f of the two slots in
     // different banks, so a round that mixes the two particles reads both without a bank conflict
     double lslot[NT / 32][2][K::kSlotDoubles];
@@ -1562,6 +1620,125 @@ __device__ __forceinline__ void tile_pairs(const typename K::Args &A, const type
     }
 }
 
+// tile_pairs for loop bodies whose term has a part that vanishes for receding pairs (K::kSplit: the force's
+// viscosity).  The filter queues its hits in the warp's ring Q as tile_pairs does; 32 of them at a time are then
+// sorted by an FP32 estimate of v_ij . r_ij into two lists, A (approaching, or the estimate not positive) and B
+// (receding).  Rounds of 32 A entries take the whole term, rounds of 32 B entries the term without the viscosity
+// (which still takes it where the FP64 v_ij . r_ij is negative, so a wrong estimate costs time only).  What is left
+// after the tile (fewer than 32 in each list) goes into one round of the whole term, A entries first, then B
+// entries (or, without A entries, of the term without the viscosity); B entries beyond 32 take a last round
+// without the viscosity.  The entries, their order and the rounds follow from the tile and the pair of particles
+// alone, as in tile_pairs.  The term has one call site: the loop below visits every round in one place.
+template <class K, int NT>
+__device__ __forceinline__ void tile_pairs_split(const typename K::Args &A, const typename K::Tile &T,
+                                                 PairShared<K, NT> &S, int ib, int nloc, int tb, int tnp,
+                                                 float margin, bool wrap, unsigned long long &my_pairs)
+{
+    static_assert(K::kSkipSelf && K::kGroup == 2,
+                  "split queues: self pairs dropped, sums reduced two particles at a time");
+    constexpr int W = NT / 32;
+    constexpr int kTag = 1 << 14;  // entry = candidate | kTag for the second particle (candidates < 4096)
+    constexpr int kQ = kRing - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned short *q = S.ring2[warp][0], *qa = S.ring2[warp][1], *qb = S.ring2[warp][1] + kRing / 2;
+    const NbrTable &nb = S.nb;
+    unsigned npair = 0;  // lane 0: in-support pairs of this tile (added to my_pairs at the end)
+    for (int li0 = 2 * warp; li0 < nloc; li0 += 2 * W) {
+        const bool two = li0 + 1 < nloc;  // warp-uniform
+        const int i0 = ib + li0, i1 = two ? i0 + 1 : i0;
+        const typename K::Lhs L0 = K::load(A, i0, margin, S.lslot[warp][0]);
+        const typename K::Lhs L1 = K::load(A, i1, margin, S.lslot[warp][1]);
+        typename K::Part P0, P1;
+        P0.zero();
+        P1.zero();
+        // warp-uniform: the cursors of ring Q (at most 31 + 64 entries) and the lengths of A and B (at most 31 + 32
+        // each; their entries start at 0)
+        int head = 0, tail = 0, na = 0, nbq = 0;
+        const int self0 = nb.pref[13] + (i0 - nb.start[13]) - tb;  // tile position of i0 (i1 follows it)
+        for (int jb = 0;; jb += 32) {
+            const bool more = jb < tnp;  // warp-uniform
+            if (more) {
+                const int k = jb + lane;
+                const bool p0 = K::filter(L0, T, k) && k != self0;
+                const bool p1 = two && K::filter(L1, T, k) && k != self0 + 1;
+                const unsigned b0 = __ballot_sync(kFull, p0);
+                const unsigned b1 = __ballot_sync(kFull, p1);
+                const int c0 = __popc(b0);
+                if (p0) q[(tail + __popc(b0 & lt_mask)) & kQ] = (unsigned short)k;
+                if (p1) q[(tail + c0 + __popc(b1 & lt_mask)) & kQ] = (unsigned short)(k | kTag);
+                tail += c0 + __popc(b1);
+            }
+            // Rounds of 32 A or 32 B entries while there are, else 32 entries of Q (after the tile: the rest) sorted
+            // into A and B, else (after the tile) the rest of A and B.  A and B thus hold fewer than 32 entries
+            // before each sort and at most 31 + 32 after it.
+            for (;;) {
+                const int nq = tail - head;
+                int n1, ca;  // entries of the round, of them from A (first)
+                if (na >= 32) {
+                    n1 = 32;
+                    ca = 32;
+                } else if (nbq >= 32) {
+                    n1 = 32;
+                    ca = 0;
+                } else if (nq >= 32 || (!more && nq > 0)) {
+                    __syncwarp();
+                    const int n = min(32, nq);
+                    const bool act = lane < n;
+                    const int e = act ? q[(head + lane) & kQ] : 0;
+                    const bool tag = (e & kTag) != 0;
+                    const bool rec = act && K::receding(tag ? L1 : L0, T, e & (kTag - 1));
+                    const unsigned ma = __ballot_sync(kFull, act && !rec), mb = __ballot_sync(kFull, rec);
+                    if (act) {
+                        if (rec) qb[nbq + __popc(mb & lt_mask)] = (unsigned short)e;
+                        else qa[na + __popc(ma & lt_mask)] = (unsigned short)e;
+                    }
+                    head += n;
+                    na += __popc(ma);
+                    nbq += __popc(mb);
+                    continue;
+                } else if (!more && na + nbq > 0) {
+                    n1 = min(32, na + nbq);
+                    ca = na;
+                } else {
+                    break;
+                }
+                __syncwarp();
+                const int e = lane < ca ? qa[lane] : (lane < n1 ? qb[lane - ca] : 0);
+                bool in = false;
+                if (lane < n1) {
+                    const bool tag = (e & kTag) != 0;
+                    typename K::Part Pt = tag ? P1 : P0;
+                    in = K::eval(A, tag ? L1 : L0, T, nb, wrap, tag ? i1 : i0, e & (kTag - 1), Pt, ca > 0);
+                    if (tag) P1 = Pt; else P0 = Pt;
+                }
+                const unsigned b = __ballot_sync(kFull, in);  // every lane votes (and the reads above are done)
+                if (lane == 0) npair += __popc(b);
+                // the list the round drew from keeps its rest (fewer than 32 entries) at the front
+                unsigned short *r = ca == 32 ? qa : qb;
+                const int used = ca == 32 ? 32 : n1 - ca, len = ca == 32 ? na : nbq;
+                const int rem = len - used;
+                const int ek = lane < rem ? r[used + lane] : 0;
+                __syncwarp();
+                if (lane < rem) r[lane] = (unsigned short)ek;
+                if (ca == 32) {
+                    na = rem;
+                } else {
+                    nbq = rem;
+                    na -= ca;
+                }
+            }
+            if (!more) break;
+        }
+        __syncwarp();  // the rings and the slots are reused by the next two particles
+        typename K::Group G2;  // one reduction per pair of particles
+        G2.put(0, P0, li0);
+        G2.put(1, P1, li0 + 1);  // (all zero when the warp has a single particle)
+        G2.accumulate(S.acc, two ? 2 : 1, lane);
+    }
+    my_pairs += npair;
+}
+
 // One cell: local set = the cell's particles, active set = its 3^3 neighbour cells, all of the CTA's threads.
 template <class K, int NT>
 __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, const typename K::Tile &T,
@@ -1597,7 +1774,11 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
                 }
             }
             __syncthreads();
-            tile_pairs<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, my_pairs);
+            if constexpr (K::kSplit) {
+                tile_pairs_split<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, my_pairs);
+            } else {
+                tile_pairs<K, NT>(A, T, S, ib, nloc, tb, tnp, margin, wrap, my_pairs);
+            }
         }
         __syncthreads();
         for (int t = tid; t < nloc; t += NT) K::finish(A, ib + t, S.acc[t]);
