@@ -79,6 +79,37 @@ def test_viscosity_parameters(sph, oracle, prec, visc):
     _check(oracle, f, prec, label=f"visc{visc['eps']}", params=dict(wl.SPH_PARAMS, **visc))
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_receding_estimate_of_the_wrong_sign_matches_oracle(sph, oracle, seed):
+    """The FP64 force sorts its pairs by an FP32 estimate of v_ij . r_ij and evaluates the pairs estimated receding
+    without the viscosity, except where the FP64 v_ij . r_ij is negative after all.  Here every velocity is
+    1000 + eps_i along x (eps_i < 2e-5, below FP32 resolution at 1000) plus small y, z parts, so the estimate sees
+    only the y, z parts and gets the sign wrong for many pairs; their viscosity must still be there, to the FP64
+    bar.  (Without any viscosity the oracle's a and du/dt of this input change by 3.6e-5 normwise.)"""
+    f = wl.jittered_lattice(14, jitter=0.3, seed=seed)
+    rng = np.random.default_rng(100 + seed)
+    n = f["x"].shape[0]
+    v = np.empty((n, 3))
+    v[:, 0] = 1000.0 + rng.uniform(0.0, 2e-5, size=n)
+    v[:, 1:] = rng.uniform(-2e-5, 2e-5, size=(n, 2))
+    f["v"] = v
+    # the input does what it is for: many neighbour pairs whose FP32-rounded velocities give v.r > 0 while the
+    # FP64 v.r is negative
+    vf = v.astype(np.float32).astype(np.float64)
+    box = f["box"]
+    wrong = 0
+    for i in range(0, n, 7):
+        d = f["x"][i] - f["x"]
+        d -= box * np.round(d / box)
+        near = np.einsum("ij,ij->i", d, d) < (2 * f["h"][i]) ** 2
+        near[i] = False
+        exact = np.einsum("ij,ij->i", v[i] - v[near], d[near])
+        est = np.einsum("ij,ij->i", vf[i] - vf[near], d[near])
+        wrong += int(np.count_nonzero((est > 0) & (exact < 0)))
+    assert wrong > 1000, wrong
+    _check(oracle, f, 0, label=f"receding estimate, seed {seed}")
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_open_box(sph, oracle, prec):
     rng = np.random.default_rng(3)
