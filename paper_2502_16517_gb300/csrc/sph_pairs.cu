@@ -2106,15 +2106,22 @@ __global__ void k_force_prep_f32(const float *__restrict__ h, const float *__res
     A[s] = P[s] / (r * r);
 }
 
-// Per-particle quantities of the FP64 force loop (see ForceF64); sc = sqrt(eps) with softening, else 1.
+// Per-particle quantities of the FP64 force loop (see ForceF64); sc = sqrt(eps) with softening, else 1.  Also the
+// filter's FP32 copies (k_pos32's work, in the same pass over the particles).
 __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__restrict__ P,
                                  const double *__restrict__ rho, const double *__restrict__ cs, double alpha,
                                  double sc, int n, double *__restrict__ hs, double *__restrict__ q2,
                                  double *__restrict__ S0, double *__restrict__ K1, double *__restrict__ K2i,
-                                 double *__restrict__ K2o, double *__restrict__ A, double *__restrict__ acs)
+                                 double *__restrict__ K2o, double *__restrict__ A, double *__restrict__ acs,
+                                 const double *__restrict__ x, const double *__restrict__ y,
+                                 const double *__restrict__ z, const int *__restrict__ cell_of_slot, CellSpace g,
+                                 float *__restrict__ xf, float *__restrict__ yf, float *__restrict__ zf,
+                                 float *__restrict__ hf)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    cell_relative_f32(g, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
+    hf[s] = __double2float_ru(h[s]);
     const double hv = h[s];
     const double hi = 1.0 / hv, h2 = hi * hi;
     const double s4 = kInvPi * h2 * h2;  // 1/(pi h^4)
@@ -2314,9 +2321,6 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
     const int nb = (n + 255) / 256;
     const double alpha = prm.alpha;
     if (!f32) {
-        k_pos32<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
-                                    (const double *)soa.p[SPH_X][2], (const double *)soa.p[SPH_H][0], cell_of_slot,
-                                    n, g, scr.xf, scr.yf, scr.zf, scr.hf);
         const bool ext = prm.scheme == SPH_SCHEME_EXTENDED;
         if (prm.kernel == SPH_KERNEL_M4 && !ext) {
             const double sc = prm.eps > 0.0 ? sqrt(prm.eps) : 1.0;
@@ -2325,14 +2329,22 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
                                                  (const double *)soa.p[SPH_CS][0], alpha, sc, n, (double *)scr.d[0],
                                                  (double *)scr.d[7], (double *)scr.d[1], (double *)scr.d[2],
                                                  (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
-                                                 (double *)scr.d[6]);
-        } else if (prm.kernel == SPH_KERNEL_M5) {
-            if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, st);
-            else force_prep_g<KerM5, false>(soa, scr, n, alpha, st);
+                                                 (double *)scr.d[6], (const double *)soa.p[SPH_X][0],
+                                                 (const double *)soa.p[SPH_X][1], (const double *)soa.p[SPH_X][2],
+                                                 cell_of_slot, g, scr.xf, scr.yf, scr.zf, scr.hf);
+            *nl += 1;
         } else {
-            force_prep_g<KerM4, true>(soa, scr, n, alpha, st);
+            k_pos32<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
+                                        (const double *)soa.p[SPH_X][2], (const double *)soa.p[SPH_H][0],
+                                        cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, scr.hf);
+            if (prm.kernel == SPH_KERNEL_M5) {
+                if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, st);
+                else force_prep_g<KerM5, false>(soa, scr, n, alpha, st);
+            } else {
+                force_prep_g<KerM4, true>(soa, scr, n, alpha, st);
+            }
+            *nl += 2;
         }
-        *nl += 2;
     } else {
         k_force_prep_f32<<<nb, 256, 0, st>>>((const float *)soa.p[SPH_H][0], (const float *)soa.p[SPH_P][0],
                                              (const float *)soa.p[SPH_RHO][0], n, (float *)scr.d[0],
