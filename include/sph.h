@@ -323,7 +323,9 @@ SPH_API sph_status sph_step(sph_view view, void *aos_dev, int64_t n, const sph_p
  * on, nothing is copied in bulk: the kernels read the view members from the records and write the written
  * members back across the host link, in place (the views of Section 4 applied to host-resident records).  That
  * needs aos_host page-locked and mapped into the device's address space (cudaHostAlloc, cudaHostRegister);
- * other memory returns SPH_E_INVAL before any launch.  In both modes aos_host must hold n records. */
+ * other memory returns SPH_E_INVAL before any launch.  In place, repeated calls with the same records and
+ * arguments (and stats_out NULL) replay the step as one captured CUDA graph, as sph_step_graph does (a view with
+ * the legacy default stream runs it uncaptured).  In both modes aos_host must hold n records. */
 SPH_API sph_status sph_step_host(sph_view view, void *aos_host, int64_t n, const sph_params *params, double dt,
                          int32_t nsteps, double *stats_out);
 

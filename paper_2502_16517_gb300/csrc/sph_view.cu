@@ -1345,7 +1345,10 @@ sph_status sph_step_host(sph_view v, void *aos_host, int64_t n, const sph_params
             return SPH_E_INVAL;
         }
         if (at.type != cudaMemoryTypeHost || !at.devicePointer) return SPH_E_INVAL;
-        sph_status s = do_step(v, at.devicePointer, n, params, dt, nsteps, stats_out);
+        // the step's launches replay as one captured graph when the records and the arguments repeat (as
+        // sph_step_graph); with stats_out, or on the legacy default stream, the step runs uncaptured
+        sph_status s = stats_out || !v->st ? do_step(v, at.devicePointer, n, params, dt, nsteps, stats_out)
+                                           : do_step_graph(v, at.devicePointer, n, params, dt, nsteps);
         if (s != SPH_OK) return s;
         return sph_view_sync(v);
     }

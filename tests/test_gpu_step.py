@@ -90,6 +90,28 @@ def test_step_host_in_place_equals_staged(sph, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_step_host_in_place_replays(sph, prec):
+    """Repeated in-place sph_step_host calls with the same records and arguments replay the step as a captured
+    graph: three leapfrog calls in a row leave the bytes the staged-copy mode leaves."""
+    import torch
+    f, lay, aos_h, ncell = _tiny_aos()
+    n = aos_h.shape[0]
+    out = {}
+    for direct in (False, True):
+        host = torch.from_numpy(aos_h.copy()).pin_memory()
+        v = H.new_view(lay, prec, n, f["box"], ncell)
+        try:
+            sph.sph_view_set_host_direct(v, direct)
+            for _ in range(3):
+                sph.sph_step_host(v, host, n, wl.SPH_PARAMS, dt=1e-3, nsteps=1)
+        finally:
+            sph.sph_view_destroy(v)
+        out[direct] = host.numpy().copy()
+    assert np.array_equal(out[True], out[False])
+    assert not np.array_equal(out[True], aos_h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_reduce_matches_oracle_sums(sph, oracle, prec):
     """The FP64 sums run over the view's values: FP64 views hold the records' values, FP32 views their
     round-to-nearest casts (numpy's float32 cast), so the oracle sums those."""
