@@ -97,6 +97,9 @@ enum {
 #define SPH_DEV_NONFINITE 0x4u  /* a density, pressure or sound speed came out non-finite or <= 0           */
 #define SPH_DEV_TIMEOUT 0x8u    /* reserved (as SPH_E_TIMEOUT): no kernel of this library waits             */
 #define SPH_DEV_NOTCONV 0x10u   /* a smoothing-length iteration inside sph_step left particles unconverged   */
+#define SPH_DEV_BOUNDS 0x20u    /* checked build only (compiled with -DSPH_CHECKED): an index read from device
+                                   data (cell, slot range, permutation, work list) was out of range; the access
+                                   it guarded was skipped */
 
 /* Record layout: `stride` bytes per record (a multiple of 8, at most 65536); off[f] is the byte offset of
  * member f inside a record (a multiple of 8), or -1 if the record has no such member.  Present members must
@@ -396,6 +399,11 @@ SPH_API sph_status sph_view_phase_times(sph_view view, double ms[SPH_NPHASES], i
  * waits.  This is the arithmetic peak that the pair kernels' pipe fractions are compared with.  The paper has no
  * counterpart; it reports no hardware peaks. */
 SPH_API sph_status sph_probe_fma_rate(int32_t prec, double *flops_per_s);
+
+/* Which build of the library is loaded: *checked = 1 for the checked build (compiled with -DSPH_CHECKED: index
+ * checks on the device, see SPH_DEV_BOUNDS), else 0.  Errors: SPH_E_INVAL (checked NULL).  The paper has no
+ * counterpart; the checked build stands in for a memory checker where none can run. */
+SPH_API sph_status sph_build_info(int32_t *checked);
 
 /* Capacity of sph_bin_static's fixed scratch. */
 #define SPH_BIN_STATIC_MAX_PARTICLES 262144

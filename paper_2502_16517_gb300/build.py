@@ -1,5 +1,6 @@
 """Build libsph for sm_103a in-tree: every .cu under csrc/ compiled in parallel with nvcc, then linked into
-paper_2502_16517_gb300/_build/libsph.so.  Rebuilds only what changed (source or header newer than object)."""
+paper_2502_16517_gb300/_build/libsph.so (the checked build, -DSPH_CHECKED: _build_checked/libsph.so).  Rebuilds
+only what changed (source or header newer than object)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsph.so")
+# the checked build (-DSPH_CHECKED: index checks that set SPH_DEV_BOUNDS instead of accessing out of range)
+OUT_CHECKED = os.path.join(HERE, "_build_checked")
 INCLUDE = os.path.join(ROOT, "include")
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -32,8 +35,8 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, out=OUT):
+    obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _headers()):
         cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -44,22 +47,24 @@ def _compile(src, extra):
     return obj
 
 
-def build(verbose_ptxas: bool = False) -> str:
-    """Compile and link libsph; returns the path of the shared library."""
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Compile and link libsph (checked: the -DSPH_CHECKED build into _build_checked/); returns the library path."""
+    out = OUT_CHECKED if checked else OUT
+    lib_path = os.path.join(out, "libsph.so")
+    os.makedirs(out, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DSPH_CHECKED"] if checked else [])
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+    if _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-cudart=static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose_ptxas="-v" in sys.argv))
+    print(build(verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -336,12 +336,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
 }
 
 __global__ void k_bin_place(const int *__restrict__ cell_of, int n, int *__restrict__ fill,
-                            int *__restrict__ perm_tmp)
+                            int *__restrict__ perm_tmp, unsigned *status)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int s = atomicAdd(&fill[cell_of[i]], 1);
-    perm_tmp[s] = i;
+    if (SPH_CHECK(s >= 0 && s < n, status)) perm_tmp[s] = i;
 }
 
 // One warp per cell: rank every record index of the cell among the cell's indices (all distinct), write it to
@@ -489,7 +489,10 @@ __global__ void __launch_bounds__(kTile) k_gather(const uint8_t *__restrict__ ao
     const int base = blockIdx.x * kTile;
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
-    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    for (int s = tid; s < cnt; s += kTile) {
+        const int r = perm[base + s];
+        srec[s] = SPH_CHECK(r >= 0 && r < n, plan.status) ? r : 0;  // checked build: a bad entry reads record 0
+    }
     bool haspos = false;
     if (F32) {
         for (int k = 0; k < plan.nitems; ++k) haspos = haspos || plan.item_pos[k] >= 0;
@@ -605,7 +608,8 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         // phase 1, one slot per thread: its record, its SoA values and (kick) the record's v and u, all loads
         // independent, so they are in flight together
         const int s = tid;
-        const int rec = perm[base + s];
+        int rec = perm[base + s];
+        if (!SPH_CHECK(rec >= 0 && rec < n, plan.status)) rec = -1;  // checked build: nothing of it is read or written
         srec[s] = rec;
         double w[kMaxItems];
 #pragma unroll
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
                            : static_cast<const double *>(plan.soa[k])[base + s];
         }
         double kv[4];
-        if (kick) {
+        if (kick && rec >= 0) {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 kv[c] = *reinterpret_cast<const double *>(aos + (int64_t)rec * stride + plan.kick_off[c]);
@@ -642,6 +646,9 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
     for (int idx = tid; idx < nin; idx += kTile) {
         const int s = div_small(idx, inv_ni);
         const int k = idx - s * ni;
+#ifdef SPH_CHECKED
+        if (srec[s] < 0) continue;
+#endif
         double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.item_off[k]);
         *p = sval[s * sst + k];
     }
@@ -650,6 +657,9 @@ __global__ void __launch_bounds__(kTile) k_scatter(uint8_t *__restrict__ aos, in
         // written (the same doubles the record now holds)
         for (int idx = tid; idx < 4 * cnt; idx += kTile) {
             const int s = idx >> 2, c = idx & 3;
+#ifdef SPH_CHECKED
+            if (srec[s] < 0) continue;
+#endif
             double *p = reinterpret_cast<double *>(aos + (int64_t)srec[s] * stride + plan.kick_off[c]);
             *p = kick1(skick[idx], sval[s * sst + plan.kick_item[c]], plan.kick_dt);
         }
@@ -805,7 +815,10 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
     const int base = blockIdx.x * kTile;
     const int cnt = min(kTile, n - base);
     const int tid = threadIdx.x;
-    for (int s = tid; s < cnt; s += kTile) srec[s] = perm[base + s];
+    for (int s = tid; s < cnt; s += kTile) {
+        const int r = perm[base + s];
+        srec[s] = SPH_CHECK(r >= 0 && r < n, pp.status) ? r : 0;  // checked build: a bad entry reads row 0
+    }
     bool haspos = false;
     if (F32) {
         for (int k = 0; k < pp.nitems; ++k) haspos = haspos || pp.item_pos[k] >= 0;
@@ -1022,7 +1035,7 @@ cudaError_t launch_bin(const uint8_t *aos, int64_t stride, int off_x, int n, con
     launch_scan(count, ncells, nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
         *nl += 2;
-        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp, status);
         const long long threads = (long long)ncells * 32;
         const long long blocks = (threads + 255) / 256;
         k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,
@@ -1059,7 +1072,7 @@ cudaError_t launch_bin_patches(const uint8_t *aos, int64_t stride, int off_x, in
     }
     launch_scan(count, ncells_cap, ncells_dev, ncells_cap, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
-        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp, status);
         k_cell_sort<<<2048, 256, 0, st>>>(cell_start, ncells_cap, ncells_dev, perm_tmp, perm, cell_of_slot);
         *nl += 2;
     }
@@ -1186,7 +1199,7 @@ cudaError_t launch_bin_staged(uint8_t *aos, int64_t stride, int n, const RecordP
     launch_scan(count, ncells, nullptr, ncells, cell_start, fill, scan_tmp, st, nl);
     if (n > 0) {
         *nl += 2;
-        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp);
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, fill, perm_tmp, status);
         const long long threads = (long long)ncells * 32;
         const long long blocks = (threads + 255) / 256;
         k_cell_sort<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(cell_start, ncells, nullptr,

@@ -10,6 +10,16 @@
 
 namespace sphk {
 
+// Index checks of the checked build (compiled with -DSPH_CHECKED): where an index is read from device data (a
+// cell's slot range, a neighbour cell, a work-list entry, a placement slot, a permutation entry), SPH_CHECK(ok,
+// status) is ok, and a false ok also sets SPH_DEV_BOUNDS in the status word; the caller then skips the access it
+// guards.  In the default build the check is the constant true and compiles away.
+#ifdef SPH_CHECKED
+#define SPH_CHECK(ok, status) ((ok) ? true : (atomicOr((status), SPH_DEV_BOUNDS), false))
+#else
+#define SPH_CHECK(ok, status) true
+#endif
+
 // 1/pi: normalisation of the 3D cubic spline W(r,h) = f(r/h) / (pi h^3) (Monaghan & Lattanzio 1985).
 constexpr double kInvPi = 0.318309886183790671537767526745028724;
 
@@ -91,6 +101,7 @@ __device__ __forceinline__ double cell_edge(const CellSpace &cs, const CellLoc &
 // Items are the double components moved; for the 16-byte path the record bytes holding them are loaded as a
 // few 16-byte chunks per record, for the 8-byte path every item is its own 8-byte chunk.
 struct ConvPlan {
+    unsigned *status;  // checked build: SPH_DEV_BOUNDS
     int nitems;
     int nchunks;
     int chunk_off[kMaxChunks];  // byte offset of each loaded chunk inside a record
@@ -172,6 +183,7 @@ struct RecordPlan {
 // The permutation of a staged gather: dst[k][s] = src[k][perm[s]], positions of FP32 views cast relative to the
 // slot's cell origin as the gather does.
 struct PermutePlan {
+    unsigned *status;  // checked build: SPH_DEV_BOUNDS
     int nitems;
     int item_pos[kMaxItems];
     const uint8_t *rows;  // the record pass's packed rows (RecordPlan)

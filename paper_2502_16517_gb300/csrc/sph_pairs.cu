@@ -62,7 +62,10 @@ struct NbrTable {
     float margin;         // slack of the FP64 paths' FP32 filter
 };
 
-__device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellSpace &cs, const int *cell_start)
+// n, ncells, status: the checked build's range checks of the neighbour cells and their slot ranges (a neighbour
+// that fails one counts as empty).
+__device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellSpace &cs, const int *cell_start,
+                                                int n, int ncells, unsigned *status)
 {
     // one warp: lane q < 27 fills neighbour q, then the counts are prefix-summed with shuffles
     const int tid = threadIdx.x;
@@ -104,8 +107,11 @@ __device__ __forceinline__ void build_nbr_table(NbrTable &nb, int c, const CellS
             int st = 0;
             if (valid) {
                 const int c2 = L.base + kk[0] + L.n[0] * (kk[1] + L.n[1] * kk[2]);
-                st = cell_start[c2];
-                cnt = cell_start[c2 + 1] - st;
+                if (SPH_CHECK(c2 >= 0 && c2 < ncells, status)) {
+                    st = cell_start[c2];
+                    cnt = cell_start[c2 + 1] - st;
+                    if (!SPH_CHECK(st >= 0 && cnt >= 0 && st <= n - cnt, status)) st = cnt = 0;
+                }
             }
             nb.start[tid] = st;
         }
@@ -306,6 +312,7 @@ struct PairCommon {
     Counters *counters;
     int tj;            // staged particles per tile (a multiple of kStep)
     const int *skip;   // device flag: nonzero = return at once (a converged smoothing-length iteration)
+    int n, ncells;     // particles and cells (patch views: the cell capacity), for the checked build's checks
 };
 
 // ---- density, FP64 ----
@@ -1747,11 +1754,12 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
     if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
+    if (!SPH_CHECK(ls >= 0 && le <= A.cm.n, A.cm.status)) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31;
     const int tj = A.cm.tj;
     NbrTable &nb = S.nb;
     if (tid == 0) S.pairs = 0ull;
-    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start);
+    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start, A.cm.n, A.cm.ncells, A.cm.status);
     const int NJ = nb.pref[27];
     const bool wrap = nb.wrap != 0;
     const float margin = nb.margin;
@@ -1846,11 +1854,12 @@ __device__ __forceinline__ void process_cell_lanes(const typename K::Args &A, in
     if (A.cm.skip && *A.cm.skip) return;  // CTA-uniform
     const int ls = A.cm.cell_start[c], le = A.cm.cell_start[c + 1];
     if (ls >= le) return;  // CTA-uniform
+    if (!SPH_CHECK(ls >= 0 && le <= A.cm.n, A.cm.status)) return;  // CTA-uniform
     const int tid = threadIdx.x, lane = tid & 31;
     const int tj = A.cm.tj;
     NbrTable &nb = S.nb;
     if (tid == 0) S.pairs = 0ull;
-    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start);
+    build_nbr_table(nb, c, A.cm.cs, A.cm.cell_start, A.cm.n, A.cm.ncells, A.cm.status);
     const int NJ = nb.pref[27];
     unsigned my_pairs = 0;
     typename K::Part *part = reinterpret_cast<typename K::Part *>(smem);  // reuses the tile after the last one
@@ -1932,7 +1941,8 @@ __global__ void __launch_bounds__(NT, K::min_ctas_persist(NT)) k_cell_lanes_pers
         const int wi = w;
         __syncthreads();
         if (wi >= total) break;
-        process_cell_lanes<K, NT>(A, order[wi], T, S, smem);
+        const int c = order[wi];
+        if (SPH_CHECK(c >= 0 && c < A.cm.ncells, A.cm.status)) process_cell_lanes<K, NT>(A, c, T, S, smem);
     }
 }
 
@@ -1964,7 +1974,8 @@ __global__ void __launch_bounds__(NT, K::min_ctas(NT)) k_cell_pairs_persist(cons
         const int wi = w;
         __syncthreads();  // every thread has read w before thread 0 fetches the next item
         if (wi >= total) break;
-        process_cell<K, NT>(A, order[wi], T, S);
+        const int c = order[wi];
+        if (SPH_CHECK(c >= 0 && c < A.cm.ncells, A.cm.status)) process_cell<K, NT>(A, c, T, S);
     }
 }
 
@@ -2438,7 +2449,7 @@ cudaError_t launch_density_pairs(bool f32, const SoaPtrs &soa, const Scratch &sc
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
-    PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
+    PairCommon cm{cell_start, g, status, counters, 0, pl.skip, n, ncells};
     const int tj = pl.tj;
     const double gamma = prm.gamma;
     if (!f32 && prm.kernel == SPH_KERNEL_M5) {
@@ -2535,7 +2546,7 @@ cudaError_t launch_force_pairs(bool f32, const SoaPtrs &soa, const Scratch &scr,
 {
     if (n <= 0) return cudaSuccess;
     ++*nl;
-    PairCommon cm{cell_start, g, status, counters, 0, pl.skip};
+    PairCommon cm{cell_start, g, status, counters, 0, pl.skip, n, ncells};
     const int tj = pl.tj;
     if (!f32 && prm.kernel == SPH_KERNEL_M5) {
         return prm.scheme == SPH_SCHEME_EXTENDED ? force_pairs_g<KerM5, true>(soa, scr, cm, tj, prm, ncells, pl, st)

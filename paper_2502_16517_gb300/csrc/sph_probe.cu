@@ -63,3 +63,14 @@ extern "C" sph_status sph_probe_fma_rate(int32_t prec, double *flops_per_s)
     *flops_per_s = 2.0 * 8.0 * (double)iters * (double)blocks * (double)threads / (best_ms * 1e-3);
     return SPH_OK;
 }
+
+extern "C" sph_status sph_build_info(int32_t *checked)
+{
+    if (!checked) return SPH_E_INVAL;
+#ifdef SPH_CHECKED
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
+    return SPH_OK;
+}

@@ -184,6 +184,7 @@ int pred_source(int f) { return f == SPH_V ? SPH_A : (f == SPH_U ? SPH_DUDT : -1
 void build_plan(const sph_view_s *v, uint32_t mask, bool vec16, ConvPlan *p, double pred_dt = 0.0)
 {
     memset(p, 0, sizeof(*p));
+    p->status = v->status;
     std::vector<int> chunks;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         if (!(mask & SPH_BIT(f))) continue;
@@ -468,12 +469,14 @@ sph_status do_bin_gather(sph_view_s *v, void *aos, int64_t n, uint32_t mask, con
         *sub = (off - c0) / 8;
     };
     ConvPlan &p = rp.conv;
+    p.status = v->status;
     p.nchunks = (int)chunks.size();
     for (size_t k = 0; k < chunks.size(); ++k) p.chunk_off[k] = chunks[k];
     const bool f32 = v->prec == SPH_F32;
     int k = 0;
     sphk::PermutePlan pp;
     memset(&pp, 0, sizeof(pp));
+    pp.status = v->status;
     for (int f = 0; f < SPH_NFIELDS; ++f) {
         if (!(mask & SPH_BIT(f))) continue;
         const int src = pred_dt != 0.0 ? pred_source(f) : -1;

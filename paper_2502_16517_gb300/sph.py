@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsph.so")
+# SPH_CHECKED=1 in the environment loads the checked build (index checks on the device, build(checked=True))
+CHECKED = os.environ.get("SPH_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_HERE, "_build_checked" if CHECKED else "_build", "libsph.so")
 
 # ---- constants (mirror include/sph.h) ----
 SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_DEVICE, SPH_E_TIMEOUT, SPH_E_NOTCONV, SPH_E_STATE = range(8)
@@ -44,6 +46,7 @@ SPH_FORCE_OUT_EXT = SPH_FORCE_OUT | SPH_BIT(SPH_VSIG)
 SPH_ALL_FIELDS = (1 << SPH_NFIELDS) - 1
 SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 0x2, 0x4, 0x8
 SPH_DEV_NOTCONV = 0x10
+SPH_DEV_BOUNDS = 0x20  # checked build only
 (SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
  SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
 SPH_NPHASES = 9
@@ -118,6 +121,7 @@ _SIGS = {
     "sph_view_h_rounds": [_VP, _VP, _VP],
     "sph_autotune": [_VP, _VP, _I64, ctypes.POINTER(sph_params), ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
     "sph_bin_static": [ctypes.POINTER(sph_layout), ctypes.POINTER(sph_domain), _VP, _I64, _VP, _VP, _VP, _VP, _VP],
+    "sph_build_info": [ctypes.POINTER(ctypes.c_int32)],
 }
 EXPORTED = tuple(_SIGS) + ("sph_strerror",)
 
@@ -416,3 +420,10 @@ def sph_autotune(view, aos_dev, n, params):
     ms = (ctypes.c_float * 2)()
     _check("sph_autotune", lib().sph_autotune(view, _addr(aos_dev), int(n), ctypes.byref(P), chosen, ms))
     return (chosen[0], chosen[1]), (ms[0], ms[1])
+
+
+def sph_build_info():
+    """1 if the loaded library is the checked build (compiled with -DSPH_CHECKED), else 0."""
+    v = ctypes.c_int32(0)
+    _check("sph_build_info", lib().sph_build_info(ctypes.byref(v)))
+    return int(v.value)
