@@ -349,7 +349,10 @@ struct DensF64 {
     using Acc = double;
     static constexpr int kStageBytes = 4 * 8 + 16;
     static constexpr int kSlotDoubles = 17;  // slot of a local particle's members (odd: see PairShared)
-    static constexpr bool kSkipSelf = false;  // rho_i includes m_i W(0, h_i)
+    // rho_i includes m_i W(0, h_i) = m_i / (pi h^3): the filter drops the self candidate and finish adds m_i f(0) =
+    // m_i to the sum of the others (kSelfInFinish: the self pair is still counted)
+    static constexpr bool kSkipSelf = true;
+    static constexpr bool kSelfInFinish = true;
     static constexpr bool kSplit = false;     // one queue (see tile_pairs_split)
     // CTAs per SM the register allocation must allow: shared memory allows seven of 128 threads at a 512 tile
     static constexpr int min_ctas(int nt) { return nt == 128 ? 7 : 3; }
@@ -461,7 +464,7 @@ struct DensF64 {
     static __device__ __forceinline__ void finish(const Args &A, int i, const Acc &a)
     {
         const double h = A.f[H][i];
-        const double rho = a * A.rk[i];
+        const double rho = (a + A.m[i]) * A.rk[i];  // + the self term m_i f(0), f(0) = 1
         const double P = (A.gamma - 1.0) * rho * A.u[i];
         const double cs = A.cs0[i];
         A.rho[i] = rho;
@@ -676,6 +679,7 @@ struct ForceF64 {
     static constexpr int kVelF = 16;  // the FP32 velocity's place in the slot (in doubles)
     // The self pair contributes nothing (j != i in the sums), so the queue driver drops it at the filter.
     static constexpr bool kSkipSelf = true;
+    static constexpr bool kSelfInFinish = false;
     // Receding pairs (v_ij . r_ij >= 0) have no viscosity: the queued hits are sorted by an FP32 estimate of
     // v_ij . r_ij, and rounds of estimated receding pairs skip the viscosity terms (tile_pairs_split).
     static constexpr bool kSplit = true;
@@ -1015,6 +1019,7 @@ struct DensF64G {
     static constexpr int kStageBytes = kRow * 8 + 16;
     static constexpr int kSlotDoubles = 17;
     static constexpr bool kSkipSelf = false;  // the sums include the self term
+    static constexpr bool kSelfInFinish = false;
     static constexpr bool kSplit = false;
     static constexpr int min_ctas(int nt) { return nt == 128 ? 6 : 3; }
     // the two particles of a warp's queue: Ext reduces 12 sums with one 16-value reduce-scatter, the plain
@@ -1207,6 +1212,7 @@ struct ForceF64G {
     static constexpr int kStageBytes = NF * 8 + 16;
     static constexpr int kSlotDoubles = 17;
     static constexpr bool kSkipSelf = true;  // as ForceF64
+    static constexpr bool kSelfInFinish = false;
     static constexpr bool kSplit = false;
     // three 256-thread CTAs per SM, as ForceF64 (the 448 tile's shared memory allows three)
     static constexpr int min_ctas(int) { return 3; }
@@ -1793,7 +1799,11 @@ __device__ __forceinline__ void process_cell(const typename K::Args &A, int c, c
     }
     if (lane == 0 && my_pairs) atomicAdd(&S.pairs, my_pairs);
     __syncthreads();
-    if (tid == 0) K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, S.pairs);
+    if (tid == 0) {
+        // a self term added in finish is still a pair of the sum
+        const unsigned long long self = K::kSelfInFinish ? (unsigned long long)(le - ls) : 0ull;
+        K::count(A, (unsigned long long)(le - ls) * (unsigned long long)NJ, S.pairs + self);
+    }
 }
 
 // Lane driver of the FP32 loop bodies: each of the CTA's threads owns one (local particle, candidate stream)
