@@ -58,7 +58,7 @@ typedef enum sph_status {
 typedef enum sph_prec {
     SPH_F64 = 0, /* SoA views and pair loops in FP64                                                       */
     SPH_F32 = 1  /* SoA views in FP32 (positions relative to their cell's origin), FP32 pair loops with
-                    Kahan-compensated sums, FP64 global reductions                                          */
+                    Kahan-compensated sums, global sums with FP64 results (see sph_reduce)                  */
 } sph_prec;
 
 /* Particle members known to the library, in the order of sph_layout.off[].  x, v, a and curl v are three
@@ -337,8 +337,10 @@ SPH_API sph_status sph_step_host(sph_view view, void *aos_host, int64_t n, const
 SPH_API sph_status sph_view_set_host_direct(sph_view view, int32_t on);
 
 /* FP64 global sums over the SoA members, in a fixed order (deterministic): out[0..2] = sum m v,
- * out[3..5] = sum m a, out[6] = sum m (|v|^2/2 + u), out[7] = sum m (v . a + du/dt).  Needs x, v, a, mass, u,
- * dudt resident.  Waits. */
+ * out[3..5] = sum m a, out[6] = sum m (|v|^2/2 + u), out[7] = sum m (v . a + du/dt).  FP64 views sum in FP64;
+ * FP32 views sum their float members in double-float arithmetic (exact products, compensated additions), which
+ * agrees with FP64 sums of the same float values to ~1e-14 of the sums of absolute terms.  Needs x, v, a, mass,
+ * u, dudt resident.  Waits. */
 SPH_API sph_status sph_reduce(sph_view view, double out[8]);
 
 /* Wait for the view's stream; SPH_E_DEVICE if the device status word is non-zero. */
