@@ -113,24 +113,45 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_part_f32(SoaPtrs s, int 
     DF acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = {0.f, 0.f};
-    for (int i = b0 + threadIdx.x; i < b1; i += kRedThreads) {
-        const float mm = m[i];
-        const float v0 = vx[i], v1 = vy[i], v2 = vz[i];
-        const float a0 = ax[i], a1 = ay[i], a2 = az[i];
-        acc[0] = df_add(acc[0], two_prod(mm, v0));
-        acc[1] = df_add(acc[1], two_prod(mm, v1));
-        acc[2] = df_add(acc[2], two_prod(mm, v2));
-        acc[3] = df_add(acc[3], two_prod(mm, a0));
-        acc[4] = df_add(acc[4], two_prod(mm, a1));
-        acc[5] = df_add(acc[5], two_prod(mm, a2));
-        // m (|v|^2 / 2 + u): the halving is exact
-        DF e = df_add(df_add(two_prod(v0, v0), two_prod(v1, v1)), two_prod(v2, v2));
-        e.hi = __fmul_rn(0.5f, e.hi);
-        e.lo = __fmul_rn(0.5f, e.lo);
-        acc[6] = df_add(acc[6], df_mul_f(df_add_f(e, u[i]), mm));
-        // m (v . a + du/dt)
-        const DF w = df_add(df_add(two_prod(v0, a0), two_prod(v1, a1)), two_prod(v2, a2));
-        acc[7] = df_add(acc[7], df_mul_f(df_add_f(w, du[i]), mm));
+    // kGroup particles per trip (i, i + kRedThreads, ...): their loads are issued together, then they are added in
+    // the same order as one at a time
+    constexpr int kGroup = 4;
+    for (int i0 = b0 + threadIdx.x; i0 < b1; i0 += kGroup * kRedThreads) {
+        float r[kGroup][9];
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+            const int i = i0 + g * kRedThreads;
+            const bool in = i < b1;
+            r[g][0] = in ? m[i] : 0.f;
+            r[g][1] = in ? vx[i] : 0.f;
+            r[g][2] = in ? vy[i] : 0.f;
+            r[g][3] = in ? vz[i] : 0.f;
+            r[g][4] = in ? ax[i] : 0.f;
+            r[g][5] = in ? ay[i] : 0.f;
+            r[g][6] = in ? az[i] : 0.f;
+            r[g][7] = in ? u[i] : 0.f;
+            r[g][8] = in ? du[i] : 0.f;
+        }
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+            if (i0 + g * kRedThreads >= b1) break;
+            const float mm = r[g][0], v0 = r[g][1], v1 = r[g][2], v2 = r[g][3];
+            const float a0 = r[g][4], a1 = r[g][5], a2 = r[g][6];
+            acc[0] = df_add(acc[0], two_prod(mm, v0));
+            acc[1] = df_add(acc[1], two_prod(mm, v1));
+            acc[2] = df_add(acc[2], two_prod(mm, v2));
+            acc[3] = df_add(acc[3], two_prod(mm, a0));
+            acc[4] = df_add(acc[4], two_prod(mm, a1));
+            acc[5] = df_add(acc[5], two_prod(mm, a2));
+            // m (|v|^2 / 2 + u): the halving is exact
+            DF e = df_add(df_add(two_prod(v0, v0), two_prod(v1, v1)), two_prod(v2, v2));
+            e.hi = __fmul_rn(0.5f, e.hi);
+            e.lo = __fmul_rn(0.5f, e.lo);
+            acc[6] = df_add(acc[6], df_mul_f(df_add_f(e, r[g][7]), mm));
+            // m (v . a + du/dt)
+            const DF w = df_add(df_add(two_prod(v0, a0), two_prod(v1, a1)), two_prod(v2, a2));
+            acc[7] = df_add(acc[7], df_mul_f(df_add_f(w, r[g][8]), mm));
+        }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
