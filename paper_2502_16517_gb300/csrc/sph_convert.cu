@@ -804,7 +804,12 @@ __global__ void __launch_bounds__(kTile, 6) k_record_pass(uint8_t *__restrict__ 
 }
 
 // Permutation of staged items into slot order (PermutePlan), CTA per tile of kTile slots; FP32 positions become
-// (float)(x - origin of the slot's cell), with the origin as the gather computes it.
+// (float)(x - origin of the slot's cell), with the origin as the gather computes it.  Slots are in cell order, so
+// a tile's slots lie in the cells cell_of_slot[base] .. cell_of_slot[base + cnt - 1]: when there are at most
+// kTile of them, each origin is formed once per cell in shared memory, else once per slot (the same products
+// either way).  The other FP32 members move as the float bits the record pass stored.  Conversions to and from
+// FP64 run on the FP64 pipe, 1/64 of the FP32 rate on this part: per slot, only the positions' subtraction and
+// rounding remain.
 template <bool F32>
 __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm, const int *__restrict__ cell_of_slot,
                                                    int n, const PermutePlan pp, const CellSpace cs)
@@ -820,45 +825,74 @@ __global__ void __launch_bounds__(kTile) k_permute(const int *__restrict__ perm,
         srec[s] = SPH_CHECK(r >= 0 && r < n, pp.status) ? r : 0;  // checked build: a bad entry reads row 0
     }
     bool haspos = false;
+    int c0 = 0, ncl = 0;  // the tile's cells c0 .. c0 + ncl - 1 (FP32 positions)
     if (F32) {
         for (int k = 0; k < pp.nitems; ++k) haspos = haspos || pp.item_pos[k] >= 0;
-        if (haspos && cs.npatch > 0 && tid < 2) {
-            CellLoc L;
-            locate_cell(cs, cell_of_slot[base + (tid == 0 ? 0 : cnt - 1)], L);
-            prange[tid] = L.patch;
+        if (haspos) {
+            c0 = cell_of_slot[base];
+            ncl = cell_of_slot[base + cnt - 1] - c0 + 1;
+            if (cs.npatch > 0 && tid < 2) {
+                CellLoc L;
+                locate_cell(cs, tid == 0 ? c0 : c0 + ncl - 1, L);
+                prange[tid] = L.patch;
+            }
         }
     }
     __syncthreads();
+    const bool per_cell = ncl >= 1 && ncl <= kTile;  // CTA-uniform
+    int lo = 0, hi = 0;                               // the patches of the tile's cells
     if (F32 && haspos) {
-        const int lo = cs.npatch > 0 ? prange[0] : 0, hi = cs.npatch > 0 ? prange[1] + 1 : 0;
-        for (int s = tid; s < cnt; s += kTile) {
+        lo = cs.npatch > 0 ? prange[0] : 0;
+        hi = cs.npatch > 0 ? prange[1] + 1 : 0;
+        for (int j = tid; j < (per_cell ? ncl : cnt); j += kTile) {
             CellLoc L;
-            locate_cell_in(cs, cell_of_slot[base + s], lo, hi, L);
+            locate_cell_in(cs, per_cell ? c0 + j : cell_of_slot[base + j], lo, hi, L);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) sorg[3 * s + a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
+            for (int a = 0; a < 3; ++a) sorg[3 * j + a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
         }
         __syncthreads();
     }
     if (tid < cnt) {  // one slot per thread: its record's packed row, all loads in flight before the stores
         const int s = tid;
         const uint8_t *row = pp.rows + (int64_t)srec[s] * pp.row_bytes;
-        double w[kMaxItems];
+        unsigned long long w[kMaxItems];  // an item's bits: a double, or an FP32 member's float (not a position)
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) {
             if (k < pp.nitems)
-                w[k] = (!F32 || pp.item_pos[k] >= 0) ? *reinterpret_cast<const double *>(row + pp.row_off[k])
-                                                     : (double)*reinterpret_cast<const float *>(row + pp.row_off[k]);
+                w[k] = (!F32 || pp.item_pos[k] >= 0)
+                           ? *reinterpret_cast<const unsigned long long *>(row + pp.row_off[k])
+                           : (unsigned long long)*reinterpret_cast<const unsigned *>(row + pp.row_off[k]);
+        }
+        double org[3] = {0.0, 0.0, 0.0};
+        if (F32 && haspos) {
+            // the slot's cell in the tile's range (always, for slots in cell order); else its origin afresh
+            const int j = per_cell ? cell_of_slot[base + s] - c0 : s;
+            if (!per_cell || (unsigned)j < (unsigned)ncl) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) org[a] = sorg[3 * j + a];
+            } else {
+                CellLoc L;
+                locate_cell(cs, cell_of_slot[base + s], L);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) org[a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
+            }
         }
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) {
             if (k >= pp.nitems) break;
             if (!F32) {
-                static_cast<double *>(pp.dst[k])[base + s] = w[k];
+                static_cast<unsigned long long *>(pp.dst[k])[base + s] = w[k];
             } else {
                 const int axis = pp.item_pos[k];
-                // positions: (float)(x - origin); other members: the float the record pass stored (exact)
-                const float o = axis >= 0 ? __double2float_rn(__dsub_rn(w[k], sorg[3 * s + axis])) : (float)w[k];
-                static_cast<float *>(pp.dst[k])[base + s] = o;
+                if (axis >= 0) {  // (float)(x - origin)
+                    double o = org[0];
+                    if (axis == 1) o = org[1];
+                    if (axis == 2) o = org[2];
+                    static_cast<float *>(pp.dst[k])[base + s] =
+                        __double2float_rn(__dsub_rn(__longlong_as_double((long long)w[k]), o));
+                } else {
+                    static_cast<unsigned *>(pp.dst[k])[base + s] = (unsigned)w[k];
+                }
             }
         }
     }
