@@ -2064,15 +2064,16 @@ __global__ void __launch_bounds__(256) k_work_place(const CellSpace cs, const in
     }
 }
 
-// FP32 cell-relative copies of FP64 positions and (float) h rounded up: the filter inputs of the FP64 force loop.
+// FP32 cell-relative copies of FP64 positions, (float)(x - k edge) with the product and the difference each rounded
+// once (as the FP32 view's positions and BlockCells form them): the filter inputs of the FP64 loops.
 __device__ __forceinline__ void cell_relative_f32(const CellSpace &cs, int c, double x, double y, double z,
                                                   float &xf, float &yf, float &zf)
 {
     CellLoc L;
     locate_cell(cs, c, L);
-    xf = __double2float_rn(x - (double)L.k[0] * cell_edge(cs, L, 0));
-    yf = __double2float_rn(y - (double)L.k[1] * cell_edge(cs, L, 1));
-    zf = __double2float_rn(z - (double)L.k[2] * cell_edge(cs, L, 2));
+    xf = __double2float_rn(__dsub_rn(x, __dmul_rn((double)L.k[0], cell_edge(cs, L, 0))));
+    yf = __double2float_rn(__dsub_rn(y, __dmul_rn((double)L.k[1], cell_edge(cs, L, 1))));
+    zf = __double2float_rn(__dsub_rn(z, __dmul_rn((double)L.k[2], cell_edge(cs, L, 2))));
 }
 
 __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
@@ -2086,20 +2087,83 @@ __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__
     hf[s] = __double2float_ru(h[s]);
 }
 
+// ---- per-particle set-up of the FP64 loops ----
+// These kernels are bound by the FP64 pipe (1/64 of the FP32 rate on this part), so they avoid its long
+// sequences: 1/x and sqrt(x) come from the seeded forms above (an FP32 seed, one FP64 correction, within an ulp
+// or two of the IEEE results) where x lies well inside the float range, and from the IEEE operations elsewhere (a
+// branch that physical inputs never take); and each cell's origin is formed once per block (BlockCells).
+__device__ __forceinline__ bool seedable(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    return hi >= 0x38200000u && hi < 0x47C00000u;  // 2^-125 <= |x| < 2^125: seed and result are float normals
+}
+__device__ __forceinline__ double rcp_prep(double x) { return seedable(x) ? rcp_seeded(x) : 1.0 / x; }
+__device__ __forceinline__ double sqrt_prep(double x) { return seedable(x) ? sqrt_seeded(x) : sqrt(x); }
+
+// The cell origins of a block's slots.  Slots are in cell order, so the block's slots lie in the cells c0 .. c0 +
+// ncl - 1; with at most kPrepThreads of them each origin k edge is formed once per cell in shared memory, and a
+// slot outside that range (none, for slots in cell order) forms its own.  The FP32 copy of a position is then
+// (float)(x - origin), as the FP32 view's positions are.  The range lives in each thread's registers (BlockCells),
+// the origins in shared memory.
+constexpr int kPrepThreads = 256;
+struct BlockCells {
+    int c0, ncl;
+    // called by the whole block (one __syncthreads); o: the block's shared origins
+    __device__ __forceinline__ void build(double (*o)[3], const CellSpace &cs, const int *cell_of_slot, int n)
+    {
+        const int base = blockIdx.x * kPrepThreads;
+        const int cnt = min(kPrepThreads, n - base);
+        c0 = cell_of_slot[base];
+        ncl = cell_of_slot[base + cnt - 1] - c0 + 1;
+        if (ncl >= 1 && ncl <= kPrepThreads) {
+            for (int j = threadIdx.x; j < ncl; j += kPrepThreads) {
+                CellLoc L;
+                locate_cell(cs, c0 + j, L);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) o[j][a] = __dmul_rn((double)L.k[a], cell_edge(cs, L, a));
+            }
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ void rel_f32(const double (*o)[3], const CellSpace &cs, int c, double x, double y,
+                                            double z, float &xf, float &yf, float &zf) const
+    {
+        double ox, oy, oz;
+        const int j = c - c0;
+        if (ncl >= 1 && ncl <= kPrepThreads && (unsigned)j < (unsigned)ncl) {
+            ox = o[j][0];
+            oy = o[j][1];
+            oz = o[j][2];
+        } else {
+            CellLoc L;
+            locate_cell(cs, c, L);
+            ox = __dmul_rn((double)L.k[0], cell_edge(cs, L, 0));
+            oy = __dmul_rn((double)L.k[1], cell_edge(cs, L, 1));
+            oz = __dmul_rn((double)L.k[2], cell_edge(cs, L, 2));
+        }
+        xf = __double2float_rn(__dsub_rn(x, ox));
+        yf = __double2float_rn(__dsub_rn(y, oy));
+        zf = __double2float_rn(__dsub_rn(z, oz));
+    }
+};
+
 // Per-particle set-up of the FP64 density loop: cell-relative float positions (filter) and f(r/h) of the cubic
 // spline as a cubic in r: inner piece 1 - 3/2 (r/h)^2 + 3/4 (r/h)^3, outer 2 - 3 (r/h) + 3/2 (r/h)^2 - 1/4 (r/h)^3.
-__global__ void k_density_prep_f64(const double *__restrict__ x, const double *__restrict__ y,
-                                   const double *__restrict__ z, const double *__restrict__ h,
-                                   const int *__restrict__ cell_of_slot, int n, CellSpace cs, float *__restrict__ xf,
-                                   float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2,
-                                   double *__restrict__ e3, double *__restrict__ o1, double *__restrict__ o2,
-                                   double *__restrict__ o3, const double *__restrict__ u, double gamma,
-                                   double *__restrict__ rk, double *__restrict__ cs0)
+// g1 = gamma (gamma - 1).
+__global__ void __launch_bounds__(kPrepThreads) k_density_prep_f64(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, CellSpace cs, float *__restrict__ xf,
+    float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2, double *__restrict__ e3,
+    double *__restrict__ o1, double *__restrict__ o2, double *__restrict__ o3, const double *__restrict__ u,
+    double g1, double *__restrict__ rk, double *__restrict__ cs0)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double org[kPrepThreads][3];
+    BlockCells B;
+    B.build(org, cs, cell_of_slot, n);
+    const int s = blockIdx.x * kPrepThreads + threadIdx.x;
     if (s >= n) return;
-    cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
-    const double hi = 1.0 / h[s], h2 = hi * hi, h3 = h2 * hi;
+    B.rel_f32(org, cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
+    const double hi = rcp_prep(h[s]), h2 = hi * hi, h3 = h2 * hi;
     e2[s] = -1.5 * h2;
     e3[s] = 0.75 * h3;
     o1[s] = -3.0 * hi;
@@ -2109,7 +2173,7 @@ __global__ void k_density_prep_f64(const double *__restrict__ x, const double *_
     // c_s = sqrt(gamma P / rho) = sqrt(gamma (gamma - 1) u), which needs no density (so the pair kernel's per-particle
     // epilogue, run by few lanes of a warp, has no division or square root left)
     rk[s] = kInvPi * h3;
-    cs0[s] = sqrt(gamma * (gamma - 1.0) * u[s]);
+    cs0[s] = sqrt_prep(g1 * u[s]);
 }
 
 // Per-particle quantities of the FP32 force loop: 1/h, 3/(pi h^4), P/rho^2.
@@ -2127,24 +2191,25 @@ __global__ void k_force_prep_f32(const float *__restrict__ h, const float *__res
     A[s] = P[s] / (r * r);
 }
 
-// Per-particle quantities of the FP64 force loop (see ForceF64); sc = sqrt(eps) with softening, else 1.  Also the
-// filter's FP32 copies (k_pos32's work, in the same pass over the particles).
-__global__ void k_force_prep_f64(const double *__restrict__ h, const double *__restrict__ P,
-                                 const double *__restrict__ rho, const double *__restrict__ cs, double alpha,
-                                 double sc, int n, double *__restrict__ hs, double *__restrict__ q2,
-                                 double *__restrict__ S0, double *__restrict__ K1, double *__restrict__ K2i,
-                                 double *__restrict__ K2o, double *__restrict__ A, double *__restrict__ acs,
-                                 const double *__restrict__ x, const double *__restrict__ y,
-                                 const double *__restrict__ z, const int *__restrict__ cell_of_slot, CellSpace g,
-                                 float *__restrict__ xf, float *__restrict__ yf, float *__restrict__ zf,
-                                 float *__restrict__ hf)
+// Per-particle quantities of the FP64 force loop (see ForceF64); sc = sqrt(eps) with softening, else 1, and
+// acs_k = alpha / (2 sc).  Also the filter's FP32 copies (k_pos32's work, in the same pass over the particles).
+__global__ void __launch_bounds__(kPrepThreads) k_force_prep_f64(
+    const double *__restrict__ h, const double *__restrict__ P, const double *__restrict__ rho,
+    const double *__restrict__ cs, double acs_k, double sc, int n, double *__restrict__ hs, double *__restrict__ q2,
+    double *__restrict__ S0, double *__restrict__ K1, double *__restrict__ K2i, double *__restrict__ K2o,
+    double *__restrict__ A, double *__restrict__ acs, const double *__restrict__ x, const double *__restrict__ y,
+    const double *__restrict__ z, const int *__restrict__ cell_of_slot, CellSpace g, float *__restrict__ xf,
+    float *__restrict__ yf, float *__restrict__ zf, float *__restrict__ hf)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double org[kPrepThreads][3];
+    BlockCells B;
+    B.build(org, g, cell_of_slot, n);
+    const int s = blockIdx.x * kPrepThreads + threadIdx.x;
     if (s >= n) return;
-    cell_relative_f32(g, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
-    hf[s] = __double2float_ru(h[s]);
+    B.rel_f32(org, g, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
     const double hv = h[s];
-    const double hi = 1.0 / hv, h2 = hi * hi;
+    hf[s] = __double2float_ru(hv);
+    const double hi = rcp_prep(hv), h2 = hi * hi;
     const double s4 = kInvPi * h2 * h2;  // 1/(pi h^4)
     const double hh = 0.5 * hv;
     hs[s] = sc * hh;
@@ -2153,9 +2218,9 @@ __global__ void k_force_prep_f64(const double *__restrict__ h, const double *__r
     K1[s] = 3.0 * s4 * hi;
     K2i[s] = 2.25 * s4 * h2;
     K2o[s] = -0.75 * s4 * h2;
-    const double r = rho[s];
-    A[s] = P[s] / (r * r);
-    acs[s] = (0.5 * alpha) * cs[s] / sc;
+    const double ri = rcp_prep(rho[s]);  // P / rho^2 as P (1/rho)^2: 1/rho^2 may leave the float range, 1/rho not
+    A[s] = P[s] * (ri * ri);
+    acs[s] = acs_k * cs[s];
 }
 
 // Per-particle set-up of the kernel-family density (DensF64G): cell-relative float positions (filter), 1/h,
@@ -2304,8 +2369,9 @@ cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr
                  *u = (const double *)soa.p[SPH_U][0];
     double *const *d = reinterpret_cast<double *const *>(scr.d);
     if (prm.kernel == SPH_KERNEL_M4 && prm.scheme == SPH_SCHEME_MINIMAL) {
-        k_density_prep_f64<<<nb, 256, 0, st>>>(x, y, z, h, cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, d[0], d[1],
-                                              d[2], d[3], d[4], u, gamma, d[5], d[6]);
+        k_density_prep_f64<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, st>>>(
+            x, y, z, h, cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, d[0], d[1], d[2], d[3], d[4], u,
+            gamma * (gamma - 1.0), d[5], d[6]);
     } else if (prm.kernel == SPH_KERNEL_M5) {
         k_density_prep_g<KerM5><<<nb, 256, 0, st>>>(x, y, z, h, u, cell_of_slot, n, g, gamma, scr.xf, scr.yf,
                                                     scr.zf, d[0], d[1], d[2], d[6]);
@@ -2345,9 +2411,11 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
         const bool ext = prm.scheme == SPH_SCHEME_EXTENDED;
         if (prm.kernel == SPH_KERNEL_M4 && !ext) {
             const double sc = prm.eps > 0.0 ? sqrt(prm.eps) : 1.0;
-            k_force_prep_f64<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
+            k_force_prep_f64<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, st>>>(
+                                                 (const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0],
                                                  (const double *)soa.p[SPH_RHO][0],
-                                                 (const double *)soa.p[SPH_CS][0], alpha, sc, n, (double *)scr.d[0],
+                                                 (const double *)soa.p[SPH_CS][0], 0.5 * alpha / sc, sc, n,
+                                                 (double *)scr.d[0],
                                                  (double *)scr.d[7], (double *)scr.d[1], (double *)scr.d[2],
                                                  (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
                                                  (double *)scr.d[6], (const double *)soa.p[SPH_X][0],
