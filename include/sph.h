@@ -100,6 +100,11 @@ enum {
 #define SPH_DEV_BOUNDS 0x20u    /* checked build only (compiled with -DSPH_CHECKED): an index read from device
                                    data (cell, slot range, permutation, work list) was out of range; the access
                                    it guarded was skipped */
+#define SPH_DEV_MAGNITUDE 0x40u /* FP64 views: a particle with h outside [2^-50, 2^50) or h^2 rho outside
+                                   [2^-105, 2^105) in the caller's units.  The FP64 pair loops refine FP32-seeded
+                                   reciprocals and square roots of r^2 and (r^2 + eps hbar^2)(rho_i + rho_j),
+                                   which must lie in the float range; outside these bounds the results may be
+                                   wrong: rescale the units */
 
 /* Record layout: `stride` bytes per record (a multiple of 8, at most 65536); off[f] is the byte offset of
  * member f inside a record (a multiple of 8), or -1 if the record has no such member.  Present members must

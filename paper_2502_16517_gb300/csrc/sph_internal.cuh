@@ -233,11 +233,14 @@ cudaError_t launch_scatter(uint8_t *aos, int64_t stride, const int *perm, const 
                            const ConvPlan &plan, const CellSpace &cs, bool f32, cudaStream_t st, int *nl);
 
 // Per-particle preparation of the pair loops (FP64 views: float filter copies of x (and h) and coefficient
-// tables; FP32 force: 1/h, 1/(pi h^5), P/rho^2).
+// tables, and SPH_DEV_MAGNITUDE in *status for an h or rho outside the FP64 loops' band; FP32 force: 1/h,
+// 1/(pi h^5), P/rho^2).
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &cs, const sph_params &prm, cudaStream_t st, int *nl);
+                                const CellSpace &cs, const sph_params &prm, unsigned *status, cudaStream_t st,
+                                int *nl);
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const CellSpace &cs, const sph_params &prm, cudaStream_t st, int *nl);
+                              const CellSpace &cs, const sph_params &prm, unsigned *status, cudaStream_t st,
+                              int *nl);
 
 // Pair-kernel launch shape: active particles staged per tile (0 = default of the path), and for patch views the
 // largest-first work list the persistent kernel pulls cells from.

@@ -2064,6 +2064,31 @@ __global__ void __launch_bounds__(256) k_work_place(const CellSpace cs, const in
     }
 }
 
+// The magnitudes the FP64 pair loops need.  They refine FP32-seeded reciprocals and square roots of r^2 (r below
+// kappa h in the support) and of (r^2 + eps hbar^2)(rho_i + rho_j), which must lie in the float normal range
+// (2^-126 .. 2^128).  That holds, with room for kappa^2, the pair means and pairs down to h/100 apart (closer
+// pairs give a tiny r^2, whose seeded forms stay finite and whose terms vanish), when 2^-50 <= h < 2^50 and
+// 2^-105 <= h^2 rho < 2^105.  The set-up kernels flag a particle outside these bounds (SPH_DEV_MAGNITUDE: its
+// results may be wrong; rescale the units).  rho alone is never seeded there.  Exponents are compared on the
+// integer pipe.
+__device__ __forceinline__ bool h_in_band(double h)
+{
+    const unsigned hi = (unsigned)__double2hiint(h);  // negative values and NaN fall outside
+    return hi >= 0x3CD00000u && hi < 0x43100000u;     // 2^-50 <= h < 2^50
+}
+__device__ __forceinline__ void check_h_band(double h, unsigned *status)
+{
+    if (!h_in_band(h)) atomicOr(status, SPH_DEV_MAGNITUDE);
+}
+__device__ __forceinline__ void check_h_rho_band(double h, double rho, unsigned *status)
+{
+    const unsigned hr = (unsigned)__double2hiint(rho);
+    const int eh = (int)((unsigned)__double2hiint(h) >> 20) - 1023, er = (int)(hr >> 20) - 1023;  // exponents
+    const bool rho_ok = hr >= 0x00100000u && hr < 0x7FF00000u;  // positive, normal, finite
+    const int e = 2 * eh + er;                                   // h^2 rho in [2^e, 2^(e+3))
+    if (!h_in_band(h) || !rho_ok || e < -105 || e > 101) atomicOr(status, SPH_DEV_MAGNITUDE);
+}
+
 // FP32 cell-relative copies of FP64 positions, (float)(x - k edge) with the product and the difference each rounded
 // once (as the FP32 view's positions and BlockCells form them): the filter inputs of the FP64 loops.
 __device__ __forceinline__ void cell_relative_f32(const CellSpace &cs, int c, double x, double y, double z,
@@ -2079,12 +2104,13 @@ __device__ __forceinline__ void cell_relative_f32(const CellSpace &cs, int c, do
 __global__ void k_pos32(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                         const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, CellSpace cs,
                         float *__restrict__ xf, float *__restrict__ yf, float *__restrict__ zf,
-                        float *__restrict__ hf)
+                        float *__restrict__ hf, unsigned *status)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
     hf[s] = __double2float_ru(h[s]);
+    check_h_band(h[s], status);
 }
 
 // ---- per-particle set-up of the FP64 loops ----
@@ -2155,7 +2181,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_density_prep_f64(
     const double *__restrict__ h, const int *__restrict__ cell_of_slot, int n, CellSpace cs, float *__restrict__ xf,
     float *__restrict__ yf, float *__restrict__ zf, double *__restrict__ e2, double *__restrict__ e3,
     double *__restrict__ o1, double *__restrict__ o2, double *__restrict__ o3, const double *__restrict__ u,
-    double g1, double *__restrict__ rk, double *__restrict__ cs0)
+    double g1, double *__restrict__ rk, double *__restrict__ cs0, unsigned *status)
 {
     __shared__ double org[kPrepThreads][3];
     BlockCells B;
@@ -2163,6 +2189,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_density_prep_f64(
     const int s = blockIdx.x * kPrepThreads + threadIdx.x;
     if (s >= n) return;
     B.rel_f32(org, cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
+    check_h_band(h[s], status);
     const double hi = rcp_prep(h[s]), h2 = hi * hi, h3 = h2 * hi;
     e2[s] = -1.5 * h2;
     e3[s] = 0.75 * h3;
@@ -2199,7 +2226,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_force_prep_f64(
     double *__restrict__ S0, double *__restrict__ K1, double *__restrict__ K2i, double *__restrict__ K2o,
     double *__restrict__ A, double *__restrict__ acs, const double *__restrict__ x, const double *__restrict__ y,
     const double *__restrict__ z, const int *__restrict__ cell_of_slot, CellSpace g, float *__restrict__ xf,
-    float *__restrict__ yf, float *__restrict__ zf, float *__restrict__ hf)
+    float *__restrict__ yf, float *__restrict__ zf, float *__restrict__ hf, unsigned *status)
 {
     __shared__ double org[kPrepThreads][3];
     BlockCells B;
@@ -2209,6 +2236,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_force_prep_f64(
     B.rel_f32(org, g, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
     const double hv = h[s];
     hf[s] = __double2float_ru(hv);
+    check_h_rho_band(hv, rho[s], status);
     const double hi = rcp_prep(hv), h2 = hi * hi;
     const double s4 = kInvPi * h2 * h2;  // 1/(pi h^4)
     const double hh = 0.5 * hv;
@@ -2231,11 +2259,12 @@ __global__ void k_density_prep_g(const double *__restrict__ x, const double *__r
                                  const double *__restrict__ u, const int *__restrict__ cell_of_slot, int n,
                                  CellSpace cs, double gamma, float *__restrict__ xf, float *__restrict__ yf,
                                  float *__restrict__ zf, double *__restrict__ hinv, double *__restrict__ s0,
-                                 double *__restrict__ s1, double *__restrict__ cs0)
+                                 double *__restrict__ s1, double *__restrict__ cs0, unsigned *status)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     cell_relative_f32(cs, cell_of_slot[s], x[s], y[s], z[s], xf[s], yf[s], zf[s]);
+    check_h_band(h[s], status);
     const double hi = 1.0 / h[s], h3 = hi * hi * hi;
     hinv[s] = hi;
     s0[s] = Ker::sigma * h3;
@@ -2252,10 +2281,11 @@ __global__ void k_force_prep_g(const double *__restrict__ h, const double *__res
                                const double *__restrict__ cx, const double *__restrict__ cy,
                                const double *__restrict__ cz, double alpha, int n, double *__restrict__ hh,
                                double *__restrict__ hinv, double *__restrict__ s1, double *__restrict__ A,
-                               double *__restrict__ ach, double *__restrict__ bal)
+                               double *__restrict__ ach, double *__restrict__ bal, unsigned *status)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    check_h_rho_band(h[s], rho[s], status);
     const double hv = h[s];
     const double hi = 1.0 / hv, h2 = hi * hi;
     hh[s] = 0.5 * hv;
@@ -2359,7 +2389,8 @@ int tile_or_default(int tj, int dflt)
 }  // namespace
 
 cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                                const CellSpace &g, const sph_params &prm, cudaStream_t st, int *nl)
+                                const CellSpace &g, const sph_params &prm, unsigned *status, cudaStream_t st,
+                                int *nl)
 {
     if (n <= 0 || f32) return cudaSuccess;  // FP32 views are already cell-relative floats
     const double gamma = prm.gamma;
@@ -2371,13 +2402,13 @@ cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr
     if (prm.kernel == SPH_KERNEL_M4 && prm.scheme == SPH_SCHEME_MINIMAL) {
         k_density_prep_f64<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, st>>>(
             x, y, z, h, cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, d[0], d[1], d[2], d[3], d[4], u,
-            gamma * (gamma - 1.0), d[5], d[6]);
+            gamma * (gamma - 1.0), d[5], d[6], status);
     } else if (prm.kernel == SPH_KERNEL_M5) {
         k_density_prep_g<KerM5><<<nb, 256, 0, st>>>(x, y, z, h, u, cell_of_slot, n, g, gamma, scr.xf, scr.yf,
-                                                    scr.zf, d[0], d[1], d[2], d[6]);
+                                                    scr.zf, d[0], d[1], d[2], d[6], status);
     } else {
         k_density_prep_g<KerM4><<<nb, 256, 0, st>>>(x, y, z, h, u, cell_of_slot, n, g, gamma, scr.xf, scr.yf,
-                                                    scr.zf, d[0], d[1], d[2], d[6]);
+                                                    scr.zf, d[0], d[1], d[2], d[6], status);
     }
     ++*nl;
     return cudaGetLastError();
@@ -2386,7 +2417,7 @@ cudaError_t launch_density_prep(bool f32, const SoaPtrs &soa, const Scratch &scr
 namespace {
 
 template <class Ker, bool Ext>
-void force_prep_g(const SoaPtrs &soa, const Scratch &scr, int n, double alpha, cudaStream_t st)
+void force_prep_g(const SoaPtrs &soa, const Scratch &scr, int n, double alpha, unsigned *status, cudaStream_t st)
 {
     double *const *d = reinterpret_cast<double *const *>(scr.d);
     const double *omega = Ext ? (const double *)soa.p[SPH_OMEGA][0] : nullptr;
@@ -2396,13 +2427,15 @@ void force_prep_g(const SoaPtrs &soa, const Scratch &scr, int n, double alpha, c
     const double *cz = Ext ? (const double *)soa.p[SPH_CURLV][2] : nullptr;
     k_force_prep_g<Ker, Ext><<<(n + 255) / 256, 256, 0, st>>>(
         (const double *)soa.p[SPH_H][0], (const double *)soa.p[SPH_P][0], (const double *)soa.p[SPH_RHO][0],
-        (const double *)soa.p[SPH_CS][0], omega, divv, cx, cy, cz, alpha, n, d[0], d[1], d[2], d[3], d[4], d[5]);
+        (const double *)soa.p[SPH_CS][0], omega, divv, cx, cy, cz, alpha, n, d[0], d[1], d[2], d[3], d[4], d[5],
+        status);
 }
 
 }  // namespace
 
 cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, const int *cell_of_slot, int n,
-                              const CellSpace &g, const sph_params &prm, cudaStream_t st, int *nl)
+                              const CellSpace &g, const sph_params &prm, unsigned *status, cudaStream_t st,
+                              int *nl)
 {
     if (n <= 0) return cudaSuccess;
     const int nb = (n + 255) / 256;
@@ -2420,17 +2453,17 @@ cudaError_t launch_force_prep(bool f32, const SoaPtrs &soa, const Scratch &scr, 
                                                  (double *)scr.d[3], (double *)scr.d[4], (double *)scr.d[5],
                                                  (double *)scr.d[6], (const double *)soa.p[SPH_X][0],
                                                  (const double *)soa.p[SPH_X][1], (const double *)soa.p[SPH_X][2],
-                                                 cell_of_slot, g, scr.xf, scr.yf, scr.zf, scr.hf);
+                                                 cell_of_slot, g, scr.xf, scr.yf, scr.zf, scr.hf, status);
             *nl += 1;
         } else {
             k_pos32<<<nb, 256, 0, st>>>((const double *)soa.p[SPH_X][0], (const double *)soa.p[SPH_X][1],
                                         (const double *)soa.p[SPH_X][2], (const double *)soa.p[SPH_H][0],
-                                        cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, scr.hf);
+                                        cell_of_slot, n, g, scr.xf, scr.yf, scr.zf, scr.hf, status);
             if (prm.kernel == SPH_KERNEL_M5) {
-                if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, st);
-                else force_prep_g<KerM5, false>(soa, scr, n, alpha, st);
+                if (ext) force_prep_g<KerM5, true>(soa, scr, n, alpha, status, st);
+                else force_prep_g<KerM5, false>(soa, scr, n, alpha, status, st);
             } else {
-                force_prep_g<KerM4, true>(soa, scr, n, alpha, st);
+                force_prep_g<KerM4, true>(soa, scr, n, alpha, status, st);
             }
             *nl += 2;
         }

@@ -637,7 +637,8 @@ sph_status density_launch(sph_view_s *v, const sph_params *p, const int *skip)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_DENSITY_PREP);
-        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->st, &ph.nl);
+        e = sphk::launch_density_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->status, v->st,
+                                      &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {
@@ -717,7 +718,8 @@ sph_status do_force(sph_view_s *v, const sph_params *p)
     cudaError_t e;
     {
         Phase ph(v, SPH_PH_FORCE_PREP);
-        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->st, &ph.nl);
+        e = sphk::launch_force_prep(f32, v->soa, v->scr, v->cell_of_slot, (int)v->n, v->cs, *p, v->status, v->st,
+                                    &ph.nl);
     }
     if (e != cudaSuccess) return SPH_E_CUDA;
     {

@@ -47,6 +47,7 @@ SPH_ALL_FIELDS = (1 << SPH_NFIELDS) - 1
 SPH_DEV_POS_RANGE, SPH_DEV_H_TOO_BIG, SPH_DEV_NONFINITE, SPH_DEV_TIMEOUT = 0x1, 0x2, 0x4, 0x8
 SPH_DEV_NOTCONV = 0x10
 SPH_DEV_BOUNDS = 0x20  # checked build only
+SPH_DEV_MAGNITUDE = 0x40  # FP64 views: h outside [2^-50, 2^50) or h^2 rho outside [2^-105, 2^105)
 (SPH_PH_BIN, SPH_PH_GATHER, SPH_PH_DENSITY_PREP, SPH_PH_DENSITY, SPH_PH_SCATTER, SPH_PH_FORCE_PREP, SPH_PH_FORCE,
  SPH_PH_REDUCE, SPH_PH_KDK) = range(9)
 SPH_NPHASES = 9
